@@ -1,0 +1,327 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Every check compares the oracle with something other than itself: hand-derived iterates, a textbook
+system with a known solution, Gaussian elimination and scipy's LU solver, the a-priori and a-posteriori
+contraction bounds, the planted solution, the residual identity of Section 2's component update, the
+closed-form spectral radius of the paper-shaped generator, and torch's BF16 / E4M3 conversions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+
+
+def tnorm_inf(A):
+    """||T||_inf of T = D^-1 (L + U) straight from A: max_i sum_{j!=i} |a_ij| / |a_ii|."""
+    d = np.abs(np.diag(A))
+    off = np.abs(A).sum(axis=1) - d
+    return float(np.max(off / d))
+
+
+# ---------------------------------------------------------------- hand-derived and textbook fixtures
+
+def test_golden_2x2_iterates():
+    g = read_golden("jacobi_2x2.txt")
+    A = np.array(g["A"]).reshape(2, 2)
+    B = np.array(g["B"])
+    res = oracle.jacobi(A, B, max_iter=4, tol=1e-300, trace=True)
+    assert res.status == oracle.NOT_CONVERGED and res.iters == 4
+    for k, want in g["iters"].items():
+        np.testing.assert_allclose(res.trace[k - 1][:, 0], want, rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(res.X[:, 0], res.trace[3][:, 0])
+    full = oracle.jacobi(A, B, max_iter=200, tol=1e-15)
+    assert full.status == oracle.OK
+    np.testing.assert_allclose(full.X[:, 0], g["SOLUTION"], rtol=0, atol=1e-14)
+    # by hand: delta_2 = 0.1 and delta_3 = 0.04, so tol = 0.05 stops at k = 3 and returns the NEW
+    # iterate X^3 (Section 2 algorithm: "return X" after the test on X - X^t)
+    stop = oracle.jacobi(A, B, max_iter=10, tol=0.05)
+    assert stop.status == oracle.OK and stop.iters == 3
+    np.testing.assert_allclose(stop.X[:, 0], g["iters"][3], rtol=0, atol=1e-15)
+    assert abs(stop.delta - 0.04) < 1e-15
+
+
+def test_golden_4x4_textbook():
+    g = read_golden("jacobi_4x4_textbook.txt")
+    A = np.array(g["A"]).reshape(4, 4)
+    B = np.array(g["B"])
+    first = oracle.jacobi(A, B, max_iter=1, tol=1e-300)
+    np.testing.assert_allclose(first.X[:, 0], g["iters"][1], rtol=0, atol=1e-15)
+    res = oracle.jacobi(A, B, max_iter=500, tol=1e-13)
+    assert res.status == oracle.OK
+    np.testing.assert_allclose(res.X[:, 0], g["SOLUTION"], rtol=0, atol=1e-12)
+
+
+def test_split_2x2_by_hand():
+    A = np.array([[4.0, 1.0], [2.0, 5.0]])
+    st, T, C = oracle.split(A, [1.0, 2.0])
+    assert st == oracle.OK
+    np.testing.assert_array_equal(T, [[0.0, -0.25], [-0.4, 0.0]])
+    np.testing.assert_array_equal(C[:, 0], [0.25, 0.4])
+
+
+# ------------------------------------------------------------------- direct solver (Gaussian elim.)
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64])
+def test_ge_recovers_planted_and_matches_scipy(n):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(n)
+    A = rng.uniform(-1, 1, (n, n)) + np.eye(n) * 0.5   # general (not dominant) matrix
+    Xs = rng.uniform(-1, 1, (n, 2))
+    B = A @ Xs
+    st, X = oracle.ge(A, B)
+    assert st == oracle.OK
+    cond = np.linalg.cond(A)
+    np.testing.assert_allclose(X, Xs, rtol=0, atol=1e-14 * cond * n)
+    np.testing.assert_allclose(X, scipy_linalg.solve(A, B), rtol=0, atol=1e-14 * cond * n)
+
+
+def test_ge_singular():
+    A = np.array([[1.0, 2.0], [2.0, 4.0]])
+    st, _ = oracle.ge(A, [1.0, 1.0])
+    assert st == oracle.ZERO_DIAGONAL
+
+
+# ------------------------------------------------------------- Jacobi: converged value and bounds
+
+@pytest.mark.parametrize("n,f,gen", [(8, 1.25, "dom"), (33, 1.1, "dom"), (64, 1.25, "hard"),
+                                     (50, 2.0, "hard")])
+def test_jacobi_converges_to_ge(n, f, gen):
+    make = synth.dominant_system if gen == "dom" else synth.hard_system
+    A, B, Xs = make(n, f, seed=100 + n)
+    q = tnorm_inf(A)
+    assert q < 1
+    tol = 1e-13
+    res = oracle.jacobi(A, B, max_iter=5000, tol=tol)
+    assert res.status == oracle.OK
+    st, Xge = oracle.ge(A, B)
+    assert st == oracle.OK
+    # a-posteriori bound ||X^k - X*|| <= q/(1-q) ||X^k - X^(k-1)||, plus rounding
+    bound = q / (1 - q) * res.delta + 1e-14
+    assert np.max(np.abs(res.X - Xge)) <= bound
+    assert np.max(np.abs(res.X - Xs)) <= bound
+
+
+@pytest.mark.parametrize("gen,f", [("dom", 1.25), ("dom", 1.05), ("hard", 1.25)])
+def test_a_priori_and_a_posteriori_bounds(gen, f):
+    n = 40
+    make = synth.dominant_system if gen == "dom" else synth.hard_system
+    A, B, Xs = make(n, f, seed=7)
+    q = tnorm_inf(A)
+    assert abs(q - 1 / f) < 1e-12
+    X0 = np.linspace(-2, 3, n)[:, None]
+    res = oracle.jacobi(A, B, X0=X0, max_iter=60, tol=1e-300, trace=True)
+    e0 = np.max(np.abs(X0 - Xs))
+    prev = X0
+    for k in range(1, res.iters + 1):
+        Xk = res.trace[k - 1]
+        err = np.max(np.abs(Xk - Xs))
+        assert err <= q ** k * e0 * (1 + 1e-12) + 1e-14, k                  # a-priori
+        assert err <= q / (1 - q) * np.max(np.abs(Xk - prev)) + 1e-14, k    # a-posteriori
+        prev = Xk
+
+
+def test_planted_solution_recovery():
+    A, B, Xs = synth.dominant_system(200, 1.25, seed=3)
+    res = oracle.jacobi(A, B, max_iter=2000, tol=1e-12)
+    assert res.status == oracle.OK
+    q = tnorm_inf(A)
+    assert np.max(np.abs(res.X - Xs)) <= q / (1 - q) * 1e-12 + 1e-14
+
+
+def test_diagonal_matrix_one_sweep():
+    d = np.array([2.0, -3.0, 7.0, 0.1, 1e3])
+    A = np.diag(d)
+    B = np.array([1.0, 1.0, -2.0, 5.0, 3.0])
+    res = oracle.jacobi(A, B, max_iter=10, tol=1e-12, trace=True)
+    # T = 0 so X^1 = C = B / d (one correctly rounded division each) and X^2 = X^1
+    np.testing.assert_array_equal(res.trace[0][:, 0], B / d)
+    assert res.status == oracle.OK and res.iters == 2 and res.delta == 0.0
+    res1 = oracle.jacobi(A, B, X0=B / d, max_iter=10, tol=1e-12)
+    assert res1.iters == 1 and res1.delta == 0.0
+
+
+def test_residual_identity():
+    """b_i - sum_j a_ij x_j^(k) = a_ii (x_i^(k+1) - x_i^(k)) for every k (Section 2 update rearranged)."""
+    A, B, _ = synth.dominant_system(30, 1.25, seed=11)
+    res = oracle.jacobi(A, B, max_iter=8, tol=1e-300, trace=True)
+    d = np.diag(A)[:, None]
+    scale = np.abs(A).sum(axis=1, keepdims=True) * 2
+    for k in range(1, res.iters):
+        R, _ = oracle.residual(A, B, res.trace[k - 1])
+        want = d * (res.trace[k] - res.trace[k - 1])
+        assert np.all(np.abs(R - want) <= 1e-14 * scale)
+
+
+def test_residual_matches_numpy():
+    rng = np.random.default_rng(5)
+    A = rng.uniform(-1, 1, (37, 37))
+    B = rng.uniform(-1, 1, (37, 3))
+    X = rng.uniform(-1, 1, (37, 3))
+    R, rel = oracle.residual(A, B, X)
+    want = B - A @ X
+    np.testing.assert_allclose(R, want, rtol=0, atol=1e-14)
+    want_rel = max(np.max(np.abs(want[:, c])) / np.max(np.abs(B[:, c])) for c in range(3))
+    assert abs(rel - want_rel) <= 1e-14 * want_rel
+
+
+def test_hard_generator_rate_is_one_over_f():
+    """Paper-shaped generator: T = -(1/f) S with S row-stochastic, so the error contracts by 1/f."""
+    f = 1.25
+    A, B, Xs = synth.hard_system(64, f, seed=2)
+    _, T, _ = oracle.split(A, B)
+    np.testing.assert_allclose(T.sum(axis=1), -1 / f, rtol=1e-14)
+    assert abs(max(abs(np.linalg.eigvals(T))) - 1 / f) < 1e-10
+    res = oracle.jacobi(A, B, max_iter=80, tol=1e-300, trace=True)
+    errs = [np.max(np.abs(res.trace[k] - Xs)) for k in range(res.iters)]
+    ratio = errs[60] / errs[59]
+    assert abs(ratio - 1 / f) < 1e-3
+    # predicted sweep count to reach tol from ||X0 - X*|| (X0 = 0): ln(tol / e0) / ln(1/f) + O(1)
+    tol = 1e-10
+    full = oracle.jacobi(A, B, max_iter=5000, tol=tol)
+    pred = math.log(tol / np.max(np.abs(Xs))) / math.log(1 / f)
+    assert abs(full.iters - pred) < 0.15 * pred
+
+
+def test_split_fixed_point():
+    A, B, Xs = synth.dominant_system(50, 1.25, seed=4, nrhs=2)
+    st, T, C = oracle.split(A, B)
+    assert st == oracle.OK
+    assert np.all(np.diag(T) == 0)
+    np.testing.assert_allclose(T @ Xs + C, Xs, rtol=0, atol=1e-14)
+    i, j = 3, 17
+    assert T[i, j] == -A[i, j] / A[i, i]
+
+
+# ------------------------------------------------------------------------------ control flow
+
+def test_strict_stopping_test():
+    A = np.array([[1.0]])
+    B = np.array([0.5])
+    r = oracle.jacobi(A, B, max_iter=5, tol=0.5)       # delta_1 = 0.5 is not < 0.5
+    assert r.status == oracle.OK and r.iters == 2 and r.delta == 0.0
+    r = oracle.jacobi(A, B, max_iter=5, tol=0.5000001)
+    assert r.status == oracle.OK and r.iters == 1 and r.delta == 0.5
+
+
+def test_iteration_cap_returns_last_iterate():
+    A, B, _ = synth.hard_system(20, 1.05, seed=9)
+    r = oracle.jacobi(A, B, max_iter=3, tol=1e-15, trace=True)
+    assert r.status == oracle.NOT_CONVERGED and r.iters == 3
+    np.testing.assert_array_equal(r.X, r.trace[2])
+    assert r.delta == np.max(np.abs(r.trace[2] - r.trace[1]))
+
+
+def test_error_statuses():
+    A = np.array([[1.0, 0.1], [0.2, 0.0]])
+    assert oracle.jacobi(A, [1.0, 1.0]).status == oracle.ZERO_DIAGONAL
+    A[1, 1] = np.nan
+    assert oracle.jacobi(A, [1.0, 1.0]).status == oracle.NONFINITE
+    A[1, 1] = np.inf
+    assert oracle.jacobi(A, [1.0, 1.0]).status == oracle.NONFINITE
+    good = np.eye(2)
+    assert oracle.jacobi(good, [1.0, 1.0], max_iter=0).status == oracle.INVALID_ARG
+    assert oracle.jacobi(good, [1.0, 1.0], tol=0.0).status == oracle.INVALID_ARG
+    assert oracle.jacobi(good, [1.0, 1.0], tol=float("nan")).status == oracle.INVALID_ARG
+    assert oracle.jacobi(good, [1.0, 1.0], norm=7).status == oracle.INVALID_ARG
+
+
+def test_divergence_reports_nonfinite():
+    A = np.array([[1.0, 10.0], [10.0, 1.0]])              # rho(T) = 10: iterates overflow
+    r = oracle.jacobi(A, [1.0, 1.0], max_iter=2000, tol=1e-12)
+    assert r.status == oracle.NONFINITE
+    assert 300 < r.iters < 320
+
+
+def test_euclidean_norm_mode():
+    d = np.array([2.0, 4.0, 5.0])
+    B = np.array([1.0, -2.0, 3.0])
+    r = oracle.jacobi(np.diag(d), B, max_iter=1, tol=10.0, norm=oracle.NORM_2)
+    assert r.iters == 1 and abs(r.delta - np.linalg.norm(B / d)) <= 1e-16
+
+
+def test_residual_norm_mode_is_relative_residual_of_previous_iterate():
+    A, B, _ = synth.dominant_system(25, 1.1, seed=13)
+    full = oracle.jacobi(A, B, max_iter=6, tol=1e-300, norm=oracle.NORM_RESID, trace=True)
+    for k in range(2, full.iters + 1):
+        part = oracle.jacobi(A, B, max_iter=k, tol=1e-300, norm=oracle.NORM_RESID)
+        _, rel = oracle.residual(A, B, full.trace[k - 2])
+        # both sides are normalised by ||B||_inf; the residual itself is a cancellation of O(1) terms,
+        # so the rounding error is absolute in these units (~ n * eps * ||A|| ||X|| / ||B||)
+        assert abs(part.delta - rel) <= 1e-14
+
+
+def test_multi_rhs_columns_are_independent():
+    A, B, _ = synth.dominant_system(20, 1.25, seed=21, nrhs=3)
+    multi = oracle.jacobi(A, B, max_iter=5, tol=1e-300)
+    for c in range(3):
+        one = oracle.jacobi(A, B[:, c], max_iter=5, tol=1e-300)
+        np.testing.assert_array_equal(multi.X[:, c], one.X[:, 0])
+
+
+def test_thread_count_does_not_change_results():
+    A, B, _ = synth.hard_system(97, 1.1, seed=5, nrhs=2)
+    a = oracle.jacobi(A, B, max_iter=40, tol=1e-300, nthreads=1)
+    b = oracle.jacobi(A, B, max_iter=40, tol=1e-300, nthreads=4)
+    np.testing.assert_array_equal(a.X, b.X)
+
+
+# ------------------------------------------------------------------ narrow encodings of T's factors
+
+def _f32_cases():
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([
+        rng.standard_normal(20000).astype(np.float32),
+        (rng.uniform(-1, 1, 20000) * 2.0 ** rng.integers(-140, 120, 20000)).astype(np.float32),
+        np.array([0.0, -0.0, 1.0, -1.0, 3.4e38, -3.4e38, 1e-45, 1.00390625, 1.01171875, 1.0078125,
+                  np.float32(1) + np.float32(2 ** -8), 65504.0], dtype=np.float32),
+    ])
+    # exact BF16 ties: mantissa bits below the kept 7 exactly at the half-way point
+    ties = (np.arange(1000, dtype=np.uint32) << 16) | np.uint32(0x3F808000)
+    return np.concatenate([vals, ties.view(np.float32)])
+
+
+def test_bf16_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = _f32_cases()
+    want = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    got = np.array([oracle.bf16_from_f32(v) for v in x], dtype=np.uint16)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_e4m3_matches_torch_in_range_and_saturates():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-448, 448, 20000), rng.uniform(-1, 1, 5000) * 2.0 ** -7,
+                        [0.0, 448.0, -448.0, 2.0 ** -9, 2.0 ** -10, 0.5 * 2.0 ** -9, 1.5 * 2.0 ** -9,
+                         1.0625, 1.1875, 240.0, 232.0, 248.0]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    got = np.array([oracle.e4m3_from_f32(v) for v in x], dtype=np.uint8)
+    np.testing.assert_array_equal(got, want)
+    assert oracle.e4m3_from_f32(1000.0) == 0x7E and oracle.e4m3_from_f32(-1e30) == 0xFE
+    assert oracle.e4m3_from_f32(460.0) == 0x7E
+
+
+def test_offdiag_encodings():
+    torch = pytest.importorskip("torch")
+    A, _, _ = synth.dominant_system(37, 1.1, seed=8)
+    f32 = oracle.offdiag_f32(A)
+    off = A.copy()
+    np.fill_diagonal(off, 0.0)
+    np.testing.assert_array_equal(f32, off.astype(np.float32))
+    bf = oracle.offdiag_bf16(A)
+    want = torch.from_numpy(off.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
+    np.testing.assert_array_equal(bf, want.view(np.uint16))
+    q, s = oracle.offdiag_e4m3(A)
+    m = np.abs(off.astype(np.float32)).max(axis=1)
+    np.testing.assert_array_equal(s, m / np.float32(448.0))
+    assert np.all(np.diag(q) == 0)
+    scaled = (off.astype(np.float32) / s[:, None]).astype(np.float32)
+    want_q = torch.from_numpy(scaled).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    np.testing.assert_array_equal(q, want_q)
+    # the row maximum is encoded as the largest finite code, 448 (m / (m / 448) is within an FP32 ulp
+    # of 448, far inside E4M3's rounding interval there)
+    assert np.all((q & 0x7F).max(axis=1) == 0x7E)
