@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Jacobi solver on the single large dense system.
+
+Workload: n = 16384, one right-hand side, strictly diagonally dominant A (off-diagonals uniform [-1, 1),
+a_ii = 1.05 * sum_{j != i} |a_ij| * (random sign), so ||T||_inf = 1/1.05), planted X* uniform [-1, 1),
+B = A X*, X0 = 0, target ||B - A X||_inf / ||B||_inf <= 1e-10.  Inputs are synthetic and seeded
+(``synth``), resident in HBM before the timed region; A (2.15 GB) is far larger than the 129 MB L2, so
+no flush is needed between steps.
+
+One step = one complete solve through the C ABI: ``jacobi_setup_ex`` (diagonal check, 1/a_ii, the narrow
+copy of A for the mixed paths) + ``jacobi_solve_async`` (one persistent kernel).  The headline path is
+BF16 inner sweeps with FP64 iterative refinement; the plain FP64 Jacobi path and the E4M3 path are timed
+the same way beside it.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at ||AX-B||/||B||<=1e-10 (BF16 inner sweeps + FP64 refinement), n=16384"
+TARGET = 1e-10
+ESIZE = {"fp64": 8, "fp32_ir": 4, "bf16_ir": 2, "fp8_ir": 1}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+SOLVE_SRC = os.path.join(ROOT, "paper_1403_5805_gb300", "csrc", "solve.cu")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def src_hash():
+    with open(SOLVE_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh)
+    except OSError:
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_sha256_16") != src_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.rows = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc.stdout.readline()  # wait until sampling runs
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import synth
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_1403_5805_gb300 as jac
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n, f = args.n, args.f
+    A, B, Xs = synth.dominant_system(n, f, seed=synth.BASE_SEED + 1)
+    At = torch.from_numpy(A).to(dev)
+    Bt = torch.from_numpy(B[:, 0].copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ws = torch.empty(0, dtype=torch.uint8, device=dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    Xs_t = torch.from_numpy(Xs[:, 0].copy()).to(dev)
+
+    def one_step(prec, ev=None):
+        nonlocal ws
+        s = jac.DeviceSolver(At, Bt, precision=prec, workspace=ws if ws.numel() else None)
+        ws = s.workspace
+        if ev is not None:
+            ev[0].record(stream)
+        s.solve_async(None, args.max_iter, TARGET if prec != "fp64" else args.fp64_tol, out)
+        if ev is not None:
+            ev[1].record(stream)
+        return s
+
+    def timed(prec, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            s = one_step(prec)
+        torch.cuda.synchronize(dev)
+        launch_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                     for _ in range(steps)]
+        sampler = ClockSampler(local) if sample_clocks else None
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            s = one_step(prec, launch_ev[k])
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop() if sampler else None
+        ms = t0.elapsed_time(t1)
+        kernel_ms = sum(a.elapsed_time(b) for a, b in launch_ev) / steps
+        st = s.last_stats()
+        rel = s.residual(out)
+        err = float((out - Xs_t).abs().max().item())
+        return {"ms_total": ms, "kernel_ms": kernel_ms, "stats": st.as_dict(), "rel_residual_check": rel,
+                "err_vs_xstar": err, "clocks": clocks}
+
+    main = timed(args.precision, args.steps, args.warmup, sample_clocks=True)
+    ms_step = main["ms_total"] / args.steps
+    ms_max = ms_step
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world / (ms_max * 1e-3)
+
+    # algorithmic bytes of the dominant kernel (the persistent solve kernel) per launch
+    st = main["stats"]
+    es = ESIZE[args.precision]
+    outer_with_matrix = max(st["outer_steps"] - 1, 0)  # X0 = 0: the first residual needs no matrix pass
+    bytes_launch = outer_with_matrix * 8.0 * n * n + st["sweeps"] * es * float(n) * n
+    peaks, peak_kind = measured_peaks()
+    achieved = bytes_launch / (main["kernel_ms"] * 1e-3) / 1e9
+    kname = {"bf16_ir": "ir_solve_kernel<__nv_bfloat16>", "fp8_ir": "ir_solve_kernel<__nv_fp8_e4m3>",
+             "fp32_ir": "ir_solve_kernel<float>", "fp64": "fp64_solve_kernel"}[args.precision]
+    traffic = committed_traffic(kname)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": bytes_launch, "kernel_ms": round(main["kernel_ms"], 4),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+
+    paths = {args.precision: summarize(main, args.steps, n, args.precision)}
+    if not args.quick:
+        for prec in [p for p in ("fp64", "fp8_ir", "fp32_ir") if p != args.precision]:
+            paths[prec] = summarize(timed(prec, args.steps, args.warmup), args.steps, n, prec)
+    fp64_ratio = None
+    if "fp64" in paths:
+        fp64_ratio = round(paths[args.precision]["solves_per_s"] / paths["fp64"]["solves_per_s"], 3)
+
+    e2e = run_e2e(args, jac, torch, dev, A, B, ws)
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16_ir" else args.precision,
+        "data": "synthetic (seeded Philox4x32-10), resident in HBM",
+        "config": {"workload": f"single dense system n={n}, f={f}, 1 RHS, BF16 inner sweeps + FP64 "
+                               f"refinement to rel. residual 1e-10; one step = setup + solve",
+                   "n": n, "dominance": f, "nrhs": 1, "precision": args.precision, "global_batch": world,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs (2.15 GB A) larger than the 129 MB L2; no flush"},
+        "gpu_launches": (4 if args.precision != "fp64" else 3) * args.steps,
+        "clocks": main["clocks"], "roofline": roofline, "paths": paths,
+        "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(A, B, n)
+    return result
+
+
+def summarize(r, steps, n, prec):
+    st = r["stats"]
+    ms = r["ms_total"] / steps
+    es = ESIZE[prec]
+    if prec == "fp64":
+        bytes_launch = st["sweeps"] * 8.0 * n * n
+    else:
+        bytes_launch = max(st["outer_steps"] - 1, 0) * 8.0 * n * n + st["sweeps"] * es * float(n) * n
+    return {"solves_per_s": round(1e3 / ms, 3), "ms_per_solve": round(ms, 4), "kernel_ms": round(r["kernel_ms"], 4),
+            "sweeps": st["sweeps"], "outer_steps": st["outer_steps"], "status": st["status"],
+            "rel_residual": r["rel_residual_check"], "err_vs_xstar": r["err_vs_xstar"],
+            "kernel_algorithmic_gbs": round(bytes_launch / (r["kernel_ms"] * 1e-3) / 1e9, 1),
+            "gbs_per_sweep": round((8.0 if prec == "fp64" else es) * n * n / (r["kernel_ms"] * 1e-3 /
+                                   max(st["sweeps"], 1)) / 1e9, 1) if prec == "fp64" else None}
+
+
+def run_e2e(args, jac, torch, dev, A, B, ws):
+    """Same metric through the public API from pinned host buffers: H2D of A and B, setup, solve and the
+    D2H read of X inside the timed region."""
+    n = args.n
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B[:, 0].copy()).pin_memory()
+    Xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    steps = max(1, min(args.steps, args.e2e_steps))
+
+    def step():
+        s = jac.DeviceSolver(Ah, Bh, precision=args.precision, workspace=ws, device=dev)
+        s.solve_async(None, args.max_iter, TARGET, out)
+        Xh.copy_(out, non_blocking=True)
+        st = s.last_stats()  # waits for the stream (the result has landed in Xh)
+        return st
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = step()
+    torch.cuda.synchronize(dev)
+    sec = (time.perf_counter() - t0) / steps
+    ok = st.status == 0
+    return {"value": round(1.0 / sec, 3) if ok else 0.0, "unit": "solves/s", "steps": steps,
+            "h2d_bytes_per_step": int(8 * n * n + 8 * n), "d2h_bytes_per_step": int(8 * n),
+            "path": "host pinned A,B -> jacobi_setup_ex (copy) -> jacobi_solve_async -> X to host"}
+
+
+# --------------------------------------------------------------------------------- CPU oracle
+
+def oracle_solve(A, B, threads):
+    import oracle
+    # FP64 Jacobi with the relative-residual stop (previous iterate), the same 1e-10 target
+    return oracle.jacobi(A, B, max_iter=2000, tol=TARGET, norm=oracle.NORM_RESID, nthreads=threads)
+
+
+def cpu_baseline(A, B, n, budget_s: float = 12.0):
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    solves = 0
+    res = None
+    while True:
+        res = oracle_solve(A, B, threads)
+        solves += 1
+        if time.perf_counter() - t0 >= budget_s or solves >= 5:
+            break
+    sec = (time.perf_counter() - t0) / solves
+    return {"value": round(1.0 / sec, 4), "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{solves} full FP64 oracle solve(s) of the n={n} system (OpenMP rows, "
+                      f"{res.iters} sweeps each, relative-residual stop 1e-10)"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the plain FP64 CPU oracle on the machine's host cores (rank 0 only)."""
+    import numpy as np  # noqa: F401
+
+    import synth
+    if rank != 0:
+        return None
+    n, f = args.n, args.f
+    A, B, _ = synth.dominant_system(n, f, seed=synth.BASE_SEED + 1)
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_solve(A, B, threads)
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = oracle_solve(A, B, threads)
+    sec = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / sec
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Philox4x32-10)",
+            "config": {"workload": f"single dense system n={n}, f={f}, 1 RHS, FP64 Jacobi (CPU oracle) to "
+                                   f"rel. residual 1e-10", "n": n, "dominance": f},
+            "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} full oracle solves, {res.iters} sweeps each"},
+            "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--f", type=float, default=1.05)
+    ap.add_argument("--precision", default="bf16_ir", choices=list(ESIZE))
+    ap.add_argument("--fp64-tol", type=float, default=1e-12, dest="fp64_tol",
+                    help="stopping threshold of the plain FP64 path (max-norm change)")
+    ap.add_argument("--max-iter", type=int, default=5000, dest="max_iter")
+    ap.add_argument("--e2e-steps", type=int, default=10, dest="e2e_steps")
+    ap.add_argument("--quick", action="store_true", help="skip the comparison paths")
+    ap.add_argument("--no-cpu-baseline", action="store_true", dest="no_cpu_baseline")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        res = run_reference(args, world, rank)
+        print(json.dumps(res), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = run_ours(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * jacobi.h - C ABI of the GB300 (sm_103a) dense Jacobi solver.
+ *
+ * The method is the Jacobi iteration of Margaris, Souravlas & Roumeliotis, "Parallel Implementations
+ * of the Jacobi Linear Algebraic Systems Solver" (arXiv:1403.5805), Section 2: split A = D - L - U,
+ * iterate X^(k) = T X^(k-1) + C with T = D^-1 (L + U) and C = D^-1 B, stop when the change between
+ * consecutive iterates drops below a tolerance or after a maximum number of sweeps.
+ *
+ * Every sweep runs on the GPU inside one persistent kernel per solve: the matrix is streamed from HBM
+ * once per sweep, the convergence reduction is fused into the sweep and decided on the device, so no
+ * host round trip happens between sweeps.
+ *
+ * Conventions shared by all calls
+ *   - A is row-major n x n: element (i, j) at A[i*lda + j] (lda = n in the host-pointer calls).
+ *   - B and X are column-major n x nrhs: element (i, c) at B[c*ldb + i] (one right-hand side per
+ *     column; ldb = n in the host-pointer calls).
+ *   - Return value: a jacobi_status.  Values > 0 are warnings with a valid X, values < 0 are errors.
+ *   - All calls use the CUDA device that is current on the calling thread when the handle is created.
+ *   - A handle is not thread-safe: use one handle per thread (handles are independent).
+ */
+#ifndef JACOBI_H
+#define JACOBI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define JACOBI_API __attribute__((visibility("default")))
+#else
+#define JACOBI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum jacobi_status {
+  JACOBI_OK = 0,                  /* converged */
+  JACOBI_NOT_CONVERGED = 1,       /* iteration cap reached; X holds the last iterate X^(L) */
+  JACOBI_ERR_INVALID_ARG = -1,    /* null pointer, n < 1, max_iter < 1, tol <= 0 or NaN, bad enum */
+  JACOBI_ERR_ZERO_DIAGONAL = -2,  /* some a_ii == 0: the method is undefined (Section 2) */
+  JACOBI_ERR_NONFINITE = -3,      /* non-finite diagonal, or the iteration produced inf/NaN */
+  JACOBI_ERR_OUT_OF_MEMORY = -4,  /* device allocation failed or workspace too small */
+  JACOBI_ERR_CUDA = -5,           /* a CUDA runtime call failed (see jacobi_last_cuda_error) */
+  JACOBI_ERR_TIMEOUT = -6,        /* a bounded device-side wait expired; the context stays usable */
+  JACOBI_ERR_UNSUPPORTED = -8     /* valid request this build does not implement (e.g. nrhs > 1 here) */
+} jacobi_status;
+
+/* Arithmetic of the solve.
+ *   JACOBI_FP64     plain Jacobi in FP64 (Section 2 iteration exactly; the stopping test is `change < tol`).
+ *   JACOBI_*_IR     mixed precision: inner Jacobi sweeps read the off-diagonal part of A stored as FP32,
+ *                   BF16 or FP8 E4M3 (with an FP32 scale per row) and accumulate in FP32; an outer FP64
+ *                   iterative refinement (r = B - A X in FP64, X += delta) runs until
+ *                   ||B - A X||_inf / ||B||_inf <= tol.  The paper does not discuss precision; this
+ *                   refinement is the library's own design around the Section 2 sweep. */
+typedef enum jacobi_precision {
+  JACOBI_FP64 = 0,
+  JACOBI_FP32_IR = 1,
+  JACOBI_BF16_IR = 2,
+  JACOBI_FP8_IR = 3
+} jacobi_precision;
+
+/* Stopping norm of the FP64 path (the change between consecutive iterates, Section 2 algorithm).
+ *   JACOBI_NORM_INF    max_i |x_i^(k) - x_i^(k-1)|
+ *   JACOBI_NORM_2      sqrt(sum_i (x_i^(k) - x_i^(k-1))^2), the paper's Euclidean test (Section 3.1)
+ *   JACOBI_NORM_RESID  max_i |a_ii (x_i^(k) - x_i^(k-1))| / ||B||_inf, which is the relative residual
+ *                      ||B - A X^(k-1)||_inf / ||B||_inf of the previous iterate. */
+typedef enum jacobi_norm { JACOBI_NORM_INF = 0, JACOBI_NORM_2 = 1, JACOBI_NORM_RESID = 2 } jacobi_norm;
+
+/* Result record of one solve. */
+typedef struct jacobi_stats {
+  int64_t sweeps;       /* FP64: Jacobi sweeps executed (k of the returned X^(k)); IR: inner sweeps */
+  int64_t outer_steps;  /* IR: FP64 residual evaluations; FP64 path: 0 */
+  double final_delta;   /* FP64: stopping norm of the last sweep; IR: last inner max-norm change */
+  double rel_residual;  /* IR: ||B - A X||_inf / ||B||_inf of the returned X (FP64, on the device);
+                           FP64 path: NaN */
+  int32_t status;       /* jacobi_status of the solve */
+  int32_t converged;    /* 1 if status == JACOBI_OK */
+} jacobi_stats;
+
+typedef struct jacobi_handle jacobi_handle;
+
+/* ------------------------------------------------------------------------------------------------
+ * Host-pointer interface (the problem statement of Section 2: inputs A, B, X^0, tol, L; output X).
+ * ------------------------------------------------------------------------------------------------ */
+
+/* Copy A (n x n, row-major, host) and B (n, host) to the device and prepare the FP64 sweep.
+ * The library allocates the device memory (cudaMalloc) and owns it until jacobi_destroy; A and B may be
+ * freed when the call returns.  Fails with JACOBI_ERR_ZERO_DIAGONAL / JACOBI_ERR_NONFINITE if some
+ * a_ii is 0 or not finite (the handle is then not created; *out is set to NULL). */
+JACOBI_API int jacobi_setup(const double* A, const double* B, int64_t n, jacobi_handle** out);
+
+/* Run the FP64 Jacobi iteration from X0 (n, host; NULL means zeros) for at most max_iter sweeps with
+ * the max-norm test `max|X^(k) - X^(k-1)| < tol` (Section 2).  On return X_out (n, host, caller-owned)
+ * holds X^(k) (the new iterate of the converging sweep, or X^(L) at the cap), *iters_out = k and
+ * *final_delta_out = max|X^(k) - X^(k-1)|.  iters_out / final_delta_out may be NULL.  Blocks until done. */
+JACOBI_API int jacobi_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                 int64_t* iters_out, double* final_delta_out);
+
+/* Release every resource of the handle (NULL is a no-op). */
+JACOBI_API void jacobi_destroy(jacobi_handle* h);
+
+/* Short English description of a status value (static storage). */
+JACOBI_API const char* jacobi_status_string(int status);
+
+/* Last CUDA error string seen by the library on this thread ("" if none). */
+JACOBI_API const char* jacobi_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------------------------------
+ * Device-pointer interface (PyTorch or any other owner of device memory and streams).
+ * ------------------------------------------------------------------------------------------------ */
+
+typedef struct jacobi_desc {
+  int64_t n;              /* system size, >= 1 */
+  int64_t nrhs;           /* right-hand sides; this build supports 1 */
+  int32_t precision;      /* jacobi_precision */
+  int32_t norm;           /* jacobi_norm (FP64 path only) */
+  const double* A;        /* row-major, A[i*lda + j], device or host memory.  Borrowed (read by every
+                             solve, so it must stay unchanged and alive until jacobi_destroy) when it is
+                             16-byte aligned device memory with n and lda even and JACOBI_FLAG_COPY_A is
+                             not set; otherwise copied into the workspace during setup (host memory:
+                             a host-to-device copy, fastest from pinned memory) and not referenced
+                             afterwards */
+  int64_t lda;            /* >= n */
+  const double* B;        /* column-major, B[c*ldb + i], device or host memory; read during setup only */
+  int64_t ldb;            /* >= n */
+  void* workspace;        /* device buffer of >= jacobi_workspace_size() bytes, 256-byte aligned,
+                             owned by the caller and borrowed until jacobi_destroy; NULL: the library
+                             allocates it with cudaMalloc */
+  size_t workspace_bytes; /* size of workspace when given */
+  void* stream;           /* cudaStream_t every call of this handle is ordered on; NULL: legacy default */
+  int32_t grid;           /* CTAs of the persistent kernels; 0: one per SM (capped by the row count) */
+  int32_t max_outer;      /* IR: cap on FP64 residual evaluations (0: 60) */
+  double inner_rtol;      /* IR: stop inner sweeps when max|delta change| <= inner_rtol * max|delta|
+                             (0: 2^-10 for FP32/BF16, 2^-6 for FP8) */
+  int32_t max_inner;      /* IR: cap on inner sweeps per outer step (0: 64) */
+  int32_t flags;          /* JACOBI_FLAG_* */
+} jacobi_desc;
+
+#define JACOBI_FLAG_COPY_A 1 /* always copy A into the workspace (never borrow it) */
+
+/* Fill *d with defaults (n = 0 and null pointers: the caller sets those). */
+JACOBI_API void jacobi_desc_init(jacobi_desc* d);
+
+/* Bytes of device workspace a handle for *d needs (written to *bytes). */
+JACOBI_API int jacobi_workspace_size(const jacobi_desc* d, size_t* bytes);
+
+/* Prepare a solver from device-resident A and B, on d->stream: reads the diagonal (rejecting zero or
+ * non-finite entries), stores 1/a_ii, copies B, copies A into the padded streaming layout unless it is
+ * borrowed (see jacobi_desc.A) and, for the IR precisions, writes the FP32/BF16/E4M3 copy of the
+ * off-diagonal part of A.  Synchronises the stream once, to read the diagonal check.  B is not
+ * referenced after the call returns. */
+JACOBI_API int jacobi_setup_ex(const jacobi_desc* d, jacobi_handle** out);
+
+/* Solve asynchronously on the handle's stream.  X0 (device, n x nrhs column-major, ld = n; NULL means
+ * zeros) and X_out (device, same layout) may alias.  stats_dev, if not NULL, is a device jacobi_stats
+ * the kernel fills.  For JACOBI_FP64, tol is the stopping threshold of the handle's norm (strict <);
+ * for the IR precisions, tol is the relative-residual target (<=) and max_iter caps inner sweeps.
+ * Returns an error only for invalid arguments or launch failures; the solve's own status lands in
+ * stats_dev and in the handle (jacobi_last_stats). */
+JACOBI_API int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                       jacobi_stats* stats_dev);
+
+/* jacobi_solve_async, then wait for the stream and return the solve's status; *stats (host) filled if
+ * not NULL. */
+JACOBI_API int jacobi_solve_ex(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                    jacobi_stats* stats);
+
+/* Stats of the handle's last solve (waits for its stream). */
+JACOBI_API int jacobi_last_stats(jacobi_handle* h, jacobi_stats* stats);
+
+/* Relative residual ||B - A X||_inf / ||B||_inf of a device X (n, ld = n) against the handle's FP64 A and
+ * B, computed on the device in FP64 with the handle's streaming kernel; waits for the stream. */
+JACOBI_API int jacobi_residual(jacobi_handle* h, const double* X, double* rel_out);
+
+/* Copy the narrow off-diagonal matrix that the inner sweeps of an IR handle read to host memory:
+ * dst_host is row-major n x ld_dst (ld_dst >= n) of the precision's element type (FP32 values, BF16
+ * codes as uint16, E4M3 codes as uint8; the diagonal holds zero codes), scale_host (n floats, may be
+ * NULL) the per-row E4M3 scales (1.0 for FP32/BF16).  JACOBI_ERR_INVALID_ARG for an FP64 handle.
+ * Waits for the stream. */
+JACOBI_API int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* scale_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JACOBI_H */

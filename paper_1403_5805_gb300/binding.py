@@ -1,0 +1,237 @@
+"""ctypes binding of ``libjacobi.so`` (the C ABI in ``include/jacobi.h``).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA kernels.  There is no CPU
+fallback; if the library has not been built, loading it raises.  PyTorch is used for device memory and
+streams (the workspace tensor, the caller's stream), nothing else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libjacobi.so")
+
+# jacobi_status
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_ZERO_DIAGONAL, ERR_NONFINITE, ERR_OUT_OF_MEMORY = -1, -2, -3, -4
+ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = -5, -6, -8
+# jacobi_precision
+FP64, FP32_IR, BF16_IR, FP8_IR = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR, "bf16_ir": BF16_IR, "fp8_ir": FP8_IR}
+# jacobi_norm
+NORM_INF, NORM_2, NORM_RESID = 0, 1, 2
+NORMS = {"inf": NORM_INF, "2": NORM_2, "resid": NORM_RESID}
+FLAG_COPY_A = 1
+
+EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
+           "jacobi_desc_init", "jacobi_workspace_size", "jacobi_setup_ex", "jacobi_solve_async",
+           "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual", "jacobi_get_narrow")
+
+
+class JacobiStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("outer_steps", ctypes.c_int64), ("final_delta", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("converged", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class JacobiDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nrhs", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("norm", ctypes.c_int32), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p), ("grid", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("max_inner", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class JacobiError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.jacobi_status_string(status).decode()
+        cuda = lib.jacobi_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({status})" + (f" [{cuda}]" if cuda else ""))
+        self.status = status
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        H = ctypes.c_void_p
+        lib.jacobi_setup.argtypes = [vp, vp, i64, ctypes.POINTER(H)]
+        lib.jacobi_solve.argtypes = [H, vp, i64, dbl, vp, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+        lib.jacobi_destroy.argtypes = [H]
+        lib.jacobi_destroy.restype = None
+        lib.jacobi_status_string.argtypes = [i32]
+        lib.jacobi_status_string.restype = ctypes.c_char_p
+        lib.jacobi_last_cuda_error.restype = ctypes.c_char_p
+        lib.jacobi_desc_init.argtypes = [ctypes.POINTER(JacobiDesc)]
+        lib.jacobi_desc_init.restype = None
+        lib.jacobi_workspace_size.argtypes = [ctypes.POINTER(JacobiDesc), ctypes.POINTER(ctypes.c_size_t)]
+        lib.jacobi_setup_ex.argtypes = [ctypes.POINTER(JacobiDesc), ctypes.POINTER(H)]
+        lib.jacobi_solve_async.argtypes = [H, vp, i64, dbl, vp, vp]
+        lib.jacobi_solve_ex.argtypes = [H, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats)]
+        lib.jacobi_last_stats.argtypes = [H, ctypes.POINTER(JacobiStats)]
+        lib.jacobi_residual.argtypes = [H, vp, ctypes.POINTER(dbl)]
+        lib.jacobi_get_narrow.argtypes = [H, vp, i64, vp]
+        for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
+                     "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
+                     "jacobi_get_narrow"):
+            getattr(lib, name).restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str, allow_warn: bool = True) -> int:
+    if status < 0 or (status > 0 and not allow_warn):
+        raise JacobiError(status, where)
+    return status
+
+
+# ------------------------------------------------------------------------- host-pointer interface
+
+class HostSolver:
+    """``jacobi_setup`` / ``jacobi_solve`` with numpy arrays (FP64 path, one right-hand side)."""
+
+    def __init__(self, A: np.ndarray, B: np.ndarray):
+        lib = load()
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(-1))
+        n = A.shape[0]
+        if A.shape != (n, n) or B.shape != (n,):
+            raise ValueError("A must be (n, n) and B (n,)")
+        self.n = n
+        self._h = ctypes.c_void_p()
+        st = lib.jacobi_setup(A.ctypes.data, B.ctypes.data, n, ctypes.byref(self._h))
+        _check(st, "jacobi_setup", allow_warn=False)
+
+    def solve(self, X0=None, max_iter: int = 1000, tol: float = 1e-12):
+        """Returns ``(status, X, iters, final_delta)``."""
+        lib = load()
+        X = np.zeros(self.n)
+        x0 = None if X0 is None else np.ascontiguousarray(np.asarray(X0, dtype=np.float64).reshape(-1))
+        it = ctypes.c_int64(0)
+        de = ctypes.c_double(0.0)
+        st = lib.jacobi_solve(self._h, None if x0 is None else x0.ctypes.data, max_iter, tol, X.ctypes.data,
+                              ctypes.byref(it), ctypes.byref(de))
+        _check(st, "jacobi_solve")
+        return st, X, int(it.value), float(de.value)
+
+    def close(self):
+        if self._h:
+            load().jacobi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------ device-pointer interface
+
+class DeviceSolver:
+    """``jacobi_setup_ex`` / ``jacobi_solve_*`` on CUDA tensors; torch owns the workspace and stream."""
+
+    def __init__(self, A, B, precision: str = "fp64", norm: str = "inf", grid: int = 0, stream=None,
+                 copy_a: bool = False, max_outer: int = 0, max_inner: int = 0, inner_rtol: float = 0.0,
+                 workspace=None, device=None):
+        """A, B: float64 tensors on the GPU (A may be borrowed, see jacobi_desc.A) or on the host (copied
+        to the device during setup; pin them for full link bandwidth).  workspace: optional uint8 CUDA
+        tensor of at least workspace_size() bytes to reuse across solvers."""
+        import torch
+        lib = load()
+        if A.dtype != torch.float64 or B.dtype != torch.float64:
+            raise ValueError("A and B must be float64 tensors")
+        if device is None:
+            device = A.device if A.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        n = A.shape[0]
+        if A.dim() != 2 or A.shape[1] != n or A.stride(1) != 1:
+            raise ValueError("A must be (n, n) with unit column stride")
+        Bv = B.reshape(-1)
+        if Bv.numel() != n or Bv.stride(0) != 1:
+            raise ValueError("B must hold n contiguous values")
+        self.n = n
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        d = JacobiDesc()
+        lib.jacobi_desc_init(ctypes.byref(d))
+        d.n, d.nrhs = n, 1
+        d.precision = PRECISIONS[precision]
+        d.norm = NORMS[norm]
+        d.A, d.lda = A.data_ptr(), A.stride(0)
+        d.B, d.ldb = Bv.data_ptr(), n
+        d.stream = self.stream.cuda_stream
+        d.grid, d.max_outer, d.max_inner, d.inner_rtol = grid, max_outer, max_inner, inner_rtol
+        d.flags = FLAG_COPY_A if copy_a else 0
+        nbytes = ctypes.c_size_t(0)
+        with torch.cuda.device(device):
+            _check(lib.jacobi_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_workspace_size")
+        if workspace is None or workspace.numel() < nbytes.value:
+            workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=device)
+        self.workspace = workspace
+        d.workspace, d.workspace_bytes = self.workspace.data_ptr(), self.workspace.numel()
+        self._A, self._B = A, Bv  # keep the borrowed operands alive
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            _check(lib.jacobi_setup_ex(ctypes.byref(d), ctypes.byref(self._h)), "jacobi_setup_ex", False)
+        self.precision = precision
+
+    def solve_async(self, X0=None, max_iter: int = 1000, tol: float = 1e-12, out=None, stats_dev=None):
+        """Queue a solve on the solver's stream; returns ``out`` (a float64 CUDA tensor of n values)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        x0 = None if X0 is None else X0.reshape(-1)
+        if x0 is not None and (x0.dtype != torch.float64 or x0.numel() != self.n or x0.stride(0) != 1):
+            raise ValueError("X0 must hold n contiguous float64 values")
+        st = load().jacobi_solve_async(self._h, None if x0 is None else x0.data_ptr(), max_iter, tol,
+                                       out.data_ptr(), None if stats_dev is None else stats_dev.data_ptr())
+        _check(st, "jacobi_solve_async")
+        return out
+
+    def last_stats(self) -> JacobiStats:
+        st = JacobiStats()
+        _check(load().jacobi_last_stats(self._h, ctypes.byref(st)), "jacobi_last_stats")
+        return st
+
+    def solve(self, X0=None, max_iter: int = 1000, tol: float = 1e-12, out=None):
+        """Synchronous solve: returns ``(X, stats)``; raises on error statuses (< 0)."""
+        out = self.solve_async(X0, max_iter, tol, out)
+        st = self.last_stats()
+        _check(st.status, "solve")
+        return out, st
+
+    def residual(self, X) -> float:
+        """||B - A X||_inf / ||B||_inf on the device in FP64."""
+        rel = ctypes.c_double(0.0)
+        _check(load().jacobi_residual(self._h, X.data_ptr(), ctypes.byref(rel)), "jacobi_residual")
+        return float(rel.value)
+
+    def close(self):
+        if self._h:
+            load().jacobi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

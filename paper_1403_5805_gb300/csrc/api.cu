@@ -1,0 +1,440 @@
+// C ABI of the solver library (declared in include/jacobi.h): handles, workspace layout, launches.
+//
+// The problem statement follows Section 2 of the paper: inputs A (alpha_ii != 0), B, the start vector
+// X^0, the tolerance and the iteration limit L; output X.  All arithmetic runs in the kernels of
+// prepare.cu and solve.cu; this file only validates arguments, lays out device memory and orders the
+// work on the handle's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "solver.cuh"
+
+using namespace jac;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return JACOBI_ERR_OUT_OF_MEMORY;
+  return JACOBI_ERR_CUDA;
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t narrow_size(int precision) {
+  switch (precision) {
+    case JACOBI_FP32_IR: return 4;
+    case JACOBI_BF16_IR: return 2;
+    case JACOBI_FP8_IR: return 1;
+    default: return 0;
+  }
+}
+
+Narrow narrow_kind(int precision) {
+  return precision == JACOBI_FP32_IR ? Narrow::F32 : precision == JACOBI_BF16_IR ? Narrow::BF16 : Narrow::E4M3;
+}
+
+bool is_device_memory(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown host pointer
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// The sweep streams A in place when its rows are 16-byte aligned device memory (no padding overread:
+// n even); host memory and other layouts are copied into the workspace.
+bool can_borrow(const jacobi_desc* d) {
+  if (!d->A || (d->flags & JACOBI_FLAG_COPY_A)) return false;
+  if (reinterpret_cast<uintptr_t>(d->A) % 16 != 0 || d->n % 2 != 0 || d->lda % 2 != 0) return false;
+  return is_device_memory(d->A);
+}
+
+// Offsets of every sub-buffer inside one workspace allocation.
+struct Layout {
+  int64_t ld;  // padded length of vectors and row stride of owned matrices
+  size_t A64, Nlow, b, d, rinv, bnorm, rowfac, scale, xa, xb, xout, c1, da, db, part, ctl, keys, stats, total;
+};
+
+Layout make_layout(int64_t n, int precision, bool copy_A) {
+  Layout L{};
+  L.ld = round_up(n, kLdAlign);
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t vd = static_cast<size_t>(L.ld) * sizeof(double);
+  const size_t vf = static_cast<size_t>(L.ld) * sizeof(float);
+  L.A64 = copy_A ? take(static_cast<size_t>(n) * L.ld * sizeof(double)) : 0;
+  const size_t ns = narrow_size(precision);
+  L.Nlow = ns ? take(static_cast<size_t>(n) * L.ld * ns) : 0;
+  L.b = take(vd);
+  L.d = take(vd);
+  L.rinv = take(vd);
+  L.bnorm = take(sizeof(double));
+  L.rowfac = take(vf);
+  L.scale = take(vf);
+  L.xa = take(vd);
+  L.xb = take(vd);
+  L.xout = take(vd);
+  L.c1 = take(vf);
+  L.da = take(vf);
+  L.db = take(vf);
+  L.part = take(2 * kMaxGrid * sizeof(double));
+  L.ctl = take(sizeof(Ctl));
+  L.keys = take(4 * sizeof(unsigned long long));
+  L.stats = take(sizeof(jacobi_stats));
+  L.total = o;
+  return L;
+}
+
+int validate_desc(const jacobi_desc* d) {
+  if (!d || d->n < 1 || !d->A || !d->B) return JACOBI_ERR_INVALID_ARG;
+  if (d->lda < d->n || d->ldb < d->n) return JACOBI_ERR_INVALID_ARG;
+  if (d->precision < JACOBI_FP64 || d->precision > JACOBI_FP8_IR) return JACOBI_ERR_INVALID_ARG;
+  if (d->norm < JACOBI_NORM_INF || d->norm > JACOBI_NORM_RESID) return JACOBI_ERR_INVALID_ARG;
+  if (d->grid < 0 || d->grid > kMaxGrid) return JACOBI_ERR_INVALID_ARG;
+  if (d->nrhs != 1) return JACOBI_ERR_UNSUPPORTED;
+  return JACOBI_OK;
+}
+
+}  // namespace
+
+struct jacobi_handle {
+  int device = 0;
+  int64_t n = 0;
+  int precision = JACOBI_FP64;
+  int norm = JACOBI_NORM_INF;
+  cudaStream_t stream = nullptr;
+  bool own_ws = false;
+  char* ws = nullptr;
+  Layout L{};
+  const double* A64 = nullptr;
+  int64_t lda64 = 0;
+  int grid = 0;
+  int max_outer = 60;
+  int max_inner = 64;
+  float inner_rtol = 0.0f;
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(ws + off);
+  }
+};
+
+namespace {
+
+// Runs the preparation kernels on h's stream.  A and B are device pointers (or, for the host-pointer
+// entry point, A has already been placed in the workspace and B in b).
+int prepare(jacobi_handle* h, const double* A, int64_t lda, const double* B, bool copy_A) {
+  const int64_t n = h->n;
+  cudaStream_t s = h->stream;
+  if (copy_A) {
+    double* dst = h->at<double>(h->L.A64);
+    if (A != dst)
+      CK(cudaMemcpy2DAsync(dst, h->L.ld * sizeof(double), A, lda * sizeof(double), n * sizeof(double), n,
+                           cudaMemcpyDefault, s));
+    CK(launch_pad_zero(dst, n, h->L.ld, s));
+    h->A64 = dst;
+    h->lda64 = h->L.ld;
+  } else {
+    h->A64 = A;
+    h->lda64 = lda;
+  }
+  unsigned long long* keys = h->at<unsigned long long>(h->L.keys);
+  CK(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long), s));       // diagonal-check key
+  CK(cudaMemsetAsync(h->at<char>(h->L.bnorm), 0, sizeof(double), s));   // ||B|| bits
+  CK(launch_diag(h->A64, h->lda64, n, h->at<double>(h->L.d), h->at<double>(h->L.rinv), keys, s));
+  double* b = h->at<double>(h->L.b);
+  if (B != b && !is_device_memory(B)) {
+    CK(cudaMemcpyAsync(b, B, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    B = b;
+  }
+  CK(launch_rhs(B, n, b, h->at<unsigned long long>(h->L.bnorm), s));
+  // vectors start zeroed so that every padding entry is 0
+  CK(cudaMemsetAsync(h->at<char>(h->L.xa), 0, h->L.ld * sizeof(double), s));
+  CK(cudaMemsetAsync(h->at<char>(h->L.xb), 0, h->L.ld * sizeof(double), s));
+  CK(cudaMemsetAsync(h->at<char>(h->L.c1), 0, h->L.ld * sizeof(float), s));
+  CK(cudaMemsetAsync(h->at<char>(h->L.da), 0, h->L.ld * sizeof(float), s));
+  CK(cudaMemsetAsync(h->at<char>(h->L.db), 0, h->L.ld * sizeof(float), s));
+  if (h->precision != JACOBI_FP64)
+    CK(launch_narrow(narrow_kind(h->precision), h->A64, h->lda64, n, h->at<void>(h->L.Nlow), h->L.ld,
+                     h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac), s));
+  unsigned long long key = 0;
+  CK(cudaMemcpyAsync(&key, keys, sizeof(key), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (key != ~0ull) return (key & 0xFF) == 2 ? JACOBI_ERR_ZERO_DIAGONAL : JACOBI_ERR_NONFINITE;
+  return JACOBI_OK;
+}
+
+int pick_grid(jacobi_handle* h, int requested) {
+  const bool ir = h->precision != JACOBI_FP64;
+  const int cap = max_coresident_grid(ir, narrow_kind(h->precision));
+  if (cap <= 0) return 0;
+  int g = requested > 0 ? requested : static_cast<int>((h->n + kRows - 1) / kRows);
+  if (g > cap) g = cap;
+  if (g > kMaxGrid) g = kMaxGrid;
+  if (g < 1) g = 1;
+  return g;
+}
+
+int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
+  jacobi_handle* h = new (std::nothrow) jacobi_handle();
+  if (!h) return JACOBI_ERR_OUT_OF_MEMORY;
+  cudaGetDevice(&h->device);
+  h->n = d->n;
+  h->precision = d->precision;
+  h->norm = d->norm;
+  h->stream = static_cast<cudaStream_t>(d->stream);
+  h->L = make_layout(d->n, d->precision, copy_A);
+  h->max_outer = d->max_outer > 0 ? d->max_outer : 60;
+  h->max_inner = d->max_inner > 0 ? d->max_inner : 64;
+  h->inner_rtol = static_cast<float>(
+      d->inner_rtol > 0 ? d->inner_rtol : (d->precision == JACOBI_FP8_IR ? 1.0 / 64 : 1.0 / 1024));
+  if (d->workspace) {
+    if (d->workspace_bytes < h->L.total || reinterpret_cast<uintptr_t>(d->workspace) % kAlign != 0) {
+      delete h;
+      return JACOBI_ERR_INVALID_ARG;
+    }
+    h->ws = static_cast<char*>(d->workspace);
+  } else {
+    cudaError_t e = cudaMalloc(&h->ws, h->L.total);
+    if (e != cudaSuccess) {
+      delete h;
+      return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    h->own_ws = true;
+  }
+  h->grid = pick_grid(h, d->grid);
+  if (h->grid <= 0) {
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return cuda_fail(cudaGetLastError(), "occupancy query");
+  }
+  *out = h;
+  return JACOBI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void jacobi_desc_init(jacobi_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->nrhs = 1;
+  d->precision = JACOBI_FP64;
+  d->norm = JACOBI_NORM_INF;
+}
+
+int jacobi_workspace_size(const jacobi_desc* d, size_t* bytes) {
+  if (!d || !bytes || d->n < 1) return JACOBI_ERR_INVALID_ARG;
+  *bytes = make_layout(d->n, d->precision, !can_borrow(d)).total;
+  return JACOBI_OK;
+}
+
+int jacobi_setup_ex(const jacobi_desc* d, jacobi_handle** out) {
+  if (!out) return JACOBI_ERR_INVALID_ARG;
+  *out = nullptr;
+  int st = validate_desc(d);
+  if (st != JACOBI_OK) return st;
+  const bool copy_A = !can_borrow(d);
+  jacobi_handle* h = nullptr;
+  st = make_handle(d, copy_A, &h);
+  if (st != JACOBI_OK) return st;
+  st = prepare(h, d->A, d->lda, d->B, copy_A);
+  if (st != JACOBI_OK) {
+    jacobi_destroy(h);
+    return st;
+  }
+  *out = h;
+  return JACOBI_OK;
+}
+
+int jacobi_setup(const double* A, const double* B, int64_t n, jacobi_handle** out) {
+  if (!out) return JACOBI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!A || !B || n < 1) return JACOBI_ERR_INVALID_ARG;
+  jacobi_desc d;
+  jacobi_desc_init(&d);
+  d.n = n;
+  d.A = A;
+  d.lda = n;
+  d.B = B;
+  d.ldb = n;
+  d.flags = JACOBI_FLAG_COPY_A;
+  jacobi_handle* h = nullptr;
+  int st = make_handle(&d, true, &h);
+  if (st != JACOBI_OK) return st;
+  // host -> device: A straight into its padded place in the workspace, B into b
+  double* A64 = h->at<double>(h->L.A64);
+  double* b = h->at<double>(h->L.b);
+  cudaError_t e = cudaMemcpy2DAsync(A64, h->L.ld * sizeof(double), A, n * sizeof(double), n * sizeof(double), n,
+                                    cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b, B, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    jacobi_destroy(h);
+    return cuda_fail(e, "host-to-device copy of A, B");
+  }
+  st = prepare(h, A64, h->L.ld, b, true);
+  if (st != JACOBI_OK) {
+    jacobi_destroy(h);
+    return st;
+  }
+  *out = h;
+  return JACOBI_OK;
+}
+
+int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                       jacobi_stats* stats_dev) {
+  if (!h || !X_out || max_iter < 1 || !(tol > 0.0) || !std::isfinite(tol)) return JACOBI_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  CK(cudaMemsetAsync(h->at<char>(h->L.ctl), 0, sizeof(Ctl), s));
+  if (X0)
+    CK(cudaMemcpyAsync(h->at<double>(h->L.xa), X0, n * sizeof(double), cudaMemcpyDefault, s));
+  else
+    CK(cudaMemsetAsync(h->at<char>(h->L.xa), 0, n * sizeof(double), s));
+  SolveParams p{};
+  p.n = n;
+  p.A = h->A64;
+  p.lda = h->lda64;
+  p.Nlow = h->precision != JACOBI_FP64 ? h->at<void>(h->L.Nlow) : nullptr;
+  p.ldn = h->L.ld;
+  p.b = h->at<double>(h->L.b);
+  p.d = h->at<double>(h->L.d);
+  p.rinv = h->at<double>(h->L.rinv);
+  p.rowfac = h->at<float>(h->L.rowfac);
+  p.bnorm = h->at<double>(h->L.bnorm);
+  p.xa = h->at<double>(h->L.xa);
+  p.xb = h->at<double>(h->L.xb);
+  p.c1 = h->at<float>(h->L.c1);
+  p.da = h->at<float>(h->L.da);
+  p.db = h->at<float>(h->L.db);
+  p.part = h->at<double>(h->L.part);
+  p.ctl = h->at<Ctl>(h->L.ctl);
+  p.x_out = X_out;
+  p.stats_out = stats_dev;
+  p.max_iter = max_iter;
+  p.tol = tol;
+  p.norm = h->norm;
+  p.x0_zero = X0 ? 0 : 1;
+  p.max_outer = h->max_outer;
+  p.max_inner = h->max_inner;
+  p.inner_rtol = h->inner_rtol;
+  cudaError_t e = h->precision == JACOBI_FP64 ? launch_fp64_solve(p, h->grid, s)
+                                               : launch_ir_solve(narrow_kind(h->precision), p, h->grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");
+  return JACOBI_OK;
+}
+
+int jacobi_last_stats(jacobi_handle* h, jacobi_stats* stats) {
+  if (!h || !stats) return JACOBI_ERR_INVALID_ARG;
+  Ctl* ctl = h->at<Ctl>(h->L.ctl);
+  CK(cudaMemcpyAsync(stats, &ctl->result, sizeof(jacobi_stats), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return JACOBI_OK;
+}
+
+int jacobi_solve_ex(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                    jacobi_stats* stats) {
+  int st = jacobi_solve_async(h, X0, max_iter, tol, X_out, nullptr);
+  if (st != JACOBI_OK) return st;
+  jacobi_stats local;
+  st = jacobi_last_stats(h, &local);
+  if (st != JACOBI_OK) return st;
+  if (stats) *stats = local;
+  return local.status;
+}
+
+int jacobi_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                 int64_t* iters_out, double* final_delta_out) {
+  if (!h || !X_out) return JACOBI_ERR_INVALID_ARG;
+  double* xout = h->at<double>(h->L.xout);
+  int st = jacobi_solve_async(h, X0, max_iter, tol, xout, nullptr);
+  if (st != JACOBI_OK) return st;
+  jacobi_stats local;
+  Ctl* ctl = h->at<Ctl>(h->L.ctl);
+  CK(cudaMemcpyAsync(&local, &ctl->result, sizeof(local), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(X_out, xout, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (iters_out) *iters_out = local.sweeps;
+  if (final_delta_out) *final_delta_out = local.final_delta;
+  return local.status;
+}
+
+int jacobi_residual(jacobi_handle* h, const double* X, double* rel_out) {
+  if (!h || !X || !rel_out) return JACOBI_ERR_INVALID_ARG;
+  unsigned long long* bits = h->at<unsigned long long>(h->L.keys) + 1;
+  CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long), h->stream));
+  CK(launch_residual(h->A64, h->lda64, h->n, h->at<double>(h->L.b), X, bits, h->stream));
+  unsigned long long host[1];
+  double bn = 0.0;
+  CK(cudaMemcpyAsync(host, bits, sizeof(host), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&bn, h->at<double>(h->L.bnorm), sizeof(bn), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  double rmax;
+  std::memcpy(&rmax, host, sizeof(rmax));
+  *rel_out = rmax / bn;
+  return JACOBI_OK;
+}
+
+int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* scale_host) {
+  if (!h || !dst_host || ld_dst < h->n || h->precision == JACOBI_FP64) return JACOBI_ERR_INVALID_ARG;
+  const size_t es = narrow_size(h->precision);
+  CK(cudaMemcpy2DAsync(dst_host, ld_dst * es, h->at<char>(h->L.Nlow), h->L.ld * es, h->n * es, h->n,
+                       cudaMemcpyDeviceToHost, h->stream));
+  if (scale_host) {
+    if (h->precision == JACOBI_FP8_IR) {
+      CK(cudaMemcpyAsync(scale_host, h->at<float>(h->L.scale), h->n * sizeof(float), cudaMemcpyDeviceToHost,
+                         h->stream));
+    } else {
+      for (int64_t i = 0; i < h->n; ++i) scale_host[i] = 1.0f;
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return JACOBI_OK;
+}
+
+void jacobi_destroy(jacobi_handle* h) {
+  if (!h) return;
+  if (h->own_ws && h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+  }
+  delete h;
+}
+
+const char* jacobi_status_string(int status) {
+  switch (status) {
+    case JACOBI_OK: return "converged";
+    case JACOBI_NOT_CONVERGED: return "iteration limit reached without convergence";
+    case JACOBI_ERR_INVALID_ARG: return "invalid argument";
+    case JACOBI_ERR_ZERO_DIAGONAL: return "zero diagonal entry (a_ii == 0)";
+    case JACOBI_ERR_NONFINITE: return "non-finite value (diagonal or iterate)";
+    case JACOBI_ERR_OUT_OF_MEMORY: return "out of device memory or workspace too small";
+    case JACOBI_ERR_CUDA: return "CUDA runtime error";
+    case JACOBI_ERR_TIMEOUT: return "device-side wait timed out";
+    case JACOBI_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char* jacobi_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

@@ -1,0 +1,632 @@
+// Persistent Jacobi solve kernels for GB300 (sm_103a).
+//
+// One cooperative launch runs a whole solve.  Each CTA owns a contiguous block of rows (the paper's
+// row-wise distribution of Section 3.1, here over the SMs of one GPU).  Per sweep it streams its rows
+// of the matrix from HBM exactly once through a shared-memory ring: one producer warp issues 1-D TMA
+// bulk copies (4 KB row segments, 8 rows per ring item) that complete on mbarriers, eight consumer
+// warps read them with 128-bit shared-memory loads and accumulate row dot products against the
+// current iterate (read from L2), reduce them with warp shuffles and a fixed-order cross-warp sum, and
+// apply the component update of Section 2 in the epilogue.  The max-norm change is reduced in the
+// same epilogue (order-free integer max on the IEEE bits), combined over the grid with one atomic and
+// one grid barrier per sweep, and every CTA takes the same stop decision from it - the stopping test
+// of the Section 2 algorithm with no host round trip.
+//
+// Kernels
+//   fp64_solve_kernel        X^(k) = D^-1 (B - (A - D) X^(k-1)), all FP64 (Section 2 update).
+//   ir_solve_kernel<Narrow>  FP64 iterative refinement around inner Jacobi sweeps on a narrow copy of
+//                            the off-diagonal part of A (FP32 / BF16 / E4M3 + row scale), FP32
+//                            accumulation; FP64 residual r = B - A X and update X += delta.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "device_util.cuh"
+#include "solver.cuh"
+
+namespace jac {
+namespace {
+
+struct Ring {
+  uint64_t full[kStages];   // producer -> consumers: stage filled (1 arrival + transaction bytes)
+  uint64_t empty[kStages];  // consumers -> producer: stage free again (one arrival per consumer warp)
+};
+
+template <typename TM>
+struct MatTraits;
+template <>
+struct MatTraits<double> {
+  static constexpr int kVec = 2;
+  using X = double;
+  using Acc = double;
+};
+template <>
+struct MatTraits<float> {
+  static constexpr int kVec = 4;
+  using X = float;
+  using Acc = float;
+};
+template <>
+struct MatTraits<__nv_bfloat16> {
+  static constexpr int kVec = 8;
+  using X = float;
+  using Acc = float;
+};
+template <>
+struct MatTraits<__nv_fp8_e4m3> {
+  static constexpr int kVec = 16;
+  using X = float;
+  using Acc = float;
+};
+
+template <typename TM>
+__host__ __device__ constexpr int chunk_cols() {
+  return kConsumerWarps * 32 * MatTraits<TM>::kVec;
+}
+
+// ---- x loads (L2 only: the iterate is rewritten by other CTAs between sweeps, so L1 may be stale)
+__device__ __forceinline__ void load_x(double (&xv)[2], const double* x) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(x));
+  xv[0] = v.x;
+  xv[1] = v.y;
+}
+template <int V>
+__device__ __forceinline__ void load_x(float (&xv)[V], const float* x) {
+#pragma unroll
+  for (int q = 0; q < V / 4; ++q) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(x) + q);
+    xv[4 * q + 0] = v.x;
+    xv[4 * q + 1] = v.y;
+    xv[4 * q + 2] = v.z;
+    xv[4 * q + 3] = v.w;
+  }
+}
+
+// ---- one 16-byte segment of a row times the matching x values
+__device__ __forceinline__ void seg_dot(double& acc, uint4 m, const double (&xv)[2]) {
+  const double m0 = __hiloint2double(static_cast<int>(m.y), static_cast<int>(m.x));
+  const double m1 = __hiloint2double(static_cast<int>(m.w), static_cast<int>(m.z));
+  acc = fma(m0, xv[0], acc);
+  acc = fma(m1, xv[1], acc);
+}
+__device__ __forceinline__ void seg_dot(float& acc, uint4 m, const float (&xv)[4]) {
+  acc = fmaf(__uint_as_float(m.x), xv[0], acc);
+  acc = fmaf(__uint_as_float(m.y), xv[1], acc);
+  acc = fmaf(__uint_as_float(m.z), xv[2], acc);
+  acc = fmaf(__uint_as_float(m.w), xv[3], acc);
+}
+__device__ __forceinline__ void bf16x2_fma(float& acc, uint32_t w, float x0, float x1) {
+  acc = fmaf(__uint_as_float(w << 16), x0, acc);          // element 2q   (low half)
+  acc = fmaf(__uint_as_float(w & 0xFFFF0000u), x1, acc);  // element 2q+1 (high half)
+}
+__device__ __forceinline__ void seg_dot(float& acc, uint4 m, const float (&xv)[8]) {
+  bf16x2_fma(acc, m.x, xv[0], xv[1]);
+  bf16x2_fma(acc, m.y, xv[2], xv[3]);
+  bf16x2_fma(acc, m.z, xv[4], xv[5]);
+  bf16x2_fma(acc, m.w, xv[6], xv[7]);
+}
+__device__ __forceinline__ void e4m3x4_fma(float& acc, uint32_t w, const float* x) {
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w & 0xFFFFu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w >> 16), __NV_E4M3);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  acc = fmaf(a.x, x[0], acc);
+  acc = fmaf(a.y, x[1], acc);
+  acc = fmaf(b.x, x[2], acc);
+  acc = fmaf(b.y, x[3], acc);
+}
+__device__ __forceinline__ void seg_dot(float& acc, uint4 m, const float (&xv)[16]) {
+  e4m3x4_fma(acc, m.x, xv + 0);
+  e4m3x4_fma(acc, m.y, xv + 4);
+  e4m3x4_fma(acc, m.z, xv + 8);
+  e4m3x4_fma(acc, m.w, xv + 12);
+}
+
+// Zero the x values of columns >= n (the segment that straddles the end of a row may carry matrix
+// padding that is not guaranteed to be zero or finite).
+template <typename XT, int V>
+__device__ __forceinline__ void mask_tail(XT (&xv)[V], int64_t col, int64_t n) {
+#pragma unroll
+  for (int e = 0; e < V; ++e)
+    if (col + e >= n) xv[e] = XT(0);
+}
+
+struct Block {
+  Ring* ring;
+  char* stages;
+  volatile int* abort;   // CTA-wide abort flag (shared memory)
+  int* gstatus;          // grid-wide status word (Ctl::status)
+};
+
+__device__ __forceinline__ void raise_abort(const Block& B) {
+  *B.abort = 1;
+  atomicCAS(B.gstatus, 0, kStatusTimeout);
+}
+
+// Producer warp: stream rows [r0, r1) of M (columns [0, n)) into the ring, one item per (row group,
+// column chunk).  u counts ring items over the whole kernel (shared by producer and consumers).
+template <typename TM>
+__device__ void produce_phase(const Block& B, uint32_t& u, const TM* M, int64_t ld, int64_t n,
+                              int64_t r0, int64_t r1) {
+  constexpr int K = chunk_cols<TM>();
+  const int lane = threadIdx.x & 31;
+  const int64_t nch = (n + K - 1) / K;
+  for (int64_t g0 = r0; g0 < r1; g0 += kRows) {
+    const int rows = static_cast<int>(i64min(kRows, r1 - g0));
+    for (int64_t c = 0; c < nch; ++c) {
+      const int s = static_cast<int>(u % kStages);
+      const uint32_t par = ((u / kStages) & 1u) ^ 1u;
+      const int64_t j0 = c * K;
+      const int64_t wcols = i64min(K, n - j0);
+      const uint32_t rbytes = static_cast<uint32_t>((wcols * static_cast<int64_t>(sizeof(TM)) + 15) & ~int64_t(15));
+      int ok = 1;
+      if (lane == 0) {
+        ok = (*B.abort == 0) && mbar_wait(&B.ring->empty[s], par);
+        if (ok) mbar_arrive_expect_tx(&B.ring->full[s], rbytes * static_cast<uint32_t>(rows));
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) raise_abort(B);
+        return;
+      }
+      if (lane < rows)
+        bulk_copy_g2s(B.stages + s * kStageBytes + lane * kRowBytes, M + (g0 + lane) * ld + j0, rbytes,
+                      &B.ring->full[s]);
+      ++u;
+    }
+  }
+}
+
+// Consumer warps: row dot products of rows [r0, r1) against x, then epi.row(i, dot) by warp 0, lane
+// (i - group start).  with_matrix == false skips the matrix (dot = 0).
+template <typename TM, typename Epi>
+__device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTraits<TM>::X* x, int64_t n,
+                              int64_t r0, int64_t r1, bool with_matrix,
+                              typename MatTraits<TM>::Acc (*red)[kRows], Epi& epi) {
+  using XT = typename MatTraits<TM>::X;
+  using Acc = typename MatTraits<TM>::Acc;
+  constexpr int V = MatTraits<TM>::kVec;
+  constexpr int K = chunk_cols<TM>();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int co = (warp * 32 + lane) * V;  // first column of this lane inside a chunk
+  const int64_t nch = with_matrix ? (n + K - 1) / K : 0;
+  for (int64_t g0 = r0; g0 < r1; g0 += kRows) {
+    const int rows = static_cast<int>(i64min(kRows, r1 - g0));
+    Acc acc[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) acc[r] = Acc(0);
+    XT xv[V], xn[V];
+    if (nch > 0 && co < n) load_x(xv, x + co);
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t col = c * K + co;
+      const int64_t ncol = col + K;
+      if (c + 1 < nch && ncol < n) load_x(xn, x + ncol);  // prefetch the next chunk's x
+      const int s = static_cast<int>(u % kStages);
+      const uint32_t par = (u / kStages) & 1u;
+      bool ok = (*B.abort == 0);
+      if (ok) ok = mbar_wait(&B.ring->full[s], par);
+      if (!ok) {
+        raise_abort(B);
+      } else if (col < n) {
+        if (col + V > n) mask_tail(xv, col, n);
+        const char* base = B.stages + s * kStageBytes + co * static_cast<int>(sizeof(TM));
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+          if (r < rows) {
+            const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+            seg_dot(acc[r], m, xv);
+          }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.ring->empty[s]);
+      ++u;
+#pragma unroll
+      for (int e = 0; e < V; ++e) xv[e] = xn[e];
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) acc[r] = warp_sum(acc[r]);
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) red[warp][r] = acc[r];
+    }
+    named_barrier(1, kConsumers);
+    if (warp == 0 && lane < rows) {
+      Acc dot = red[0][lane];
+#pragma unroll
+      for (int w = 1; w < kConsumerWarps; ++w) dot += red[w][lane];  // fixed order: deterministic
+      epi.row(g0 + lane, dot);
+    }
+    named_barrier(1, kConsumers);
+  }
+}
+
+// Wait for every bulk copy this producer issued (the last kStages items) before the CTA exits.
+__device__ void drain_ring(const Block& B, uint32_t u_issued) {
+  const uint32_t first = u_issued > kStages ? u_issued - kStages : 0;
+  for (uint32_t v = first; v < u_issued; ++v) mbar_wait(&B.ring->full[v % kStages], (v / kStages) & 1u);
+}
+
+__device__ __forceinline__ void init_ring(Ring* ring) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&ring->full[s], 1);
+      mbar_init(&ring->empty[s], kConsumerWarps);
+    }
+    mbar_init_fence();
+  }
+}
+
+__device__ __forceinline__ double bits_to_double(unsigned long long v) {
+  return __longlong_as_double(static_cast<long long>(v));
+}
+
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
+  return __ldcg(p);
+}
+
+// Publish this CTA's reduction values into slot (phase % 3), clear the slot of phase + 1, and wait at
+// the grid barrier.  Called by lane 0 of warp 0.  Returns false on timeout / remote error.
+__device__ bool publish_and_sync(Ctl* ctl, uint32_t phase, unsigned long long v0, unsigned long long v1) {
+  const int slot = static_cast<int>(phase % 3);
+  if (v0) atomicMax(&ctl->red[slot][0], v0);
+  if (v1) atomicMax(&ctl->red[slot][1], v1);
+  if (blockIdx.x == 0) {
+    const int nxt = static_cast<int>((phase + 1) % 3);
+    ctl->red[nxt][0] = 0ull;
+    ctl->red[nxt][1] = 0ull;
+  }
+  return grid_arrive_and_wait(&ctl->arrive, &ctl->status, (phase + 1) * gridDim.x);
+}
+
+__device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+// ================================================================================ FP64 path
+
+struct Fp64SweepEpi {
+  const double* b;
+  const double* d;
+  const double* rinv;
+  const double* xc;  // X^(k-1)
+  double* xn;        // X^(k)
+  int norm;
+  unsigned long long mx;  // running max (bits) over this lane's rows
+  double sq;              // running sum of squares (Euclidean norm)
+  __device__ __forceinline__ void row(int64_t i, double dot) {
+    const double xo = __ldcg(xc + i);
+    const double s = fma(-d[i], xo, dot);     // sum_{j != i} a_ij x_j: the diagonal term taken back out
+    const double xi = (b[i] - s) * rinv[i];   // Section 2 component update, 1/a_ii precomputed
+    xn[i] = xi;
+    const double diff = xi - xo;
+    if (norm == JACOBI_NORM_RESID)
+      mx = umax(mx, abs_bits(d[i] * diff));
+    else
+      mx = umax(mx, abs_bits(diff));
+    sq = fma(diff, diff, sq);
+  }
+};
+
+enum Next : int { kContinue = 0, kStop = 1 };
+
+__global__ void __launch_bounds__(kThreads, 1) fp64_solve_kernel(SolveParams p) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ Ring ring;
+  __shared__ double red[kConsumerWarps][kRows];
+  __shared__ int s_abort, s_next;
+  char* stages = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+
+  const int G = gridDim.x;
+  const int64_t r0 = p.n * blockIdx.x / G, r1 = p.n * (blockIdx.x + 1) / G;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_next = kContinue;
+  }
+  init_ring(&ring);
+  __syncthreads();
+  Block B{&ring, stages, &s_abort, &p.ctl->status};
+  const bool producer = threadIdx.x >= kConsumers;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  uint32_t u = 0;
+  int cur = 0;                    // buffer holding X^(k-1): 0 -> xa, 1 -> xb
+  int64_t k = 1;
+  double delta = 0.0;
+  int status = kStatusNotConverged;
+  for (;; ++k) {
+    const double* xc = cur ? p.xb : p.xa;
+    double* xn = cur ? p.xa : p.xb;
+    Fp64SweepEpi epi{p.b, p.d, p.rinv, xc, xn, p.norm, 0ull, 0.0};
+    if (producer) {
+      produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
+    } else {
+      consume_phase<double>(B, u, xc, p.n, r0, r1, true, red, epi);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // CTA reduction over warp 0 (lanes that own rows hold the running values)
+      const unsigned long long mx = warp_max_u64(epi.mx);
+      const double sq = warp_sum(epi.sq);
+      const uint32_t phase = static_cast<uint32_t>(k - 1);
+      int ok = 1;
+      if (lane == 0) {
+        if (p.norm == JACOBI_NORM_2) p.part[(k & 1) * kMaxGrid + blockIdx.x] = sq;
+        ok = (s_abort == 0) && publish_and_sync(p.ctl, phase, p.norm == JACOBI_NORM_2 ? 0ull : mx, 0ull);
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();  // order the other lanes' reads after lane 0's acquire of the grid barrier
+      double dk;
+      if (p.norm == JACOBI_NORM_2) {
+        double acc = 0.0;
+        for (int j = lane; j < G; j += 32) acc += __ldcg(p.part + (k & 1) * kMaxGrid + j);
+        dk = sqrt(warp_sum(acc));
+      } else {
+        dk = bits_to_double(ld_cg_u64(&p.ctl->red[phase % 3][0]));
+        if (p.norm == JACOBI_NORM_RESID) dk = dk / __ldg(p.bnorm);
+      }
+      if (lane == 0) {
+        int next = kContinue;
+        if (!ok) {
+          status = kStatusTimeout;
+          next = kStop;
+        } else if (!isfinite(dk)) {
+          status = kStatusNonfinite;
+          next = kStop;
+        } else if (dk < p.tol) {
+          status = kStatusOk;
+          next = kStop;
+        } else if (k >= p.max_iter) {
+          status = kStatusNotConverged;
+          next = kStop;
+        }
+        delta = dk;
+        s_next = next;
+        if (!ok) s_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (s_next != kContinue) break;
+    cur ^= 1;
+  }
+  if (producer) {
+    if (lane == 0) drain_ring(B, u);
+    return;
+  }
+  // X^(k) is in the buffer written by the last sweep; each row is copied by the lane that wrote it.
+  const double* xres = cur ? p.xa : p.xb;
+  if (warp == 0 && s_abort == 0) {
+    for (int64_t g0 = r0; g0 < r1; g0 += kRows)
+      if (g0 + lane < r1 && lane < kRows) p.x_out[g0 + lane] = xres[g0 + lane];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    jacobi_stats st;
+    st.sweeps = k;
+    st.outer_steps = 0;
+    st.final_delta = delta;
+    st.rel_residual = __longlong_as_double(0x7FF8000000000000ll);
+    st.status = status;
+    st.converged = status == kStatusOk;
+    p.ctl->result = st;
+    if (p.stats_out) *p.stats_out = st;
+  }
+}
+
+// ================================================================================ IR path
+
+// Residual phase: r_i = b_i - sum_j a_ij x_j (FP64, the full row of A), inner right-hand side
+// c1_i = r_i / a_ii, first inner iterate delta^(1) = c1 (the inner iteration starts from zero).
+struct ResidEpi {
+  const double* b;
+  const double* rinv;
+  float* c1;
+  float* d1;
+  unsigned long long mr, mc;
+  __device__ __forceinline__ void row(int64_t i, double dot) {
+    const double r = b[i] - dot;
+    const float c = static_cast<float>(r * rinv[i]);
+    c1[i] = c;
+    d1[i] = c;
+    mr = umax(mr, abs_bits(r));
+    mc = umax(mc, abs_bits(c));
+  }
+};
+
+// Inner sweep on the narrow matrix: delta^(m)_i = c1_i - f_i * sum_j n_ij delta^(m-1)_j (the Section 2
+// update of A delta = r with the stored factor f_i = 1/a_ii (times the E4M3 row scale)), plus the
+// candidate X + delta^(m) in FP64, used if this is the last inner sweep of the outer step.
+struct InnerEpi {
+  const float* c1;
+  const float* rowfac;
+  const float* dc;
+  float* dn;
+  const double* xc;
+  double* xalt;
+  unsigned long long mchg, mmag;
+  __device__ __forceinline__ void row(int64_t i, float dot) {
+    const float v = fmaf(-rowfac[i], dot, c1[i]);
+    const float old = dc[i];
+    dn[i] = v;
+    xalt[i] = xc[i] + static_cast<double>(v);
+    mchg = umax(mchg, abs_bits(v - old));
+    mmag = umax(mmag, abs_bits(v));
+  }
+};
+
+enum Kind : int { kResid = 0, kInner = 1, kDone = 2 };
+
+template <typename TL>
+__global__ void __launch_bounds__(kThreads, 1) ir_solve_kernel(SolveParams p) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ Ring ring;
+  __shared__ double red64[kConsumerWarps][kRows];
+  __shared__ float red32[kConsumerWarps][kRows];
+  __shared__ int s_abort, s_kind, s_xcur, s_dcur, s_first;
+  char* stages = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+
+  const int G = gridDim.x;
+  const int64_t r0 = p.n * blockIdx.x / G, r1 = p.n * (blockIdx.x + 1) / G;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_kind = kResid;
+    s_xcur = 0;
+    s_dcur = 0;
+    s_first = 1;
+  }
+  init_ring(&ring);
+  __syncthreads();
+  Block B{&ring, stages, &s_abort, &p.ctl->status};
+  const bool producer = threadIdx.x >= kConsumers;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TL* Nl = static_cast<const TL*>(p.Nlow);
+
+  uint32_t u = 0;
+  uint32_t phase = 0;
+  // decision state (meaningful in warp 0 lane 0; identical in every CTA)
+  int64_t outer = 0, inner_total = 0, inner_step = 0;
+  double rho = 0.0, last_change = 0.0;
+  int status = kStatusNotConverged;
+  for (;; ++phase) {
+    const int kind = s_kind;
+    const int xcur = s_xcur, dcur = s_dcur;
+    const bool skip_matrix = s_first && p.x0_zero;
+    double* xc = xcur ? p.xb : p.xa;
+    double* xalt = xcur ? p.xa : p.xb;
+    float* dc = dcur ? p.db : p.da;
+    float* dn = dcur ? p.da : p.db;
+    unsigned long long v0 = 0, v1 = 0;
+    if (kind == kResid) {
+      ResidEpi epi{p.b, p.rinv, p.c1, p.da, 0ull, 0ull};
+      if (producer) {
+        if (!skip_matrix) produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
+      } else {
+        consume_phase<double>(B, u, xc, p.n, r0, r1, !skip_matrix, red64, epi);
+      }
+      v0 = epi.mr;
+      v1 = epi.mc;
+    } else {
+      InnerEpi epi{p.c1, p.rowfac, dc, dn, xc, xalt, 0ull, 0ull};
+      if (producer) {
+        produce_phase<TL>(B, u, Nl, p.ldn, p.n, r0, r1);
+      } else {
+        consume_phase<TL>(B, u, dc, p.n, r0, r1, true, red32, epi);
+      }
+      v0 = epi.mchg;
+      v1 = epi.mmag;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      v0 = warp_max_u64(v0);
+      v1 = warp_max_u64(v1);
+      int ok = 1;
+      if (lane == 0) ok = (s_abort == 0) && publish_and_sync(p.ctl, phase, v0, v1);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (lane == 0) {
+        const double g0v = bits_to_double(ld_cg_u64(&p.ctl->red[phase % 3][0]));
+        const double g1v = bits_to_double(ld_cg_u64(&p.ctl->red[phase % 3][1]));
+        int next = kDone;
+        if (!ok) {
+          status = kStatusTimeout;
+          s_abort = 1;
+        } else if (kind == kResid) {
+          ++outer;
+          rho = g0v / __ldg(p.bnorm);
+          if (!isfinite(rho)) {
+            status = kStatusNonfinite;
+          } else if (rho <= p.tol) {
+            status = kStatusOk;
+          } else if (outer >= p.max_outer || inner_total >= p.max_iter) {
+            status = kStatusNotConverged;
+          } else {
+            next = kInner;
+            inner_step = 0;
+            s_dcur = 0;  // delta^(1) was written into da
+          }
+        } else {
+          ++inner_total;
+          ++inner_step;
+          last_change = g0v;
+          if (!isfinite(g0v) || !isfinite(g1v)) {
+            status = kStatusNonfinite;
+          } else if (g0v <= static_cast<double>(p.inner_rtol) * g1v || inner_step >= p.max_inner ||
+                     inner_total >= p.max_iter) {
+            next = kResid;
+            s_xcur = xcur ^ 1;  // X + delta becomes the current iterate
+          } else {
+            next = kInner;
+            s_dcur = dcur ^ 1;
+          }
+        }
+        s_kind = next;
+        s_first = 0;
+      }
+    }
+    __syncthreads();
+    if (s_kind == kDone) break;
+  }
+  if (producer) {
+    if (lane == 0) drain_ring(B, u);
+    return;
+  }
+  const double* xres = s_xcur ? p.xb : p.xa;
+  if (warp == 0 && s_abort == 0) {
+    for (int64_t g0 = r0; g0 < r1; g0 += kRows)
+      if (g0 + lane < r1 && lane < kRows) p.x_out[g0 + lane] = xres[g0 + lane];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    jacobi_stats st;
+    st.sweeps = inner_total;
+    st.outer_steps = outer;
+    st.final_delta = last_change;
+    st.rel_residual = rho;
+    st.status = status;
+    st.converged = status == kStatusOk;
+    p.ctl->result = st;
+    if (p.stats_out) *p.stats_out = st;
+  }
+}
+
+template <typename K>
+cudaError_t launch_coop(K kernel, const SolveParams& p, int grid, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+  if (e != cudaSuccess) return e;
+  SolveParams copy = p;
+  void* args[] = {&copy};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel), dim3(grid), dim3(kThreads), args,
+                                     kDynSmem, s);
+}
+
+template <typename K>
+int coresident(K kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, kDynSmem) != cudaSuccess) return 0;
+  return per_sm * sms;
+}
+
+}  // namespace
+
+cudaError_t launch_fp64_solve(const SolveParams& p, int grid, cudaStream_t s) {
+  return launch_coop(fp64_solve_kernel, p, grid, s);
+}
+
+cudaError_t launch_ir_solve(Narrow kind, const SolveParams& p, int grid, cudaStream_t s) {
+  switch (kind) {
+    case Narrow::F32: return launch_coop(ir_solve_kernel<float>, p, grid, s);
+    case Narrow::BF16: return launch_coop(ir_solve_kernel<__nv_bfloat16>, p, grid, s);
+    case Narrow::E4M3: return launch_coop(ir_solve_kernel<__nv_fp8_e4m3>, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int max_coresident_grid(bool ir, Narrow kind) {
+  if (!ir) return coresident(fp64_solve_kernel);
+  switch (kind) {
+    case Narrow::F32: return coresident(ir_solve_kernel<float>);
+    case Narrow::BF16: return coresident(ir_solve_kernel<__nv_bfloat16>);
+    case Narrow::E4M3: return coresident(ir_solve_kernel<__nv_fp8_e4m3>);
+  }
+  return 0;
+}
+
+}  // namespace jac

@@ -1,0 +1,89 @@
+// Shared declarations of the CUDA solver library (kernels <-> host C-ABI layer).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "jacobi.h"
+
+namespace jac {
+
+// ---------------------------------------------------------------- persistent streaming kernels
+constexpr int kConsumerWarps = 8;                       // warps that compute dot products
+constexpr int kConsumers = kConsumerWarps * 32;          // 256 threads
+constexpr int kThreads = kConsumers + 32;                // + one producer warp (bulk copies)
+constexpr int kRows = 8;                                 // rows of a row group (one ring item)
+constexpr int kRowBytes = kConsumerWarps * 32 * 16;      // 4 KB of one row per ring item
+constexpr int kStageBytes = kRows * kRowBytes;           // 32 KB per ring stage
+constexpr int kStages = 6;                               // ring depth
+constexpr int kDynSmem = kStages * kStageBytes + 128;    // + alignment slack
+constexpr int kMaxGrid = 1024;                           // size of the per-CTA partial-sum arrays
+constexpr int kLdAlign = 16;                             // leading dimensions are multiples of 16
+
+// Control block of one solve (device memory, zeroed before each launch).
+struct Ctl {
+  unsigned int arrive;               // grid-barrier arrival counter
+  int status;                        // < 0 once any CTA hit an error (timeout)
+  unsigned long long red[3][2];      // rotating reduction slots (order-free max of |.| bits)
+  jacobi_stats result;               // written by CTA 0 at the end
+};
+
+enum class Narrow : int { F32 = 1, BF16 = 2, E4M3 = 3 };
+
+struct SolveParams {
+  int64_t n;
+  const double* A;        // FP64 A including the diagonal, row-major, row stride lda (16-B aligned rows)
+  int64_t lda;
+  const void* Nlow;       // IR: narrow off-diagonal copy, row stride ldn, zero diagonal
+  int64_t ldn;
+  const double* b;        // n
+  const double* d;        // n, a_ii
+  const double* rinv;     // n, 1 / a_ii (correctly rounded)
+  const float* rowfac;    // IR: n, factor of the narrow row dot (1/a_ii, times the E4M3 row scale)
+  const double* bnorm;    // ||B||_inf (one value)
+  double* xa;             // FP64 iterate buffers, length >= round_up(n, 16), zero padding
+  double* xb;
+  float* c1;              // IR: inner right-hand side D^-1 r
+  float* da;              // IR: inner iterate buffers
+  float* db;
+  double* part;           // [2][kMaxGrid] per-CTA partial sums (Euclidean norm)
+  Ctl* ctl;
+  double* x_out;          // device result (n)
+  jacobi_stats* stats_out;  // optional device copy of the result record
+  int64_t max_iter;
+  double tol;
+  int norm;               // jacobi_norm
+  int x0_zero;            // 1: the start vector is zero (the first IR residual needs no matrix pass)
+  int max_outer;
+  int max_inner;
+  float inner_rtol;
+};
+
+// Host launchers (solve.cu).  Each returns a cudaError_t from the launch.
+cudaError_t launch_fp64_solve(const SolveParams& p, int grid, cudaStream_t s);
+cudaError_t launch_ir_solve(Narrow kind, const SolveParams& p, int grid, cudaStream_t s);
+int max_coresident_grid(bool ir, Narrow kind);
+
+// Preparation kernels (prepare.cu).
+// Reads a_ii, checks it (zero / non-finite), writes d, rinv; key_out receives the smallest
+// (row << 8 | code) of a failing row (code 2: zero, 3: non-finite), or all ones if none.
+cudaError_t launch_diag(const double* A, int64_t lda, int64_t n, double* d, double* rinv,
+                        unsigned long long* key_out, cudaStream_t s);
+// b (FP64 copy) and ||b||_inf bits into *bnorm_bits (must be zeroed before).
+cudaError_t launch_rhs(const double* B, int64_t n, double* b, unsigned long long* bnorm_bits,
+                       cudaStream_t s);
+// Narrow copy of the off-diagonal part of A (zero diagonal, zero padding up to ldn) and the FP32
+// per-row factor of the inner sweep.
+cudaError_t launch_narrow(Narrow kind, const double* A, int64_t lda, int64_t n, void* Nlow, int64_t ldn,
+                          const double* rinv, float* scale, float* rowfac, cudaStream_t s);
+// Zero columns [n, ld) of an n x ld row-major FP64 matrix.
+cudaError_t launch_pad_zero(double* M, int64_t n, int64_t ld, cudaStream_t s);
+// Relative residual ||b - A x||_inf / ||b||_inf (FP64) into *rel_bits (zeroed before) as max bits of
+// |r_i|; the host divides by ||b||.
+cudaError_t launch_residual(const double* A, int64_t lda, int64_t n, const double* b, const double* x,
+                            unsigned long long* rmax_bits, cudaStream_t s);
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace jac

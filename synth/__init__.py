@@ -54,6 +54,18 @@ def philox4x32_10(ctr: np.ndarray, key: tuple[int, int]) -> np.ndarray:
     return np.stack([c0, c1, c2, c3], axis=1).astype(np.uint32)
 
 
+def _blocks(seed: int, stream: int, first: int, last: int) -> np.ndarray:
+    q = np.arange(first, last + 1, dtype=np.uint64)
+    ctr = np.zeros((q.size, 4), dtype=np.uint32)
+    ctr[:, 0] = (q & _MASK32).astype(np.uint32)
+    ctr[:, 1] = (q >> np.uint64(32)).astype(np.uint32)
+    ctr[:, 2] = np.uint32(stream & 0xFFFFFFFF)
+    return philox4x32_10(ctr, (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)).reshape(-1)
+
+
+_PAR_BLOCKS = 1 << 20  # split larger requests over threads (numpy releases the GIL in its kernels)
+
+
 def random_u32(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
     """``count`` uint32 words of the sequence ``(seed, stream)`` starting at word ``offset``.
 
@@ -63,12 +75,21 @@ def random_u32(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarra
         return np.zeros(0, dtype=np.uint32)
     first = offset // 4
     last = (offset + count - 1) // 4
-    q = np.arange(first, last + 1, dtype=np.uint64)
-    ctr = np.zeros((q.size, 4), dtype=np.uint32)
-    ctr[:, 0] = (q & _MASK32).astype(np.uint32)
-    ctr[:, 1] = (q >> np.uint64(32)).astype(np.uint32)
-    ctr[:, 2] = np.uint32(stream & 0xFFFFFFFF)
-    out = philox4x32_10(ctr, (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)).reshape(-1)
+    nblk = last - first + 1
+    if nblk <= _PAR_BLOCKS:
+        out = _blocks(seed, stream, first, last)
+    else:
+        import concurrent.futures as cf
+        import os
+        out = np.empty(nblk * 4, dtype=np.uint32)
+        step = _PAR_BLOCKS
+
+        def work(a):
+            b = min(a + step, nblk) - 1
+            out[4 * a:4 * (b + 1)] = _blocks(seed, stream, first + a, first + b)
+
+        with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+            list(ex.map(work, range(0, nblk, step)))
     start = offset - first * 4
     return out[start:start + count]
 

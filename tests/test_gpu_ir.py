@@ -1,0 +1,120 @@
+"""Mixed-precision paths (FP32 / BF16 / E4M3 inner sweeps, FP64 refinement) on the GPU.
+
+Parity of the iterates with the oracle is not expected (different arithmetic by design); what is pinned:
+  * the narrow copies of A are bit-identical to the oracle's encoders (integer / byte work);
+  * the returned X meets ||B - A X||_inf / ||B||_inf <= 1e-10, recomputed by the oracle in FP64;
+  * the residual the kernel reports equals the oracle's residual of the returned X;
+  * the error against the oracle's converged FP64 solution is within the residual bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32_ir", "bf16_ir", "fp8_ir"]
+
+
+@pytest.fixture(scope="module")
+def jac():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_5805_gb300 as jac
+    return jac
+
+
+def dev_solver(jac, A, B, **kw):
+    import torch
+    At = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    Bt = torch.from_numpy(np.ascontiguousarray(B).reshape(-1)).cuda()
+    return jac.DeviceSolver(At, Bt, **kw)
+
+
+def qnorm(A):
+    d = np.abs(np.diag(A))
+    M = np.abs(A)
+    np.fill_diagonal(M, 0.0)
+    return float(np.max(M.sum(axis=1) / d))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [1, 33, 100, 1000])
+def test_narrow_copy_bit_exact(jac, prec, n):
+    A, B, _ = synth.dominant_system(n, 1.1, seed=40 + n)
+    s = dev_solver(jac, A, B, precision=prec)
+    got, scale = s.narrow()
+    if prec == "fp32_ir":
+        np.testing.assert_array_equal(got, oracle.offdiag_f32(A))
+    elif prec == "bf16_ir":
+        np.testing.assert_array_equal(got, oracle.offdiag_bf16(A))
+    else:
+        q, sc = oracle.offdiag_e4m3(A)
+        np.testing.assert_array_equal(scale, sc)
+        np.testing.assert_array_equal(got, q)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("gen,n,f", [("dom", 1, 1.25), ("dom", 33, 1.25), ("dom", 512, 1.25), ("dom", 4096, 1.05),
+                                     ("hard", 300, 1.25), ("hard", 2000, 1.1)])
+def test_refinement_reaches_target(jac, prec, gen, n, f):
+    make = synth.dominant_system if gen == "dom" else synth.hard_system
+    A, B, Xs = make(n, f, seed=50 + n)
+    target = 1e-10
+    s = dev_solver(jac, A, B, precision=prec)
+    X, st = s.solve(max_iter=5000, tol=target)
+    Xh = X.cpu().numpy()
+    _, rel = oracle.residual(A, B, Xh)
+    assert st.status == 0 and rel <= target, (st.as_dict(), rel)
+    assert abs(st.rel_residual - rel) <= 1e-13 + 1e-3 * rel
+    q = qnorm(A)
+    ref = oracle.jacobi(A, B, max_iter=20000, tol=1e-14)
+    err = np.max(np.abs(Xh[:, None] - ref.X)) / np.max(np.abs(ref.X))
+    assert err <= 2 * target * (1 + q) / (1 - q) + 1e-13, err
+    print(f"{prec} {gen} n={n}: outer={st.outer_steps} inner={st.sweeps} residual={rel:.2e} err={err:.2e}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_single_system(jac, prec):
+    """n = 16384, f = 1.05: relative residual <= 1e-10 recomputed on the CPU."""
+    A, B, _ = synth.dominant_system(16384, 1.05, seed=synth.BASE_SEED + 1)
+    s = dev_solver(jac, A, B, precision=prec)
+    X, st = s.solve(max_iter=5000, tol=1e-10)
+    _, rel = oracle.residual(A, B, X.cpu().numpy())
+    assert st.status == 0 and rel <= 1e-10, (st.as_dict(), rel)
+
+
+def test_nonzero_start_vector(jac):
+    import torch
+    A, B, Xs = synth.dominant_system(700, 1.25, seed=61)
+    X0 = Xs[:, 0] + 1e-3 * np.linspace(-1, 1, 700)
+    s = dev_solver(jac, A, B, precision="bf16_ir")
+    X, st = s.solve(X0=torch.from_numpy(X0).cuda(), max_iter=500, tol=1e-10)
+    _, rel = oracle.residual(A, B, X.cpu().numpy())
+    assert st.status == 0 and rel <= 1e-10
+    # a start vector that already meets the target returns after one residual evaluation
+    X2, st2 = s.solve(X0=X.clone(), max_iter=500, tol=1e-10)
+    assert st2.outer_steps == 1 and st2.sweeps == 0
+    assert torch.equal(X2, X)
+
+
+def test_outer_cap_reports_not_converged(jac):
+    A, B, _ = synth.hard_system(500, 1.1, seed=62)
+    s = dev_solver(jac, A, B, precision="bf16_ir", max_outer=2)
+    X, st = s.solve(max_iter=5000, tol=1e-14)
+    assert st.status == jac.NOT_CONVERGED and st.outer_steps == 2
+    _, rel = oracle.residual(A, B, X.cpu().numpy())
+    assert abs(st.rel_residual - rel) <= 1e-13 + 1e-3 * rel
+
+
+def test_device_residual_entry_point(jac):
+    import torch
+    A, B, Xs = synth.dominant_system(777, 1.1, seed=63)
+    s = dev_solver(jac, A, B)
+    x = torch.from_numpy(Xs[:, 0] + 1e-6).cuda()
+    _, rel = oracle.residual(A, B, x.cpu().numpy())
+    assert abs(s.residual(x) - rel) <= 1e-14 + 1e-9 * rel
