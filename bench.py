@@ -163,7 +163,7 @@ def run_ours(args, world, rank, local):
         rel = s.residual(out)
         err = float((out - Xs_t).abs().max().item())
         return {"ms_total": ms, "kernel_ms": kernel_ms, "stats": st.as_dict(), "rel_residual_check": rel,
-                "err_vs_xstar": err, "clocks": clocks}
+                "err_vs_xstar": err, "clocks": clocks, "phases": phase_bandwidth(s.trace(), n, prec)}
 
     main = timed(args.precision, args.steps, args.warmup, sample_clocks=True)
     ms_step = main["ms_total"] / args.steps
@@ -197,7 +197,7 @@ def run_ours(args, world, rank, local):
     if "fp64" in paths:
         fp64_ratio = round(paths[args.precision]["solves_per_s"] / paths["fp64"]["solves_per_s"], 3)
 
-    e2e = run_e2e(args, jac, torch, dev, A, B, ws)
+    e2e = None if args.no_e2e else run_e2e(args, jac, torch, dev, A, B, ws)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
@@ -217,6 +217,22 @@ def run_ours(args, world, rank, local):
     return result
 
 
+def phase_bandwidth(trace, n, prec):
+    """Per-phase-kind mean duration and algorithmic matrix bandwidth from the device-side trace of the
+    last solve (each phase streams the whole matrix once: FP64 A, or the narrow copy)."""
+    names = {0: ("sweep64", 8), 1: ("resid64", 8), 2: ("resid0", 0), 3: ("inner", ESIZE.get(prec, 8))}
+    out = {}
+    for kind, (name, es) in names.items():
+        d = [(e - b) for k, b, e in trace if k == kind]
+        if not d:
+            continue
+        # the first phase of a kind includes the kernel start-up; the mean over all is what is reported
+        mean_ns = sum(d) / len(d)
+        out[name] = {"count": len(d), "mean_us": round(mean_ns / 1e3, 2),
+                     "gbs": round(es * float(n) * n / mean_ns, 1) if es and mean_ns > 0 else None}
+    return out
+
+
 def summarize(r, steps, n, prec):
     st = r["stats"]
     ms = r["ms_total"] / steps
@@ -229,6 +245,7 @@ def summarize(r, steps, n, prec):
             "sweeps": st["sweeps"], "outer_steps": st["outer_steps"], "status": st["status"],
             "rel_residual": r["rel_residual_check"], "err_vs_xstar": r["err_vs_xstar"],
             "kernel_algorithmic_gbs": round(bytes_launch / (r["kernel_ms"] * 1e-3) / 1e9, 1),
+            "phases": r["phases"],
             "gbs_per_sweep": round((8.0 if prec == "fp64" else es) * n * n / (r["kernel_ms"] * 1e-3 /
                                    max(st["sweeps"], 1)) / 1e9, 1) if prec == "fp64" else None}
 
@@ -337,6 +354,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10, dest="e2e_steps")
     ap.add_argument("--quick", action="store_true", help="skip the comparison paths")
     ap.add_argument("--no-cpu-baseline", action="store_true", dest="no_cpu_baseline")
+    ap.add_argument("--no-e2e", action="store_true", dest="no_e2e")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.warmup < 3 and args.impl == "ours":

@@ -180,6 +180,17 @@ JACOBI_API int jacobi_residual(jacobi_handle* h, const double* X, double* rel_ou
  * Waits for the stream. */
 JACOBI_API int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* scale_host);
 
+/* Device-side trace of the last solve: the persistent kernel records, for each phase (one sweep or one
+ * residual evaluation, ended by a grid-wide barrier), the %globaltimer nanoseconds since the kernel
+ * started and the phase kind (JACOBI_PHASE_*).  Writes min(cap, phases) entries, the phase count to
+ * *count (phases beyond the first 512 are not recorded).  Waits for the stream. */
+#define JACOBI_PHASE_SWEEP64 0  /* FP64 Jacobi sweep over A */
+#define JACOBI_PHASE_RESID64 1  /* FP64 residual r = B - A X over A */
+#define JACOBI_PHASE_RESID0 2   /* residual of a zero start vector (r = B, no matrix pass) */
+#define JACOBI_PHASE_INNER 3    /* inner sweep over the narrow copy of A */
+JACOBI_API int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap,
+                                 int32_t* count);
+
 #ifdef __cplusplus
 }
 #endif

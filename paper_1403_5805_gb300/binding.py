@@ -24,12 +24,15 @@ FP64, FP32_IR, BF16_IR, FP8_IR = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR, "bf16_ir": BF16_IR, "fp8_ir": FP8_IR}
 # jacobi_norm
 NORM_INF, NORM_2, NORM_RESID = 0, 1, 2
+# trace phase kinds (JACOBI_PHASE_*)
+PHASE_SWEEP64, PHASE_RESID64, PHASE_RESID0, PHASE_INNER = 0, 1, 2, 3
 NORMS = {"inf": NORM_INF, "2": NORM_2, "resid": NORM_RESID}
 FLAG_COPY_A = 1
 
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
            "jacobi_desc_init", "jacobi_workspace_size", "jacobi_setup_ex", "jacobi_solve_async",
-           "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual", "jacobi_get_narrow")
+           "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual", "jacobi_get_narrow",
+           "jacobi_last_trace")
 
 
 class JacobiStats(ctypes.Structure):
@@ -89,9 +92,10 @@ def load() -> ctypes.CDLL:
         lib.jacobi_last_stats.argtypes = [H, ctypes.POINTER(JacobiStats)]
         lib.jacobi_residual.argtypes = [H, vp, ctypes.POINTER(dbl)]
         lib.jacobi_get_narrow.argtypes = [H, vp, i64, vp]
+        lib.jacobi_last_trace.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
                      "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
-                     "jacobi_get_narrow"):
+                     "jacobi_get_narrow", "jacobi_last_trace"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -217,6 +221,30 @@ class DeviceSolver:
         st = self.last_stats()
         _check(st.status, "solve")
         return out, st
+
+    def narrow(self):
+        """Host copy of the narrow off-diagonal matrix the inner sweeps read, as raw codes
+        (float32 / uint16 BF16 codes / uint8 E4M3 codes, shape (n, n)), and the E4M3 row scales."""
+        dt = {"fp32_ir": np.float32, "bf16_ir": np.uint16, "fp8_ir": np.uint8}[self.precision]
+        out = np.zeros((self.n, self.n), dtype=dt)
+        scale = np.zeros(self.n, dtype=np.float32)
+        _check(load().jacobi_get_narrow(self._h, out.ctypes.data, self.n, scale.ctypes.data), "jacobi_get_narrow")
+        return out, scale
+
+    def trace(self):
+        """Device-side phase trace of the last solve: list of (kind, start_ns, end_ns) per phase."""
+        cap = 512
+        t = np.zeros(cap, dtype=np.int64)
+        k = np.zeros(cap, dtype=np.int32)
+        cnt = ctypes.c_int32(0)
+        _check(load().jacobi_last_trace(self._h, t.ctypes.data, k.ctypes.data, cap, ctypes.byref(cnt)),
+               "jacobi_last_trace")
+        m = min(cap, cnt.value)
+        out, prev = [], 0
+        for i in range(m):
+            out.append((int(k[i]), prev, int(t[i])))
+            prev = int(t[i])
+        return out
 
     def residual(self, X) -> float:
         """||B - A X||_inf / ||B||_inf on the device in FP64."""

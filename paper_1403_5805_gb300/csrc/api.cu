@@ -411,6 +411,27 @@ int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* s
   return JACOBI_OK;
 }
 
+int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && (!t_end_ns || !kinds))) return JACOBI_ERR_INVALID_ARG;
+  Ctl* ctl = h->at<Ctl>(h->L.ctl);
+  Ctl* host = static_cast<Ctl*>(std::malloc(sizeof(Ctl)));
+  if (!host) return JACOBI_ERR_OUT_OF_MEMORY;
+  cudaError_t e = cudaMemcpyAsync(host, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    std::free(host);
+    return cuda_fail(e, "trace read");
+  }
+  *count = host->nphase;
+  const int m = host->nphase < cap ? host->nphase : cap;
+  for (int i = 0; i < m; ++i) {
+    t_end_ns[i] = static_cast<int64_t>(host->t_end[i] - host->t_start);
+    kinds[i] = host->kind[i];
+  }
+  std::free(host);
+  return JACOBI_OK;
+}
+
 void jacobi_destroy(jacobi_handle* h) {
   if (!h) return;
   if (h->own_ws && h->ws) {

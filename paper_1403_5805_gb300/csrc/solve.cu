@@ -121,13 +121,23 @@ __device__ __forceinline__ void seg_dot(float& acc, uint4 m, const float (&xv)[1
   e4m3x4_fma(acc, m.w, xv + 12);
 }
 
-// Zero the x values of columns >= n (the segment that straddles the end of a row may carry matrix
-// padding that is not guaranteed to be zero or finite).
+// The segment that straddles the end of a row (columns >= n inside it) may carry row padding that is
+// not guaranteed to be zero or even finite when A is read in place.  x is zeroed there, and for FP64
+// rows the padding element is skipped, not multiplied (NaN * 0 would poison the sum).  The narrow
+// copies are written by this library with zero padding, so their full segment is safe.
 template <typename XT, int V>
 __device__ __forceinline__ void mask_tail(XT (&xv)[V], int64_t col, int64_t n) {
 #pragma unroll
   for (int e = 0; e < V; ++e)
     if (col + e >= n) xv[e] = XT(0);
+}
+__device__ __forceinline__ void seg_dot_tail(double& acc, uint4 m, const double (&xv)[2], int64_t valid) {
+  acc = fma(__hiloint2double(static_cast<int>(m.y), static_cast<int>(m.x)), xv[0], acc);
+  if (valid > 1) acc = fma(__hiloint2double(static_cast<int>(m.w), static_cast<int>(m.z)), xv[1], acc);
+}
+template <int V>
+__device__ __forceinline__ void seg_dot_tail(float& acc, uint4 m, const float (&xv)[V], int64_t) {
+  seg_dot(acc, m, xv);
 }
 
 struct Block {
@@ -207,14 +217,23 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
       if (!ok) {
         raise_abort(B);
       } else if (col < n) {
-        if (col + V > n) mask_tail(xv, col, n);
         const char* base = B.stages + s * kStageBytes + co * static_cast<int>(sizeof(TM));
+        if (col + V <= n) {
 #pragma unroll
-        for (int r = 0; r < kRows; ++r)
-          if (r < rows) {
-            const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
-            seg_dot(acc[r], m, xv);
-          }
+          for (int r = 0; r < kRows; ++r)
+            if (r < rows) {
+              const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+              seg_dot(acc[r], m, xv);
+            }
+        } else {
+          mask_tail(xv, col, n);
+#pragma unroll
+          for (int r = 0; r < kRows; ++r)
+            if (r < rows) {
+              const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+              seg_dot_tail(acc[r], m, xv, n - col);
+            }
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.ring->empty[s]);
@@ -277,6 +296,15 @@ __device__ bool publish_and_sync(Ctl* ctl, uint32_t phase, unsigned long long v0
   return grid_arrive_and_wait(&ctl->arrive, &ctl->status, (phase + 1) * gridDim.x);
 }
 
+// Device-side trace (CTA 0, lane 0 of warp 0): end time of phase `phase` and its kind.
+__device__ __forceinline__ void trace_phase(Ctl* ctl, uint32_t phase, int kind) {
+  if (blockIdx.x == 0 && phase < static_cast<uint32_t>(kTraceCap)) {
+    ctl->t_end[phase] = global_timer_ns();
+    ctl->kind[phase] = kind;
+    ctl->nphase = static_cast<int>(phase) + 1;
+  }
+}
+
 __device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) {
   return a > b ? a : b;
 }
@@ -320,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_solve_kernel(SolveParams p) 
   if (threadIdx.x == 0) {
     s_abort = 0;
     s_next = kContinue;
+    if (blockIdx.x == 0) p.ctl->t_start = global_timer_ns();
   }
   init_ring(&ring);
   __syncthreads();
@@ -364,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_solve_kernel(SolveParams p) 
         if (p.norm == JACOBI_NORM_RESID) dk = dk / __ldg(p.bnorm);
       }
       if (lane == 0) {
+        trace_phase(p.ctl, phase, JACOBI_PHASE_SWEEP64);
         int next = kContinue;
         if (!ok) {
           status = kStatusTimeout;
@@ -465,6 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) ir_solve_kernel(SolveParams p) {
   const int G = gridDim.x;
   const int64_t r0 = p.n * blockIdx.x / G, r1 = p.n * (blockIdx.x + 1) / G;
   if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) p.ctl->t_start = global_timer_ns();
     s_abort = 0;
     s_kind = kResid;
     s_xcur = 0;
@@ -520,6 +551,8 @@ __global__ void __launch_bounds__(kThreads, 1) ir_solve_kernel(SolveParams p) {
       if (lane == 0) ok = (s_abort == 0) && publish_and_sync(p.ctl, phase, v0, v1);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (lane == 0) {
+        trace_phase(p.ctl, phase,
+                    kind == kInner ? JACOBI_PHASE_INNER : (skip_matrix ? JACOBI_PHASE_RESID0 : JACOBI_PHASE_RESID64));
         const double g0v = bits_to_double(ld_cg_u64(&p.ctl->red[phase % 3][0]));
         const double g1v = bits_to_double(ld_cg_u64(&p.ctl->red[phase % 3][1]));
         int next = kDone;

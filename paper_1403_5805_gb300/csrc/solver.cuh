@@ -21,12 +21,20 @@ constexpr int kDynSmem = kStages * kStageBytes + 128;    // + alignment slack
 constexpr int kMaxGrid = 1024;                           // size of the per-CTA partial-sum arrays
 constexpr int kLdAlign = 16;                             // leading dimensions are multiples of 16
 
+constexpr int kTraceCap = 512;                           // phases recorded by the device-side trace
+
 // Control block of one solve (device memory, zeroed before each launch).
 struct Ctl {
   unsigned int arrive;               // grid-barrier arrival counter
   int status;                        // < 0 once any CTA hit an error (timeout)
   unsigned long long red[3][2];      // rotating reduction slots (order-free max of |.| bits)
   jacobi_stats result;               // written by CTA 0 at the end
+  // trace: %globaltimer when CTA 0 leaves the grid barrier that ends each phase, and the phase kind
+  unsigned long long t_start;
+  int nphase;
+  int pad_;
+  unsigned long long t_end[kTraceCap];
+  int kind[kTraceCap];
 };
 
 enum class Narrow : int { F32 = 1, BF16 = 2, E4M3 = 3 };
