@@ -191,6 +191,34 @@ JACOBI_API int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_ds
 JACOBI_API int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap,
                                  int32_t* count);
 
+/* ------------------------------------------------------------------------------------------------
+ * Allocation-free FP64 solve.  The paper has no counterpart to this entry point: it exists for callers
+ * that must not allocate device memory while they run, such as a plugin inside a host application that
+ * owns the GPU's memory pool and forbids other allocations, or a latency-bound loop that cannot afford
+ * cudaMalloc's implicit synchronisation and its possible failure.
+ * ------------------------------------------------------------------------------------------------ */
+
+/* Largest n jacobi_solve_fp64_noalloc accepts. */
+#define JACOBI_NOALLOC_MAX_N 32768
+
+/* The same FP64 Jacobi solve as jacobi_setup_ex + jacobi_solve_ex (max-norm test, strict < tol), with
+ * no device allocation: the library's own scratch (about 1 MB: control block, iterate buffers, diagonal
+ * reciprocals) is a fixed array in device memory that every device loading the library keeps until the
+ * process exits.
+ *   A      device, row-major n x n, A[i*lda + j]; 16-byte aligned, lda even; for odd n, lda > n and the
+ *          element A[i*lda + n] of each row is read (its value is ignored).  Read in place.
+ *   B      device, n values.  X0: device, n values, or NULL for zeros.  X_out: device, n values.
+ *   stats  host, filled if not NULL.  stream: cudaStream_t (NULL: legacy default stream).
+ * Returns the solve's jacobi_status; JACOBI_ERR_INVALID_ARG for n > JACOBI_NOALLOC_MAX_N, a misaligned
+ * or non-device A / B / X_out, max_iter < 1 or tol <= 0.  Blocks until the solve is done.
+ * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call shares the one array and it keeps the last
+ * call's contents (each call clears what must start at zero), so calls that overlap on the GPU - from
+ * two streams or two host threads on one device - race: serialise them. */
+JACOBI_API int jacobi_solve_fp64_noalloc(const double* A, int64_t lda, const double* B, int64_t n,
+                                         const double* X0, int64_t max_iter, double tol, double* X_out,
+                                         jacobi_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ FLAG_COPY_A = 1
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
            "jacobi_desc_init", "jacobi_workspace_size", "jacobi_setup_ex", "jacobi_solve_async",
            "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual", "jacobi_get_narrow",
-           "jacobi_last_trace")
+           "jacobi_last_trace", "jacobi_solve_fp64_noalloc")
 
 
 class JacobiStats(ctypes.Structure):
@@ -93,9 +93,10 @@ def load() -> ctypes.CDLL:
         lib.jacobi_residual.argtypes = [H, vp, ctypes.POINTER(dbl)]
         lib.jacobi_get_narrow.argtypes = [H, vp, i64, vp]
         lib.jacobi_last_trace.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_solve_fp64_noalloc.argtypes = [vp, i64, vp, i64, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats), vp]
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
                      "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
-                     "jacobi_get_narrow", "jacobi_last_trace"):
+                     "jacobi_get_narrow", "jacobi_last_trace", "jacobi_solve_fp64_noalloc"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
