@@ -130,7 +130,8 @@ def run_ours(args, world, rank, local):
 
     def one_step(prec, ev=None):
         nonlocal ws
-        s = jac.DeviceSolver(At, Bt, precision=prec, workspace=ws if ws.numel() else None)
+        s = jac.DeviceSolver(At, Bt, precision=prec, workspace=ws if ws.numel() else None,
+                             inner_rtol=args.inner_rtol, max_inner=args.max_inner)
         ws = s.workspace
         if ev is not None:
             ev[0].record(stream)
@@ -262,7 +263,8 @@ def run_e2e(args, jac, torch, dev, A, B, ws):
     steps = max(1, min(args.steps, args.e2e_steps))
 
     def step():
-        s = jac.DeviceSolver(Ah, Bh, precision=args.precision, workspace=ws, device=dev)
+        s = jac.DeviceSolver(Ah, Bh, precision=args.precision, workspace=ws, device=dev,
+                             inner_rtol=args.inner_rtol, max_inner=args.max_inner)
         s.solve_async(None, args.max_iter, TARGET, out)
         Xh.copy_(out, non_blocking=True)
         st = s.last_stats()  # waits for the stream (the result has landed in Xh)
@@ -352,6 +354,9 @@ def main():
                     help="stopping threshold of the plain FP64 path (max-norm change)")
     ap.add_argument("--max-iter", type=int, default=5000, dest="max_iter")
     ap.add_argument("--e2e-steps", type=int, default=10, dest="e2e_steps")
+    ap.add_argument("--inner-rtol", type=float, default=0.0, dest="inner_rtol",
+                    help="mixed paths: inner-sweep stop (relative change); 0 = library default")
+    ap.add_argument("--max-inner", type=int, default=0, dest="max_inner")
     ap.add_argument("--quick", action="store_true", help="skip the comparison paths")
     ap.add_argument("--no-cpu-baseline", action="store_true", dest="no_cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", dest="no_e2e")

@@ -60,7 +60,7 @@ struct MatTraits<__nv_fp8_e4m3> {
 
 template <typename TM>
 __host__ __device__ constexpr int chunk_cols() {
-  return kConsumerWarps * 32 * MatTraits<TM>::kVec;
+  return kColWarps * 32 * MatTraits<TM>::kVec;
 }
 
 // ---- x loads (L2 only: the iterate is rewritten by other CTAs between sweeps, so L1 may be stale)
@@ -186,24 +186,61 @@ __device__ void produce_phase(const Block& B, uint32_t& u, const TM* M, int64_t 
   }
 }
 
+// Sum each of the 8 per-lane accumulators over the 32 lanes of a warp in 9 shuffle+add steps: every
+// exchange halves the values a lane keeps, so after the xor-16/8/4 steps lane l holds the partial of row
+// row_of_lane(l) over 8 lanes, and the xor-2/1 steps finish it.  The order of additions is fixed.
+template <typename Acc>
+__device__ __forceinline__ Acc transpose_reduce8(const Acc (&v)[kRowsPerWarp], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  Acc w4[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const Acc send = b4 ? v[r] : v[r + 4];
+    const Acc keep = b4 ? v[r + 4] : v[r];
+    w4[r] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  Acc w2[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const Acc send = b3 ? w4[r] : w4[r + 2];
+    const Acc keep = b3 ? w4[r + 2] : w4[r];
+    w2[r] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const Acc send = b2 ? w2[0] : w2[1];
+  const Acc keep = b2 ? w2[1] : w2[0];
+  Acc w1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  w1 += __shfl_xor_sync(0xffffffffu, w1, 2);
+  w1 += __shfl_xor_sync(0xffffffffu, w1, 1);
+  return w1;
+}
+__device__ __forceinline__ int row_of_lane(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
 // Consumer warps: row dot products of rows [r0, r1) against x, then epi.row(i, dot) by warp 0, lane
-// (i - group start).  with_matrix == false skips the matrix (dot = 0).
+// (i - group start); epi.prefetch(i) runs on the same lane when the group starts, so the epilogue's
+// operands arrive while the group streams.  Warp w covers column slice w % kColWarps of every chunk
+// and rows [8 * (w / kColWarps), +8) of the group.  with_matrix == false skips the matrix (dot = 0).
 template <typename TM, typename Epi>
 __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTraits<TM>::X* x, int64_t n,
                               int64_t r0, int64_t r1, bool with_matrix,
-                              typename MatTraits<TM>::Acc (*red)[kRows], Epi& epi) {
+                              typename MatTraits<TM>::Acc (*red)[kConsumerWarps][kRowsPerWarp], Epi& epi) {
   using XT = typename MatTraits<TM>::X;
   using Acc = typename MatTraits<TM>::Acc;
   constexpr int V = MatTraits<TM>::kVec;
   constexpr int K = chunk_cols<TM>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int co = (warp * 32 + lane) * V;  // first column of this lane inside a chunk
+  const int cw = warp % kColWarps, rh = warp / kColWarps;
+  const int co = (cw * 32 + lane) * V;  // first column of this lane inside a chunk
   const int64_t nch = with_matrix ? (n + K - 1) / K : 0;
-  for (int64_t g0 = r0; g0 < r1; g0 += kRows) {
+  int grp = 0;
+  for (int64_t g0 = r0; g0 < r1; g0 += kRows, ++grp) {
     const int rows = static_cast<int>(i64min(kRows, r1 - g0));
-    Acc acc[kRows];
+    const int myrows = rows - rh * kRowsPerWarp;  // rows of this warp's half that exist (may be <= 0)
+    if (warp == 0 && lane < rows) epi.prefetch(g0 + lane);
+    Acc acc[kRowsPerWarp];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) acc[r] = Acc(0);
+    for (int r = 0; r < kRowsPerWarp; ++r) acc[r] = Acc(0);
     XT xv[V], xn[V];
     if (nch > 0 && co < n) load_x(xv, x + co);
     for (int64_t c = 0; c < nch; ++c) {
@@ -216,20 +253,21 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
       if (ok) ok = mbar_wait(&B.ring->full[s], par);
       if (!ok) {
         raise_abort(B);
-      } else if (col < n) {
-        const char* base = B.stages + s * kStageBytes + co * static_cast<int>(sizeof(TM));
+      } else if (col < n && myrows > 0) {
+        const char* base = B.stages + s * kStageBytes + rh * kRowsPerWarp * kRowBytes +
+                           co * static_cast<int>(sizeof(TM));
         if (col + V <= n) {
 #pragma unroll
-          for (int r = 0; r < kRows; ++r)
-            if (r < rows) {
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            if (r < myrows) {
               const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
               seg_dot(acc[r], m, xv);
             }
         } else {
           mask_tail(xv, col, n);
 #pragma unroll
-          for (int r = 0; r < kRows; ++r)
-            if (r < rows) {
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            if (r < myrows) {
               const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
               seg_dot_tail(acc[r], m, xv, n - col);
             }
@@ -241,20 +279,18 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
 #pragma unroll
       for (int e = 0; e < V; ++e) xv[e] = xn[e];
     }
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) acc[r] = warp_sum(acc[r]);
-    if (lane == 0) {
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) red[warp][r] = acc[r];
-    }
+    const Acc part = transpose_reduce8(acc, lane);
+    if ((lane & 3) == 0) red[grp & 1][warp][row_of_lane(lane)] = part;
+    // one barrier per group: red is double-buffered, and a buffer is rewritten only two groups later,
+    // after every warp has passed the next group's barrier (so warp 0 has finished reading it)
     named_barrier(1, kConsumers);
     if (warp == 0 && lane < rows) {
-      Acc dot = red[0][lane];
+      const int half = lane / kRowsPerWarp, r = lane % kRowsPerWarp;
+      Acc dot = red[grp & 1][half * kColWarps][r];
 #pragma unroll
-      for (int w = 1; w < kConsumerWarps; ++w) dot += red[w][lane];  // fixed order: deterministic
+      for (int w = 1; w < kColWarps; ++w) dot += red[grp & 1][half * kColWarps + w][r];  // fixed order
       epi.row(g0 + lane, dot);
     }
-    named_barrier(1, kConsumers);
   }
 }
 
@@ -320,14 +356,20 @@ struct Fp64SweepEpi {
   int norm;
   unsigned long long mx;  // running max (bits) over this lane's rows
   double sq;              // running sum of squares (Euclidean norm)
+  double pb, pd, pr, px;  // this lane's row operands, loaded when its row group starts
+  __device__ __forceinline__ void prefetch(int64_t i) {
+    pb = b[i];
+    pd = d[i];
+    pr = rinv[i];
+    px = __ldcg(xc + i);
+  }
   __device__ __forceinline__ void row(int64_t i, double dot) {
-    const double xo = __ldcg(xc + i);
-    const double s = fma(-d[i], xo, dot);     // sum_{j != i} a_ij x_j: the diagonal term taken back out
-    const double xi = (b[i] - s) * rinv[i];   // Section 2 component update, 1/a_ii precomputed
+    const double s = fma(-pd, px, dot);  // sum_{j != i} a_ij x_j: the diagonal term taken back out
+    const double xi = (pb - s) * pr;     // Section 2 component update, 1/a_ii precomputed
     xn[i] = xi;
-    const double diff = xi - xo;
+    const double diff = xi - px;
     if (norm == JACOBI_NORM_RESID)
-      mx = umax(mx, abs_bits(d[i] * diff));
+      mx = umax(mx, abs_bits(pd * diff));
     else
       mx = umax(mx, abs_bits(diff));
     sq = fma(diff, diff, sq);
@@ -336,10 +378,10 @@ struct Fp64SweepEpi {
 
 enum Next : int { kContinue = 0, kStop = 1 };
 
-__global__ void __launch_bounds__(kThreads, 1) fp64_solve_kernel(SolveParams p) {
+__global__ void __maxnreg__(kMaxRegs) fp64_solve_kernel(SolveParams p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ Ring ring;
-  __shared__ double red[kConsumerWarps][kRows];
+  __shared__ double red[2][kConsumerWarps][kRowsPerWarp];
   __shared__ int s_abort, s_next;
   char* stages = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
 
@@ -364,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_solve_kernel(SolveParams p) 
   for (;; ++k) {
     const double* xc = cur ? p.xb : p.xa;
     double* xn = cur ? p.xa : p.xb;
-    Fp64SweepEpi epi{p.b, p.d, p.rinv, xc, xn, p.norm, 0ull, 0.0};
+    Fp64SweepEpi epi{p.b, p.d, p.rinv, xc, xn, p.norm, 0ull, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (producer) {
       produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
     } else {
@@ -450,9 +492,14 @@ struct ResidEpi {
   float* c1;
   float* d1;
   unsigned long long mr, mc;
+  double pb, pr;
+  __device__ __forceinline__ void prefetch(int64_t i) {
+    pb = b[i];
+    pr = rinv[i];
+  }
   __device__ __forceinline__ void row(int64_t i, double dot) {
-    const double r = b[i] - dot;
-    const float c = static_cast<float>(r * rinv[i]);
+    const double r = pb - dot;
+    const float c = static_cast<float>(r * pr);
     c1[i] = c;
     d1[i] = c;
     mr = umax(mr, abs_bits(r));
@@ -471,11 +518,19 @@ struct InnerEpi {
   const double* xc;
   double* xalt;
   unsigned long long mchg, mmag;
+  float pc, pf, pd;
+  double px;
+  __device__ __forceinline__ void prefetch(int64_t i) {
+    pc = c1[i];
+    pf = rowfac[i];
+    pd = dc[i];
+    px = xc[i];
+  }
   __device__ __forceinline__ void row(int64_t i, float dot) {
-    const float v = fmaf(-rowfac[i], dot, c1[i]);
-    const float old = dc[i];
+    const float v = fmaf(-pf, dot, pc);
+    const float old = pd;
     dn[i] = v;
-    xalt[i] = xc[i] + static_cast<double>(v);
+    xalt[i] = px + static_cast<double>(v);
     mchg = umax(mchg, abs_bits(v - old));
     mmag = umax(mmag, abs_bits(v));
   }
@@ -484,11 +539,11 @@ struct InnerEpi {
 enum Kind : int { kResid = 0, kInner = 1, kDone = 2 };
 
 template <typename TL>
-__global__ void __launch_bounds__(kThreads, 1) ir_solve_kernel(SolveParams p) {
+__global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ Ring ring;
-  __shared__ double red64[kConsumerWarps][kRows];
-  __shared__ float red32[kConsumerWarps][kRows];
+  __shared__ double red64[2][kConsumerWarps][kRowsPerWarp];
+  __shared__ float red32[2][kConsumerWarps][kRowsPerWarp];
   __shared__ int s_abort, s_kind, s_xcur, s_dcur, s_first;
   char* stages = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
 
@@ -525,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, 1) ir_solve_kernel(SolveParams p) {
     float* dn = dcur ? p.da : p.db;
     unsigned long long v0 = 0, v1 = 0;
     if (kind == kResid) {
-      ResidEpi epi{p.b, p.rinv, p.c1, p.da, 0ull, 0ull};
+      ResidEpi epi{p.b, p.rinv, p.c1, p.da, 0ull, 0ull, 0.0, 0.0};
       if (producer) {
         if (!skip_matrix) produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
       } else {
@@ -534,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 1) ir_solve_kernel(SolveParams p) {
       v0 = epi.mr;
       v1 = epi.mc;
     } else {
-      InnerEpi epi{p.c1, p.rowfac, dc, dn, xc, xalt, 0ull, 0ull};
+      InnerEpi epi{p.c1, p.rowfac, dc, dn, xc, xalt, 0ull, 0ull, 0.f, 0.f, 0.f, 0.0};
       if (producer) {
         produce_phase<TL>(B, u, Nl, p.ldn, p.n, r0, r1);
       } else {

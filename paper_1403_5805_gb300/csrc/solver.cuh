@@ -10,14 +10,33 @@
 namespace jac {
 
 // ---------------------------------------------------------------- persistent streaming kernels
-constexpr int kConsumerWarps = 8;                       // warps that compute dot products
-constexpr int kConsumers = kConsumerWarps * 32;          // 256 threads
+// Warp layout of the persistent CTA (compile-time; the defaults are the measured best on GB300):
+// JAC_COL_WARPS warps split the columns of a ring item, JAC_ROW_GROUPS groups of 8 rows split its rows,
+// plus one producer warp.
+#ifndef JAC_COL_WARPS
+#define JAC_COL_WARPS 6
+#endif
+#ifndef JAC_ROW_GROUPS
+#define JAC_ROW_GROUPS 2
+#endif
+constexpr int kColWarps = JAC_COL_WARPS;                 // warps across the columns of a ring item
+constexpr int kRowsPerWarp = 8;                          // rows each consumer warp accumulates
+constexpr int kRowHalves = JAC_ROW_GROUPS;               // warp groups splitting the item's rows
+constexpr int kConsumerWarps = kColWarps * kRowHalves;   // warps that compute dot products
+constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;                // + one producer warp (bulk copies)
-constexpr int kRows = 8;                                 // rows of a row group (one ring item)
-constexpr int kRowBytes = kConsumerWarps * 32 * 16;      // 4 KB of one row per ring item
-constexpr int kStageBytes = kRows * kRowBytes;           // 32 KB per ring stage
-constexpr int kStages = 6;                               // ring depth
+// The register file is split over the SM's 4 schedulers (16 K registers each) and a warp lives on
+// one of them, so the per-thread budget follows from the warps per scheduler.
+constexpr int kWarpsPerScheduler = (kThreads / 32 + 3) / 4;
+constexpr int kMaxRegsRaw = 16384 / (kWarpsPerScheduler * 32) / 8 * 8;
+constexpr int kMaxRegs = kMaxRegsRaw > 255 ? 255 : kMaxRegsRaw;
+constexpr int kRows = kRowsPerWarp * kRowHalves;         // rows of a row group (one ring item)
+constexpr int kRowBytes = kColWarps * 32 * 16;           // bytes of one row per ring item
+constexpr int kStageBytes = kRows * kRowBytes;           // bytes per ring stage
+constexpr int kStages = (192 * 1024) / kStageBytes;      // ring depth within 192 KB
 constexpr int kDynSmem = kStages * kStageBytes + 128;    // + alignment slack
+static_assert(kRows <= 32, "one epilogue lane per row of a group");
+static_assert(kStages >= 2, "ring needs two stages");
 constexpr int kMaxGrid = 1024;                           // size of the per-CTA partial-sum arrays
 constexpr int kLdAlign = 16;                             // leading dimensions are multiples of 16
 
