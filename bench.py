@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -106,7 +108,6 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------- our arm
 
 def run_ours(args, world, rank, local):
-    import numpy as np
     import torch
 
     import synth
@@ -199,6 +200,7 @@ def run_ours(args, world, rank, local):
         fp64_ratio = round(paths[args.precision]["solves_per_s"] / paths["fp64"]["solves_per_s"], 3)
 
     e2e = None if args.no_e2e else run_e2e(args, jac, torch, dev, A, B, ws)
+    batched = None if (args.quick or args.no_batch) else run_batch(args, jac, torch, dev)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
@@ -211,7 +213,7 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs (2.15 GB A) larger than the 129 MB L2; no flush"},
         "gpu_launches": (4 if args.precision != "fp64" else 3) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
-        "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e,
+        "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(A, B, n)
@@ -249,6 +251,75 @@ def summarize(r, steps, n, prec):
             "phases": r["phases"],
             "gbs_per_sweep": round((8.0 if prec == "fp64" else es) * n * n / (r["kernel_ms"] * 1e-3 /
                                    max(st["sweeps"], 1)) / 1e9, 1) if prec == "fp64" else None}
+
+
+def make_batch_inputs(count, seed, n_lo=64, n_hi=1024, f_lo=1.05, f_hi=2.0):
+    """The batched workload: `count` dominant systems, n log-uniform in [n_lo, n_hi], f uniform in
+    [f_lo, f_hi], generated on a thread pool."""
+    import concurrent.futures as cf
+
+    import synth
+    ns, fs = synth.batch_shapes(count, n_lo, n_hi, f_lo, f_hi, seed)
+
+    def one(k):
+        A, B, _ = synth.dominant_system(int(ns[k]), float(fs[k]), synth.system_seed(seed, k))
+        return A, B[:, 0].copy()
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        systems = list(ex.map(one, range(count)))
+    return ns, fs, systems
+
+
+def run_batch(args, jac, torch, dev):
+    """4096 independent systems (n log-uniform in [64, 1024], f uniform in [1.05, 2.0]): one persistent
+    work-queue kernel per solve, replayed from a CUDA graph, FP32 storage with FP64 refinement against
+    the plain FP64 batched path, both to a 1e-10 relative residual; launch shapes from the autotuner."""
+    import synth
+    from paper_1403_5805_gb300 import autotune
+    count = args.batch_count
+    ns, fs, systems = make_batch_inputs(count, synth.BASE_SEED + 2)
+    As = [torch.from_numpy(A).to(dev) for A, _ in systems]
+    Bs = [torch.from_numpy(b).to(dev) for _, b in systems]
+    sum_n2 = float(np.sum(ns.astype(np.float64) ** 2))
+    stream = torch.cuda.current_stream(dev)
+    out = {"count": count, "n_range": [64, 1024], "f_range": [1.05, 2.0], "sum_n2": sum_n2}
+    for prec in ("fp32_ir", "fp64"):
+        tuned = autotune.tune_batch(As, Bs, precision=prec, tol=TARGET, use_cache=True)
+        bs = jac.BatchSolver(As, Bs, precision=prec, rows_per_warp=tuned["rows_per_warp"],
+                             ctas_per_sm=tuned["ctas_per_sm"], inner_rtol=tuned["inner_rtol"])
+        for _ in range(args.warmup):
+            bs.solve_async(args.max_iter, TARGET)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps = args.batch_steps
+        for _ in range(steps):
+            bs.solve_async(args.max_iter, TARGET)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        st = bs.stats()
+        ok = sum(1 for x in st if x.status == 0)
+        sweeps = np.array([x.sweeps for x in st], dtype=np.float64)
+        n2 = ns.astype(np.float64) ** 2
+        if prec == "fp64":
+            alg = float(np.sum(sweeps * 8.0 * n2))
+            worst = float(max(x.final_delta for x in st))
+        else:
+            outer = np.array([x.outer_steps for x in st], dtype=np.float64)
+            # setup pass (read A, write the FP32 copy) + FP64 residual passes + FP32 inner sweeps
+            alg = float(np.sum((8.0 + 4.0) * n2 + np.maximum(outer - 1, 0) * 8.0 * n2 + sweeps * 4.0 * n2))
+            worst = float(max(x.rel_residual for x in st))
+        out[prec] = {"solves_per_s": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 4),
+                     "converged": ok, "mean_sweeps": round(float(sweeps.mean()), 3),
+                     "worst_rel_residual": worst, "algorithmic_gbs": round(alg / (ms * 1e-3) / 1e9, 1),
+                     "grid": bs.grid, "tuned": {k: tuned[k] for k in ("rows_per_warp", "ctas_per_sm", "inner_rtol",
+                                                                      "cached")}}
+        if prec != "fp64":
+            out[prec]["mean_outer_steps"] = round(float(np.mean([x.outer_steps for x in st])), 3)
+        bs.close()
+    out["mixed_vs_fp64_solves_ratio"] = round(out["fp32_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
+    return out
 
 
 def run_e2e(args, jac, torch, dev, A, B, ws):
@@ -360,6 +431,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the comparison paths")
     ap.add_argument("--no-cpu-baseline", action="store_true", dest="no_cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", dest="no_e2e")
+    ap.add_argument("--no-batch", action="store_true", dest="no_batch")
+    ap.add_argument("--batch-count", type=int, default=4096, dest="batch_count")
+    ap.add_argument("--batch-steps", type=int, default=10, dest="batch_steps")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.warmup < 3 and args.impl == "ours":

@@ -192,6 +192,67 @@ JACOBI_API int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* k
                                  int32_t* count);
 
 /* ------------------------------------------------------------------------------------------------
+ * Batched solves of many independent systems of uneven size.
+ *
+ * Section 2's Jacobi iteration applied to `count` independent systems A_k X_k = B_k (n_k <=
+ * JACOBI_BATCH_MAX_N) in one persistent kernel: each CTA takes a whole system from a device work queue
+ * (largest first), keeps its iterates in shared memory, and sweeps its rows with its warps (the
+ * row-wise distribution of Section 3.1 applied to systems over SMs and rows over warps).  The launch
+ * is captured once into a CUDA graph and replayed.
+ * ------------------------------------------------------------------------------------------------ */
+
+#define JACOBI_BATCH_MAX_N 4096
+
+typedef struct jacobi_batch jacobi_batch;
+
+typedef struct jacobi_batch_desc {
+  int64_t count;              /* number of systems, >= 1 */
+  const int64_t* n;           /* host array [count]: sizes, 1 <= n_k <= JACOBI_BATCH_MAX_N */
+  const double* const* A;     /* host array [count] of device pointers: row-major n_k x n_k (stride n_k),
+                                 read in place by every solve (keep unchanged until destroy) */
+  const double* const* B;     /* host array [count] of device pointers: n_k values */
+  double* const* X;           /* host array [count] of device pointers: n_k outputs */
+  int32_t precision;          /* JACOBI_FP64: plain Jacobi with the previous-iterate relative-residual
+                                 stop (strict <); JACOBI_FP32_IR / JACOBI_BF16_IR: FP64 refinement around
+                                 narrow inner sweeps, stop at ||B - A X||_inf / ||B||_inf <= tol */
+  int32_t rows_per_warp;      /* 1, 2, 4 or 8 rows a warp accumulates at once (0: 4) */
+  int32_t ctas_per_sm;        /* cap on resident CTAs per SM (0: as many as fit) */
+  int32_t max_outer;          /* IR: cap on residual evaluations per system (0: 30) */
+  int32_t max_inner;          /* IR: cap on inner sweeps per outer step (0: 64) */
+  int32_t reserved;
+  double inner_rtol;          /* IR: inner stop, max|change| <= inner_rtol * max|delta| (0: 2^-14) */
+  void* workspace;            /* device, >= jacobi_batch_workspace_size bytes, 256-byte aligned; NULL:
+                                 the library allocates it */
+  size_t workspace_bytes;
+  void* stream;               /* cudaStream_t the solves are ordered on (NULL: legacy default) */
+} jacobi_batch_desc;
+
+/* Device bytes the batch needs: per system its narrow copy (IR) and four n-vectors, plus the system
+ * table, the queue counter and the per-system records. */
+JACOBI_API int jacobi_batch_workspace_size(const jacobi_batch_desc* d, size_t* bytes);
+
+/* Validate, lay out the workspace, upload the system table (sorted by decreasing n).  Synchronises the
+ * stream once.  *out is NULL on error. */
+JACOBI_API int jacobi_batch_create(const jacobi_batch_desc* d, jacobi_batch** out);
+
+/* Solve every system from X = 0, asynchronously on the batch's stream: one graph launch (queue reset
+ * + the persistent kernel; captured on the first call for this (max_iter, tol) and replayed after).
+ * max_iter caps sweeps per system (FP64) or inner sweeps per system (IR).  Each system's status lands
+ * in its record (jacobi_batch_stats); a system with a zero or non-finite diagonal gets
+ * JACOBI_ERR_ZERO_DIAGONAL / JACOBI_ERR_NONFINITE and its X is left as zeros. */
+JACOBI_API int jacobi_batch_solve_async(jacobi_batch* b, int64_t max_iter, double tol);
+
+/* Copy the per-system records of the last solve (host array [count], in the caller's order); waits
+ * for the stream. */
+JACOBI_API int jacobi_batch_stats(jacobi_batch* b, jacobi_stats* stats);
+
+/* CTAs of the persistent batch kernel (0 for NULL). */
+JACOBI_API int jacobi_batch_grid(jacobi_batch* b);
+
+/* Release the batch (waits for its stream; NULL is a no-op). */
+JACOBI_API void jacobi_batch_destroy(jacobi_batch* b);
+
+/* ------------------------------------------------------------------------------------------------
  * Allocation-free FP64 solve.  The paper has no counterpart to this entry point: it exists for callers
  * that must not allocate device memory while they run, such as a plugin inside a host application that
  * owns the GPU's memory pool and forbids other allocations, or a latency-bound loop that cannot afford

@@ -32,7 +32,9 @@ FLAG_COPY_A = 1
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
            "jacobi_desc_init", "jacobi_workspace_size", "jacobi_setup_ex", "jacobi_solve_async",
            "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual", "jacobi_get_narrow",
-           "jacobi_last_trace", "jacobi_solve_fp64_noalloc")
+           "jacobi_last_trace", "jacobi_solve_fp64_noalloc", "jacobi_batch_workspace_size",
+           "jacobi_batch_create", "jacobi_batch_solve_async", "jacobi_batch_stats", "jacobi_batch_grid",
+           "jacobi_batch_destroy")
 
 
 class JacobiStats(ctypes.Structure):
@@ -41,6 +43,14 @@ class JacobiStats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class JacobiBatchDesc(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("n", ctypes.c_void_p), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("X", ctypes.c_void_p), ("precision", ctypes.c_int32), ("rows_per_warp", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
 
 
 class JacobiDesc(ctypes.Structure):
@@ -93,10 +103,19 @@ def load() -> ctypes.CDLL:
         lib.jacobi_residual.argtypes = [H, vp, ctypes.POINTER(dbl)]
         lib.jacobi_get_narrow.argtypes = [H, vp, i64, vp]
         lib.jacobi_last_trace.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_batch_workspace_size.argtypes = [ctypes.POINTER(JacobiBatchDesc), ctypes.POINTER(ctypes.c_size_t)]
+        lib.jacobi_batch_create.argtypes = [ctypes.POINTER(JacobiBatchDesc), ctypes.POINTER(H)]
+        lib.jacobi_batch_solve_async.argtypes = [H, i64, dbl]
+        lib.jacobi_batch_stats.argtypes = [H, vp]
+        lib.jacobi_batch_grid.argtypes = [H]
+        lib.jacobi_batch_destroy.argtypes = [H]
+        lib.jacobi_batch_destroy.restype = None
         lib.jacobi_solve_fp64_noalloc.argtypes = [vp, i64, vp, i64, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats), vp]
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
                      "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
-                     "jacobi_get_narrow", "jacobi_last_trace", "jacobi_solve_fp64_noalloc"):
+                     "jacobi_get_narrow", "jacobi_last_trace", "jacobi_solve_fp64_noalloc",
+                     "jacobi_batch_workspace_size", "jacobi_batch_create", "jacobi_batch_solve_async",
+                     "jacobi_batch_stats", "jacobi_batch_grid"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -264,3 +283,69 @@ class DeviceSolver:
         except Exception:
             pass
 
+
+
+# ------------------------------------------------------------------------------ batched interface
+
+class BatchSolver:
+    """``jacobi_batch_*``: many independent systems (lists of float64 CUDA tensors), one persistent
+    kernel per solve, replayed from a captured CUDA graph."""
+
+    def __init__(self, As, Bs, precision: str = "fp32_ir", rows_per_warp: int = 0, ctas_per_sm: int = 0,
+                 max_outer: int = 0, max_inner: int = 0, inner_rtol: float = 0.0, stream=None, workspace=None):
+        import torch
+        lib = load()
+        if len(As) != len(Bs) or not As:
+            raise ValueError("need one B per A")
+        self.count = len(As)
+        self.device = As[0].device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._A = [a.contiguous() for a in As]
+        self._B = [b.reshape(-1).contiguous() for b in Bs]
+        for a, b in zip(self._A, self._B):
+            if a.dtype != torch.float64 or b.dtype != torch.float64 or not a.is_cuda or a.shape[0] != b.numel():
+                raise ValueError("A_k (n_k x n_k) and B_k (n_k) must be float64 CUDA tensors")
+        self.n = np.array([a.shape[0] for a in self._A], dtype=np.int64)
+        self.X = [torch.zeros(int(k), dtype=torch.float64, device=self.device) for k in self.n]
+        self._pa = (ctypes.c_void_p * self.count)(*[a.data_ptr() for a in self._A])
+        self._pb = (ctypes.c_void_p * self.count)(*[b.data_ptr() for b in self._B])
+        self._px = (ctypes.c_void_p * self.count)(*[x.data_ptr() for x in self.X])
+        d = JacobiBatchDesc()
+        d.count = self.count
+        d.n = self.n.ctypes.data
+        d.A, d.B, d.X = ctypes.addressof(self._pa), ctypes.addressof(self._pb), ctypes.addressof(self._px)
+        d.precision = PRECISIONS[precision]
+        d.rows_per_warp, d.ctas_per_sm = rows_per_warp, ctas_per_sm
+        d.max_outer, d.max_inner, d.inner_rtol = max_outer, max_inner, inner_rtol
+        d.stream = self.stream.cuda_stream
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.jacobi_batch_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_batch_workspace_size")
+        if workspace is None or workspace.numel() < nbytes.value:
+            workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self.workspace = workspace
+        d.workspace, d.workspace_bytes = workspace.data_ptr(), workspace.numel()
+        self._desc = d
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.jacobi_batch_create(ctypes.byref(d), ctypes.byref(self._h)), "jacobi_batch_create", False)
+        self.grid = lib.jacobi_batch_grid(self._h)
+
+    def solve_async(self, max_iter: int = 5000, tol: float = 1e-10):
+        _check(load().jacobi_batch_solve_async(self._h, max_iter, tol), "jacobi_batch_solve_async")
+        return self.X
+
+    def stats(self):
+        arr = (JacobiStats * self.count)()
+        _check(load().jacobi_batch_stats(self._h, ctypes.addressof(arr)), "jacobi_batch_stats")
+        return list(arr)
+
+    def close(self):
+        if self._h:
+            load().jacobi_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
