@@ -349,3 +349,59 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+class MultiSolver:
+    """Many right-hand sides through ``jacobi_setup_ex`` (nrhs = r) / ``jacobi_solve_ex``: plain FP64
+    Jacobi, or BF16 inner sweeps on tcgen05 tensor cores with FP64 refinement.  B and X are (r, n)
+    float64 CUDA tensors (row c is right-hand side c, i.e. column-major n x r)."""
+
+    def __init__(self, A, B, precision: str = "bf16_ir", stream=None, max_outer: int = 0, max_inner: int = 0,
+                 inner_rtol: float = 0.0):
+        import torch
+        lib = load()
+        n = A.shape[0]
+        if B.dim() != 2 or B.shape[1] != n or B.stride(1) != 1:
+            raise ValueError("B must be (r, n) with unit stride along n")
+        self.n, self.r = n, B.shape[0]
+        self.device = A.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(A.device)
+        d = JacobiDesc()
+        lib.jacobi_desc_init(ctypes.byref(d))
+        d.n, d.nrhs = n, self.r
+        d.precision = PRECISIONS[precision]
+        d.A, d.lda = A.data_ptr(), A.stride(0)
+        d.B, d.ldb = B.data_ptr(), B.stride(0)
+        d.stream = self.stream.cuda_stream
+        d.max_outer, d.max_inner, d.inner_rtol = max_outer, max_inner, inner_rtol
+        nbytes = ctypes.c_size_t(0)
+        with torch.cuda.device(A.device):
+            _check(lib.jacobi_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_workspace_size")
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=A.device)
+        d.workspace, d.workspace_bytes = self.workspace.data_ptr(), self.workspace.numel()
+        self._A, self._B = A, B
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(A.device):
+            _check(lib.jacobi_setup_ex(ctypes.byref(d), ctypes.byref(self._h)), "jacobi_setup_ex", False)
+
+    def solve(self, X0=None, max_iter: int = 5000, tol: float = 1e-10, out=None):
+        """Returns ``(X, stats)`` with X an (r, n) tensor; raises on error statuses (< 0)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.r, self.n, dtype=torch.float64, device=self.device)
+        st = JacobiStats()
+        rc = load().jacobi_solve_ex(self._h, None if X0 is None else X0.data_ptr(), max_iter, tol, out.data_ptr(),
+                                    ctypes.byref(st))
+        _check(rc, "jacobi_solve_ex")
+        return out, st
+
+    def close(self):
+        if self._h:
+            load().jacobi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

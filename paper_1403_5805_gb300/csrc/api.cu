@@ -9,7 +9,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
+#include "mrhs.cuh"
 #include "solver.cuh"
 
 using namespace jac;
@@ -105,13 +107,49 @@ Layout make_layout(int64_t n, int precision, bool copy_A) {
 }
 
 int validate_desc(const jacobi_desc* d) {
-  if (!d || d->n < 1 || !d->A || !d->B) return JACOBI_ERR_INVALID_ARG;
+  if (!d || d->n < 1 || d->nrhs < 1 || !d->A || !d->B) return JACOBI_ERR_INVALID_ARG;
   if (d->lda < d->n || d->ldb < d->n) return JACOBI_ERR_INVALID_ARG;
   if (d->precision < JACOBI_FP64 || d->precision > JACOBI_FP8_IR) return JACOBI_ERR_INVALID_ARG;
   if (d->norm < JACOBI_NORM_INF || d->norm > JACOBI_NORM_RESID) return JACOBI_ERR_INVALID_ARG;
   if (d->grid < 0 || d->grid > kMaxGrid) return JACOBI_ERR_INVALID_ARG;
-  if (d->nrhs != 1) return JACOBI_ERR_UNSUPPORTED;
+  if (d->nrhs > 1) {
+    // many right-hand sides: plain FP64 (max-norm stop) or BF16 inner sweeps on tcgen05
+    if (d->precision == JACOBI_FP64 && d->norm != JACOBI_NORM_INF) return JACOBI_ERR_UNSUPPORTED;
+    if (d->precision != JACOBI_FP64 && d->precision != JACOBI_BF16_IR) return JACOBI_ERR_UNSUPPORTED;
+    if (d->precision == JACOBI_BF16_IR && !mrhs_supported_r(d->nrhs)) return JACOBI_ERR_UNSUPPORTED;
+  }
   return JACOBI_OK;
+}
+
+// Extra device buffers of a many-right-hand-side handle (vectors v[c*ld + i]).
+struct MrhsLayout {
+  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, bcol, stats, status, total;
+};
+
+MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
+  MrhsLayout M{};
+  size_t o = base;
+  auto take = [&o](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t v8 = static_cast<size_t>(ld) * r * 8, v4 = static_cast<size_t>(ld) * r * 4,
+               v2 = static_cast<size_t>(ld) * r * 2;
+  M.b = take(v8);
+  M.xa = take(v8);
+  M.xb = take(v8);
+  M.c1 = take(v4);
+  M.da = take(v4);
+  M.db = take(v4);
+  M.dah = take(v2);
+  M.dbh = take(v2);
+  M.colmax = take(static_cast<size_t>(r) * 8);
+  M.bcol = take(static_cast<size_t>(r) * 8);
+  M.stats = take(16);
+  M.status = take(16);
+  M.total = o;
+  return M;
 }
 
 }  // namespace
@@ -119,6 +157,9 @@ int validate_desc(const jacobi_desc* d) {
 struct jacobi_handle {
   int device = 0;
   int64_t n = 0;
+  int64_t nrhs = 1;
+  MrhsLayout M{};
+  double last_colres_max = 0.0;
   int precision = JACOBI_FP64;
   int norm = JACOBI_NORM_INF;
   cudaStream_t stream = nullptr;
@@ -202,6 +243,11 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   h->norm = d->norm;
   h->stream = static_cast<cudaStream_t>(d->stream);
   h->L = make_layout(d->n, d->precision, copy_A);
+  h->nrhs = d->nrhs;
+  if (h->nrhs > 1) {
+    h->M = mrhs_layout(h->L.total, h->L.ld, h->nrhs);
+    h->L.total = h->M.total;
+  }
   h->max_outer = d->max_outer > 0 ? d->max_outer : 60;
   h->max_inner = d->max_inner > 0 ? d->max_inner : 64;
   h->inner_rtol = static_cast<float>(
@@ -230,6 +276,158 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   return JACOBI_OK;
 }
 
+// B (column-major, ldb) into the padded column layout and ||b_c||_inf per column.
+int mrhs_prepare(jacobi_handle* h, const double* B, int64_t ldb) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, r = h->nrhs, ld = h->L.ld;
+  double* b = h->at<double>(h->M.b);
+  CK(cudaMemsetAsync(b, 0, static_cast<size_t>(ld) * r * 8, s));
+  CK(cudaMemcpy2DAsync(b, ld * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), r, cudaMemcpyDefault, s));
+  for (size_t off : {h->M.xa, h->M.xb})
+    CK(cudaMemsetAsync(h->at<char>(off), 0, static_cast<size_t>(ld) * r * 8, s));
+  for (size_t off : {h->M.c1, h->M.da, h->M.db})
+    CK(cudaMemsetAsync(h->at<char>(off), 0, static_cast<size_t>(ld) * r * 4, s));
+  for (size_t off : {h->M.dah, h->M.dbh})
+    CK(cudaMemsetAsync(h->at<char>(off), 0, static_cast<size_t>(ld) * r * 2, s));
+  // per-column ||b||: the init kernel's column maxima of |B|
+  unsigned long long* bcol = h->at<unsigned long long>(h->M.bcol);
+  CK(cudaMemsetAsync(bcol, 0, static_cast<size_t>(r) * 8, s));
+  CK(launch_mrhs_init(n, r, ld, b, h->at<double>(h->L.rinv), h->at<float>(h->M.c1), h->at<float>(h->M.da),
+                      h->at<__nv_bfloat16>(h->M.dah), bcol, s));
+  CK(cudaStreamSynchronize(s));
+  return JACOBI_OK;
+}
+
+// Host-driven loop for many right-hand sides (each FP64 pass over A is a full matrix-matrix product,
+// milliseconds to a hundred milliseconds, so one small device-to-host read per phase costs nothing).
+int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out, jacobi_stats* st) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, r = h->nrhs, ld = h->L.ld;
+  double* xa = h->at<double>(h->M.xa);
+  double* xb = h->at<double>(h->M.xb);
+  unsigned long long* colmax = h->at<unsigned long long>(h->M.colmax);
+  std::vector<unsigned long long> hc(static_cast<size_t>(r)), hb(static_cast<size_t>(r));
+  CK(cudaMemcpyAsync(hb.data(), h->at<char>(h->M.bcol), static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
+  if (X0)
+    CK(cudaMemcpy2DAsync(xa, ld * 8, X0, n * 8, n * 8, r, cudaMemcpyDefault, s));
+  else
+    CK(cudaMemsetAsync(xa, 0, static_cast<size_t>(ld) * r * 8, s));
+  auto bits = [](unsigned long long u) {
+    double v;
+    std::memcpy(&v, &u, 8);
+    return v;
+  };
+  jacobi_stats out{};
+  out.rel_residual = std::nan("");
+  out.status = JACOBI_NOT_CONVERGED;
+  double* xc = xa;
+  double* xo = xb;
+  if (h->precision == JACOBI_FP64) {
+    for (int64_t k = 1;; ++k) {
+      CK(cudaMemsetAsync(colmax, 0, static_cast<size_t>(r) * 8, s));
+      MrhsDenseParams p{n, r, ld, h->lda64, 1, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
+                        h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax};
+      CK(launch_mrhs_dense(p, s));
+      CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      double delta = 0.0;
+      for (auto u : hc) delta = std::isnan(bits(u)) || bits(u) > delta ? bits(u) : delta;
+      std::swap(xc, xo);
+      out.sweeps = k;
+      out.final_delta = delta;
+      if (!std::isfinite(delta)) {
+        out.status = JACOBI_ERR_NONFINITE;
+        break;
+      }
+      if (delta < tol) {
+        out.status = JACOBI_OK;
+        break;
+      }
+      if (k >= max_iter) break;
+    }
+  } else {
+    float* c1 = h->at<float>(h->M.c1);
+    float* dA = h->at<float>(h->M.da);
+    float* dB = h->at<float>(h->M.db);
+    __nv_bfloat16* hA = h->at<__nv_bfloat16>(h->M.dah);
+    __nv_bfloat16* hB = h->at<__nv_bfloat16>(h->M.dbh);
+    unsigned long long* sst = h->at<unsigned long long>(h->M.stats);
+    int* status = h->at<int>(h->M.status);
+    CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    bool first = (X0 == nullptr);
+    int64_t outer = 0, inner_total = 0;
+    for (;;) {
+      CK(cudaMemsetAsync(colmax, 0, static_cast<size_t>(r) * 8, s));
+      if (first) {
+        CK(launch_mrhs_init(n, r, ld, h->at<double>(h->M.b), h->at<double>(h->L.rinv), c1, dA, hA, colmax, s));
+      } else {
+        MrhsDenseParams p{n, r, ld, h->lda64, 0, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
+                          h->at<double>(h->L.rinv), c1, dA, hA, nullptr, colmax};
+        CK(launch_mrhs_dense(p, s));
+      }
+      first = false;
+      ++outer;
+      CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      double rho = 0.0;
+      for (int64_t c = 0; c < r; ++c) {
+        const double v = bits(hc[static_cast<size_t>(c)]) / bits(hb[static_cast<size_t>(c)]);
+        rho = (std::isnan(v) || v > rho) ? v : rho;
+      }
+      out.rel_residual = rho;
+      if (!std::isfinite(rho)) {
+        out.status = JACOBI_ERR_NONFINITE;
+        break;
+      }
+      if (rho <= tol) {
+        out.status = JACOBI_OK;
+        break;
+      }
+      if (outer >= h->max_outer || inner_total >= max_iter) break;
+      float* dcur = dA;
+      float* dnew = dB;
+      __nv_bfloat16* hcur = hA;
+      __nv_bfloat16* hnew = hB;
+      for (int64_t m = 1;; ++m) {
+        CK(cudaMemsetAsync(sst, 0, 16, s));
+        MrhsSweepParams q{n, r, ld, h->at<float>(h->L.rowfac), c1, dcur, dnew, hnew, xc, xo, sst, status};
+        CK(launch_mrhs_sweep(h->at<void>(h->L.Nlow), hcur, q, s));
+        unsigned long long hs[2];
+        int hst = 0;
+        CK(cudaMemcpyAsync(hs, sst, 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ++inner_total;
+        if (hst != 0) {
+          out.status = hst;
+          break;
+        }
+        const double chg = bits(hs[0]), mag = bits(hs[1]);
+        out.final_delta = chg;
+        std::swap(dcur, dnew);
+        std::swap(hcur, hnew);
+        if (!std::isfinite(chg) || !std::isfinite(mag)) {
+          out.status = JACOBI_ERR_NONFINITE;
+          break;
+        }
+        if (chg <= h->inner_rtol * mag || m >= h->max_inner || inner_total >= max_iter) break;
+      }
+      if (out.status != JACOBI_NOT_CONVERGED) break;
+      std::swap(xc, xo);  // X + delta becomes the current iterate (the next residual rewrites dA / hA)
+    }
+    out.sweeps = inner_total;
+    out.outer_steps = outer;
+  }
+  CK(cudaMemcpy2DAsync(X_out, n * 8, xc, ld * 8, n * 8, r, cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  out.converged = out.status == JACOBI_OK;
+  if (st) *st = out;
+  // keep the record where jacobi_last_stats finds it
+  CK(cudaMemcpyAsync(&h->at<Ctl>(h->L.ctl)->result, &out, sizeof(out), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return out.status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -243,8 +441,9 @@ void jacobi_desc_init(jacobi_desc* d) {
 }
 
 int jacobi_workspace_size(const jacobi_desc* d, size_t* bytes) {
-  if (!d || !bytes || d->n < 1) return JACOBI_ERR_INVALID_ARG;
-  *bytes = make_layout(d->n, d->precision, !can_borrow(d)).total;
+  if (!d || !bytes || d->n < 1 || d->nrhs < 1) return JACOBI_ERR_INVALID_ARG;
+  const Layout L = make_layout(d->n, d->precision, !can_borrow(d));
+  *bytes = d->nrhs > 1 ? mrhs_layout(L.total, L.ld, d->nrhs).total : L.total;
   return JACOBI_OK;
 }
 
@@ -258,6 +457,7 @@ int jacobi_setup_ex(const jacobi_desc* d, jacobi_handle** out) {
   st = make_handle(d, copy_A, &h);
   if (st != JACOBI_OK) return st;
   st = prepare(h, d->A, d->lda, d->B, copy_A);
+  if (st == JACOBI_OK && h->nrhs > 1) st = mrhs_prepare(h, d->B, d->ldb);
   if (st != JACOBI_OK) {
     jacobi_destroy(h);
     return st;
@@ -303,6 +503,7 @@ int jacobi_setup(const double* A, const double* B, int64_t n, jacobi_handle** ou
 int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
                        jacobi_stats* stats_dev) {
   if (!h || !X_out || max_iter < 1 || !(tol > 0.0) || !std::isfinite(tol)) return JACOBI_ERR_INVALID_ARG;
+  if (h->nrhs > 1) return JACOBI_ERR_UNSUPPORTED;  // many right-hand sides: jacobi_solve_ex
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
   CK(cudaMemsetAsync(h->at<char>(h->L.ctl), 0, sizeof(Ctl), s));
@@ -353,6 +554,10 @@ int jacobi_last_stats(jacobi_handle* h, jacobi_stats* stats) {
 
 int jacobi_solve_ex(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
                     jacobi_stats* stats) {
+  if (h && h->nrhs > 1) {
+    if (!X_out || max_iter < 1 || !(tol > 0.0) || !std::isfinite(tol)) return JACOBI_ERR_INVALID_ARG;
+    return mrhs_solve(h, X0, max_iter, tol, X_out, stats);
+  }
   int st = jacobi_solve_async(h, X0, max_iter, tol, X_out, nullptr);
   if (st != JACOBI_OK) return st;
   jacobi_stats local;
@@ -365,6 +570,7 @@ int jacobi_solve_ex(jacobi_handle* h, const double* X0, int64_t max_iter, double
 int jacobi_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
                  int64_t* iters_out, double* final_delta_out) {
   if (!h || !X_out) return JACOBI_ERR_INVALID_ARG;
+  if (h->nrhs > 1) return JACOBI_ERR_UNSUPPORTED;
   double* xout = h->at<double>(h->L.xout);
   int st = jacobi_solve_async(h, X0, max_iter, tol, xout, nullptr);
   if (st != JACOBI_OK) return st;

@@ -1,0 +1,405 @@
+// Many right-hand sides: X (n x r) <- T X + C is a dense matrix-matrix product, so the sweep runs on
+// the 5th-generation tensor cores.
+//
+// mrhs_sweep_kernel   one inner sweep of the mixed-precision refinement for r right-hand sides,
+//                     delta^(m) = C1 - diag(1/a_ii) (N delta^(m-1)), on tcgen05: N (the BF16 copy of the
+//                     off-diagonal part of A, the A operand) and delta (BF16, the B operand) are loaded by
+//                     TMA into a 128-byte-swizzled shared-memory ring, one thread issues
+//                     tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M = 128, N = r, K = 16) into a tensor-
+//                     memory accumulator, and four epilogue warps read it back with tcgen05.ld and apply
+//                     the update, the FP64 candidate X + delta and the convergence reduction.
+// mrhs_dense_kernel   the FP64 pass over A for all r columns on CUDA cores (shared-memory tiles, FP64
+//                     FMA): either the residual R = B - A X (mixed path) or a plain FP64 Jacobi sweep
+//                     X^(k) = D^-1 (B - (A - D) X^(k-1)) (FP64 path), Section 2.
+//
+// Vectors of r columns are stored column by column with a padded leading dimension ld: v[c*ld + i].
+#include <cuda.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "device_util.cuh"
+#include "mrhs.cuh"
+
+namespace jac {
+namespace {
+
+constexpr int kMTile = 128;                 // rows per tile (tcgen05 M)
+constexpr int kKBlock = 64;                 // BF16 elements per 128-byte swizzled row
+constexpr int kMStages = 6;
+constexpr int kSweepThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kATileBytes = kMTile * kKBlock * 2;  // 16 KB
+
+__device__ __forceinline__ uint32_t cvta_smem(const void* p) { return smem_addr(p); }
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading-dimension byte offset >> 4 (bits 16-29, unused for swizzled
+// K-major, 1), stride-dimension byte offset >> 4 (bits 32-45: 1024 B between 8-row groups), the fixed
+// 0b001 at bits 46-48, base offset 0 (1024-byte aligned tiles), swizzle mode 2 (128 B) at bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16 (bits
+// 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t mma_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          cvta_smem(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(cvta_smem(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cvta_smem(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on `bar` once every tcgen05.mma issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cvta_smem(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct SweepSmem {
+  uint64_t full[kMStages];
+  uint64_t empty[kMStages];
+  uint64_t accum;
+  uint32_t tmem;
+  volatile int abort;
+};
+
+template <int R>
+__global__ void __launch_bounds__(kSweepThreads, 1)
+    mrhs_sweep_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      MrhsSweepParams p) {
+  constexpr int kBTileBytes = R * kKBlock * 2;
+  constexpr int kStageBytes = kATileBytes + kBTileBytes;
+  constexpr uint32_t kTmemCols = R < 32 ? 32 : R;
+  extern __shared__ __align__(1024) unsigned char msmem[];
+  __shared__ SweepSmem S;
+  unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(msmem) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kMTile;
+  const int kb_count = static_cast<int>((p.n + kKBlock - 1) / kKBlock);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kMStages; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
+    }
+    mbar_init(&S.accum, 1);
+    S.abort = 0;
+    mbar_init_fence();
+  }
+  if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < kb_count; ++kb) {
+        const int s = kb % kMStages;
+        const uint32_t par = ((kb / kMStages) & 1) ^ 1;
+        if (S.abort || !mbar_wait(&S.empty[s], par)) {
+          S.abort = 1;
+          atomicCAS(p.status, 0, kStatusTimeout);
+          break;
+        }
+        unsigned char* a = ring + s * kStageBytes;
+        mbar_arrive_expect_tx(&S.full[s], kStageBytes);
+        tma_load_2d(a, &tmA, kb * kKBlock, static_cast<int>(m0), &S.full[s]);
+        tma_load_2d(a + kATileBytes, &tmB, kb * kKBlock, 0, &S.full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = mma_idesc(kMTile, R);
+      for (int kb = 0; kb < kb_count; ++kb) {
+        const int s = kb % kMStages;
+        if (S.abort || !mbar_wait(&S.full[s], (kb / kMStages) & 1)) {
+          S.abort = 1;
+          atomicCAS(p.status, 0, kStatusTimeout);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a = cvta_smem(ring + s * kStageBytes);
+        const uint32_t b = a + kATileBytes;
+#pragma unroll
+        for (int k = 0; k < kKBlock / 16; ++k)  // K = 16 BF16 = 32 bytes per instruction
+          mma_bf16(tmem, sw128_desc(a + 32 * k), sw128_desc(b + 32 * k), idesc, (kb | k) != 0);
+        mma_commit(&S.empty[s]);  // the stage is free once these MMAs have read it
+      }
+      mma_commit(&S.accum);  // the accumulator is complete once every MMA has finished
+    }
+  } else {
+    // epilogue warps 2..5: warp w reads TMEM lanes 32*(w % 4) .. +31 (one output row per thread)
+    const int q = warp & 3;
+    const int64_t i = m0 + 32 * q + lane;
+    bool ok = mbar_wait(&S.accum, 0) && !S.abort;
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;  // tcgen05.ld below is warp-collective
+    tc_fence_after();
+    unsigned long long mchg = 0, mmag = 0;
+    if (ok) {
+      const float f = i < p.n ? p.rowfac[i] : 0.0f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < R; c0 += 32) {
+        float acc[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c0), acc);
+        if (i < p.n) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (c0 + j >= R) break;
+            const int64_t o = static_cast<int64_t>(c0 + j) * p.ld + i;
+            const float v = fmaf(-f, acc[j], p.c1[o]);
+            const float old = p.dc[o];
+            p.dn[o] = v;
+            p.dnh[o] = __float2bfloat16_rn(v);
+            p.xalt[o] = p.xc[o] + static_cast<double>(v);
+            const unsigned long long a1 = abs_bits(v - old), a2 = abs_bits(v);
+            mchg = a1 > mchg ? a1 : mchg;
+            mmag = a2 > mmag ? a2 : mmag;
+          }
+        }
+      }
+    } else {
+      atomicCAS(p.status, 0, kStatusTimeout);
+    }
+    mchg = warp_max_u64(mchg);
+    mmag = warp_max_u64(mmag);
+    if (lane == 0) {
+      if (mchg) atomicMax(p.stats + 0, mchg);
+      if (mmag) atomicMax(p.stats + 1, mmag);
+    }
+  }
+  // every MMA has been waited for (accum barrier) or none is in flight (abort); free TMEM
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------- FP64 dense pass, all r columns
+constexpr int kDM = 64;   // rows per tile
+constexpr int kDN = 64;   // columns (right-hand sides) per tile
+constexpr int kDK = 32;   // K step
+constexpr int kDThreads = 256;
+
+// mode 0: residual R = B - A X; writes C1 = R / a_ii (FP32), delta^(1) = C1 (FP32 + BF16), and the
+//         per-column max |R|.
+// mode 1: FP64 Jacobi sweep X^(k) = (B - A X + a_ii x_i) / a_ii; writes X^(k) and the max |change|.
+__global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p) {
+  __shared__ double As[kDK][kDM + 1];
+  __shared__ double Xs[kDK][kDN + 1];
+  const int tid = threadIdx.x;
+  const int tr = tid / 16, tc = tid % 16;  // 16 x 16 threads, each 4 rows x 4 columns
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kDM;
+  const int c0 = blockIdx.y * kDN;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int64_t k0 = 0; k0 < p.n; k0 += kDK) {
+    // A tile: kDM rows x kDK columns (row-major A), stored transposed As[k][m]
+    for (int e = tid; e < kDM * kDK; e += kDThreads) {
+      const int m = e / kDK, k = e % kDK;
+      const int64_t gi = m0 + m, gk = k0 + k;
+      As[k][m] = (gi < p.n && gk < p.n) ? __ldg(p.A + gi * p.lda + gk) : 0.0;
+    }
+    // X tile: kDK rows x kDN columns from the column-major X (x[c*ld + k])
+    for (int e = tid; e < kDK * kDN; e += kDThreads) {
+      const int c = e / kDK, k = e % kDK;
+      const int64_t gk = k0 + k;
+      Xs[k][c] = (gk < p.n && c0 + c < p.r) ? p.x[static_cast<int64_t>(c0 + c) * p.ld + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kDK; ++k) {
+      double a[4], x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[k][tr + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = Xs[k][tc + 16 * u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], x[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  unsigned long long mloc[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = m0 + tr + 16 * u;
+    if (i >= p.n) continue;
+    const double di = p.d[i], ri = p.rinv[i];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = c0 + tc + 16 * v;
+      if (c >= p.r) continue;
+      const int64_t o = static_cast<int64_t>(c) * p.ld + i;
+      const double b = p.b[o];
+      if (p.mode == 0) {
+        const double r = b - acc[u][v];
+        const float cc = static_cast<float>(r * ri);
+        p.c1[o] = cc;
+        p.d1[o] = cc;
+        p.d1h[o] = __float2bfloat16_rn(cc);
+        const unsigned long long bits = abs_bits(r);
+        mloc[v] = bits > mloc[v] ? bits : mloc[v];
+      } else {
+        const double xo = p.x[o];
+        const double s = fma(-di, xo, acc[u][v]);
+        const double xi = (b - s) * ri;
+        p.xn[o] = xi;
+        const unsigned long long bits = abs_bits(xi - xo);
+        mloc[v] = bits > mloc[v] ? bits : mloc[v];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int c = c0 + tc + 16 * v;
+    if (c < p.r && mloc[v]) atomicMax(p.colmax + c, mloc[v]);
+  }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(ptr);
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map: `rows` rows of `cols` valid elements, row pitch `ld` elements; box = 64 columns
+// (128 bytes, one swizzle row) x box_rows rows, 128-byte swizzle, zero fill outside the tensor.
+bool make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t ld, int box_rows) {
+  EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kKBlock), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int R>
+cudaError_t launch_sweep_r(const CUtensorMap& ta, const CUtensorMap& tb, const MrhsSweepParams& p, cudaStream_t s) {
+  constexpr int smem = kMStages * (kATileBytes + R * kKBlock * 2) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(mrhs_sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = static_cast<unsigned>((p.n + kMTile - 1) / kMTile);
+  mrhs_sweep_kernel<R><<<grid, kSweepThreads, smem, s>>>(ta, tb, p);
+  return cudaGetLastError();
+}
+
+__global__ void mrhs_init_kernel(int64_t n, int64_t r, int64_t ld, const double* __restrict__ b,
+                                 const double* __restrict__ rinv, float* c1, float* d1, __nv_bfloat16* d1h,
+                                 unsigned long long* colmax) {
+  const int64_t total = n * r;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t c = e / n, i = e % n;
+    const int64_t o = c * ld + i;
+    const double v = b[o];
+    const float cc = static_cast<float>(v * rinv[i]);
+    c1[o] = cc;
+    d1[o] = cc;
+    d1h[o] = __float2bfloat16_rn(cc);
+    atomicMax(colmax + c, abs_bits(v));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_mrhs_init(int64_t n, int64_t r, int64_t ld, const double* b, const double* rinv, float* c1,
+                             float* d1, __nv_bfloat16* d1h, unsigned long long* colmax, cudaStream_t s) {
+  int64_t blocks = (n * r + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  mrhs_init_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(n, r, ld, b, rinv, c1, d1, d1h, colmax);
+  return cudaGetLastError();
+}
+
+bool mrhs_supported_r(int64_t r) { return r == 16 || r == 32 || r == 64 || r == 128; }
+
+cudaError_t launch_mrhs_sweep(const void* Nlow, const void* dh, const MrhsSweepParams& p, cudaStream_t s) {
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, Nlow, p.n, p.n, p.ld, kMTile)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, dh, p.n, p.r, p.ld, static_cast<int>(p.r))) return cudaErrorInvalidValue;
+  switch (p.r) {
+    case 16: return launch_sweep_r<16>(ta, tb, p, s);
+    case 32: return launch_sweep_r<32>(ta, tb, p, s);
+    case 64: return launch_sweep_r<64>(ta, tb, p, s);
+    case 128: return launch_sweep_r<128>(ta, tb, p, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mrhs_dense(const MrhsDenseParams& p, cudaStream_t s) {
+  const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM), static_cast<unsigned>((p.r + kDN - 1) / kDN));
+  mrhs_dense_kernel<<<grid, kDThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace jac

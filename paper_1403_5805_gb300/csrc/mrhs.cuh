@@ -1,0 +1,52 @@
+// Multi-right-hand-side kernels (mrhs.cu): the tcgen05 BF16 sweep and the FP64 dense pass.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace jac {
+
+// One inner sweep for r right-hand sides (vectors stored v[c*ld + i]).
+struct MrhsSweepParams {
+  int64_t n, r, ld;
+  const float* rowfac;      // n: 1 / a_ii (FP32)
+  const float* c1;          // inner right-hand side D^-1 R
+  const float* dc;          // previous inner iterate (FP32)
+  float* dn;                // new inner iterate (FP32)
+  __nv_bfloat16* dnh;       // its BF16 copy: the B operand of the next sweep
+  const double* xc;         // current FP64 iterate
+  double* xalt;             // xc + dn
+  unsigned long long* stats;  // [0] max |dn - dc|, [1] max |dn| (IEEE bits, order-free max)
+  int* status;              // set to a timeout code if a bounded wait expires
+};
+
+// FP64 pass over A for all r columns.  mode 0: residual R = B - A X -> c1 = R / a_ii, d1 = c1 (FP32 and
+// BF16), colmax[c] = max_i |R_ic|.  mode 1: Jacobi sweep xn = (B - A x + a_ii x) / a_ii, colmax[c] =
+// max_i |xn - x|.
+struct MrhsDenseParams {
+  int64_t n, r, ld, lda;
+  int mode;
+  const double* A;
+  const double* b;
+  const double* x;
+  const double* d;
+  const double* rinv;
+  float* c1;
+  float* d1;
+  __nv_bfloat16* d1h;
+  double* xn;
+  unsigned long long* colmax;
+};
+
+bool mrhs_supported_r(int64_t r);
+// Encodes the TMA maps of the BF16 matrix (n x n, row pitch ld) and of the BF16 iterate block (r x n,
+// row pitch ld) and launches one sweep.
+cudaError_t launch_mrhs_sweep(const void* Nlow, const void* dh, const MrhsSweepParams& p, cudaStream_t s);
+cudaError_t launch_mrhs_dense(const MrhsDenseParams& p, cudaStream_t s);
+// Residual of the zero start vector (R = B): c1 = B / a_ii, d1 = c1 (FP32, BF16), colmax = max |B|.
+cudaError_t launch_mrhs_init(int64_t n, int64_t r, int64_t ld, const double* b, const double* rinv, float* c1,
+                             float* d1, __nv_bfloat16* d1h, unsigned long long* colmax, cudaStream_t s);
+
+}  // namespace jac

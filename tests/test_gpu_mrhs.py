@@ -1,0 +1,110 @@
+"""Many right-hand sides: the FP64 path (dense FP64 passes) and BF16 inner sweeps on tcgen05.
+
+* FP64, r columns: every iterate within 1e-12 of the oracle's (which runs all columns together, max-norm
+  over every entry), equal sweep count.
+* The tcgen05 product itself: with one outer step and one inner sweep, X = c1 - f * (Q . bf16(c1)), where
+  Q holds the oracle's BF16 codes of the off-diagonal part of A and f = fp32(1 / a_ii); the kernel
+  accumulates in FP32, so the tolerance is FP32 rounding over n terms.
+* BF16 refinement: ||B - A X||_inf / ||B||_inf <= 1e-10 for every column (oracle, FP64), and the error
+  against the planted solution within the residual bound.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def jac():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_5805_gb300 as jac
+    return jac
+
+
+def dev(A, B):
+    import torch
+    return torch.from_numpy(A).cuda(), torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+
+
+def bf16_values(codes):
+    return (codes.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("n,r", [(100, 3), (300, 16), (517, 64)])
+def test_fp64_many_rhs_matches_oracle(jac, n, r):
+    A, B, _ = synth.dominant_system(n, 1.2, seed=600 + n, nrhs=r)
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="fp64")
+    for k in (1, 4):
+        X, st = s.solve(max_iter=k, tol=1e-300)
+        ref = oracle.jacobi(A, B, max_iter=k, tol=1e-300)
+        assert st.sweeps == k
+        err = np.max(np.abs(X.cpu().numpy().T - ref.X)) / np.max(np.abs(ref.X))
+        assert err <= 1e-12, (k, err)
+    X, st = s.solve(max_iter=1000, tol=1e-12)
+    ref = oracle.jacobi(A, B, max_iter=1000, tol=1e-12)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters)
+    assert np.max(np.abs(X.cpu().numpy().T - ref.X)) <= 1e-12 * np.max(np.abs(ref.X))
+
+
+@pytest.mark.parametrize("n,r", [(256, 16), (300, 64), (1000, 32), (1536, 128)])
+def test_tcgen05_sweep_product(jac, n, r):
+    A, B, _ = synth.dominant_system(n, 1.1, seed=700 + n, nrhs=r)
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", max_outer=2, max_inner=1)
+    X, st = s.solve(max_iter=10, tol=1e-300)
+    assert st.outer_steps == 2 and st.sweeps == 1
+    got = X.cpu().numpy().T  # (n, r)
+    d = np.diag(A)
+    rinv = 1.0 / d
+    c1 = (B * rinv[:, None]).astype(np.float32).astype(np.float64)
+    c1h = bf16_values(np.array([[oracle.bf16_from_f32(v) for v in col] for col in c1.T.astype(np.float32)],
+                               dtype=np.uint16)).T
+    Q = bf16_values(oracle.offdiag_bf16(A))
+    f = rinv.astype(np.float32).astype(np.float64)
+    prod = Q @ c1h
+    want = c1 - f[:, None] * prod
+    scale = np.abs(f)[:, None] * (np.abs(Q) @ np.abs(c1h))  # size of the FP32-accumulated sum
+    assert np.all(np.abs(got - want) <= 2e-6 * scale + 1e-12), np.max(np.abs(got - want) / (scale + 1e-300))
+
+
+@pytest.mark.parametrize("n,r,gen", [(300, 16, "dom"), (777, 64, "dom"), (1024, 64, "hard"), (2000, 32, "dom")])
+def test_bf16_refinement_many_rhs(jac, n, r, gen):
+    make = synth.dominant_system if gen == "dom" else synth.hard_system
+    A, B, Xs = make(n, 1.1, seed=800 + n, nrhs=r)
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir")
+    X, st = s.solve(max_iter=5000, tol=1e-10)
+    Xh = X.cpu().numpy().T
+    _, rel = oracle.residual(A, B, Xh)
+    assert st.status == 0 and rel <= 1e-10, (st.as_dict(), rel)
+    q = 1 / 1.1
+    err = np.max(np.abs(Xh - Xs), axis=0)
+    assert np.all(err <= 2e-10 * (1 + q) / (1 - q) * np.max(np.abs(Xs))), err.max()
+
+
+def test_full_size_many_rhs_sampled(jac):
+    """n = 32768, 64 right-hand sides, f = 1.1: BF16 tcgen05 sweeps with FP64 refinement; the residual
+    of 64 sampled rows (all columns) is recomputed on the host in FP64."""
+    import torch
+    n, r = 32768, 64
+    A, B, Xs = synth.dominant_system(n, 1.1, seed=synth.BASE_SEED + 3, nrhs=r)
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir")
+    X, st = s.solve(max_iter=5000, tol=1e-10)
+    assert st.status == 0 and st.rel_residual <= 1e-10
+    Xh = X.cpu().numpy().T
+    rows = np.random.default_rng(1).choice(n, size=64, replace=False)
+    R = B[rows] - A[rows] @ Xh
+    rel = np.max(np.abs(R), axis=0) / np.max(np.abs(B), axis=0)
+    assert np.all(rel <= 1e-10), rel.max()
+    assert np.max(np.abs(Xh - Xs)) <= 1e-8
