@@ -120,6 +120,10 @@ def run_ours(args, world, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.only == "mrhs":
+        return {"section": "many_rhs", **run_many_rhs(args, jac, torch, dev)}
+    if args.only == "batch":
+        return {"section": "batched", **run_batch(args, jac, torch, dev)}
     n, f = args.n, args.f
     A, B, Xs = synth.dominant_system(n, f, seed=synth.BASE_SEED + 1)
     At = torch.from_numpy(A).to(dev)
@@ -200,7 +204,10 @@ def run_ours(args, world, rank, local):
         fp64_ratio = round(paths[args.precision]["solves_per_s"] / paths["fp64"]["solves_per_s"], 3)
 
     e2e = None if args.no_e2e else run_e2e(args, jac, torch, dev, A, B, ws)
+    cpu = cpu_baseline(A, B, n) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     batched = None if (args.quick or args.no_batch) else run_batch(args, jac, torch, dev)
+    del At, Bt, A, B  # free the single-system inputs before the large many-right-hand-side workload
+    many_rhs = None if (args.quick or args.no_mrhs) else run_many_rhs(args, jac, torch, dev)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
@@ -213,10 +220,10 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs (2.15 GB A) larger than the 129 MB L2; no flush"},
         "gpu_launches": (4 if args.precision != "fp64" else 3) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
-        "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched,
+        "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(A, B, n)
+    if cpu is not None:
+        result["cpu_baseline"] = cpu
     return result
 
 
@@ -319,6 +326,47 @@ def run_batch(args, jac, torch, dev):
             out[prec]["mean_outer_steps"] = round(float(np.mean([x.outer_steps for x in st])), 3)
         bs.close()
     out["mixed_vs_fp64_solves_ratio"] = round(out["fp32_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
+    return out
+
+
+def run_many_rhs(args, jac, torch, dev):
+    """n = 32768 with 64 right-hand sides, f = 1.1: BF16 sweeps on tcgen05 tensor cores with FP64
+    refinement against the plain FP64 path (each sweep a dense FP64 pass), both to 1e-10."""
+    import synth
+    n, r = args.mrhs_n, 64
+    A, B, Xs = synth.dominant_system(n, 1.1, seed=synth.BASE_SEED + 3, nrhs=r)
+    At = torch.from_numpy(A).to(dev)
+    del A
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(dev)
+    Xst = torch.from_numpy(np.ascontiguousarray(Xs.T)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"n": n, "nrhs": r, "dominance": 1.1}
+    for prec, steps in (("bf16_ir", args.mrhs_steps), ("fp64", 1)):
+        solver = jac.MultiSolver(At, Bt, precision=prec)
+        X, st = solver.solve(max_iter=5000, tol=TARGET if prec != "fp64" else args.fp64_tol)  # warm-up
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            X, st = solver.solve(max_iter=5000, tol=TARGET if prec != "fp64" else args.fp64_tol, out=X)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        err = (X - Xst).abs().amax(dim=1)
+        phases = {}
+        for kind, name, es, flop in ((3, "inner_tcgen05_bf16", 2, True), (1, "resid64_fp64", 8, True),
+                                     (0, "sweep64_fp64", 8, True)):
+            d = [(e - b) for k, b, e in solver.trace() if k == kind]
+            if d:
+                mean = sum(d) / len(d)
+                phases[name] = {"count": len(d), "mean_us": round(mean / 1e3, 1),
+                                "matrix_gbs": round(es * float(n) * n / mean, 1),
+                                "tflops": round(2.0 * n * n * r / mean / 1e3, 2)}
+        out[prec] = {"solves_per_s": round(1e3 / ms, 3), "ms_per_solve": round(ms, 2), "status": st.status,
+                     "sweeps": st.sweeps, "outer_steps": st.outer_steps, "rel_residual": st.rel_residual,
+                     "max_err_vs_xstar_per_rhs": float(err.max().item()), "phases": phases}
+        solver.close()
+    out["mixed_vs_fp64_solves_ratio"] = round(out["bf16_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     return out
 
 
@@ -432,6 +480,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", dest="no_cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", dest="no_e2e")
     ap.add_argument("--no-batch", action="store_true", dest="no_batch")
+    ap.add_argument("--no-mrhs", action="store_true", dest="no_mrhs")
+    ap.add_argument("--only", choices=["batch", "mrhs"], default=None,
+                    help="run one secondary workload alone (profiling)")
+    ap.add_argument("--mrhs-n", type=int, default=32768, dest="mrhs_n")
+    ap.add_argument("--mrhs-steps", type=int, default=3, dest="mrhs_steps")
     ap.add_argument("--batch-count", type=int, default=4096, dest="batch_count")
     ap.add_argument("--batch-steps", type=int, default=10, dest="batch_steps")
     args = ap.parse_args()

@@ -180,10 +180,11 @@ JACOBI_API int jacobi_residual(jacobi_handle* h, const double* X, double* rel_ou
  * Waits for the stream. */
 JACOBI_API int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* scale_host);
 
-/* Device-side trace of the last solve: the persistent kernel records, for each phase (one sweep or one
- * residual evaluation, ended by a grid-wide barrier), the %globaltimer nanoseconds since the kernel
- * started and the phase kind (JACOBI_PHASE_*).  Writes min(cap, phases) entries, the phase count to
- * *count (phases beyond the first 512 are not recorded).  Waits for the stream. */
+/* Trace of the last solve: for each phase (one sweep or one residual evaluation) its end time in
+ * nanoseconds since the solve started and its kind (JACOBI_PHASE_*).  Single right-hand side: recorded
+ * by the persistent kernel from %globaltimer at each grid-wide barrier (the first 512 phases).  Many
+ * right-hand sides: CUDA events around each phase's kernel.  Writes min(cap, phases) entries and the
+ * phase count to *count.  Waits for the stream. */
 #define JACOBI_PHASE_SWEEP64 0  /* FP64 Jacobi sweep over A */
 #define JACOBI_PHASE_RESID64 1  /* FP64 residual r = B - A X over A */
 #define JACOBI_PHASE_RESID0 2   /* residual of a zero start vector (r = B, no matrix pass) */

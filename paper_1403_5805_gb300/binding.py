@@ -384,6 +384,10 @@ class MultiSolver:
         with torch.cuda.device(A.device):
             _check(lib.jacobi_setup_ex(ctypes.byref(d), ctypes.byref(self._h)), "jacobi_setup_ex", False)
 
+    def trace(self):
+        """Per-phase CUDA-event timeline of the last solve: list of (kind, start_ns, end_ns)."""
+        return DeviceSolver.trace(self)
+
     def solve(self, X0=None, max_iter: int = 5000, tol: float = 1e-10, out=None):
         """Returns ``(X, stats)`` with X an (r, n) tensor; raises on error statuses (< 0)."""
         import torch

@@ -159,7 +159,9 @@ struct jacobi_handle {
   int64_t n = 0;
   int64_t nrhs = 1;
   MrhsLayout M{};
-  double last_colres_max = 0.0;
+  // host-driven paths: per-phase trace from CUDA events (kind, end time since the solve started)
+  std::vector<int32_t> htrace_kind;
+  std::vector<int64_t> htrace_end;
   int precision = JACOBI_FP64;
   int norm = JACOBI_NORM_INF;
   cudaStream_t stream = nullptr;
@@ -300,8 +302,38 @@ int mrhs_prepare(jacobi_handle* h, const double* B, int64_t ldb) {
 
 // Host-driven loop for many right-hand sides (each FP64 pass over A is a full matrix-matrix product,
 // milliseconds to a hundred milliseconds, so one small device-to-host read per phase costs nothing).
+// CUDA-event timeline of a host-driven solve: one event after every phase.
+struct PhaseClock {
+  cudaStream_t s;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int32_t> kind;
+  explicit PhaseClock(cudaStream_t st) : s(st) { mark(-1); }
+  void mark(int32_t k) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    kind.push_back(k);
+  }
+  // after a stream synchronisation: fill the handle's trace
+  void flush(jacobi_handle* h) {
+    h->htrace_kind.clear();
+    h->htrace_end.clear();
+    for (size_t i = 1; i < ev.size(); ++i) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, ev[0], ev[i]);
+      h->htrace_kind.push_back(kind[i]);
+      h->htrace_end.push_back(static_cast<int64_t>(static_cast<double>(ms) * 1e6));
+    }
+  }
+  ~PhaseClock() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
 int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out, jacobi_stats* st) {
   cudaStream_t s = h->stream;
+  PhaseClock clk(s);
   const int64_t n = h->n, r = h->nrhs, ld = h->L.ld;
   double* xa = h->at<double>(h->M.xa);
   double* xb = h->at<double>(h->M.xb);
@@ -328,6 +360,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
       MrhsDenseParams p{n, r, ld, h->lda64, 1, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
                         h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax};
       CK(launch_mrhs_dense(p, s));
+      clk.mark(JACOBI_PHASE_SWEEP64);
       CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       double delta = 0.0;
@@ -360,10 +393,12 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
       CK(cudaMemsetAsync(colmax, 0, static_cast<size_t>(r) * 8, s));
       if (first) {
         CK(launch_mrhs_init(n, r, ld, h->at<double>(h->M.b), h->at<double>(h->L.rinv), c1, dA, hA, colmax, s));
+        clk.mark(JACOBI_PHASE_RESID0);
       } else {
         MrhsDenseParams p{n, r, ld, h->lda64, 0, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
                           h->at<double>(h->L.rinv), c1, dA, hA, nullptr, colmax};
         CK(launch_mrhs_dense(p, s));
+        clk.mark(JACOBI_PHASE_RESID64);
       }
       first = false;
       ++outer;
@@ -392,6 +427,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
         CK(cudaMemsetAsync(sst, 0, 16, s));
         MrhsSweepParams q{n, r, ld, h->at<float>(h->L.rowfac), c1, dcur, dnew, hnew, xc, xo, sst, status};
         CK(launch_mrhs_sweep(h->at<void>(h->L.Nlow), hcur, q, s));
+        clk.mark(JACOBI_PHASE_INNER);
         unsigned long long hs[2];
         int hst = 0;
         CK(cudaMemcpyAsync(hs, sst, 16, cudaMemcpyDeviceToHost, s));
@@ -420,6 +456,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
   }
   CK(cudaMemcpy2DAsync(X_out, n * 8, xc, ld * 8, n * 8, r, cudaMemcpyDefault, s));
   CK(cudaStreamSynchronize(s));
+  clk.flush(h);
   out.converged = out.status == JACOBI_OK;
   if (st) *st = out;
   // keep the record where jacobi_last_stats finds it
@@ -619,6 +656,15 @@ int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* s
 
 int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap, int32_t* count) {
   if (!h || !count || cap < 0 || (cap > 0 && (!t_end_ns || !kinds))) return JACOBI_ERR_INVALID_ARG;
+  if (h->nrhs > 1) {  // host-driven path: CUDA-event timeline
+    const int32_t m = static_cast<int32_t>(h->htrace_kind.size());
+    *count = m;
+    for (int32_t i = 0; i < m && i < cap; ++i) {
+      t_end_ns[i] = h->htrace_end[static_cast<size_t>(i)];
+      kinds[i] = h->htrace_kind[static_cast<size_t>(i)];
+    }
+    return JACOBI_OK;
+  }
   Ctl* ctl = h->at<Ctl>(h->L.ctl);
   Ctl* host = static_cast<Ctl*>(std::malloc(sizeof(Ctl)));
   if (!host) return JACOBI_ERR_OUT_OF_MEMORY;
