@@ -254,6 +254,71 @@ JACOBI_API int jacobi_batch_grid(jacobi_batch* b);
 JACOBI_API void jacobi_batch_destroy(jacobi_batch* b);
 
 /* ------------------------------------------------------------------------------------------------
+ * Serving: continuous batching of independent solve requests.
+ *
+ * Each request is a system A X = B (n <= JACOBI_SERVE_MAX_N, 1 <= r <= JACOBI_SERVE_MAX_RHS right-hand
+ * sides) solved by Section 2's Jacobi iteration as FP32 inner sweeps inside an FP64 refinement, to
+ * ||B - A X||_inf / ||B||_inf <= tol per column.  Admitted requests keep all their state on the device
+ * inside an arena of budget_bytes.  jacobi_server_step runs one round: admit waiting requests in arrival
+ * order while the arena has room, advance every active request by one phase in one kernel launch, retire
+ * the finished ones (their X is copied to the caller's X_out and their memory freed).  A request's
+ * arithmetic does not depend on the other requests in the round.
+ * ------------------------------------------------------------------------------------------------ */
+
+#define JACOBI_SERVE_MAX_N 8192
+#define JACOBI_SERVE_MAX_RHS 16
+
+typedef struct jacobi_server jacobi_server;
+
+typedef struct jacobi_server_desc {
+  size_t budget_bytes;  /* device arena for admitted requests (allocated once at create) */
+  double tol;           /* relative-residual target (0: 1e-10) */
+  int64_t max_iter;     /* cap on inner sweeps per request (0: 5000) */
+  int32_t max_inner;    /* cap on inner sweeps per refinement step (0: 64) */
+  int32_t max_outer;    /* cap on residual evaluations per request (0: 30) */
+  double inner_rtol;    /* inner stop: max|change| <= inner_rtol * max|delta| (0: 2^-10) */
+  int32_t max_active;   /* cap on concurrently active requests (0: only the budget limits) */
+  int32_t reserved;
+  void* stream;         /* cudaStream_t of every round (NULL: legacy default stream) */
+} jacobi_server_desc;
+
+JACOBI_API int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out);
+
+/* Queue a request whose A (n x n row-major, stride n) and B (n x r column-major, stride n) are in device
+ * or host memory; they are copied into the arena when the request is admitted, so they must stay valid
+ * until then.  X_out (n x r column-major, device or pinned host) receives the solution when the request
+ * finishes.  *id_out identifies the request in jacobi_server_poll.  JACOBI_ERR_OUT_OF_MEMORY if the
+ * request could never fit the budget. */
+JACOBI_API int jacobi_server_submit(jacobi_server* s, int64_t n, int64_t r, const double* A, const double* B,
+                                    double* X_out, int64_t* id_out);
+
+/* Queue a request generated on the device at admission from (seed, f): the generator of
+ * jacobi_generate_request. */
+JACOBI_API int jacobi_server_submit_generated(jacobi_server* s, int64_t n, int64_t r, double f, uint64_t seed,
+                                              double* X_out, int64_t* id_out);
+
+/* One round (see above); waits for it.  *active_out / *pending_out: requests on the device / waiting. */
+JACOBI_API int jacobi_server_step(jacobi_server* s, int32_t* active_out, int32_t* pending_out);
+
+/* Requests finished since the last poll (up to cap): their ids and records (status, sweeps = inner
+ * sweeps, outer_steps = residual evaluations, rel_residual = final max over columns).  Their X_out is
+ * complete when this returns. */
+JACOBI_API int jacobi_server_poll(jacobi_server* s, int64_t* ids, jacobi_stats* stats, int32_t cap, int32_t* count);
+
+/* Rounds run so far. */
+JACOBI_API int jacobi_server_rounds(jacobi_server* s, int64_t* rounds);
+
+/* Release the server and every queued or active request (waits for the stream). */
+JACOBI_API void jacobi_server_destroy(jacobi_server* s);
+
+/* Write a seeded dominant system on the device: A (n x n, row stride n) with off-diagonals
+ * int32(w) * 2^-31 (w word i*n + j of Philox4x32-10 stream 0 under key `seed`), a_ii = f * sum_{j != i}
+ * |a_ij| * (-1 if bit 0 of word i of stream 1 is set), and B[c*ldb + i] = int32(w) * 2^-31 (word c*n + i
+ * of stream 5).  Asynchronous on `stream`. */
+JACOBI_API int jacobi_generate_request(int64_t n, int64_t r, double f, uint64_t seed, double* A, double* B,
+                                       int64_t ldb, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
  * Allocation-free FP64 solve.  The paper has no counterpart to this entry point: it exists for callers
  * that must not allocate device memory while they run, such as a plugin inside a host application that
  * owns the GPU's memory pool and forbids other allocations, or a latency-bound loop that cannot afford

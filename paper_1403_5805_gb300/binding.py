@@ -34,7 +34,9 @@ EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_stri
            "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual", "jacobi_get_narrow",
            "jacobi_last_trace", "jacobi_solve_fp64_noalloc", "jacobi_batch_workspace_size",
            "jacobi_batch_create", "jacobi_batch_solve_async", "jacobi_batch_stats", "jacobi_batch_grid",
-           "jacobi_batch_destroy")
+           "jacobi_batch_destroy", "jacobi_server_create", "jacobi_server_submit", "jacobi_server_submit_generated",
+           "jacobi_server_step", "jacobi_server_poll", "jacobi_server_rounds", "jacobi_server_destroy",
+           "jacobi_generate_request")
 
 
 class JacobiStats(ctypes.Structure):
@@ -51,6 +53,12 @@ class JacobiBatchDesc(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
+class JacobiServerDesc(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
+                ("max_inner", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
+                ("max_active", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class JacobiDesc(ctypes.Structure):
@@ -110,12 +118,23 @@ def load() -> ctypes.CDLL:
         lib.jacobi_batch_grid.argtypes = [H]
         lib.jacobi_batch_destroy.argtypes = [H]
         lib.jacobi_batch_destroy.restype = None
+        lib.jacobi_server_create.argtypes = [ctypes.POINTER(JacobiServerDesc), ctypes.POINTER(H)]
+        lib.jacobi_server_submit.argtypes = [H, i64, i64, vp, vp, vp, ctypes.POINTER(i64)]
+        lib.jacobi_server_submit_generated.argtypes = [H, i64, i64, dbl, ctypes.c_uint64, vp, ctypes.POINTER(i64)]
+        lib.jacobi_server_step.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_server_poll.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_server_rounds.argtypes = [H, ctypes.POINTER(i64)]
+        lib.jacobi_server_destroy.argtypes = [H]
+        lib.jacobi_server_destroy.restype = None
+        lib.jacobi_generate_request.argtypes = [i64, i64, dbl, ctypes.c_uint64, vp, vp, i64, vp]
         lib.jacobi_solve_fp64_noalloc.argtypes = [vp, i64, vp, i64, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats), vp]
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
                      "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
                      "jacobi_get_narrow", "jacobi_last_trace", "jacobi_solve_fp64_noalloc",
                      "jacobi_batch_workspace_size", "jacobi_batch_create", "jacobi_batch_solve_async",
-                     "jacobi_batch_stats", "jacobi_batch_grid"):
+                     "jacobi_batch_stats", "jacobi_batch_grid", "jacobi_server_create", "jacobi_server_submit",
+                     "jacobi_server_submit_generated", "jacobi_server_step", "jacobi_server_poll",
+                     "jacobi_server_rounds", "jacobi_generate_request"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -402,6 +421,85 @@ class MultiSolver:
     def close(self):
         if self._h:
             load().jacobi_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------ serving interface
+
+def generate_request(n: int, r: int, f: float, seed: int, device=None, stream=None):
+    """A (n, n) and B (r, n) float64 CUDA tensors of the seeded serving generator (bit-identical to
+    ``synth.serving_request``)."""
+    import torch
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    stream = stream if stream is not None else torch.cuda.current_stream(device)
+    A = torch.empty(n, n, dtype=torch.float64, device=device)
+    B = torch.zeros(r, n, dtype=torch.float64, device=device)
+    _check(load().jacobi_generate_request(n, r, f, seed, A.data_ptr(), B.data_ptr(), n, stream.cuda_stream),
+           "jacobi_generate_request")
+    return A, B
+
+
+class Server:
+    """``jacobi_server_*``: continuous batching of independent requests (see include/jacobi.h)."""
+
+    def __init__(self, budget_bytes: int, tol: float = 1e-10, max_active: int = 0, inner_rtol: float = 0.0,
+                 max_inner: int = 0, max_outer: int = 0, stream=None):
+        import torch
+        lib = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d = JacobiServerDesc()
+        d.budget_bytes, d.tol, d.max_active = budget_bytes, tol, max_active
+        d.inner_rtol, d.max_inner, d.max_outer = inner_rtol, max_inner, max_outer
+        d.stream = self.stream.cuda_stream
+        self._h = ctypes.c_void_p()
+        _check(lib.jacobi_server_create(ctypes.byref(d), ctypes.byref(self._h)), "jacobi_server_create", False)
+        self._keep = {}
+
+    def submit_generated(self, n: int, r: int, f: float, seed: int, out) -> int:
+        rid = ctypes.c_int64(0)
+        _check(load().jacobi_server_submit_generated(self._h, n, r, f, seed, out.data_ptr(), ctypes.byref(rid)),
+               "jacobi_server_submit_generated")
+        self._keep[rid.value] = out
+        return rid.value
+
+    def submit(self, A, B, out) -> int:
+        """A (n, n), B (r, n) float64 tensors (device or host); out (r, n) receives X."""
+        rid = ctypes.c_int64(0)
+        _check(load().jacobi_server_submit(self._h, A.shape[0], B.shape[0], A.data_ptr(), B.data_ptr(),
+                                           out.data_ptr(), ctypes.byref(rid)), "jacobi_server_submit")
+        self._keep[rid.value] = (A, B, out)
+        return rid.value
+
+    def step(self):
+        a, p = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().jacobi_server_step(self._h, ctypes.byref(a), ctypes.byref(p)), "jacobi_server_step")
+        return a.value, p.value
+
+    def poll(self, cap: int = 4096):
+        ids = np.zeros(cap, dtype=np.int64)
+        sts = (JacobiStats * cap)()
+        cnt = ctypes.c_int32(0)
+        _check(load().jacobi_server_poll(self._h, ids.ctypes.data, ctypes.addressof(sts), cap, ctypes.byref(cnt)),
+               "jacobi_server_poll")
+        out = [(int(ids[i]), sts[i]) for i in range(cnt.value)]
+        for rid, _ in out:
+            self._keep.pop(rid, None)
+        return out
+
+    def rounds(self) -> int:
+        r = ctypes.c_int64(0)
+        _check(load().jacobi_server_rounds(self._h, ctypes.byref(r)), "jacobi_server_rounds")
+        return r.value
+
+    def close(self):
+        if self._h:
+            load().jacobi_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

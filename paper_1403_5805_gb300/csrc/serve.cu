@@ -1,0 +1,716 @@
+// Serving: continuous batching of many independent solve requests (Section 2's Jacobi iteration with
+// FP64 refinement around FP32 inner sweeps), each request up to JACOBI_SERVE_MAX_N unknowns and
+// JACOBI_SERVE_MAX_RHS right-hand sides.
+//
+// The server keeps every admitted request's state on the device (A, its FP32 copy, X, the inner
+// iterates) inside one arena whose size is the memory budget.  Work proceeds in rounds: one launch of
+// serve_round_kernel advances EVERY active request by one phase (setup, FP64 residual, or one FP32 inner
+// sweep), its 16-row blocks spread over all SMs as independent work items.  Between rounds the host
+// reads each request's reductions, moves its state machine, retires finished requests (copying X out
+// and freeing their arena space) and admits waiting ones as memory frees up, so requests that arrive
+// while others run join the next round and overlap with them on the device.  A request's arithmetic
+// does not depend on what else is in the round, so its result is the same alone and in the mix.
+//
+// Requests can bring their own A and B (device or host memory) or be generated on the device from a
+// seed by serve_generate_kernel, a twin of the host generator in synth/ (Philox4x32-10, Salmon et al.
+// SC'11): A with off-diagonals int32(w) 2^-31 and a_ii = f * sum_{j != i} |a_ij| * (+-1), B uniform.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "device_util.cuh"
+#include "solver.cuh"
+
+namespace jac {
+namespace {
+
+constexpr int kSRows = 16;        // rows per work item
+constexpr int kSThreads = 256;    // 8 warps x 2 rows
+constexpr int kStatSlots = 64;    // per request per round: [0,16) |R| or change per column, [16,32) |B|,
+                                  // 32 inner change, 33 inner magnitude, 34 bad-diagonal key (~key)
+
+enum SrvPhase : int { kPhPrep = 0, kPhResid = 1, kPhInner = 2 };
+
+struct SrvReq {
+  int64_t n, r, ld;
+  const double* A;   // n x n row-major, row stride n
+  float* Nl;         // FP32 copy of the off-diagonal part, row stride ld
+  double* d;
+  double* rinv;
+  float* rowfac;
+  const double* B;   // [r][ld]
+  double* X[2];      // FP64 iterate buffers [r][ld]
+  float* C1;         // inner right-hand side [r][ld]
+  float* D[2];       // inner iterates [r][ld]
+  unsigned long long* st;  // kStatSlots reduction slots (zeroed every round)
+  int phase, xsel, dsel, rb;
+};
+
+// ------------------------------------------------------------------------ Philox4x32-10 (device)
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Word w of the sequence (seed, stream): lane w % 4 of the block with counter (w / 4, stream, 0).
+__device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint32_t stream, uint64_t w) {
+  const uint64_t q = w >> 2;
+  const uint4 o = philox(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32), stream, 0u),
+                         make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+  switch (w & 3) {
+    case 0: return o.x;
+    case 1: return o.y;
+    case 2: return o.z;
+    default: return o.w;
+  }
+}
+
+__device__ __forceinline__ double signed_unit(uint32_t w) { return static_cast<double>(static_cast<int32_t>(w)) * 0x1p-31; }
+
+// One CTA per row (grid-stride): A row i, its diagonal, and B (all columns, zero padding up to ld).
+__global__ void serve_generate_kernel(int64_t n, int64_t r, int64_t ld, double f, uint64_t seed, double* A,
+                                      double* B) {
+  __shared__ double part[kSThreads / 32];
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double a = (j == i) ? 0.0 : signed_unit(philox_word(seed, 0u, static_cast<uint64_t>(i * n + j)));
+      if (j != i) A[i * n + j] = a;
+      s += fabs(a);  // integers times 2^-31 below 2^13: exact in any order
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
+      const double sign = (philox_word(seed, 1u, static_cast<uint64_t>(i)) & 1u) ? -1.0 : 1.0;
+      A[i * n + i] = n > 1 ? f * t * sign : f * sign;
+    }
+    __syncthreads();
+    for (int64_t c = threadIdx.x; c < r; c += blockDim.x)
+      B[c * ld + i] = signed_unit(philox_word(seed, 5u, static_cast<uint64_t>(c * n + i)));
+  }
+}
+
+// ------------------------------------------------------------------------------- round kernel
+template <int R, int OFF, typename Acc>
+struct TRs {
+  static __device__ __forceinline__ Acc run(const Acc (&v)[R], int lane) {
+    constexpr int H = R / 2;
+    Acc w[H];
+    const bool hi = lane & OFF;
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      const Acc send = hi ? v[q] : v[q + H];
+      const Acc keep = hi ? v[q + H] : v[q];
+      w[q] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+    }
+    return TRs<H, OFF / 2, Acc>::run(w, lane);
+  }
+};
+template <int OFF, typename Acc>
+struct TRs<1, OFF, Acc> {
+  static __device__ __forceinline__ Acc run(const Acc (&v)[1], int) { return v[0]; }
+};
+// After TRs<V, 16>, lanes sharing bits [4 .. 5 - log2 V] hold value index (those bits); finish the sum
+// over the remaining low lane bits.
+template <int V, typename Acc>
+__device__ __forceinline__ Acc tr_finish(Acc w) {
+#pragma unroll
+  for (int o = 16 / V; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  return w;
+}
+template <int V>
+__device__ __forceinline__ int tr_index(int lane) {
+  int idx = 0, bit = 4;
+#pragma unroll
+  for (int k = V; k > 1; k >>= 1, --bit) idx = (idx << 1) | ((lane >> bit) & 1);
+  return idx;
+}
+
+__device__ __forceinline__ void umax_to(unsigned long long* p, unsigned long long v) {
+  if (v) atomicMax(p, v);
+}
+
+// Setup of rows [i0, i0 + 2) handled by one warp: diagonal and reciprocals, FP32 copy of the off-
+// diagonal row, the first inner right-hand side C1 = B / a_ii (the residual of X = 0) and D0 = C1.
+__device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
+  for (int rr = 0; rr < 2; ++rr) {
+    const int64_t i = i0 + rr;
+    if (i >= q.n) break;
+    const double* Ai = q.A + i * q.n;
+    for (int64_t j = lane; j < q.ld; j += 32)
+      q.Nl[i * q.ld + j] = (j < q.n && j != i) ? __double2float_rn(Ai[j]) : 0.0f;
+    const double a = Ai[i];
+    const double ri = (a != 0.0 && isfinite(a)) ? __drcp_rn(a) : 0.0;
+    if (lane == 0) {
+      q.d[i] = a;
+      q.rinv[i] = ri;
+      q.rowfac[i] = __double2float_rn(ri);
+      if (!isfinite(a) || a == 0.0)
+        atomicMax(q.st + 34, ~((static_cast<unsigned long long>(i) << 8) | (isfinite(a) ? 2ull : 3ull)));
+    }
+    for (int64_t c = lane; c < q.r; c += 32) {
+      const double b = q.B[c * q.ld + i];
+      const float cc = static_cast<float>(b * ri);
+      q.C1[c * q.ld + i] = cc;
+      q.D[0][c * q.ld + i] = cc;
+      umax_to(q.st + 16 + c, abs_bits(b));
+    }
+  }
+}
+
+// FP64 residual R = B - A X of rows [i0, i0 + 2) for RB >= r columns.
+template <int RB>
+__device__ void resid_rows(const SrvReq& q, int64_t i0, int lane) {
+  double acc[2 * RB];
+#pragma unroll
+  for (int v = 0; v < 2 * RB; ++v) acc[v] = 0.0;
+  const bool has1 = i0 + 1 < q.n;
+  const double* A0 = q.A + i0 * q.n;
+  const double* A1 = has1 ? A0 + q.n : A0;
+  const double* X = q.X[q.xsel];
+  for (int64_t j = lane; j < q.n; j += 32) {
+    const double a0 = __ldg(A0 + j), a1 = has1 ? __ldg(A1 + j) : 0.0;
+#pragma unroll
+    for (int c = 0; c < RB; ++c)
+      if (c < q.r) {
+        const double x = __ldg(X + c * q.ld + j);
+        acc[c] = fma(a0, x, acc[c]);
+        acc[RB + c] = fma(a1, x, acc[RB + c]);
+      }
+  }
+  const double tot = tr_finish<2 * RB>(TRs<2 * RB, 16, double>::run(acc, lane));
+  const int v = tr_index<2 * RB>(lane);
+  const int64_t i = i0 + v / RB;
+  const int c = v % RB;
+  if ((lane & (32 / (2 * RB) - 1)) == 0 && i < q.n && c < q.r) {
+    const int64_t o = c * q.ld + i;
+    const double R = q.B[o] - tot;
+    const float cc = static_cast<float>(R * q.rinv[i]);
+    q.C1[o] = cc;
+    q.D[0][o] = cc;
+    umax_to(q.st + c, abs_bits(R));
+  }
+}
+
+// FP32 inner sweep of rows [i0, i0 + 2): D_new = C1 - (1/a_ii) N D_cur, X_alt = X_cur + D_new.
+template <int RB>
+__device__ void inner_rows(const SrvReq& q, int64_t i0, int lane) {
+  float acc[2 * RB];
+#pragma unroll
+  for (int v = 0; v < 2 * RB; ++v) acc[v] = 0.0f;
+  const bool has1 = i0 + 1 < q.n;
+  const float* N0 = q.Nl + i0 * q.ld;
+  const float* N1 = has1 ? N0 + q.ld : N0;
+  const float* Dc = q.D[q.dsel];
+  for (int64_t j = 4 * lane; j < q.n; j += 128) {
+    const float4 m0 = __ldcg(reinterpret_cast<const float4*>(N0 + j));
+    const float4 m1 = has1 ? __ldcg(reinterpret_cast<const float4*>(N1 + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < RB; ++c)
+      if (c < q.r) {
+        const float4 x = __ldcg(reinterpret_cast<const float4*>(Dc + c * q.ld + j));
+        acc[c] = fmaf(m0.x, x.x, fmaf(m0.y, x.y, fmaf(m0.z, x.z, fmaf(m0.w, x.w, acc[c]))));
+        acc[RB + c] = fmaf(m1.x, x.x, fmaf(m1.y, x.y, fmaf(m1.z, x.z, fmaf(m1.w, x.w, acc[RB + c]))));
+      }
+  }
+  const float tot = tr_finish<2 * RB>(TRs<2 * RB, 16, float>::run(acc, lane));
+  const int v = tr_index<2 * RB>(lane);
+  const int64_t i = i0 + v / RB;
+  const int c = v % RB;
+  unsigned long long chg = 0, mag = 0;
+  if ((lane & (32 / (2 * RB) - 1)) == 0 && i < q.n && c < q.r) {
+    const int64_t o = c * q.ld + i;
+    const float val = fmaf(-q.rowfac[i], tot, q.C1[o]);
+    const float old = Dc[o];
+    q.D[q.dsel ^ 1][o] = val;
+    q.X[q.xsel ^ 1][o] = q.X[q.xsel][o] + static_cast<double>(val);
+    chg = abs_bits(val - old);
+    mag = abs_bits(val);
+  }
+  chg = warp_max_u64(chg);
+  mag = warp_max_u64(mag);
+  if (lane == 0) {
+    umax_to(q.st + 32, chg);
+    umax_to(q.st + 33, mag);
+  }
+}
+
+template <int RB>
+__device__ __forceinline__ void run_item(const SrvReq& q, int64_t i0, int lane) {
+  if (q.phase == kPhResid)
+    resid_rows<RB>(q, i0, lane);
+  else
+    inner_rows<RB>(q, i0, lane);
+}
+
+__global__ void __launch_bounds__(kSThreads) serve_round_kernel(const SrvReq* __restrict__ reqs, int nreq,
+                                                                const int64_t* __restrict__ first, int64_t items) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    int lo = 0, hi = nreq - 1;  // request owning this item: last k with first[k] <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (first[mid] <= it)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const SrvReq q = reqs[lo];
+    const int64_t i0 = (it - first[lo]) * kSRows + 2 * warp;
+    if (i0 >= q.n) continue;  // warp-uniform
+    if (q.phase == kPhPrep) {
+      prep_rows(q, i0, lane);
+      continue;
+    }
+    switch (q.rb) {
+      case 1: run_item<1>(q, i0, lane); break;
+      case 2: run_item<2>(q, i0, lane); break;
+      case 4: run_item<4>(q, i0, lane); break;
+      case 8: run_item<8>(q, i0, lane); break;
+      default: run_item<16>(q, i0, lane); break;
+    }
+  }
+}
+
+size_t a256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace jac
+
+using namespace jac;
+
+namespace {
+
+// First-fit allocator over the arena (host-side bookkeeping of device offsets).
+struct Arena {
+  size_t size = 0;
+  std::map<size_t, size_t> free;  // offset -> bytes
+  void reset(size_t bytes) {
+    size = bytes;
+    free.clear();
+    free[0] = bytes;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    for (auto it = free.begin(); it != free.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t at = it->first + bytes;
+        free.erase(it);
+        if (rest) free[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free.erase(nx);
+    }
+    if (it != free.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free.erase(it);
+      }
+    }
+  }
+};
+
+struct Request {
+  int64_t id = 0, n = 0, r = 0, ld = 0;
+  double f = 0.0;
+  uint64_t seed = 0;
+  bool generate = false;
+  const double* A_in = nullptr;
+  const double* B_in = nullptr;
+  double* X_out = nullptr;
+  size_t off = 0, bytes = 0;
+  SrvReq q{};
+  int64_t outer = 0, inner_total = 0, inner_step = 0;
+  std::vector<double> bnorm;  // ||b_c||_inf per column (from the setup round)
+  jacobi_stats st{};
+};
+
+size_t request_bytes(int64_t n, int64_t r, int64_t ld, bool own_A) {
+  size_t b = 0;
+  if (own_A) b += a256(static_cast<size_t>(n) * n * 8);
+  b += a256(static_cast<size_t>(n) * ld * 4);                // Nl
+  b += 2 * a256(static_cast<size_t>(ld) * 8) + a256(static_cast<size_t>(ld) * 4);  // d, rinv, rowfac
+  b += 3 * a256(static_cast<size_t>(r) * ld * 8);             // B, X0, X1
+  b += 3 * a256(static_cast<size_t>(r) * ld * 4);             // C1, D0, D1
+  return b;
+}
+
+}  // namespace
+
+struct jacobi_server {
+  cudaStream_t stream = nullptr;
+  char* arena_base = nullptr;
+  Arena arena;
+  double tol = 1e-10;
+  int64_t max_iter = 5000;
+  int max_inner = 64, max_outer = 30;
+  float inner_rtol = 1.0f / 1024;
+  int max_active = 0;
+  int64_t next_id = 1;
+  std::deque<Request*> pending;
+  std::vector<Request*> active;
+  std::vector<std::pair<int64_t, jacobi_stats>> done;
+  // per-round device / pinned buffers
+  SrvReq* d_reqs = nullptr;
+  int64_t* d_first = nullptr;
+  unsigned long long* d_stats = nullptr;
+  SrvReq* h_reqs = nullptr;
+  int64_t* h_first = nullptr;
+  unsigned long long* h_stats = nullptr;
+  int cap = 0;
+  int grid = 0;
+  int64_t rounds = 0;
+};
+
+namespace {
+
+int grow(jacobi_server* s, int need) {
+  if (need <= s->cap) return JACOBI_OK;
+  int cap = std::max(need, 2 * s->cap + 64);
+  cudaFree(s->d_reqs);
+  cudaFree(s->d_first);
+  cudaFree(s->d_stats);
+  cudaFreeHost(s->h_reqs);
+  cudaFreeHost(s->h_first);
+  cudaFreeHost(s->h_stats);
+  if (cudaMalloc(&s->d_reqs, sizeof(SrvReq) * cap) != cudaSuccess ||
+      cudaMalloc(&s->d_first, sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
+      cudaMalloc(&s->d_stats, sizeof(unsigned long long) * kStatSlots * cap) != cudaSuccess ||
+      cudaMallocHost(&s->h_reqs, sizeof(SrvReq) * cap) != cudaSuccess ||
+      cudaMallocHost(&s->h_first, sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
+      cudaMallocHost(&s->h_stats, sizeof(unsigned long long) * kStatSlots * cap) != cudaSuccess)
+    return JACOBI_ERR_OUT_OF_MEMORY;
+  s->cap = cap;
+  return JACOBI_OK;
+}
+
+double as_double(unsigned long long u) {
+  double v;
+  std::memcpy(&v, &u, 8);
+  return v;
+}
+
+int rbucket(int64_t r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 8 : 16; }
+
+// Admit one request: carve its arena block, lay out its buffers, fill A and B, set phase PREP.
+bool admit(jacobi_server* s, Request* rq) {
+  const bool own_A = true;  // A always lives in the arena (copied or generated), row stride n
+  rq->ld = round_up(rq->n, kLdAlign);
+  rq->bytes = request_bytes(rq->n, rq->r, rq->ld, own_A);
+  if (!s->arena.alloc(rq->bytes, &rq->off)) return false;
+  char* p = s->arena_base + rq->off;
+  SrvReq& q = rq->q;
+  q = SrvReq{};
+  q.n = rq->n;
+  q.r = rq->r;
+  q.ld = rq->ld;
+  auto take = [&p](size_t bytes) {
+    char* at = p;
+    p += a256(bytes);
+    return at;
+  };
+  const int64_t n = rq->n, r = rq->r, ld = rq->ld;
+  double* A = reinterpret_cast<double*>(take(static_cast<size_t>(n) * n * 8));
+  q.A = A;
+  q.Nl = reinterpret_cast<float*>(take(static_cast<size_t>(n) * ld * 4));
+  q.d = reinterpret_cast<double*>(take(static_cast<size_t>(ld) * 8));
+  q.rinv = reinterpret_cast<double*>(take(static_cast<size_t>(ld) * 8));
+  q.rowfac = reinterpret_cast<float*>(take(static_cast<size_t>(ld) * 4));
+  double* B = reinterpret_cast<double*>(take(static_cast<size_t>(r) * ld * 8));
+  q.B = B;
+  q.X[0] = reinterpret_cast<double*>(take(static_cast<size_t>(r) * ld * 8));
+  q.X[1] = reinterpret_cast<double*>(take(static_cast<size_t>(r) * ld * 8));
+  q.C1 = reinterpret_cast<float*>(take(static_cast<size_t>(r) * ld * 4));
+  q.D[0] = reinterpret_cast<float*>(take(static_cast<size_t>(r) * ld * 4));
+  q.D[1] = reinterpret_cast<float*>(take(static_cast<size_t>(r) * ld * 4));
+  // vectors start at zero so every padding entry is 0 (X0 = 0 is the start vector)
+  const size_t vec_bytes = static_cast<size_t>((reinterpret_cast<char*>(q.D[1]) - reinterpret_cast<char*>(B))) +
+                           a256(static_cast<size_t>(r) * ld * 4);
+  cudaMemsetAsync(B, 0, vec_bytes, s->stream);
+  if (rq->generate) {
+    int64_t blocks = std::min<int64_t>(n, 4096);
+    serve_generate_kernel<<<static_cast<unsigned>(blocks), kSThreads, 0, s->stream>>>(n, r, ld, rq->f, rq->seed, A,
+                                                                                       B);
+  } else {
+    cudaMemcpyAsync(A, rq->A_in, static_cast<size_t>(n) * n * 8, cudaMemcpyDefault, s->stream);
+    cudaMemcpy2DAsync(B, ld * 8, rq->B_in, n * 8, n * 8, r, cudaMemcpyDefault, s->stream);
+  }
+  q.phase = kPhPrep;
+  q.xsel = 0;
+  q.dsel = 0;
+  q.rb = rbucket(r);
+  rq->st = jacobi_stats{};
+  rq->st.rel_residual = std::nan("");
+  rq->outer = rq->inner_total = rq->inner_step = 0;
+  return true;
+}
+
+void retire(jacobi_server* s, Request* rq, int status) {
+  rq->st.status = status;
+  rq->st.converged = status == JACOBI_OK;
+  rq->st.sweeps = rq->inner_total;
+  rq->st.outer_steps = rq->outer;
+  if (status >= 0 && rq->X_out)
+    cudaMemcpy2DAsync(rq->X_out, rq->n * 8, rq->q.X[rq->q.xsel], rq->ld * 8, rq->n * 8, rq->r, cudaMemcpyDefault,
+                      s->stream);
+  s->arena.release(rq->off, rq->bytes);
+  s->done.emplace_back(rq->id, rq->st);
+  delete rq;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out) {
+  if (!out || !d || d->budget_bytes < (1u << 20)) return JACOBI_ERR_INVALID_ARG;
+  *out = nullptr;
+  jacobi_server* s = new (std::nothrow) jacobi_server();
+  if (!s) return JACOBI_ERR_OUT_OF_MEMORY;
+  s->stream = static_cast<cudaStream_t>(d->stream);
+  if (d->tol > 0) s->tol = d->tol;
+  if (d->max_iter > 0) s->max_iter = d->max_iter;
+  if (d->max_inner > 0) s->max_inner = d->max_inner;
+  if (d->max_outer > 0) s->max_outer = d->max_outer;
+  if (d->inner_rtol > 0) s->inner_rtol = static_cast<float>(d->inner_rtol);
+  s->max_active = d->max_active;
+  if (cudaMalloc(&s->arena_base, d->budget_bytes) != cudaSuccess) {
+    delete s;
+    return JACOBI_ERR_OUT_OF_MEMORY;
+  }
+  s->arena.reset(d->budget_bytes);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads, 0);
+  s->grid = std::max(1, per_sm) * sms;
+  if (grow(s, 64) != JACOBI_OK) {
+    jacobi_server_destroy(s);
+    return JACOBI_ERR_OUT_OF_MEMORY;
+  }
+  *out = s;
+  return JACOBI_OK;
+}
+
+static int submit(jacobi_server* s, int64_t n, int64_t r, Request* rq, int64_t* id_out) {
+  if (!s || n < 1 || n > JACOBI_SERVE_MAX_N || r < 1 || r > JACOBI_SERVE_MAX_RHS) {
+    delete rq;
+    return JACOBI_ERR_INVALID_ARG;
+  }
+  if (request_bytes(n, r, round_up(n, kLdAlign), true) > s->arena.size) {
+    delete rq;
+    return JACOBI_ERR_OUT_OF_MEMORY;  // could never be admitted
+  }
+  rq->id = s->next_id++;
+  rq->n = n;
+  rq->r = r;
+  s->pending.push_back(rq);
+  if (id_out) *id_out = rq->id;
+  return JACOBI_OK;
+}
+
+int jacobi_server_submit(jacobi_server* s, int64_t n, int64_t r, const double* A, const double* B, double* X_out,
+                         int64_t* id_out) {
+  if (!A || !B) return JACOBI_ERR_INVALID_ARG;
+  Request* rq = new (std::nothrow) Request();
+  if (!rq) return JACOBI_ERR_OUT_OF_MEMORY;
+  rq->A_in = A;
+  rq->B_in = B;
+  rq->X_out = X_out;
+  return submit(s, n, r, rq, id_out);
+}
+
+int jacobi_server_submit_generated(jacobi_server* s, int64_t n, int64_t r, double f, uint64_t seed, double* X_out,
+                                   int64_t* id_out) {
+  if (!(f > 0.0)) return JACOBI_ERR_INVALID_ARG;
+  Request* rq = new (std::nothrow) Request();
+  if (!rq) return JACOBI_ERR_OUT_OF_MEMORY;
+  rq->generate = true;
+  rq->f = f;
+  rq->seed = seed;
+  rq->X_out = X_out;
+  return submit(s, n, r, rq, id_out);
+}
+
+int jacobi_server_step(jacobi_server* s, int32_t* active_out, int32_t* pending_out) {
+  if (!s) return JACOBI_ERR_INVALID_ARG;
+  // admit in arrival order while the budget (and the active cap) allows
+  while (!s->pending.empty() && (s->max_active <= 0 || static_cast<int>(s->active.size()) < s->max_active)) {
+    Request* rq = s->pending.front();
+    if (!admit(s, rq)) break;
+    s->pending.pop_front();
+    s->active.push_back(rq);
+  }
+  const int na = static_cast<int>(s->active.size());
+  if (na > 0) {
+    if (grow(s, na) != JACOBI_OK) return JACOBI_ERR_OUT_OF_MEMORY;
+    int64_t items = 0;
+    for (int k = 0; k < na; ++k) {
+      Request* rq = s->active[static_cast<size_t>(k)];
+      rq->q.st = s->d_stats + static_cast<size_t>(k) * kStatSlots;
+      s->h_reqs[k] = rq->q;
+      s->h_first[k] = items;
+      items += (rq->n + kSRows - 1) / kSRows;
+    }
+    s->h_first[na] = items;
+    if (cudaMemcpyAsync(s->d_reqs, s->h_reqs, sizeof(SrvReq) * na, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->d_first, s->h_first, sizeof(int64_t) * (na + 1), cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(s->d_stats, 0, sizeof(unsigned long long) * kStatSlots * na, s->stream) != cudaSuccess)
+      return JACOBI_ERR_CUDA;
+    const int grid = static_cast<int>(std::min<int64_t>(items, s->grid));
+    serve_round_kernel<<<grid, kSThreads, 0, s->stream>>>(s->d_reqs, na, s->d_first, items);
+    if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    if (cudaMemcpyAsync(s->h_stats, s->d_stats, sizeof(unsigned long long) * kStatSlots * na, cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+      return JACOBI_ERR_CUDA;
+    ++s->rounds;
+    // move every request's state machine (Section 2 control flow per request, plus the refinement)
+    std::vector<Request*> still;
+    still.reserve(static_cast<size_t>(na));
+    for (int k = 0; k < na; ++k) {
+      Request* rq = s->active[static_cast<size_t>(k)];
+      const unsigned long long* st = s->h_stats + static_cast<size_t>(k) * kStatSlots;
+      SrvReq& q = rq->q;
+      int finish = 1;  // 1: keep going, else the final status
+      if (q.phase == kPhPrep) {
+        if (st[34]) {
+          const unsigned long long key = ~st[34];
+          finish = (key & 0xFF) == 2 ? JACOBI_ERR_ZERO_DIAGONAL : JACOBI_ERR_NONFINITE;
+        } else {
+          // the setup wrote C1 = B / a_ii and D0 = C1: the residual of the zero start vector is B
+          rq->bnorm.assign(static_cast<size_t>(rq->r), 0.0);
+          double bmax = 0.0;
+          for (int64_t c = 0; c < rq->r; ++c) {
+            rq->bnorm[static_cast<size_t>(c)] = as_double(st[16 + c]);
+            bmax = std::max(bmax, rq->bnorm[static_cast<size_t>(c)]);
+          }
+          rq->outer = 1;
+          rq->st.rel_residual = 1.0;
+          if (!std::isfinite(bmax)) {
+            finish = JACOBI_ERR_NONFINITE;
+          } else if (bmax == 0.0) {
+            rq->st.rel_residual = 0.0;
+            finish = JACOBI_OK;  // B = 0: X = 0 is exact
+          } else {
+            q.phase = kPhInner;
+            q.dsel = 0;
+            rq->inner_step = 0;
+          }
+        }
+      } else if (q.phase == kPhResid) {
+        ++rq->outer;
+        double rho = 0.0;
+        for (int64_t c = 0; c < rq->r; ++c) {
+          const double bn = rq->bnorm[static_cast<size_t>(c)];
+          const double v = bn > 0.0 ? as_double(st[c]) / bn : 0.0;
+          rho = (std::isnan(v) || v > rho) ? v : rho;
+        }
+        rq->st.rel_residual = rho;
+        if (!std::isfinite(rho))
+          finish = JACOBI_ERR_NONFINITE;
+        else if (rho <= s->tol)
+          finish = JACOBI_OK;
+        else if (rq->outer >= s->max_outer || rq->inner_total >= s->max_iter)
+          finish = JACOBI_NOT_CONVERGED;
+        else {
+          q.phase = kPhInner;
+          q.dsel = 0;  // the residual round wrote D0 = C1
+          rq->inner_step = 0;
+        }
+      } else {
+        ++rq->inner_total;
+        ++rq->inner_step;
+        const double chg = as_double(st[32]), mag = as_double(st[33]);
+        rq->st.final_delta = chg;
+        q.dsel ^= 1;
+        if (!std::isfinite(chg) || !std::isfinite(mag)) {
+          finish = JACOBI_ERR_NONFINITE;
+        } else if (chg <= static_cast<double>(s->inner_rtol) * mag || rq->inner_step >= s->max_inner ||
+                   rq->inner_total >= s->max_iter) {
+          q.xsel ^= 1;  // X + delta becomes the current iterate
+          q.phase = kPhResid;
+        }
+      }
+      if (finish == 1)
+        still.push_back(rq);
+      else
+        retire(s, rq, finish);
+    }
+    s->active.swap(still);
+  }
+  if (active_out) *active_out = static_cast<int32_t>(s->active.size());
+  if (pending_out) *pending_out = static_cast<int32_t>(s->pending.size());
+  return JACOBI_OK;
+}
+
+int jacobi_server_poll(jacobi_server* s, int64_t* ids, jacobi_stats* stats, int32_t cap, int32_t* count) {
+  if (!s || !count || cap < 0 || (cap > 0 && (!ids || !stats))) return JACOBI_ERR_INVALID_ARG;
+  // results copied out by the last round are complete once the stream has caught up
+  if (!s->done.empty() && cudaStreamSynchronize(s->stream) != cudaSuccess) return JACOBI_ERR_CUDA;
+  const int32_t m = static_cast<int32_t>(std::min<size_t>(s->done.size(), static_cast<size_t>(cap)));
+  for (int32_t i = 0; i < m; ++i) {
+    ids[i] = s->done[static_cast<size_t>(i)].first;
+    stats[i] = s->done[static_cast<size_t>(i)].second;
+  }
+  s->done.erase(s->done.begin(), s->done.begin() + m);
+  *count = m;
+  return JACOBI_OK;
+}
+
+int jacobi_server_rounds(jacobi_server* s, int64_t* rounds) {
+  if (!s || !rounds) return JACOBI_ERR_INVALID_ARG;
+  *rounds = s->rounds;
+  return JACOBI_OK;
+}
+
+void jacobi_server_destroy(jacobi_server* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (Request* rq : s->pending) delete rq;
+  for (Request* rq : s->active) delete rq;
+  cudaFree(s->d_reqs);
+  cudaFree(s->d_first);
+  cudaFree(s->d_stats);
+  cudaFreeHost(s->h_reqs);
+  cudaFreeHost(s->h_first);
+  cudaFreeHost(s->h_stats);
+  cudaFree(s->arena_base);
+  delete s;
+}
+
+int jacobi_generate_request(int64_t n, int64_t r, double f, uint64_t seed, double* A, double* B, int64_t ldb,
+                            void* stream) {
+  if (n < 1 || r < 1 || !A || !B || ldb < n || !(f > 0.0)) return JACOBI_ERR_INVALID_ARG;
+  const int64_t blocks = std::min<int64_t>(n, 4096);
+  serve_generate_kernel<<<static_cast<unsigned>(blocks), kSThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      n, r, ldb, f, seed, A, B);
+  return cudaGetLastError() == cudaSuccess ? JACOBI_OK : JACOBI_ERR_CUDA;
+}
+
+}  // extern "C"

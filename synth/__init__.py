@@ -105,7 +105,7 @@ def unit(words: np.ndarray) -> np.ndarray:
 
 
 # Stream ids inside one system's seed.
-STREAM_A, STREAM_SIGN, STREAM_XSTAR, STREAM_X0, STREAM_META = 0, 1, 2, 3, 4
+STREAM_A, STREAM_SIGN, STREAM_XSTAR, STREAM_X0, STREAM_META, STREAM_B = 0, 1, 2, 3, 4, 5
 
 
 def _offdiag(seed: int, n: int, signed: bool) -> np.ndarray:
@@ -163,3 +163,34 @@ def batch_shapes(count: int, n_lo: int, n_hi: int, f_lo: float, f_hi: float, see
 def system_seed(seed: int, index: int) -> int:
     """Seed of system ``index`` in a batch drawn with ``seed``."""
     return (seed * 1_000_003 + index + 1) & 0xFFFFFFFFFFFF
+
+
+def serving_request(n: int, nrhs: int, f: float, seed: int):
+    """One request of the serving workload: the dominant generator's A (off-diagonals int32(w) * 2**-31,
+    a_ii = f * sum_{j != i} |a_ij| * (+-1)) and right-hand sides drawn directly, B iid uniform [-1, 1)
+    (word c * n + i of stream 5 is B[i, c]).  Every value is a function of (seed, stream, index) alone,
+    so a device-side twin of the same generator reproduces A and B bit for bit.  Returns (A, B)."""
+    A = _offdiag(seed, n, signed=True)
+    rowsum = np.abs(A).sum(axis=1)  # exact: integers times 2**-31, the zero diagonal included
+    sign = np.where(random_u32(seed, STREAM_SIGN, n) & np.uint32(1), -1.0, 1.0)
+    A[np.arange(n), np.arange(n)] = f * rowsum * sign if n > 1 else np.array([f * sign[0]])
+    B = signed_unit(random_u32(seed, STREAM_B, n * nrhs)).reshape(nrhs, n).T.copy()
+    return A, B
+
+
+def serving_trace(rate: float, duration: float, seed: int, n_lo: int = 256, n_hi: int = 8192, r_max: int = 16,
+                  f_lo: float = 1.05, f_hi: float = 1.5):
+    """Poisson arrivals at `rate` per second for `duration` seconds: arrays (t, n, r, f, seed) of the
+    requests (exponential gaps from uniforms, n log-uniform in [n_lo, n_hi], r uniform in {1..r_max},
+    f uniform in [f_lo, f_hi])."""
+    count = int(rate * duration * 1.5) + 16
+    u = unit(random_u32(seed, STREAM_META, 4 * count)).reshape(count, 4)
+    gaps = -np.log1p(-u[:, 0]) / rate
+    t = np.cumsum(gaps)
+    keep = t < duration
+    t, u = t[keep], u[keep]
+    n = log_uniform_int(u[:, 1], n_lo, n_hi)
+    r = np.minimum((u[:, 2] * r_max).astype(np.int64) + 1, r_max)
+    f = f_lo + u[:, 3] * (f_hi - f_lo)
+    seeds = np.array([system_seed(seed, k) for k in range(len(t))], dtype=np.int64)
+    return t, n, r, f, seeds
