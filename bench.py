@@ -124,6 +124,8 @@ def run_ours(args, world, rank, local):
         return {"section": "many_rhs", **run_many_rhs(args, jac, torch, dev)}
     if args.only == "batch":
         return {"section": "batched", **run_batch(args, jac, torch, dev)}
+    if args.only == "serve":
+        return {"section": "serving", **run_serve(args, jac, torch, dev, args.serve_seconds)}
     n, f = args.n, args.f
     A, B, Xs = synth.dominant_system(n, f, seed=synth.BASE_SEED + 1)
     At = torch.from_numpy(A).to(dev)
@@ -208,6 +210,7 @@ def run_ours(args, world, rank, local):
     batched = None if (args.quick or args.no_batch) else run_batch(args, jac, torch, dev)
     del At, Bt, A, B  # free the single-system inputs before the large many-right-hand-side workload
     many_rhs = None if (args.quick or args.no_mrhs) else run_many_rhs(args, jac, torch, dev)
+    serving = None if (args.quick or args.no_serve) else run_serve(args, jac, torch, dev, args.serve_window)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
@@ -221,6 +224,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": (4 if args.precision != "fp64" else 3) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
+        "serving": serving,
     }
     if cpu is not None:
         result["cpu_baseline"] = cpu
@@ -370,6 +374,96 @@ def run_many_rhs(args, jac, torch, dev):
     return out
 
 
+def run_serve(args, jac, torch, dev, seconds):
+    """Poisson arrivals at 2000 requests/s for `seconds` (n log-uniform in [256, 8192], r uniform in
+    {1..16}, f uniform in [1.05, 1.5], FP64 inputs generated on the device at admission), served with
+    continuous batching under a 100 GB budget to a 1e-10 relative residual; latency from each request's
+    scheduled arrival to the moment its result is polled.  Beside it, the same trace's first
+    `serve_fp64_seconds` solved one request at a time by the plain FP64 path."""
+    import time as _time
+
+    import synth
+    rate = 2000.0
+    t, ns, rs, fs, seeds = synth.serving_trace(rate, seconds, seed=synth.BASE_SEED + 4)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(min(100e9, free - 8e9))
+    srv = jac.Server(budget_bytes=budget)
+    outs, arrive, lat, stats = {}, {}, {}, {}
+    k = 0
+    total = len(t)
+    active_samples = []
+    t0 = _time.perf_counter()
+    while len(lat) < total:
+        now = _time.perf_counter() - t0
+        while k < total and t[k] <= now:
+            out = torch.empty(int(rs[k]), int(ns[k]), dtype=torch.float64, device=dev)
+            rid = srv.submit_generated(int(ns[k]), int(rs[k]), float(fs[k]), int(seeds[k]), out)
+            outs[rid] = (k, out)
+            arrive[rid] = t[k]
+            k += 1
+        active, pending = srv.step()
+        active_samples.append(active + pending)
+        done_t = _time.perf_counter() - t0
+        for rid, st in srv.poll():
+            lat[rid] = done_t - arrive[rid]
+            stats[rid] = (st.status, st.rel_residual, st.outer_steps, st.sweeps)
+            kk, out = outs[rid]
+            if kk % max(1, total // 16) == 0:  # keep a sample for the host-side check
+                outs[rid] = (kk, out)
+            else:
+                del outs[rid]
+        if k >= total and active == 0 and pending == 0 and len(lat) < total:
+            for rid, st in srv.poll():
+                lat[rid] = _time.perf_counter() - t0 - arrive[rid]
+    wall = _time.perf_counter() - t0
+    rounds = srv.rounds()
+    srv.close()
+    L = np.array(sorted(lat.values())) * 1e3
+    ok = sum(1 for v in stats.values() if v[0] == 0)
+    worst = max(v[1] for v in stats.values())
+    # host check of sampled results (inputs regenerated from their seeds)
+    checked = []
+    for rid, (kk, out) in list(outs.items())[:8]:
+        A, B = synth.serving_request(int(ns[kk]), int(rs[kk]), float(fs[kk]), int(seeds[kk]))
+        X = out.cpu().numpy().T
+        R = B - A @ X
+        checked.append(float(np.max(np.abs(R).max(axis=0) / np.abs(B).max(axis=0))))
+    served = {"offered_rate": rate, "seconds": seconds, "requests": total, "converged": ok,
+              "throughput_per_s": round(total / wall, 1), "wall_s": round(wall, 3),
+              "p50_ms": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
+              "max_ms": round(float(L[-1]), 3), "rounds": rounds, "mean_in_system": round(float(np.mean(active_samples)), 1),
+              "worst_rel_residual": worst, "sampled_host_residuals_max": max(checked) if checked else None,
+              "budget_gb": round(budget / 1e9, 1)}
+
+    # the plain FP64 path, one request at a time, on the first seconds of the same trace
+    m = int(np.searchsorted(t, args.serve_fp64_seconds))
+    lat64 = []
+    t0 = _time.perf_counter()
+    for q in range(m):
+        now = _time.perf_counter() - t0
+        if t[q] > now:
+            _time.sleep(t[q] - now)
+        n, r = int(ns[q]), int(rs[q])
+        A, Bc = jac.generate_request(n, r, float(fs[q]), int(seeds[q]), device=dev)
+        if r == 1:
+            sol = jac.DeviceSolver(A, Bc.reshape(-1), precision="fp64", norm="resid")
+            X, st = sol.solve(max_iter=5000, tol=TARGET)
+        else:
+            sol = jac.MultiSolver(A, Bc, precision="fp64", norm="resid")
+            X, st = sol.solve(max_iter=5000, tol=TARGET)
+        sol.close()
+        lat64.append(_time.perf_counter() - t0 - t[q])
+    wall64 = _time.perf_counter() - t0
+    L64 = np.array(sorted(lat64)) * 1e3
+    fp64 = {"requests": m, "arrival_window_s": args.serve_fp64_seconds,
+            "throughput_per_s": round(m / wall64, 1) if m else None,
+            "p50_ms": round(float(np.percentile(L64, 50)), 3) if m else None,
+            "p99_ms": round(float(np.percentile(L64, 99)), 3) if m else None}
+    return {"served_fp32_ir": served, "one_at_a_time_fp64": fp64,
+            "throughput_ratio": round(served["throughput_per_s"] / fp64["throughput_per_s"], 2)
+            if fp64["throughput_per_s"] else None}
+
+
 def run_e2e(args, jac, torch, dev, A, B, ws):
     """Same metric through the public API from pinned host buffers: H2D of A and B, setup, solve and the
     D2H read of X inside the timed region."""
@@ -481,7 +575,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", dest="no_e2e")
     ap.add_argument("--no-batch", action="store_true", dest="no_batch")
     ap.add_argument("--no-mrhs", action="store_true", dest="no_mrhs")
-    ap.add_argument("--only", choices=["batch", "mrhs"], default=None,
+    ap.add_argument("--no-serve", action="store_true", dest="no_serve")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, dest="serve_seconds",
+                    help="arrival window of --only serve (the full serving configuration)")
+    ap.add_argument("--serve-window", type=float, default=5.0, dest="serve_window",
+                    help="arrival window of the serving section of the default run")
+    ap.add_argument("--serve-fp64-seconds", type=float, default=1.0, dest="serve_fp64_seconds")
+    ap.add_argument("--only", choices=["batch", "mrhs", "serve"], default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--mrhs-n", type=int, default=32768, dest="mrhs_n")
     ap.add_argument("--mrhs-steps", type=int, default=3, dest="mrhs_steps")

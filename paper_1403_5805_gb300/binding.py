@@ -376,7 +376,7 @@ class MultiSolver:
     float64 CUDA tensors (row c is right-hand side c, i.e. column-major n x r)."""
 
     def __init__(self, A, B, precision: str = "bf16_ir", stream=None, max_outer: int = 0, max_inner: int = 0,
-                 inner_rtol: float = 0.0):
+                 inner_rtol: float = 0.0, norm: str = "inf"):
         import torch
         lib = load()
         n = A.shape[0]
@@ -389,6 +389,7 @@ class MultiSolver:
         lib.jacobi_desc_init(ctypes.byref(d))
         d.n, d.nrhs = n, self.r
         d.precision = PRECISIONS[precision]
+        d.norm = NORMS[norm]
         d.A, d.lda = A.data_ptr(), A.stride(0)
         d.B, d.ldb = B.data_ptr(), B.stride(0)
         d.stream = self.stream.cuda_stream

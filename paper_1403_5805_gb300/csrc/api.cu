@@ -114,7 +114,7 @@ int validate_desc(const jacobi_desc* d) {
   if (d->grid < 0 || d->grid > kMaxGrid) return JACOBI_ERR_INVALID_ARG;
   if (d->nrhs > 1) {
     // many right-hand sides: plain FP64 (max-norm stop) or BF16 inner sweeps on tcgen05
-    if (d->precision == JACOBI_FP64 && d->norm != JACOBI_NORM_INF) return JACOBI_ERR_UNSUPPORTED;
+    if (d->precision == JACOBI_FP64 && d->norm == JACOBI_NORM_2) return JACOBI_ERR_UNSUPPORTED;
     if (d->precision != JACOBI_FP64 && d->precision != JACOBI_BF16_IR) return JACOBI_ERR_UNSUPPORTED;
     if (d->precision == JACOBI_BF16_IR && !mrhs_supported_r(d->nrhs)) return JACOBI_ERR_UNSUPPORTED;
   }
@@ -357,14 +357,21 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
   if (h->precision == JACOBI_FP64) {
     for (int64_t k = 1;; ++k) {
       CK(cudaMemsetAsync(colmax, 0, static_cast<size_t>(r) * 8, s));
-      MrhsDenseParams p{n, r, ld, h->lda64, 1, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
+      const int resid = h->norm == JACOBI_NORM_RESID;
+      MrhsDenseParams p{n, r, ld, h->lda64, 1, resid, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
                         h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax};
       CK(launch_mrhs_dense(p, s));
       clk.mark(JACOBI_PHASE_SWEEP64);
       CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       double delta = 0.0;
-      for (auto u : hc) delta = std::isnan(bits(u)) || bits(u) > delta ? bits(u) : delta;
+      for (int64_t c = 0; c < r; ++c) {
+        // max-norm change over every entry, or the largest column relative residual of the previous
+        // iterate (max_i |a_ii (x_i^(k) - x_i^(k-1))| / ||b_c||_inf)
+        const double v = resid ? bits(hc[static_cast<size_t>(c)]) / bits(hb[static_cast<size_t>(c)])
+                               : bits(hc[static_cast<size_t>(c)]);
+        delta = (std::isnan(v) || v > delta) ? v : delta;
+      }
       std::swap(xc, xo);
       out.sweeps = k;
       out.final_delta = delta;
@@ -395,7 +402,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
         CK(launch_mrhs_init(n, r, ld, h->at<double>(h->M.b), h->at<double>(h->L.rinv), c1, dA, hA, colmax, s));
         clk.mark(JACOBI_PHASE_RESID0);
       } else {
-        MrhsDenseParams p{n, r, ld, h->lda64, 0, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
+        MrhsDenseParams p{n, r, ld, h->lda64, 0, 0, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
                           h->at<double>(h->L.rinv), c1, dA, hA, nullptr, colmax};
         CK(launch_mrhs_dense(p, s));
         clk.mark(JACOBI_PHASE_RESID64);

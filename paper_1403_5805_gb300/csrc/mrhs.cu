@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
         const double s = fma(-di, xo, acc[u][v]);
         const double xi = (b - s) * ri;
         p.xn[o] = xi;
-        const unsigned long long bits = abs_bits(xi - xo);
+        const unsigned long long bits = abs_bits(p.resid_norm ? di * (xi - xo) : xi - xo);
         mloc[v] = bits > mloc[v] ? bits : mloc[v];
       }
     }

@@ -28,6 +28,7 @@ struct MrhsSweepParams {
 struct MrhsDenseParams {
   int64_t n, r, ld, lda;
   int mode;
+  int resid_norm;   // mode 1: colmax of |a_ii (xn - x)| (residual of x) instead of |xn - x|
   const double* A;
   const double* b;
   const double* x;

@@ -108,3 +108,13 @@ def test_full_size_many_rhs_sampled(jac):
     rel = np.max(np.abs(R), axis=0) / np.max(np.abs(B), axis=0)
     assert np.all(rel <= 1e-10), rel.max()
     assert np.max(np.abs(Xh - Xs)) <= 1e-8
+
+
+def test_fp64_many_rhs_residual_stop(jac):
+    A, B, _ = synth.hard_system(400, 1.2, seed=611, nrhs=5)
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="fp64", norm="resid")
+    X, st = s.solve(max_iter=2000, tol=1e-10)
+    ref = oracle.jacobi(A, B, max_iter=2000, tol=1e-10, norm=oracle.NORM_RESID)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters)
+    assert np.max(np.abs(X.cpu().numpy().T - ref.X)) <= 1e-12 * np.max(np.abs(ref.X))
