@@ -137,8 +137,9 @@ def run_ours(args, world, rank, local):
 
     def one_step(prec, ev=None):
         nonlocal ws
-        s = jac.DeviceSolver(At, Bt, precision=prec, workspace=ws if ws.numel() else None,
-                             inner_rtol=args.inner_rtol, max_inner=args.max_inner)
+        split = prec.endswith("+split") or (args.split_residual and prec != "fp64")
+        s = jac.DeviceSolver(At, Bt, precision=prec.replace("+split", ""), workspace=ws if ws.numel() else None,
+                             inner_rtol=args.inner_rtol, max_inner=args.max_inner, split_residual=split)
         ws = s.workspace
         if ev is not None:
             ev[0].record(stream)
@@ -199,7 +200,7 @@ def run_ours(args, world, rank, local):
 
     paths = {args.precision: summarize(main, args.steps, n, args.precision)}
     if not args.quick:
-        for prec in [p for p in ("fp64", "fp8_ir", "fp32_ir") if p != args.precision]:
+        for prec in [p for p in ("fp64", "fp8_ir", "fp32_ir", "bf16_ir+split", "fp32_ir+split") if p != args.precision]:
             paths[prec] = summarize(timed(prec, args.steps, args.warmup), args.steps, n, prec)
     fp64_ratio = None
     if "fp64" in paths:
@@ -207,6 +208,7 @@ def run_ours(args, world, rank, local):
 
     e2e = None if args.no_e2e else run_e2e(args, jac, torch, dev, A, B, ws)
     cpu = cpu_baseline(A, B, n) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    hard = None if (args.quick or args.no_hard) else run_hard(args, jac, torch, dev, ws)
     batched = None if (args.quick or args.no_batch) else run_batch(args, jac, torch, dev)
     del At, Bt, A, B  # free the single-system inputs before the large many-right-hand-side workload
     many_rhs = None if (args.quick or args.no_mrhs) else run_many_rhs(args, jac, torch, dev)
@@ -224,7 +226,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": (4 if args.precision != "fp64" else 3) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
-        "serving": serving,
+        "serving": serving, "hard_generator": hard,
     }
     if cpu is not None:
         result["cpu_baseline"] = cpu
@@ -232,6 +234,7 @@ def run_ours(args, world, rank, local):
 
 
 def phase_bandwidth(trace, n, prec):
+    prec = prec.replace("+split", "")
     """Per-phase-kind mean duration and algorithmic matrix bandwidth from the device-side trace of the
     last solve (each phase streams the whole matrix once: FP64 A, or the narrow copy)."""
     names = {0: ("sweep64", 8), 1: ("resid64", 8), 2: ("resid0", 0), 3: ("inner", ESIZE.get(prec, 8))}
@@ -250,6 +253,7 @@ def phase_bandwidth(trace, n, prec):
 def summarize(r, steps, n, prec):
     st = r["stats"]
     ms = r["ms_total"] / steps
+    prec = prec.replace("+split", "")
     es = ESIZE[prec]
     if prec == "fp64":
         bytes_launch = st["sweeps"] * 8.0 * n * n
@@ -464,6 +468,38 @@ def run_serve(args, jac, torch, dev, seconds):
             if fp64["throughput_per_s"] else None}
 
 
+def run_hard(args, jac, torch, dev, ws):
+    """The same n = 16384 solve on the paper-shaped generator (off-diagonals uniform [0, 1), positive
+    diagonal f * row sum, f = 1.05: rho(T) = 1/f exactly, so plain Jacobi needs hundreds of sweeps)."""
+    import synth
+    n = args.n
+    A, B, Xs = synth.hard_system(n, 1.05, seed=synth.BASE_SEED + 5)
+    At = torch.from_numpy(A).to(dev)
+    Bt = torch.from_numpy(B[:, 0].copy()).to(dev)
+    del A
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    res = {"n": n, "dominance": 1.05, "rho_T": round(1 / 1.05, 6)}
+    for prec, tol, norm in (("bf16_ir", TARGET, "inf"), ("fp32_ir", TARGET, "inf"), ("fp64", TARGET, "resid")):
+        s = jac.DeviceSolver(At, Bt, precision=prec, norm=norm, workspace=ws)
+        s.solve_async(None, 20000, tol, out)  # warm-up
+        torch.cuda.synchronize(dev)
+        steps = 1 if prec == "fp64" else 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s = jac.DeviceSolver(At, Bt, precision=prec, norm=norm, workspace=ws)
+            s.solve_async(None, 20000, tol, out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        st = s.last_stats()
+        res[prec] = {"solves_per_s": round(1e3 / ms, 3), "ms_per_solve": round(ms, 2), "status": st.status,
+                     "sweeps": st.sweeps, "outer_steps": st.outer_steps, "rel_residual": s.residual(out)}
+    res["bf16_vs_fp64_solves_ratio"] = round(res["bf16_ir"]["solves_per_s"] / res["fp64"]["solves_per_s"], 2)
+    return res
+
+
 def run_e2e(args, jac, torch, dev, A, B, ws):
     """Same metric through the public API from pinned host buffers: H2D of A and B, setup, solve and the
     D2H read of X inside the timed region."""
@@ -570,12 +606,15 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=0.0, dest="inner_rtol",
                     help="mixed paths: inner-sweep stop (relative change); 0 = library default")
     ap.add_argument("--max-inner", type=int, default=0, dest="max_inner")
+    ap.add_argument("--split-residual", action="store_true", dest="split_residual",
+                    help="mixed paths: FP64-accurate residual on the FP32 units (split-float)")
     ap.add_argument("--quick", action="store_true", help="skip the comparison paths")
     ap.add_argument("--no-cpu-baseline", action="store_true", dest="no_cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", dest="no_e2e")
     ap.add_argument("--no-batch", action="store_true", dest="no_batch")
     ap.add_argument("--no-mrhs", action="store_true", dest="no_mrhs")
     ap.add_argument("--no-serve", action="store_true", dest="no_serve")
+    ap.add_argument("--no-hard", action="store_true", dest="no_hard")
     ap.add_argument("--serve-seconds", type=float, default=60.0, dest="serve_seconds",
                     help="arrival window of --only serve (the full serving configuration)")
     ap.add_argument("--serve-window", type=float, default=5.0, dest="serve_window",

@@ -133,11 +133,22 @@ typedef struct jacobi_desc {
   int32_t max_outer;      /* IR: cap on FP64 residual evaluations (0: 60) */
   double inner_rtol;      /* IR: stop inner sweeps when max|delta change| <= inner_rtol * max|delta|
                              (0: 2^-10 for FP32/BF16, 2^-6 for FP8) */
-  int32_t max_inner;      /* IR: cap on inner sweeps per outer step (0: 64) */
+  int32_t max_inner;      /* IR: cap on inner sweeps per outer step (0: 1000) */
   int32_t flags;          /* JACOBI_FLAG_* */
 } jacobi_desc;
 
 #define JACOBI_FLAG_COPY_A 1 /* always copy A into the workspace (never borrow it) */
+/* IR precisions: compute the FP64 residual r = B - A X with split-float arithmetic on the FP32 units
+ * (each a_ij as two FP32 words after a per-row power-of-two scale, products with exact FMA errors,
+ * float-float sums, FP64 combination across lanes) instead of FP64 FMAs.  Accuracy ~2^-46 relative
+ * per product; GB300's FP64 FMA rate makes the FP64-instruction residual arithmetic-bound.  Requires
+ * |x_j| within FP32 range. */
+#define JACOBI_FLAG_SPLIT_RESIDUAL 2
+/* Every device-side wait of this handle's solves gives up after 50 ms instead of 4 s. */
+#define JACOBI_FLAG_SHORT_WAITS 4
+/* Test only: the first ring item of each solve is announced to the consumers but never copied, so their
+ * bounded wait expires; the solve then returns JACOBI_ERR_TIMEOUT and the context stays usable. */
+#define JACOBI_FLAG_TEST_DROP_COPY 8
 
 /* Fill *d with defaults (n = 0 and null pointers: the caller sets those). */
 JACOBI_API void jacobi_desc_init(jacobi_desc* d);
@@ -219,7 +230,7 @@ typedef struct jacobi_batch_desc {
   int32_t rows_per_warp;      /* 1, 2, 4 or 8 rows a warp accumulates at once (0: 4) */
   int32_t ctas_per_sm;        /* cap on resident CTAs per SM (0: as many as fit) */
   int32_t max_outer;          /* IR: cap on residual evaluations per system (0: 30) */
-  int32_t max_inner;          /* IR: cap on inner sweeps per outer step (0: 64) */
+  int32_t max_inner;          /* IR: cap on inner sweeps per outer step (0: 1000) */
   int32_t reserved;
   double inner_rtol;          /* IR: inner stop, max|change| <= inner_rtol * max|delta| (0: 2^-14) */
   void* workspace;            /* device, >= jacobi_batch_workspace_size bytes, 256-byte aligned; NULL:
@@ -274,7 +285,7 @@ typedef struct jacobi_server_desc {
   size_t budget_bytes;  /* device arena for admitted requests (allocated once at create) */
   double tol;           /* relative-residual target (0: 1e-10) */
   int64_t max_iter;     /* cap on inner sweeps per request (0: 5000) */
-  int32_t max_inner;    /* cap on inner sweeps per refinement step (0: 64) */
+  int32_t max_inner;    /* cap on inner sweeps per refinement step (0: 1000) */
   int32_t max_outer;    /* cap on residual evaluations per request (0: 30) */
   double inner_rtol;    /* inner stop: max|change| <= inner_rtol * max|delta| (0: 2^-10) */
   int32_t max_active;   /* cap on concurrently active requests (0: only the budget limits) */

@@ -28,6 +28,9 @@ NORM_INF, NORM_2, NORM_RESID = 0, 1, 2
 PHASE_SWEEP64, PHASE_RESID64, PHASE_RESID0, PHASE_INNER = 0, 1, 2, 3
 NORMS = {"inf": NORM_INF, "2": NORM_2, "resid": NORM_RESID}
 FLAG_COPY_A = 1
+FLAG_SPLIT_RESIDUAL = 2
+FLAG_SHORT_WAITS = 4
+FLAG_TEST_DROP_COPY = 8
 
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
            "jacobi_desc_init", "jacobi_workspace_size", "jacobi_setup_ex", "jacobi_solve_async",
@@ -194,7 +197,7 @@ class DeviceSolver:
 
     def __init__(self, A, B, precision: str = "fp64", norm: str = "inf", grid: int = 0, stream=None,
                  copy_a: bool = False, max_outer: int = 0, max_inner: int = 0, inner_rtol: float = 0.0,
-                 workspace=None, device=None):
+                 workspace=None, device=None, split_residual: bool = False, flags: int = 0):
         """A, B: float64 tensors on the GPU (A may be borrowed, see jacobi_desc.A) or on the host (copied
         to the device during setup; pin them for full link bandwidth).  workspace: optional uint8 CUDA
         tensor of at least workspace_size() bytes to reuse across solvers."""
@@ -222,7 +225,7 @@ class DeviceSolver:
         d.B, d.ldb = Bv.data_ptr(), n
         d.stream = self.stream.cuda_stream
         d.grid, d.max_outer, d.max_inner, d.inner_rtol = grid, max_outer, max_inner, inner_rtol
-        d.flags = FLAG_COPY_A if copy_a else 0
+        d.flags = (FLAG_COPY_A if copy_a else 0) | (FLAG_SPLIT_RESIDUAL if split_residual else 0) | flags
         nbytes = ctypes.c_size_t(0)
         with torch.cuda.device(device):
             _check(lib.jacobi_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_workspace_size")

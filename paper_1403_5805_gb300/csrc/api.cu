@@ -69,7 +69,7 @@ bool can_borrow(const jacobi_desc* d) {
 // Offsets of every sub-buffer inside one workspace allocation.
 struct Layout {
   int64_t ld;  // padded length of vectors and row stride of owned matrices
-  size_t A64, Nlow, b, d, rinv, bnorm, rowfac, scale, xa, xb, xout, c1, da, db, part, ctl, keys, stats, total;
+  size_t A64, Nlow, b, d, rinv, bnorm, rowfac, scale, rexp, xa, xb, xout, c1, da, db, part, ctl, keys, stats, total;
 };
 
 Layout make_layout(int64_t n, int precision, bool copy_A) {
@@ -92,6 +92,7 @@ Layout make_layout(int64_t n, int precision, bool copy_A) {
   L.bnorm = take(sizeof(double));
   L.rowfac = take(vf);
   L.scale = take(vf);
+  L.rexp = take(static_cast<size_t>(L.ld) * sizeof(int));
   L.xa = take(vd);
   L.xb = take(vd);
   L.xout = take(vd);
@@ -172,8 +173,11 @@ struct jacobi_handle {
   int64_t lda64 = 0;
   int grid = 0;
   int max_outer = 60;
-  int max_inner = 64;
+  int max_inner = 1000;
   float inner_rtol = 0.0f;
+  bool split_residual = false;
+  uint64_t wait_ns = 4000000000ull;
+  int test_drop_copy = 0;
   template <typename T>
   T* at(size_t off) const {
     return reinterpret_cast<T*>(ws + off);
@@ -217,7 +221,8 @@ int prepare(jacobi_handle* h, const double* A, int64_t lda, const double* B, boo
   CK(cudaMemsetAsync(h->at<char>(h->L.db), 0, h->L.ld * sizeof(float), s));
   if (h->precision != JACOBI_FP64)
     CK(launch_narrow(narrow_kind(h->precision), h->A64, h->lda64, n, h->at<void>(h->L.Nlow), h->L.ld,
-                     h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac), s));
+                     h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac),
+                     h->at<int>(h->L.rexp), s));
   unsigned long long key = 0;
   CK(cudaMemcpyAsync(&key, keys, sizeof(key), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -251,9 +256,12 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
     h->L.total = h->M.total;
   }
   h->max_outer = d->max_outer > 0 ? d->max_outer : 60;
-  h->max_inner = d->max_inner > 0 ? d->max_inner : 64;
+  h->max_inner = d->max_inner > 0 ? d->max_inner : 1000;
   h->inner_rtol = static_cast<float>(
       d->inner_rtol > 0 ? d->inner_rtol : (d->precision == JACOBI_FP8_IR ? 1.0 / 64 : 1.0 / 1024));
+  h->split_residual = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) && d->precision != JACOBI_FP64 && d->nrhs == 1;
+  if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
+  h->test_drop_copy = (d->flags & JACOBI_FLAG_TEST_DROP_COPY) ? 1 : 0;
   if (d->workspace) {
     if (d->workspace_bytes < h->L.total || reinterpret_cast<uintptr_t>(d->workspace) % kAlign != 0) {
       delete h;
@@ -582,6 +590,9 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
   p.max_outer = h->max_outer;
   p.max_inner = h->max_inner;
   p.inner_rtol = h->inner_rtol;
+  p.rexp = h->split_residual ? h->at<int>(h->L.rexp) : nullptr;
+  p.wait_ns = h->wait_ns;
+  p.test_drop_copy = h->test_drop_copy;
   cudaError_t e = h->precision == JACOBI_FP64 ? launch_fp64_solve(p, h->grid, s)
                                                : launch_ir_solve(narrow_kind(h->precision), p, h->grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");

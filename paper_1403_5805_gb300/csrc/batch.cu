@@ -409,7 +409,7 @@ struct jacobi_batch {
   BatchSys* dsys = nullptr;
   unsigned int* queue = nullptr;
   jacobi_stats* stats = nullptr;
-  int max_outer = 30, max_inner = 64;
+  int max_outer = 30, max_inner = 1000;
   float inner_rtol = 1.0f / 16384;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;

@@ -75,11 +75,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait; false if the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+    if (global_timer_ns() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -141,14 +141,14 @@ __device__ __forceinline__ T warp_sum(T v) {
 // `target` = (barrier index + 1) * gridDim.x.  Returns false if the wait timed out or another CTA
 // reported an error through *status.
 __device__ __forceinline__ bool grid_arrive_and_wait(unsigned int* counter, const int* status,
-                                                     uint32_t target) {
+                                                     uint32_t target, uint64_t limit_ns = kWaitLimitNs) {
   __threadfence();
   atomicAdd(counter, 1u);
   if (ld_acquire_u32(counter) >= target) return true;
   const uint64_t t0 = global_timer_ns();
   while (ld_acquire_u32(counter) < target) {
     if (ld_volatile_i32(status) < 0) return false;
-    if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+    if (global_timer_ns() - t0 > limit_ns) return false;
     __nanosleep(32);
   }
   __threadfence();

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       for (int kb = 0; kb < kb_count; ++kb) {
         const int s = kb % kMStages;
         const uint32_t par = ((kb / kMStages) & 1) ^ 1;
-        if (S.abort || !mbar_wait(&S.empty[s], par)) {
+        if (S.abort || !mbar_wait(&S.empty[s], par) || S.abort) {
           S.abort = 1;
           atomicCAS(p.status, 0, kStatusTimeout);
           break;

@@ -141,6 +141,7 @@ extern "C" int jacobi_solve_fp64_noalloc(const double* A, int64_t lda, const dou
   p.tol = tol;
   p.norm = JACOBI_NORM_INF;
   p.x0_zero = X0 ? 0 : 1;
+  p.wait_ns = 4000000000ull;
   int grid = max_coresident_grid(false, Narrow::F32);
   const int64_t want = (n + kRows - 1) / kRows;
   if (grid <= 0) return JACOBI_ERR_CUDA;

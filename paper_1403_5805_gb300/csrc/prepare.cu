@@ -100,11 +100,22 @@ __device__ __forceinline__ __nv_fp8_e4m3 narrow_encode<__nv_fp8_e4m3>(float a32,
 
 // One CTA per row (grid-stride): narrow copy of the off-diagonal part of row i, padding zeroed up to
 // ldn, and the row factor of the inner sweep.
+__device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v, unsigned long long* sh) {
+  v = warp_max_u64(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) r = sh[w] > r ? sh[w] : r;
+  return r;
+}
+
 template <typename TL, bool kScaled>
 __global__ void narrow_kernel(const double* __restrict__ A, int64_t lda, int64_t n, TL* __restrict__ Nl,
                               int64_t ldn, const double* __restrict__ rinv, float* __restrict__ scale,
-                              float* __restrict__ rowfac) {
+                              float* __restrict__ rowfac, int* __restrict__ rexp) {
   __shared__ float sh[32];
+  __shared__ unsigned long long shb[32];
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const double* row = A + i * lda;
     float s = 1.0f;
@@ -117,13 +128,26 @@ __global__ void narrow_kernel(const double* __restrict__ A, int64_t lda, int64_t
       if (s == 0.0f) s = 1.0f;
     }
     TL* out = Nl + i * ldn;
+    unsigned long long mb = 0;  // max_j |a_ij| (all j, as IEEE bits)
     for (int64_t j = threadIdx.x; j < ldn; j += blockDim.x) {
       TL q;
-      if (j < n && j != i)
-        q = narrow_encode<TL>(__double2float_rn(row[j]), s);
-      else
+      if (j < n) {
+        const double a = row[j];
+        const unsigned long long b = abs_bits(a);
+        mb = b > mb ? b : mb;
+        q = j != i ? narrow_encode<TL>(__double2float_rn(a), s) : narrow_encode<TL>(0.0f, 1.0f);
+      } else {
         q = narrow_encode<TL>(0.0f, 1.0f);
+      }
       out[j] = q;
+    }
+    if (rexp) {
+      // exponent e with max_j |a_ij| < 2^e: the row scale of the split-float FP64 residual
+      mb = block_max_bits(mb, shb);
+      if (threadIdx.x == 0) {
+        const double mx = __longlong_as_double(static_cast<long long>(mb));
+        rexp[i] = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
+      }
     }
     if (threadIdx.x == 0) {
       if (kScaled) scale[i] = s;
@@ -168,20 +192,20 @@ cudaError_t launch_pad_zero(double* M, int64_t n, int64_t ld, cudaStream_t s) {
 }
 
 cudaError_t launch_narrow(Narrow kind, const double* A, int64_t lda, int64_t n, void* Nlow, int64_t ldn,
-                          const double* rinv, float* scale, float* rowfac, cudaStream_t s) {
+                          const double* rinv, float* scale, float* rowfac, int* rexp, cudaStream_t s) {
   const int blocks = prep_blocks(n, 1);
   switch (kind) {
     case Narrow::F32:
       narrow_kernel<float, false><<<blocks, kPrepThreads, 0, s>>>(A, lda, n, static_cast<float*>(Nlow), ldn, rinv,
-                                                                  scale, rowfac);
+                                                                  scale, rowfac, rexp);
       break;
     case Narrow::BF16:
       narrow_kernel<__nv_bfloat16, false><<<blocks, kPrepThreads, 0, s>>>(
-          A, lda, n, static_cast<__nv_bfloat16*>(Nlow), ldn, rinv, scale, rowfac);
+          A, lda, n, static_cast<__nv_bfloat16*>(Nlow), ldn, rinv, scale, rowfac, rexp);
       break;
     case Narrow::E4M3:
       narrow_kernel<__nv_fp8_e4m3, true><<<blocks, kPrepThreads, 0, s>>>(
-          A, lda, n, static_cast<__nv_fp8_e4m3*>(Nlow), ldn, rinv, scale, rowfac);
+          A, lda, n, static_cast<__nv_fp8_e4m3*>(Nlow), ldn, rinv, scale, rowfac, rexp);
       break;
   }
   return cudaGetLastError();

@@ -367,7 +367,7 @@ struct jacobi_server {
   Arena arena;
   double tol = 1e-10;
   int64_t max_iter = 5000;
-  int max_inner = 64, max_outer = 30;
+  int max_inner = 1000, max_outer = 30;
   float inner_rtol = 1.0f / 1024;
   int max_active = 0;
   int64_t next_id = 1;

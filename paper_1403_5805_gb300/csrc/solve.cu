@@ -42,6 +42,8 @@ struct Block {
   char* stages;
   volatile int* abort;   // CTA-wide abort flag (shared memory)
   int* gstatus;          // grid-wide status word (Ctl::status)
+  uint64_t wait_ns;      // limit of every wait
+  int drop_first;        // test only: announce ring item 0 without copying it
 };
 
 __device__ __forceinline__ void raise_abort(const Block& B) {
@@ -67,7 +69,9 @@ __device__ void produce_phase(const Block& B, uint32_t& u, const TM* M, int64_t 
       const uint32_t rbytes = static_cast<uint32_t>((wcols * static_cast<int64_t>(sizeof(TM)) + 15) & ~int64_t(15));
       int ok = 1;
       if (lane == 0) {
-        ok = (*B.abort == 0) && mbar_wait(&B.ring->empty[s], par);
+        // abort is re-read after the wait: consumers that gave up raise it before they release the stage,
+        // and a stage whose previous item never arrived must not be armed again
+        ok = (*B.abort == 0) && mbar_wait(&B.ring->empty[s], par, B.wait_ns) && (*B.abort == 0);
         if (ok) mbar_arrive_expect_tx(&B.ring->full[s], rbytes * static_cast<uint32_t>(rows));
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -75,7 +79,7 @@ __device__ void produce_phase(const Block& B, uint32_t& u, const TM* M, int64_t 
         if (lane == 0) raise_abort(B);
         return;
       }
-      if (lane < rows)
+      if (lane < rows && !(B.drop_first && u == 0))
         bulk_copy_g2s(B.stages + s * kStageBytes + lane * kRowBytes, M + (g0 + lane) * ld + j0, rbytes,
                       &B.ring->full[s]);
       ++u;
@@ -147,7 +151,7 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
       const int s = static_cast<int>(u % kStages);
       const uint32_t par = (u / kStages) & 1u;
       bool ok = (*B.abort == 0);
-      if (ok) ok = mbar_wait(&B.ring->full[s], par);
+      if (ok) ok = mbar_wait(&B.ring->full[s], par, B.wait_ns);
       if (!ok) {
         raise_abort(B);
       } else if (col < n && myrows > 0) {
@@ -191,10 +195,132 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
   }
 }
 
+// ---- FP64-accurate row dot products on FP32 units (split-float residual).
+// GB300 issues about 2 FP64 FMA per clock per SM, so an FP64 pass over A is bound by FP64 arithmetic
+// (8 bytes per FMA, ~4.8 TB/s).  The residual only needs FP64-level accuracy, not FP64 instructions:
+// each a_ij (scaled by 2^-e_i, e_i the exponent of the row maximum, so |a| < 1) is split with integer
+// operations into hi = its top 24 significant bits and lo = the next 23, x_j into two rounded FP32
+// words, and the products are accumulated as float-float: the rounding error of hi*hi is recovered
+// exactly with an FMA, the two cross products are added to it, and a two-sum (Knuth) keeps the running
+// sum as an unevaluated pair.  The representation error is below 2^-46 per element; the lane sums
+// leave FP32 as FP64 values scaled back by 2^e_i.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void split_scaled(double a, int sh, float& hi, float& lo) {
+  // branch-free: out-of-range parts (below FP32's normal range relative to the row maximum) become 0
+  const uint32_t hw = static_cast<uint32_t>(__double2hiint(a)), lw = static_cast<uint32_t>(__double2loint(a));
+  const int E = static_cast<int>((hw >> 20) & 0x7FFu) - sh;  // biased exponent of a * 2^-sh
+  const uint32_t sign = hw & 0x80000000u;
+  const int fe = E - 896;                                     // FP32 exponent field of hi
+  const float h = __uint_as_float(sign | (static_cast<uint32_t>(fe) << 23) | (__funnelshift_l(lw, hw, 3) & 0x7FFFFFu));
+  hi = fe > 0 ? h : 0.0f;
+  const uint32_t m23 = (lw >> 6) & 0x7FFFFFu;                 // mantissa bits 28..6: the next 23 bits
+  const float ml = __fsub_rn(__uint_as_float(0x4B000000u | m23), 8388608.0f);  // m23, exactly
+  const float p2 = __uint_as_float(static_cast<uint32_t>(max(E - 942, 0)) << 23);  // 2^(e - 46), or 0
+  lo = __uint_as_float(__float_as_uint(__fmul_rn(ml, p2)) | sign);
+}
+
+__device__ __forceinline__ void ff_fma(FF& s, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  const float e = __fmaf_rn(ah, xh, -p);  // exact error of the rounded product
+  const float t = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+  const float u = __fadd_rn(s.hi, p);  // two-sum of s.hi and p
+  const float v = __fsub_rn(u, s.hi);
+  const float w = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(u, v)), __fsub_rn(p, v));
+  s.hi = u;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(w, t));
+}
+
+// Same schedule as consume_phase<double> (ring items, warp layout, transposed reduction, epilogue),
+// with the split-float arithmetic above.
+template <typename Epi>
+__device__ void consume_phase_split(const Block& B, uint32_t& u, const double* x, int64_t n, int64_t r0,
+                                    int64_t r1, const int* rexp, double (*red)[kConsumerWarps][kRowsPerWarp],
+                                    Epi& epi) {
+  constexpr int V = 2;
+  constexpr int K = chunk_cols<double>();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cw = warp % kColWarps, rh = warp / kColWarps;
+  const int co = (cw * 32 + lane) * V;
+  const int64_t nch = (n + K - 1) / K;
+  int grp = 0;
+  for (int64_t g0 = r0; g0 < r1; g0 += kRows, ++grp) {
+    const int rows = static_cast<int>(i64min(kRows, r1 - g0));
+    const int myrows = rows - rh * kRowsPerWarp;
+    if (warp == 0 && lane < rows) epi.prefetch(g0 + lane);
+    int sh[kRowsPerWarp];
+    FF acc[kRowsPerWarp];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r) {
+      const int64_t row = g0 + rh * kRowsPerWarp + r;
+      sh[r] = r < myrows ? __ldg(rexp + row) : 0;
+      acc[r] = FF{0.0f, 0.0f};
+    }
+    double xv[V], xn[V];
+    if (nch > 0 && co < n) load_x(xv, x + co);
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t col = c * K + co;
+      const int64_t ncol = col + K;
+      if (c + 1 < nch && ncol < n) load_x(xn, x + ncol);
+      const int s = static_cast<int>(u % kStages);
+      const uint32_t par = (u / kStages) & 1u;
+      bool ok = (*B.abort == 0);
+      if (ok) ok = mbar_wait(&B.ring->full[s], par, B.wait_ns);
+      if (!ok) {
+        raise_abort(B);
+      } else if (col < n && myrows > 0) {
+        if (col + V > n) mask_tail(xv, col, n);
+        float xh[V], xl[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          xh[e] = __double2float_rn(xv[e]);
+          xl[e] = __double2float_rn(xv[e] - static_cast<double>(xh[e]));
+        }
+        const bool two = col + 1 < n;  // the straddling segment's padding element is skipped
+        const char* base = B.stages + s * kStageBytes + rh * kRowsPerWarp * kRowBytes + co * 8;
+#pragma unroll
+        for (int r = 0; r < kRowsPerWarp; ++r)
+          if (r < myrows) {
+            const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+            float ah, al;
+            split_scaled(__hiloint2double(static_cast<int>(m.y), static_cast<int>(m.x)), sh[r], ah, al);
+            ff_fma(acc[r], ah, al, xh[0], xl[0]);
+            if (two) {
+              split_scaled(__hiloint2double(static_cast<int>(m.w), static_cast<int>(m.z)), sh[r], ah, al);
+              ff_fma(acc[r], ah, al, xh[1], xl[1]);
+            }
+          }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.ring->empty[s]);
+      ++u;
+      xv[0] = xn[0];
+      xv[1] = xn[1];
+    }
+    double dv[kRowsPerWarp];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r)  // back to FP64, scaled by 2^sh (exact)
+      dv[r] = (static_cast<double>(acc[r].hi) + static_cast<double>(acc[r].lo)) *
+              __longlong_as_double(static_cast<long long>(1023 + sh[r]) << 52);
+    const double part = transpose_reduce8(dv, lane);
+    if ((lane & 3) == 0) red[grp & 1][warp][row_of_lane(lane)] = part;
+    named_barrier(1, kConsumers);
+    if (warp == 0 && lane < rows) {
+      const int half = lane / kRowsPerWarp, r = lane % kRowsPerWarp;
+      double dot = red[grp & 1][half * kColWarps][r];
+#pragma unroll
+      for (int w = 1; w < kColWarps; ++w) dot += red[grp & 1][half * kColWarps + w][r];
+      epi.row(g0 + lane, dot);
+    }
+  }
+}
+
 // Wait for every bulk copy this producer issued (the last kStages items) before the CTA exits.
 __device__ void drain_ring(const Block& B, uint32_t u_issued) {
   const uint32_t first = u_issued > kStages ? u_issued - kStages : 0;
-  for (uint32_t v = first; v < u_issued; ++v) mbar_wait(&B.ring->full[v % kStages], (v / kStages) & 1u);
+  for (uint32_t v = first; v < u_issued; ++v) mbar_wait(&B.ring->full[v % kStages], (v / kStages) & 1u, B.wait_ns);
 }
 
 __device__ __forceinline__ void init_ring(Ring* ring) {
@@ -217,7 +343,8 @@ __device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long
 
 // Publish this CTA's reduction values into slot (phase % 3), clear the slot of phase + 1, and wait at
 // the grid barrier.  Called by lane 0 of warp 0.  Returns false on timeout / remote error.
-__device__ bool publish_and_sync(Ctl* ctl, uint32_t phase, unsigned long long v0, unsigned long long v1) {
+__device__ bool publish_and_sync(Ctl* ctl, uint32_t phase, unsigned long long v0, unsigned long long v1,
+                                 uint64_t wait_ns) {
   const int slot = static_cast<int>(phase % 3);
   if (v0) atomicMax(&ctl->red[slot][0], v0);
   if (v1) atomicMax(&ctl->red[slot][1], v1);
@@ -226,7 +353,7 @@ __device__ bool publish_and_sync(Ctl* ctl, uint32_t phase, unsigned long long v0
     ctl->red[nxt][0] = 0ull;
     ctl->red[nxt][1] = 0ull;
   }
-  return grid_arrive_and_wait(&ctl->arrive, &ctl->status, (phase + 1) * gridDim.x);
+  return grid_arrive_and_wait(&ctl->arrive, &ctl->status, (phase + 1) * gridDim.x, wait_ns);
 }
 
 // Device-side trace (CTA 0, lane 0 of warp 0): end time of phase `phase` and its kind.
@@ -291,7 +418,7 @@ __global__ void __maxnreg__(kMaxRegs) fp64_solve_kernel(SolveParams p) {
   }
   init_ring(&ring);
   __syncthreads();
-  Block B{&ring, stages, &s_abort, &p.ctl->status};
+  Block B{&ring, stages, &s_abort, &p.ctl->status, p.wait_ns, p.test_drop_copy};
   const bool producer = threadIdx.x >= kConsumers;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -318,7 +445,7 @@ __global__ void __maxnreg__(kMaxRegs) fp64_solve_kernel(SolveParams p) {
       int ok = 1;
       if (lane == 0) {
         if (p.norm == JACOBI_NORM_2) p.part[(k & 1) * kMaxGrid + blockIdx.x] = sq;
-        ok = (s_abort == 0) && publish_and_sync(p.ctl, phase, p.norm == JACOBI_NORM_2 ? 0ull : mx, 0ull);
+        ok = (s_abort == 0) && publish_and_sync(p.ctl, phase, p.norm == JACOBI_NORM_2 ? 0ull : mx, 0ull, p.wait_ns);
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
       __syncwarp();  // order the other lanes' reads after lane 0's acquire of the grid barrier
@@ -456,7 +583,7 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
   }
   init_ring(&ring);
   __syncthreads();
-  Block B{&ring, stages, &s_abort, &p.ctl->status};
+  Block B{&ring, stages, &s_abort, &p.ctl->status, p.wait_ns, p.test_drop_copy};
   const bool producer = threadIdx.x >= kConsumers;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TL* Nl = static_cast<const TL*>(p.Nlow);
@@ -480,6 +607,8 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
       ResidEpi epi{p.b, p.rinv, p.c1, p.da, 0ull, 0ull, 0.0, 0.0};
       if (producer) {
         if (!skip_matrix) produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
+      } else if (p.rexp && !skip_matrix) {
+        consume_phase_split(B, u, xc, p.n, r0, r1, p.rexp, red64, epi);
       } else {
         consume_phase<double>(B, u, xc, p.n, r0, r1, !skip_matrix, red64, epi);
       }
@@ -500,7 +629,7 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
       v0 = warp_max_u64(v0);
       v1 = warp_max_u64(v1);
       int ok = 1;
-      if (lane == 0) ok = (s_abort == 0) && publish_and_sync(p.ctl, phase, v0, v1);
+      if (lane == 0) ok = (s_abort == 0) && publish_and_sync(p.ctl, phase, v0, v1, p.wait_ns);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (lane == 0) {
         trace_phase(p.ctl, phase,

@@ -85,6 +85,9 @@ struct SolveParams {
   int max_outer;
   int max_inner;
   float inner_rtol;
+  const int* rexp;        // IR: per-row scale exponent; non-NULL selects the split-float FP64 residual
+  uint64_t wait_ns;       // limit of every device-side wait (nanoseconds)
+  int test_drop_copy;     // test only: the first ring item is announced but never copied (a wait expires)
 };
 
 // Host launchers (solve.cu).  Each returns a cudaError_t from the launch.
@@ -102,8 +105,9 @@ cudaError_t launch_rhs(const double* B, int64_t n, double* b, unsigned long long
                        cudaStream_t s);
 // Narrow copy of the off-diagonal part of A (zero diagonal, zero padding up to ldn) and the FP32
 // per-row factor of the inner sweep.
+// rexp (may be NULL): per row, the exponent e with max_j |a_ij| < 2^e (the split-float residual's scale).
 cudaError_t launch_narrow(Narrow kind, const double* A, int64_t lda, int64_t n, void* Nlow, int64_t ldn,
-                          const double* rinv, float* scale, float* rowfac, cudaStream_t s);
+                          const double* rinv, float* scale, float* rowfac, int* rexp, cudaStream_t s);
 // Zero columns [n, ld) of an n x ld row-major FP64 matrix.
 cudaError_t launch_pad_zero(double* M, int64_t n, int64_t ld, cudaStream_t s);
 // Relative residual ||b - A x||_inf / ||b||_inf (FP64) into *rel_bits (zeroed before) as max bits of

@@ -220,3 +220,25 @@ def test_divergence_reports_nonfinite(jac):
         s.solve(max_iter=2000, tol=1e-12)
     assert e.value.status == jac.ERR_NONFINITE == ref.status
     assert s.last_stats().sweeps == ref.iters
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16_ir"])
+def test_bounded_wait_expires_and_context_stays_usable(jac, prec):
+    """Failure detection without a GPU fault: the first ring item of the solve is announced but never
+    copied, so the consumers' bounded wait (50 ms here) runs out; the kernel reports a timeout, drains its
+    copies and returns, and the next solve on the same context is correct."""
+    A, B, _ = synth.dominant_system(2048, 1.25, seed=3)
+    flags = jac.binding.FLAG_SHORT_WAITS | jac.binding.FLAG_TEST_DROP_COPY
+    bad = dev_solver(jac, A, B, precision=prec, flags=flags)
+    with pytest.raises(jac.JacobiError) as e:
+        bad.solve(max_iter=50, tol=1e-12 if prec == "fp64" else 1e-10)
+    assert e.value.status == jac.ERR_TIMEOUT
+    good = dev_solver(jac, A, B, precision=prec)
+    X, st = good.solve(max_iter=500, tol=1e-12 if prec == "fp64" else 1e-10)
+    assert st.status == 0
+    if prec == "fp64":
+        ref = oracle.jacobi(A, B, max_iter=500, tol=1e-12)
+        assert st.sweeps == ref.iters and rel_err(X.cpu().numpy(), ref.X[:, 0]) <= TOL_ITER
+    else:
+        _, rel = oracle.residual(A, B, X.cpu().numpy())
+        assert rel <= 1e-10

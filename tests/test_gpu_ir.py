@@ -118,3 +118,35 @@ def test_device_residual_entry_point(jac):
     x = torch.from_numpy(Xs[:, 0] + 1e-6).cuda()
     _, rel = oracle.residual(A, B, x.cpu().numpy())
     assert abs(s.residual(x) - rel) <= 1e-14 + 1e-9 * rel
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("gen,n,f", [("dom", 777, 1.1), ("hard", 1500, 1.1), ("dom", 4096, 1.05)])
+def test_split_float_residual_reaches_target(jac, prec, gen, n, f):
+    make = synth.dominant_system if gen == "dom" else synth.hard_system
+    A, B, _ = make(n, f, seed=70 + n)
+    s = dev_solver(jac, A, B, precision=prec, split_residual=True)
+    X, st = s.solve(max_iter=5000, tol=1e-10)
+    _, rel = oracle.residual(A, B, X.cpu().numpy())
+    assert st.status == 0 and rel <= 1e-10, (st.as_dict(), rel)
+    assert abs(st.rel_residual - rel) <= 5e-13 + 1e-3 * rel
+
+
+def test_split_float_residual_accuracy_with_wild_row_scales(jac):
+    """One residual evaluation of a given X0 (max_outer = 1): the split-float residual equals the oracle's
+    FP64 residual to ~1e-15 of ||A|| ||X||, on rows scaled by powers of two from 2^-300 to 2^+300 and an
+    X0 whose entries span many magnitudes."""
+    import torch
+    n = 1000
+    A, B, Xs = synth.dominant_system(n, 1.3, seed=91)
+    rng = np.random.default_rng(2)
+    scale = 2.0 ** rng.integers(-300, 300, n)
+    A = A * scale[:, None]
+    B = B * scale[:, None]
+    X0 = Xs[:, 0] * (1 + 1e-6 * rng.standard_normal(n))
+    X0[::7] *= 1e3
+    s = dev_solver(jac, A, B, precision="bf16_ir", split_residual=True, max_outer=1)
+    _, st = s.solve(X0=torch.from_numpy(X0).cuda(), max_iter=10, tol=1e-300)
+    assert st.outer_steps == 1 and st.sweeps == 0
+    _, rel = oracle.residual(A, B, X0)
+    assert abs(st.rel_residual - rel) <= 1e-12 * rel, (st.rel_residual, rel)
