@@ -34,7 +34,9 @@ METRIC = "solves/s at ||AX-B||/||B||<=1e-10 (BF16 inner sweeps + FP64 refinement
 TARGET = 1e-10
 ESIZE = {"fp64": 8, "fp32_ir": 4, "bf16_ir": 2, "fp8_ir": 1}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-SOLVE_SRC = os.path.join(ROOT, "paper_1403_5805_gb300", "csrc", "solve.cu")
+# the solve kernels' translation unit and every header it includes
+SOLVE_SRC = [os.path.join(ROOT, "paper_1403_5805_gb300", "csrc", f)
+             for f in ("solve.cu", "solver.cuh", "dot.cuh", "device_util.cuh")]
 
 
 def dist_env():
@@ -53,8 +55,11 @@ def measured_peaks():
 
 
 def src_hash():
-    with open(SOLVE_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in SOLVE_SRC:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def committed_traffic(kernel: str):
@@ -349,8 +354,8 @@ def run_many_rhs(args, jac, torch, dev):
     Xst = torch.from_numpy(np.ascontiguousarray(Xs.T)).to(dev)
     stream = torch.cuda.current_stream(dev)
     out = {"n": n, "nrhs": r, "dominance": 1.1}
-    for prec, steps in (("bf16_ir", args.mrhs_steps), ("fp64", 1)):
-        solver = jac.MultiSolver(At, Bt, precision=prec)
+    for prec, steps in (("bf16_ir", args.mrhs_steps), ("bf16_ir+split", args.mrhs_steps), ("fp64", 1)):
+        solver = jac.MultiSolver(At, Bt, precision=prec.replace("+split", ""), split_residual=prec.endswith("+split"))
         X, st = solver.solve(max_iter=5000, tol=TARGET if prec != "fp64" else args.fp64_tol)  # warm-up
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -362,7 +367,8 @@ def run_many_rhs(args, jac, torch, dev):
         ms = e0.elapsed_time(e1) / steps
         err = (X - Xst).abs().amax(dim=1)
         phases = {}
-        for kind, name, es, flop in ((3, "inner_tcgen05_bf16", 2, True), (1, "resid64_fp64", 8, True),
+        rname = "resid64_split_fp32" if prec.endswith("+split") else "resid64_fp64"
+        for kind, name, es, flop in ((3, "inner_tcgen05_bf16", 2, True), (1, rname, 8, True),
                                      (0, "sweep64_fp64", 8, True)):
             d = [(e - b) for k, b, e in solver.trace() if k == kind]
             if d:
@@ -375,15 +381,18 @@ def run_many_rhs(args, jac, torch, dev):
                      "max_err_vs_xstar_per_rhs": float(err.max().item()), "phases": phases}
         solver.close()
     out["mixed_vs_fp64_solves_ratio"] = round(out["bf16_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
+    out["mixed_split_vs_fp64_solves_ratio"] = round(
+        out["bf16_ir+split"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     return out
 
 
 def run_serve(args, jac, torch, dev, seconds):
     """Poisson arrivals at 2000 requests/s for `seconds` (n log-uniform in [256, 8192], r uniform in
     {1..16}, f uniform in [1.05, 1.5], FP64 inputs generated on the device at admission), served with
-    continuous batching under a 100 GB budget to a 1e-10 relative residual; latency from each request's
-    scheduled arrival to the moment its result is polled.  Beside it, the same trace's first
-    `serve_fp64_seconds` solved one request at a time by the plain FP64 path."""
+    continuous batching under a 100 GB budget to a 1e-10 relative residual, once with FP64 residual
+    rounds and once with split-float ones; latency from each request's scheduled arrival to the moment
+    its result is polled.  Beside them, the same trace's first `serve_fp64_seconds` solved one request at
+    a time by the plain FP64 path."""
     import time as _time
 
     import synth
@@ -391,53 +400,60 @@ def run_serve(args, jac, torch, dev, seconds):
     t, ns, rs, fs, seeds = synth.serving_trace(rate, seconds, seed=synth.BASE_SEED + 4)
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(min(100e9, free - 8e9))
-    srv = jac.Server(budget_bytes=budget)
-    outs, arrive, lat, stats = {}, {}, {}, {}
-    k = 0
-    total = len(t)
-    active_samples = []
-    t0 = _time.perf_counter()
-    while len(lat) < total:
-        now = _time.perf_counter() - t0
-        while k < total and t[k] <= now:
-            out = torch.empty(int(rs[k]), int(ns[k]), dtype=torch.float64, device=dev)
-            rid = srv.submit_generated(int(ns[k]), int(rs[k]), float(fs[k]), int(seeds[k]), out)
-            outs[rid] = (k, out)
-            arrive[rid] = t[k]
-            k += 1
-        active, pending = srv.step()
-        active_samples.append(active + pending)
-        done_t = _time.perf_counter() - t0
-        for rid, st in srv.poll():
-            lat[rid] = done_t - arrive[rid]
-            stats[rid] = (st.status, st.rel_residual, st.outer_steps, st.sweeps)
-            kk, out = outs[rid]
-            if kk % max(1, total // 16) == 0:  # keep a sample for the host-side check
-                outs[rid] = (kk, out)
-            else:
-                del outs[rid]
-        if k >= total and active == 0 and pending == 0 and len(lat) < total:
+
+    def served(split):
+        srv = jac.Server(budget_bytes=budget, split_residual=split)
+        outs, arrive, lat, stats = {}, {}, {}, {}
+        k = 0
+        total = len(t)
+        active_samples = []
+        t0 = _time.perf_counter()
+        while len(lat) < total:
+            now = _time.perf_counter() - t0
+            while k < total and t[k] <= now:
+                out = torch.empty(int(rs[k]), int(ns[k]), dtype=torch.float64, device=dev)
+                rid = srv.submit_generated(int(ns[k]), int(rs[k]), float(fs[k]), int(seeds[k]), out)
+                outs[rid] = (k, out)
+                arrive[rid] = t[k]
+                k += 1
+            active, pending = srv.step()
+            active_samples.append(active + pending)
+            done_t = _time.perf_counter() - t0
             for rid, st in srv.poll():
-                lat[rid] = _time.perf_counter() - t0 - arrive[rid]
-    wall = _time.perf_counter() - t0
-    rounds = srv.rounds()
-    srv.close()
-    L = np.array(sorted(lat.values())) * 1e3
-    ok = sum(1 for v in stats.values() if v[0] == 0)
-    worst = max(v[1] for v in stats.values())
-    # host check of sampled results (inputs regenerated from their seeds)
-    checked = []
-    for rid, (kk, out) in list(outs.items())[:8]:
-        A, B = synth.serving_request(int(ns[kk]), int(rs[kk]), float(fs[kk]), int(seeds[kk]))
-        X = out.cpu().numpy().T
-        R = B - A @ X
-        checked.append(float(np.max(np.abs(R).max(axis=0) / np.abs(B).max(axis=0))))
-    served = {"offered_rate": rate, "seconds": seconds, "requests": total, "converged": ok,
-              "throughput_per_s": round(total / wall, 1), "wall_s": round(wall, 3),
-              "p50_ms": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
-              "max_ms": round(float(L[-1]), 3), "rounds": rounds, "mean_in_system": round(float(np.mean(active_samples)), 1),
-              "worst_rel_residual": worst, "sampled_host_residuals_max": max(checked) if checked else None,
-              "budget_gb": round(budget / 1e9, 1)}
+                lat[rid] = done_t - arrive[rid]
+                stats[rid] = (st.status, st.rel_residual, st.outer_steps, st.sweeps)
+                kk, out = outs[rid]
+                if kk % max(1, total // 16) == 0:  # keep a sample for the host-side check
+                    outs[rid] = (kk, out)
+                else:
+                    del outs[rid]
+            if k >= total and active == 0 and pending == 0 and len(lat) < total:
+                for rid, st in srv.poll():
+                    lat[rid] = _time.perf_counter() - t0 - arrive[rid]
+        wall = _time.perf_counter() - t0
+        rounds = srv.rounds()
+        srv.close()
+        L = np.array(sorted(lat.values())) * 1e3
+        ok = sum(1 for v in stats.values() if v[0] == 0)
+        worst = max(v[1] for v in stats.values())
+        # host check of sampled results (inputs regenerated from their seeds)
+        checked = []
+        for rid, (kk, out) in list(outs.items())[:8]:
+            A, B = synth.serving_request(int(ns[kk]), int(rs[kk]), float(fs[kk]), int(seeds[kk]))
+            X = out.cpu().numpy().T
+            R = B - A @ X
+            checked.append(float(np.max(np.abs(R).max(axis=0) / np.abs(B).max(axis=0))))
+        return {"offered_rate": rate, "seconds": seconds, "requests": total, "converged": ok,
+                "throughput_per_s": round(total / wall, 1), "wall_s": round(wall, 3),
+                "p50_ms": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
+                "max_ms": round(float(L[-1]), 3), "rounds": rounds,
+                "mean_in_system": round(float(np.mean(active_samples)), 1),
+                "worst_rel_residual": worst, "sampled_host_residuals_max": max(checked) if checked else None,
+                "budget_gb": round(budget / 1e9, 1),
+                "residual": "split-float (FP32 units)" if split else "FP64"}
+
+    served_fp64_resid = served(False)
+    served_split = served(True)
 
     # the plain FP64 path, one request at a time, on the first seconds of the same trace
     m = int(np.searchsorted(t, args.serve_fp64_seconds))
@@ -463,9 +479,10 @@ def run_serve(args, jac, torch, dev, seconds):
             "throughput_per_s": round(m / wall64, 1) if m else None,
             "p50_ms": round(float(np.percentile(L64, 50)), 3) if m else None,
             "p99_ms": round(float(np.percentile(L64, 99)), 3) if m else None}
-    return {"served_fp32_ir": served, "one_at_a_time_fp64": fp64,
-            "throughput_ratio": round(served["throughput_per_s"] / fp64["throughput_per_s"], 2)
-            if fp64["throughput_per_s"] else None}
+    ratio = (lambda a: round(a["throughput_per_s"] / fp64["throughput_per_s"], 2) if fp64["throughput_per_s"] else None)
+    return {"served_fp32_ir": served_fp64_resid, "served_fp32_ir_split_residual": served_split,
+            "one_at_a_time_fp64": fp64, "throughput_ratio": ratio(served_fp64_resid),
+            "throughput_ratio_split_residual": ratio(served_split)}
 
 
 def run_hard(args, jac, torch, dev, ws):

@@ -138,11 +138,13 @@ typedef struct jacobi_desc {
 } jacobi_desc;
 
 #define JACOBI_FLAG_COPY_A 1 /* always copy A into the workspace (never borrow it) */
-/* IR precisions: compute the FP64 residual r = B - A X with split-float arithmetic on the FP32 units
- * (each a_ij as two FP32 words after a per-row power-of-two scale, products with exact FMA errors,
- * float-float sums, FP64 combination across lanes) instead of FP64 FMAs.  Accuracy ~2^-46 relative
- * per product; GB300's FP64 FMA rate makes the FP64-instruction residual arithmetic-bound.  Requires
- * |x_j| within FP32 range. */
+/* IR precisions (one or many right-hand sides): compute the FP64 residual r = B - A X with split-float
+ * arithmetic on the FP32 units (each a_ij as two FP32 words after a per-row power-of-two scale, each
+ * x_j as two FP32 words after a power-of-two scale of its column, products with exact FMA errors,
+ * float-float sums, FP64 combination at the end) instead of FP64 FMAs.  Accuracy ~2^-46 relative per
+ * product; GB300's FP64 FMA rate makes the FP64-instruction residual arithmetic-bound.  The column
+ * scale comes from max_i |b_i / a_ii| (one right-hand side) or from max_i |x_ic| of each residual's X
+ * (many), so X may have any magnitude that stays within 2^100 of that scale. */
 #define JACOBI_FLAG_SPLIT_RESIDUAL 2
 /* Every device-side wait of this handle's solves gives up after 50 ms instead of 4 s. */
 #define JACOBI_FLAG_SHORT_WAITS 4
@@ -289,7 +291,7 @@ typedef struct jacobi_server_desc {
   int32_t max_outer;    /* cap on residual evaluations per request (0: 30) */
   double inner_rtol;    /* inner stop: max|change| <= inner_rtol * max|delta| (0: 2^-10) */
   int32_t max_active;   /* cap on concurrently active requests (0: only the budget limits) */
-  int32_t reserved;
+  int32_t flags;        /* JACOBI_FLAG_SPLIT_RESIDUAL: split-float residual rounds (see jacobi_desc) */
   void* stream;         /* cudaStream_t of every round (NULL: legacy default stream) */
 } jacobi_server_desc;
 

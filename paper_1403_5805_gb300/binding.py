@@ -61,7 +61,7 @@ class JacobiBatchDesc(ctypes.Structure):
 class JacobiServerDesc(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("max_inner", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
-                ("max_active", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("max_active", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class JacobiDesc(ctypes.Structure):
@@ -379,7 +379,7 @@ class MultiSolver:
     float64 CUDA tensors (row c is right-hand side c, i.e. column-major n x r)."""
 
     def __init__(self, A, B, precision: str = "bf16_ir", stream=None, max_outer: int = 0, max_inner: int = 0,
-                 inner_rtol: float = 0.0, norm: str = "inf"):
+                 inner_rtol: float = 0.0, norm: str = "inf", split_residual: bool = False):
         import torch
         lib = load()
         n = A.shape[0]
@@ -397,6 +397,7 @@ class MultiSolver:
         d.B, d.ldb = B.data_ptr(), B.stride(0)
         d.stream = self.stream.cuda_stream
         d.max_outer, d.max_inner, d.inner_rtol = max_outer, max_inner, inner_rtol
+        d.flags = FLAG_SPLIT_RESIDUAL if split_residual else 0
         nbytes = ctypes.c_size_t(0)
         with torch.cuda.device(A.device):
             _check(lib.jacobi_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_workspace_size")
@@ -453,12 +454,13 @@ class Server:
     """``jacobi_server_*``: continuous batching of independent requests (see include/jacobi.h)."""
 
     def __init__(self, budget_bytes: int, tol: float = 1e-10, max_active: int = 0, inner_rtol: float = 0.0,
-                 max_inner: int = 0, max_outer: int = 0, stream=None):
+                 max_inner: int = 0, max_outer: int = 0, stream=None, split_residual: bool = False):
         import torch
         lib = load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         d = JacobiServerDesc()
         d.budget_bytes, d.tol, d.max_active = budget_bytes, tol, max_active
+        d.flags = FLAG_SPLIT_RESIDUAL if split_residual else 0
         d.inner_rtol, d.max_inner, d.max_outer = inner_rtol, max_inner, max_outer
         d.stream = self.stream.cuda_stream
         self._h = ctypes.c_void_p()

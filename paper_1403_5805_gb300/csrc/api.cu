@@ -69,7 +69,8 @@ bool can_borrow(const jacobi_desc* d) {
 // Offsets of every sub-buffer inside one workspace allocation.
 struct Layout {
   int64_t ld;  // padded length of vectors and row stride of owned matrices
-  size_t A64, Nlow, b, d, rinv, bnorm, rowfac, scale, rexp, xa, xb, xout, c1, da, db, part, ctl, keys, stats, total;
+  size_t A64, Nlow, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, ctl, keys, stats,
+      total;
 };
 
 Layout make_layout(int64_t n, int precision, bool copy_A) {
@@ -90,11 +91,14 @@ Layout make_layout(int64_t n, int precision, bool copy_A) {
   L.d = take(vd);
   L.rinv = take(vd);
   L.bnorm = take(sizeof(double));
+  L.cmax = take(sizeof(double));
   L.rowfac = take(vf);
   L.scale = take(vf);
   L.rexp = take(static_cast<size_t>(L.ld) * sizeof(int));
   L.xa = take(vd);
   L.xb = take(vd);
+  L.xsa = take(2 * vf);  // (hi, lo) FP32 words of xa / xb for the split-float residual
+  L.xsb = take(2 * vf);
   L.xout = take(vd);
   L.c1 = take(vf);
   L.da = take(vf);
@@ -124,7 +128,7 @@ int validate_desc(const jacobi_desc* d) {
 
 // Extra device buffers of a many-right-hand-side handle (vectors v[c*ld + i]).
 struct MrhsLayout {
-  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, bcol, stats, status, total;
+  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, bcol, stats, status, xs, xexp, total;
 };
 
 MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
@@ -149,6 +153,8 @@ MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
   M.bcol = take(static_cast<size_t>(r) * 8);
   M.stats = take(16);
   M.status = take(16);
+  M.xs = take(v8);  // split-float residual: two FP32 words per entry of X
+  M.xexp = take(static_cast<size_t>(r) * 4);
   M.total = o;
   return M;
 }
@@ -206,23 +212,27 @@ int prepare(jacobi_handle* h, const double* A, int64_t lda, const double* B, boo
   unsigned long long* keys = h->at<unsigned long long>(h->L.keys);
   CK(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long), s));       // diagonal-check key
   CK(cudaMemsetAsync(h->at<char>(h->L.bnorm), 0, sizeof(double), s));   // ||B|| bits
+  CK(cudaMemsetAsync(h->at<char>(h->L.cmax), 0, sizeof(double), s));    // max |b_i / a_ii| bits
   CK(launch_diag(h->A64, h->lda64, n, h->at<double>(h->L.d), h->at<double>(h->L.rinv), keys, s));
   double* b = h->at<double>(h->L.b);
   if (B != b && !is_device_memory(B)) {
     CK(cudaMemcpyAsync(b, B, n * sizeof(double), cudaMemcpyHostToDevice, s));
     B = b;
   }
-  CK(launch_rhs(B, n, b, h->at<unsigned long long>(h->L.bnorm), s));
+  CK(launch_rhs(B, n, h->at<double>(h->L.rinv), b, h->at<unsigned long long>(h->L.bnorm),
+                h->at<unsigned long long>(h->L.cmax), s));
   // vectors start zeroed so that every padding entry is 0
   CK(cudaMemsetAsync(h->at<char>(h->L.xa), 0, h->L.ld * sizeof(double), s));
   CK(cudaMemsetAsync(h->at<char>(h->L.xb), 0, h->L.ld * sizeof(double), s));
+  CK(cudaMemsetAsync(h->at<char>(h->L.xsa), 0, h->L.ld * sizeof(float2), s));
+  CK(cudaMemsetAsync(h->at<char>(h->L.xsb), 0, h->L.ld * sizeof(float2), s));
   CK(cudaMemsetAsync(h->at<char>(h->L.c1), 0, h->L.ld * sizeof(float), s));
   CK(cudaMemsetAsync(h->at<char>(h->L.da), 0, h->L.ld * sizeof(float), s));
   CK(cudaMemsetAsync(h->at<char>(h->L.db), 0, h->L.ld * sizeof(float), s));
   if (h->precision != JACOBI_FP64)
     CK(launch_narrow(narrow_kind(h->precision), h->A64, h->lda64, n, h->at<void>(h->L.Nlow), h->L.ld,
                      h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac),
-                     h->at<int>(h->L.rexp), s));
+                     h->split_residual ? h->at<int>(h->L.rexp) : nullptr, s));
   unsigned long long key = 0;
   CK(cudaMemcpyAsync(&key, keys, sizeof(key), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -259,7 +269,7 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   h->max_inner = d->max_inner > 0 ? d->max_inner : 1000;
   h->inner_rtol = static_cast<float>(
       d->inner_rtol > 0 ? d->inner_rtol : (d->precision == JACOBI_FP8_IR ? 1.0 / 64 : 1.0 / 1024));
-  h->split_residual = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) && d->precision != JACOBI_FP64 && d->nrhs == 1;
+  h->split_residual = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) && d->precision != JACOBI_FP64;
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
   h->test_drop_copy = (d->flags & JACOBI_FLAG_TEST_DROP_COPY) ? 1 : 0;
   if (d->workspace) {
@@ -367,7 +377,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
       CK(cudaMemsetAsync(colmax, 0, static_cast<size_t>(r) * 8, s));
       const int resid = h->norm == JACOBI_NORM_RESID;
       MrhsDenseParams p{n, r, ld, h->lda64, 1, resid, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
-                        h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax};
+                        h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax, nullptr, nullptr, nullptr};
       CK(launch_mrhs_dense(p, s));
       clk.mark(JACOBI_PHASE_SWEEP64);
       CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
@@ -411,7 +421,13 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
         clk.mark(JACOBI_PHASE_RESID0);
       } else {
         MrhsDenseParams p{n, r, ld, h->lda64, 0, 0, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
-                          h->at<double>(h->L.rinv), c1, dA, hA, nullptr, colmax};
+                          h->at<double>(h->L.rinv), c1, dA, hA, nullptr, colmax, nullptr, nullptr, nullptr};
+        if (h->split_residual) {
+          p.rexp = h->at<int>(h->L.rexp);
+          p.xs = h->at<float2>(h->M.xs);
+          p.xexp = h->at<int>(h->M.xexp);
+          CK(launch_mrhs_split_x(n, r, ld, xc, h->at<float2>(h->M.xs), h->at<int>(h->M.xexp), s));
+        }
         CK(launch_mrhs_dense(p, s));
         clk.mark(JACOBI_PHASE_RESID64);
       }
@@ -559,10 +575,13 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
   CK(cudaMemsetAsync(h->at<char>(h->L.ctl), 0, sizeof(Ctl), s));
-  if (X0)
+  if (X0) {
     CK(cudaMemcpyAsync(h->at<double>(h->L.xa), X0, n * sizeof(double), cudaMemcpyDefault, s));
-  else
+    if (h->split_residual)
+      CK(launch_split_x(h->at<double>(h->L.xa), n, h->at<unsigned long long>(h->L.cmax), h->at<float2>(h->L.xsa), s));
+  } else {
     CK(cudaMemsetAsync(h->at<char>(h->L.xa), 0, n * sizeof(double), s));
+  }
   SolveParams p{};
   p.n = n;
   p.A = h->A64;
@@ -576,6 +595,8 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
   p.bnorm = h->at<double>(h->L.bnorm);
   p.xa = h->at<double>(h->L.xa);
   p.xb = h->at<double>(h->L.xb);
+  p.xsa = h->split_residual ? h->at<float2>(h->L.xsa) : nullptr;
+  p.xsb = h->split_residual ? h->at<float2>(h->L.xsb) : nullptr;
   p.c1 = h->at<float>(h->L.c1);
   p.da = h->at<float>(h->L.da);
   p.db = h->at<float>(h->L.db);
@@ -591,6 +612,7 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
   p.max_inner = h->max_inner;
   p.inner_rtol = h->inner_rtol;
   p.rexp = h->split_residual ? h->at<int>(h->L.rexp) : nullptr;
+  p.cmax = h->at<unsigned long long>(h->L.cmax);
   p.wait_ns = h->wait_ns;
   p.test_drop_copy = h->test_drop_copy;
   cudaError_t e = h->precision == JACOBI_FP64 ? launch_fp64_solve(p, h->grid, s)

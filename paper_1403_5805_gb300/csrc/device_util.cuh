@@ -117,9 +117,11 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 // Order-free, NaN-propagating maximum of non-negative doubles: as unsigned 64-bit integers, the IEEE
 // encodings of +0 .. +inf are increasing and every positive NaN is above +inf.
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
-  return static_cast<unsigned long long>(__double_as_longlong(fabs(v)));
+  return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
 }
 __device__ __forceinline__ unsigned long long abs_bits(float v) { return abs_bits(static_cast<double>(v)); }
+
+
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll

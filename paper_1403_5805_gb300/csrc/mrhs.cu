@@ -20,6 +20,7 @@
 
 #include "device_util.cuh"
 #include "mrhs.cuh"
+#include "splitfloat.cuh"
 
 namespace jac {
 namespace {
@@ -314,6 +315,127 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
   }
 }
 
+// ------------------------------------------------- split-float residual pass (FP32 units), all r columns
+// R = B - A X with the split-float arithmetic of splitfloat.cuh: tiles of A are split (row scale 2^-e_i)
+// as they are staged into shared memory, X arrives as two FP32 words per entry (column scale 2^-g_c),
+// and every product is accumulated float-float.  The tile schedule is the FP64 pass's: 64 rows x 16 NC
+// columns per CTA, each thread 4 rows x NC columns.  Writes what mode 0 of the FP64 pass writes.
+template <int NC>
+__global__ void __launch_bounds__(kDThreads, 2) mrhs_split_resid_kernel(MrhsDenseParams p) {
+  constexpr int kN = 16 * NC;
+  __shared__ float Ah[kDK][kDM + 1], Al[kDK][kDM + 1];
+  __shared__ float Xh[kDK][kN + 1], Xl[kDK][kN + 1];
+  __shared__ int sh_row[kDM], g_col[kN];
+  const int tid = threadIdx.x;
+  const int tr = tid / 16, tc = tid % 16;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kDM;
+  const int c0 = blockIdx.y * kN;
+  if (tid < kDM) sh_row[tid] = m0 + tid < p.n ? p.rexp[m0 + tid] : 0;
+  if (tid < kN) g_col[tid] = c0 + tid < p.r ? p.xexp[c0 + tid] : 0;
+  __syncthreads();
+  FF acc[4][NC];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < NC; ++b) acc[a][b] = FF{0.0f, 0.0f};
+  for (int64_t k0 = 0; k0 < p.n; k0 += kDK) {
+    for (int e = tid; e < kDM * kDK; e += kDThreads) {
+      const int m = e / kDK, k = e % kDK;
+      const int64_t gi = m0 + m, gk = k0 + k;
+      const double a = (gi < p.n && gk < p.n) ? __ldg(p.A + gi * p.lda + gk) : 0.0;
+      float hi, lo;
+      split_scaled(a, sh_row[m], hi, lo);
+      Ah[k][m] = hi;
+      Al[k][m] = lo;
+    }
+    for (int e = tid; e < kDK * kN; e += kDThreads) {
+      const int c = e / kDK, k = e % kDK;
+      const int64_t gk = k0 + k;
+      const float2 v = (gk < p.n && c0 + c < p.r) ? __ldg(p.xs + static_cast<int64_t>(c0 + c) * p.ld + gk)
+                                                 : make_float2(0.0f, 0.0f);
+      Xh[k][c] = v.x;
+      Xl[k][c] = v.y;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kDK; ++k) {
+      float ah[4], al[4], xh[NC], xl[NC];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ah[u] = Ah[k][tr + 16 * u];
+        al[u] = Al[k][tr + 16 * u];
+      }
+#pragma unroll
+      for (int v = 0; v < NC; ++v) {
+        xh[v] = Xh[k][tc + 16 * v];
+        xl[v] = Xl[k][tc + 16 * v];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < NC; ++v) ff_fma(acc[u][v], ah[u], al[u], xh[v], xl[v]);
+      if ((k & 7) == 7) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < NC; ++v) ff_renorm(acc[u][v]);
+      }
+    }
+    __syncthreads();
+  }
+  unsigned long long mloc[NC];
+#pragma unroll
+  for (int v = 0; v < NC; ++v) mloc[v] = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = m0 + tr + 16 * u;
+    if (i >= p.n) continue;
+    const double ri = p.rinv[i];
+    const double si = pow2(sh_row[tr + 16 * u]);
+#pragma unroll
+    for (int v = 0; v < NC; ++v) {
+      const int c = c0 + tc + 16 * v;
+      if (c >= p.r) continue;
+      const int64_t o = static_cast<int64_t>(c) * p.ld + i;
+      const double dot =
+          (static_cast<double>(acc[u][v].hi) + static_cast<double>(acc[u][v].lo)) * si * pow2(g_col[tc + 16 * v]);
+      const double r = p.b[o] - dot;
+      const float cc = static_cast<float>(r * ri);
+      p.c1[o] = cc;
+      p.d1[o] = cc;
+      p.d1h[o] = __float2bfloat16_rn(cc);
+      const unsigned long long bits = abs_bits(r);
+      mloc[v] = bits > mloc[v] ? bits : mloc[v];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NC; ++v) {
+    const int c = c0 + tc + 16 * v;
+    if (c < p.r && mloc[v]) atomicMax(p.colmax + c, mloc[v]);
+  }
+}
+
+// One CTA per column: g_c = split exponent of max_i |x_ic|, then xs = the two FP32 words of x 2^-g_c.
+__global__ void mrhs_split_x_kernel(int64_t n, int64_t ld, const double* __restrict__ x, float2* __restrict__ xs,
+                                    int* __restrict__ xexp) {
+  __shared__ unsigned long long sh[32];
+  const int64_t c = blockIdx.x;
+  const double* col = x + c * ld;
+  unsigned long long m = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long b = abs_bits(col[i]);
+    m = b > m ? b : m;
+  }
+  m = warp_max_u64(m);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  unsigned long long t = 0;
+  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t = sh[w] > t ? sh[w] : t;
+  const int g = split_exponent(t);
+  if (threadIdx.x == 0) xexp[c] = g;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[c * ld + i] = split_x(col[i], g);
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -397,8 +519,25 @@ cudaError_t launch_mrhs_sweep(const void* Nlow, const void* dh, const MrhsSweepP
 }
 
 cudaError_t launch_mrhs_dense(const MrhsDenseParams& p, cudaStream_t s) {
+  if (p.xs && p.mode == 0) {
+    const int nc = p.r <= 16 ? 1 : (p.r <= 32 ? 2 : 4);
+    const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM), static_cast<unsigned>((p.r + 16 * nc - 1) / (16 * nc)));
+    if (nc == 1)
+      mrhs_split_resid_kernel<1><<<grid, kDThreads, 0, s>>>(p);
+    else if (nc == 2)
+      mrhs_split_resid_kernel<2><<<grid, kDThreads, 0, s>>>(p);
+    else
+      mrhs_split_resid_kernel<4><<<grid, kDThreads, 0, s>>>(p);
+    return cudaGetLastError();
+  }
   const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM), static_cast<unsigned>((p.r + kDN - 1) / kDN));
   mrhs_dense_kernel<<<grid, kDThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mrhs_split_x(int64_t n, int64_t r, int64_t ld, const double* x, float2* xs, int* xexp,
+                                cudaStream_t s) {
+  mrhs_split_x_kernel<<<static_cast<unsigned>(r), 256, 0, s>>>(n, ld, x, xs, xexp);
   return cudaGetLastError();
 }
 

@@ -22,9 +22,9 @@ struct MrhsSweepParams {
   int* status;              // set to a timeout code if a bounded wait expires
 };
 
-// FP64 pass over A for all r columns.  mode 0: residual R = B - A X -> c1 = R / a_ii, d1 = c1 (FP32 and
-// BF16), colmax[c] = max_i |R_ic|.  mode 1: Jacobi sweep xn = (B - A x + a_ii x) / a_ii, colmax[c] =
-// max_i |xn - x|.
+// FP64 pass over A for all r columns (the split-float residual when xs is set).  mode 0: residual
+// R = B - A X -> c1 = R / a_ii, d1 = c1 (FP32 and BF16), colmax[c] = max_i |R_ic|.  mode 1: Jacobi sweep
+// xn = (B - A x + a_ii x) / a_ii, colmax[c] = max_i |xn - x|.
 struct MrhsDenseParams {
   int64_t n, r, ld, lda;
   int mode;
@@ -39,6 +39,11 @@ struct MrhsDenseParams {
   __nv_bfloat16* d1h;
   double* xn;
   unsigned long long* colmax;
+  // split-float residual (mode 0 only; NULL xs selects the FP64 pass): per-row scale exponents of A,
+  // the two FP32 words of x 2^-g_c per entry, and the column exponents g_c
+  const int* rexp;
+  const float2* xs;
+  const int* xexp;
 };
 
 bool mrhs_supported_r(int64_t r);
@@ -46,6 +51,9 @@ bool mrhs_supported_r(int64_t r);
 // row pitch ld) and launches one sweep.
 cudaError_t launch_mrhs_sweep(const void* Nlow, const void* dh, const MrhsSweepParams& p, cudaStream_t s);
 cudaError_t launch_mrhs_dense(const MrhsDenseParams& p, cudaStream_t s);
+// xs[c*ld + i] = the two FP32 words of x_ic 2^-g_c, xexp[c] = g_c (the split exponent of max_i |x_ic|).
+cudaError_t launch_mrhs_split_x(int64_t n, int64_t r, int64_t ld, const double* x, float2* xs, int* xexp,
+                                cudaStream_t s);
 // Residual of the zero start vector (R = B): c1 = B / a_ii, d1 = c1 (FP32, BF16), colmax = max |B|.
 cudaError_t launch_mrhs_init(int64_t n, int64_t r, int64_t ld, const double* b, const double* rinv, float* c1,
                              float* d1, __nv_bfloat16* d1h, unsigned long long* colmax, cudaStream_t s);

@@ -113,7 +113,7 @@ extern "C" int jacobi_solve_fp64_noalloc(const double* A, int64_t lda, const dou
   NA_CK(cudaMemsetAsync(bnorm, 0, sizeof(double), s));
   NA_CK(launch_diag(A, lda, n, d, rinv, key, s));
   // b is read straight from the caller's B (the kernel only takes ||B|| when source == destination)
-  NA_CK(launch_rhs(B, n, const_cast<double*>(B), reinterpret_cast<unsigned long long*>(bnorm), s));
+  NA_CK(launch_rhs(B, n, nullptr, const_cast<double*>(B), reinterpret_cast<unsigned long long*>(bnorm), nullptr, s));
   unsigned long long host_key = 0;
   NA_CK(cudaMemcpyAsync(&host_key, key, sizeof(host_key), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));

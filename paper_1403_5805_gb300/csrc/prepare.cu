@@ -15,6 +15,7 @@
 
 #include "device_util.cuh"
 #include "solver.cuh"
+#include "splitfloat.cuh"
 
 namespace jac {
 namespace {
@@ -43,17 +44,26 @@ __global__ void diag_kernel(const double* __restrict__ A, int64_t lda, int64_t n
   }
 }
 
-__global__ void rhs_kernel(const double* __restrict__ B, int64_t n, double* __restrict__ b,
-                           unsigned long long* bnorm_bits) {
-  unsigned long long m = 0;
+// b = B, ||b||_inf, and (if cmax_bits) max_i |b_i / a_ii|, the iterate's scale for the split-float residual.
+__global__ void rhs_kernel(const double* __restrict__ B, int64_t n, const double* __restrict__ rinv,
+                           double* __restrict__ b, unsigned long long* bnorm_bits, unsigned long long* cmax_bits) {
+  unsigned long long m = 0, c = 0;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const double v = B[i];
     if (b != B) b[i] = v;
     const unsigned long long bits = abs_bits(v);
     m = bits > m ? bits : m;
+    if (cmax_bits) {
+      const unsigned long long cb = abs_bits(v * rinv[i]);
+      c = cb > c ? cb : c;
+    }
   }
   m = warp_max_u64(m);
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(bnorm_bits, m);
+  c = warp_max_u64(c);
+  if ((threadIdx.x & 31) == 0) {
+    if (m) atomicMax(bnorm_bits, m);
+    if (c) atomicMax(cmax_bits, c);  // c stays 0 without cmax_bits
+  }
 }
 
 __global__ void pad_zero_kernel(double* M, int64_t n, int64_t ld) {
@@ -62,98 +72,140 @@ __global__ void pad_zero_kernel(double* M, int64_t n, int64_t ld) {
     for (int64_t j = threadIdx.x; j < w; j += blockDim.x) M[i * ld + n + j] = 0.0;
 }
 
-__device__ __forceinline__ float block_max_abs(float v, float* sh) {
-  // non-negative floats: the IEEE encodings order like unsigned integers
-  unsigned int u = __float_as_uint(v);
+// Four narrow values stored with one instruction (4 x 1, 2 or 4 bytes; the destination is aligned to it
+// because ldn is a multiple of 16 and j a multiple of 4).
+template <typename TL>
+struct alignas(4 * sizeof(TL)) Quad {
+  TL v[4];
+};
+
+// Elements [j, j + 4) of a row; entries at or past n read as 0 and are never loaded (a borrowed A's row
+// padding may hold anything).  Rows start 16-byte aligned (borrowed A: aligned base, even lda).
+__device__ __forceinline__ void load_quad(const double* row, int64_t j, int64_t n, double (&a)[4]) {
+  if (j + 4 <= n) {
+    const double2 v0 = __ldcs(reinterpret_cast<const double2*>(row + j));
+    const double2 v1 = __ldcs(reinterpret_cast<const double2*>(row + j + 2));
+    a[0] = v0.x;
+    a[1] = v0.y;
+    a[2] = v1.x;
+    a[3] = v1.y;
+  } else {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned int w = __shfl_xor_sync(0xffffffffu, u, o);
-    u = w > u ? w : u;
+    for (int e = 0; e < 4; ++e) a[e] = j + e < n ? row[j + e] : 0.0;
   }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = __uint_as_float(u);
-  __syncthreads();
-  unsigned int r = 0;
-  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
-    const unsigned int x = __float_as_uint(sh[w]);
-    r = x > r ? x : r;
-  }
-  return __uint_as_float(r);
+}
+
+// fl32(a_ij) of the quad, 0 on the diagonal and past n.
+__device__ __forceinline__ void quad_f32(const double (&a)[4], int64_t j, int64_t n, int64_t i, float (&f)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) f[e] = (j + e < n && j + e != i) ? __double2float_rn(a[e]) : 0.0f;
 }
 
 template <typename TL>
-__device__ __forceinline__ TL narrow_encode(float a32, float s);
+__device__ __forceinline__ void encode_quad(const float (&f)[4], float s, TL* dst);
 template <>
-__device__ __forceinline__ float narrow_encode<float>(float a32, float) {
-  return a32;
+__device__ __forceinline__ void encode_quad<float>(const float (&f)[4], float, float* dst) {
+  *reinterpret_cast<float4*>(dst) = make_float4(f[0], f[1], f[2], f[3]);
 }
 template <>
-__device__ __forceinline__ __nv_bfloat16 narrow_encode<__nv_bfloat16>(float a32, float) {
-  return __float2bfloat16_rn(a32);
+__device__ __forceinline__ void encode_quad<__nv_bfloat16>(const float (&f)[4], float, __nv_bfloat16* dst) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(f[0], f[1]);  // round to nearest even, pairwise
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(f[2], f[3]);
+  uint2 w;
+  w.x = *reinterpret_cast<const uint32_t*>(&lo);
+  w.y = *reinterpret_cast<const uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(dst) = w;
 }
 template <>
-__device__ __forceinline__ __nv_fp8_e4m3 narrow_encode<__nv_fp8_e4m3>(float a32, float s) {
-  __nv_fp8_e4m3 q;
-  q.__x = __nv_cvt_float_to_fp8(__fdiv_rn(a32, s), __NV_SATFINITE, __NV_E4M3);
-  return q;
+__device__ __forceinline__ void encode_quad<__nv_fp8_e4m3>(const float (&f)[4], float s, __nv_fp8_e4m3* dst) {
+  // saturating round-to-nearest-even E4M3 of fl32(a_ij) / s_i (FP32 division)
+  const __nv_fp8x2_storage_t lo =
+      __nv_cvt_float2_to_fp8x2(make_float2(__fdiv_rn(f[0], s), __fdiv_rn(f[1], s)), __NV_SATFINITE, __NV_E4M3);
+  const __nv_fp8x2_storage_t hi =
+      __nv_cvt_float2_to_fp8x2(make_float2(__fdiv_rn(f[2], s), __fdiv_rn(f[3], s)), __NV_SATFINITE, __NV_E4M3);
+  *reinterpret_cast<uint32_t*>(dst) = static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
 }
 
-// One CTA per row (grid-stride): narrow copy of the off-diagonal part of row i, padding zeroed up to
-// ldn, and the row factor of the inner sweep.
-__device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v, unsigned long long* sh) {
-  v = warp_max_u64(v);
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
   __syncthreads();
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  unsigned long long r = 0;
+  T r = 0;
   for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) r = sh[w] > r ? sh[w] : r;
   return r;
 }
 
+// One CTA per row (grid-stride over rows): narrow copy of the off-diagonal part of row i, padding
+// zeroed up to ldn, the row factor of the inner sweep and (if rexp) the row's split-float scale
+// exponent.  Each thread converts 4 consecutive elements per step: two 16-byte loads, one store.
 template <typename TL, bool kScaled>
-__global__ void narrow_kernel(const double* __restrict__ A, int64_t lda, int64_t n, TL* __restrict__ Nl,
-                              int64_t ldn, const double* __restrict__ rinv, float* __restrict__ scale,
-                              float* __restrict__ rowfac, int* __restrict__ rexp) {
-  __shared__ float sh[32];
+__global__ void __launch_bounds__(kPrepThreads) narrow_kernel(const double* __restrict__ A, int64_t lda, int64_t n,
+                                                              TL* __restrict__ Nl, int64_t ldn,
+                                                              const double* __restrict__ rinv,
+                                                              float* __restrict__ scale, float* __restrict__ rowfac,
+                                                              int* __restrict__ rexp) {
+  __shared__ unsigned int shs[32];
   __shared__ unsigned long long shb[32];
+  const int64_t step = 4 * int64_t(blockDim.x);
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const double* row = A + i * lda;
     float s = 1.0f;
     if (kScaled) {
-      float m = 0.0f;
-      for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
-        if (j != i) m = fmaxf(m, fabsf(__double2float_rn(row[j])));
-      m = block_max_abs(m, sh);
-      s = __fdiv_rn(m, 448.0f);
+      unsigned int m = 0;  // max_{j != i} |fl32(a_ij)| as bits (non-negative floats order like integers)
+      for (int64_t j = 4 * int64_t(threadIdx.x); j < n; j += step) {
+        double a[4];
+        float f[4];
+        load_quad(row, j, n, a);
+        quad_f32(a, j, n, i, f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const unsigned int b = __float_as_uint(f[e]) & 0x7FFFFFFFu;
+          if (b <= 0x7F800000u) m = b > m ? b : m;  // NaN does not raise the maximum
+        }
+      }
+      m = block_max(m, shs);
+      s = __fdiv_rn(__uint_as_float(m), 448.0f);
       if (s == 0.0f) s = 1.0f;
     }
     TL* out = Nl + i * ldn;
     unsigned long long mb = 0;  // max_j |a_ij| (all j, as IEEE bits)
-    for (int64_t j = threadIdx.x; j < ldn; j += blockDim.x) {
-      TL q;
-      if (j < n) {
-        const double a = row[j];
-        const unsigned long long b = abs_bits(a);
-        mb = b > mb ? b : mb;
-        q = j != i ? narrow_encode<TL>(__double2float_rn(a), s) : narrow_encode<TL>(0.0f, 1.0f);
-      } else {
-        q = narrow_encode<TL>(0.0f, 1.0f);
+#pragma unroll 2
+    for (int64_t j = 4 * int64_t(threadIdx.x); j < ldn; j += step) {
+      double a[4];
+      float f[4];
+      load_quad(row, j, n, a);
+      if (rexp) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const unsigned long long b = abs_bits(a[e]);
+          mb = b > mb ? b : mb;
+        }
       }
-      out[j] = q;
+      quad_f32(a, j, n, i, f);
+      encode_quad<TL>(f, s, out + j);
     }
     if (rexp) {
-      // exponent e with max_j |a_ij| < 2^e: the row scale of the split-float FP64 residual
-      mb = block_max_bits(mb, shb);
-      if (threadIdx.x == 0) {
-        const double mx = __longlong_as_double(static_cast<long long>(mb));
-        rexp[i] = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) + 1 : 0;
-      }
+      mb = block_max(mb, shb);
+      if (threadIdx.x == 0) rexp[i] = split_exponent(mb);
     }
     if (threadIdx.x == 0) {
       if (kScaled) scale[i] = s;
       rowfac[i] = __fmul_rn(__double2float_rn(rinv[i]), s);
     }
   }
+}
+
+__global__ void split_x_kernel(const double* __restrict__ x, int64_t n, const unsigned long long* __restrict__ cmax,
+                               float2* __restrict__ xs) {
+  const int g = split_exponent(*cmax);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    xs[i] = split_x(x[i], g);
 }
 
 // One warp per row: r_i = b_i - sum_j a_ij x_j in FP64, max |r_i| as bits.
@@ -180,8 +232,15 @@ cudaError_t launch_diag(const double* A, int64_t lda, int64_t n, double* d, doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_rhs(const double* B, int64_t n, double* b, unsigned long long* bnorm_bits, cudaStream_t s) {
-  rhs_kernel<<<prep_blocks(n, kPrepThreads), kPrepThreads, 0, s>>>(B, n, b, bnorm_bits);
+cudaError_t launch_rhs(const double* B, int64_t n, const double* rinv, double* b, unsigned long long* bnorm_bits,
+                       unsigned long long* cmax_bits, cudaStream_t s) {
+  rhs_kernel<<<prep_blocks(n, kPrepThreads), kPrepThreads, 0, s>>>(B, n, rinv, b, bnorm_bits, cmax_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_x(const double* x, int64_t n, const unsigned long long* cmax_bits, float2* xs,
+                           cudaStream_t s) {
+  split_x_kernel<<<prep_blocks(n, kPrepThreads), kPrepThreads, 0, s>>>(x, n, cmax_bits, xs);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 
 #include "device_util.cuh"
 #include "solver.cuh"
+#include "splitfloat.cuh"
 
 namespace jac {
 namespace {
@@ -31,7 +32,8 @@ namespace {
 constexpr int kSRows = 16;        // rows per work item
 constexpr int kSThreads = 256;    // 8 warps x 2 rows
 constexpr int kStatSlots = 64;    // per request per round: [0,16) |R| or change per column, [16,32) |B|,
-                                  // 32 inner change, 33 inner magnitude, 34 bad-diagonal key (~key)
+                                  // 32 inner change, 33 inner magnitude, 34 bad-diagonal key (~key),
+                                  // [40,56) max |b / a_ii| per column (setup round)
 
 enum SrvPhase : int { kPhPrep = 0, kPhResid = 1, kPhInner = 2 };
 
@@ -47,7 +49,12 @@ struct SrvReq {
   float* C1;         // inner right-hand side [r][ld]
   float* D[2];       // inner iterates [r][ld]
   unsigned long long* st;  // kStatSlots reduction slots (zeroed every round)
-  int phase, xsel, dsel, rb;
+  // split-float residual (split != 0): per-row scale exponents of A, the two FP32 words of X[k] 2^-g_c
+  // per entry, and the column exponents g_c (from max_i |b_ic / a_ii|)
+  int* rexp;
+  float2* xs[2];
+  int xg[16];
+  int phase, xsel, dsel, rb, split;
 };
 
 // ------------------------------------------------------------------------ Philox4x32-10 (device)
@@ -151,8 +158,17 @@ __device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
     const int64_t i = i0 + rr;
     if (i >= q.n) break;
     const double* Ai = q.A + i * q.n;
-    for (int64_t j = lane; j < q.ld; j += 32)
-      q.Nl[i * q.ld + j] = (j < q.n && j != i) ? __double2float_rn(Ai[j]) : 0.0f;
+    unsigned long long mb = 0;
+    for (int64_t j = lane; j < q.ld; j += 32) {
+      const double a = j < q.n ? Ai[j] : 0.0;
+      const unsigned long long b = abs_bits(a);
+      mb = b > mb ? b : mb;
+      q.Nl[i * q.ld + j] = (j < q.n && j != i) ? __double2float_rn(a) : 0.0f;
+    }
+    if (q.split) {
+      mb = warp_max_u64(mb);
+      if (lane == 0) q.rexp[i] = split_exponent(mb);
+    }
     const double a = Ai[i];
     const double ri = (a != 0.0 && isfinite(a)) ? __drcp_rn(a) : 0.0;
     if (lane == 0) {
@@ -168,6 +184,7 @@ __device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
       q.C1[c * q.ld + i] = cc;
       q.D[0][c * q.ld + i] = cc;
       umax_to(q.st + 16 + c, abs_bits(b));
+      umax_to(q.st + 40 + c, abs_bits(b * ri));
     }
   }
 }
@@ -181,7 +198,7 @@ __device__ void resid_rows(const SrvReq& q, int64_t i0, int lane) {
   const bool has1 = i0 + 1 < q.n;
   const double* A0 = q.A + i0 * q.n;
   const double* A1 = has1 ? A0 + q.n : A0;
-  const double* X = q.X[q.xsel];
+  const double* X = q.xsel ? q.X[1] : q.X[0];
   for (int64_t j = lane; j < q.n; j += 32) {
     const double a0 = __ldg(A0 + j), a1 = has1 ? __ldg(A1 + j) : 0.0;
 #pragma unroll
@@ -206,6 +223,54 @@ __device__ void resid_rows(const SrvReq& q, int64_t i0, int lane) {
   }
 }
 
+// The same residual with the split-float arithmetic of splitfloat.cuh (FP32 units): a_ij split with the
+// row's scale as it is read, X from its two FP32 words, float-float lane sums, FP64 across lanes.
+template <int RB>
+__device__ void resid_rows_split(const SrvReq& q, int64_t i0, int lane) {
+  FF acc[2 * RB];
+#pragma unroll
+  for (int v = 0; v < 2 * RB; ++v) acc[v] = FF{0.0f, 0.0f};
+  const bool has1 = i0 + 1 < q.n;
+  const double* A0 = q.A + i0 * q.n;
+  const double* A1 = has1 ? A0 + q.n : A0;
+  const int sh0 = q.rexp[i0], sh1 = has1 ? q.rexp[i0 + 1] : 0;
+  const float2* X = q.xsel ? q.xs[1] : q.xs[0];
+  int since = 0;
+  for (int64_t j = lane; j < q.n; j += 32) {
+    float h0, l0, h1 = 0.0f, l1 = 0.0f;
+    split_scaled(__ldg(A0 + j), sh0, h0, l0);
+    if (has1) split_scaled(__ldg(A1 + j), sh1, h1, l1);
+#pragma unroll
+    for (int c = 0; c < RB; ++c)
+      if (c < q.r) {
+        const float2 x = __ldg(X + c * q.ld + j);
+        ff_fma(acc[c], h0, l0, x.x, x.y);
+        ff_fma(acc[RB + c], h1, l1, x.x, x.y);
+      }
+    if (++since == 8) {
+      since = 0;
+#pragma unroll
+      for (int v = 0; v < 2 * RB; ++v) ff_renorm(acc[v]);
+    }
+  }
+  double dv[2 * RB];
+#pragma unroll
+  for (int v = 0; v < 2 * RB; ++v) dv[v] = static_cast<double>(acc[v].hi) + static_cast<double>(acc[v].lo);
+  const double tot = tr_finish<2 * RB>(TRs<2 * RB, 16, double>::run(dv, lane));
+  const int v = tr_index<2 * RB>(lane);
+  const int64_t i = i0 + v / RB;
+  const int c = v % RB;
+  if ((lane & (32 / (2 * RB) - 1)) == 0 && i < q.n && c < q.r) {
+    const int64_t o = c * q.ld + i;
+    const double dot = tot * pow2(v / RB ? sh1 : sh0) * pow2(q.xg[c]);
+    const double R = q.B[o] - dot;
+    const float cc = static_cast<float>(R * q.rinv[i]);
+    q.C1[o] = cc;
+    q.D[0][o] = cc;
+    umax_to(q.st + c, abs_bits(R));
+  }
+}
+
 // FP32 inner sweep of rows [i0, i0 + 2): D_new = C1 - (1/a_ii) N D_cur, X_alt = X_cur + D_new.
 template <int RB>
 __device__ void inner_rows(const SrvReq& q, int64_t i0, int lane) {
@@ -215,7 +280,7 @@ __device__ void inner_rows(const SrvReq& q, int64_t i0, int lane) {
   const bool has1 = i0 + 1 < q.n;
   const float* N0 = q.Nl + i0 * q.ld;
   const float* N1 = has1 ? N0 + q.ld : N0;
-  const float* Dc = q.D[q.dsel];
+  const float* Dc = q.dsel ? q.D[1] : q.D[0];
   for (int64_t j = 4 * lane; j < q.n; j += 128) {
     const float4 m0 = __ldcg(reinterpret_cast<const float4*>(N0 + j));
     const float4 m1 = has1 ? __ldcg(reinterpret_cast<const float4*>(N1 + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -236,8 +301,10 @@ __device__ void inner_rows(const SrvReq& q, int64_t i0, int lane) {
     const int64_t o = c * q.ld + i;
     const float val = fmaf(-q.rowfac[i], tot, q.C1[o]);
     const float old = Dc[o];
-    q.D[q.dsel ^ 1][o] = val;
-    q.X[q.xsel ^ 1][o] = q.X[q.xsel][o] + static_cast<double>(val);
+    (q.dsel ? q.D[0] : q.D[1])[o] = val;
+    const double xn = (q.xsel ? q.X[1] : q.X[0])[o] + static_cast<double>(val);
+    (q.xsel ? q.X[0] : q.X[1])[o] = xn;
+    if (q.split) (q.xsel ? q.xs[0] : q.xs[1])[o] = split_x(xn, q.xg[c]);
     chg = abs_bits(val - old);
     mag = abs_bits(val);
   }
@@ -251,9 +318,12 @@ __device__ void inner_rows(const SrvReq& q, int64_t i0, int lane) {
 
 template <int RB>
 __device__ __forceinline__ void run_item(const SrvReq& q, int64_t i0, int lane) {
-  if (q.phase == kPhResid)
-    resid_rows<RB>(q, i0, lane);
-  else
+  if (q.phase == kPhResid) {
+    if (q.split)
+      resid_rows_split<RB>(q, i0, lane);
+    else
+      resid_rows<RB>(q, i0, lane);
+  } else
     inner_rows<RB>(q, i0, lane);
 }
 
@@ -269,7 +339,7 @@ __global__ void __launch_bounds__(kSThreads) serve_round_kernel(const SrvReq* __
       else
         hi = mid - 1;
     }
-    const SrvReq q = reqs[lo];
+    const SrvReq& q = reqs[lo];  // fields read on demand (L1); dynamic indexing stays off the stack
     const int64_t i0 = (it - first[lo]) * kSRows + 2 * warp;
     if (i0 >= q.n) continue;  // warp-uniform
     if (q.phase == kPhPrep) {
@@ -349,14 +419,23 @@ struct Request {
   jacobi_stats st{};
 };
 
-size_t request_bytes(int64_t n, int64_t r, int64_t ld, bool own_A) {
+size_t request_bytes(int64_t n, int64_t r, int64_t ld, bool own_A, bool split) {
   size_t b = 0;
   if (own_A) b += a256(static_cast<size_t>(n) * n * 8);
   b += a256(static_cast<size_t>(n) * ld * 4);                // Nl
   b += 2 * a256(static_cast<size_t>(ld) * 8) + a256(static_cast<size_t>(ld) * 4);  // d, rinv, rowfac
   b += 3 * a256(static_cast<size_t>(r) * ld * 8);             // B, X0, X1
   b += 3 * a256(static_cast<size_t>(r) * ld * 4);             // C1, D0, D1
+  if (split) b += a256(static_cast<size_t>(ld) * 4) + 2 * a256(static_cast<size_t>(r) * ld * 8);  // rexp, xs
   return b;
+}
+
+// Host twin of split_exponent: e with |v| < 2^e for the IEEE bits of max |v|, clamped to [-1000, 1000].
+int host_split_exponent(unsigned long long bits) {
+  const int be = static_cast<int>((bits >> 52) & 0x7FFu);
+  if (be == 0x7FF || bits == 0) return 0;
+  const int e = be == 0 ? -1000 : be - 1022;
+  return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
 }
 
 }  // namespace
@@ -370,6 +449,7 @@ struct jacobi_server {
   int max_inner = 1000, max_outer = 30;
   float inner_rtol = 1.0f / 1024;
   int max_active = 0;
+  bool split = false;
   int64_t next_id = 1;
   std::deque<Request*> pending;
   std::vector<Request*> active;
@@ -420,7 +500,7 @@ int rbucket(int64_t r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 
 bool admit(jacobi_server* s, Request* rq) {
   const bool own_A = true;  // A always lives in the arena (copied or generated), row stride n
   rq->ld = round_up(rq->n, kLdAlign);
-  rq->bytes = request_bytes(rq->n, rq->r, rq->ld, own_A);
+  rq->bytes = request_bytes(rq->n, rq->r, rq->ld, own_A, s->split);
   if (!s->arena.alloc(rq->bytes, &rq->off)) return false;
   char* p = s->arena_base + rq->off;
   SrvReq& q = rq->q;
@@ -447,9 +527,16 @@ bool admit(jacobi_server* s, Request* rq) {
   q.C1 = reinterpret_cast<float*>(take(static_cast<size_t>(r) * ld * 4));
   q.D[0] = reinterpret_cast<float*>(take(static_cast<size_t>(r) * ld * 4));
   q.D[1] = reinterpret_cast<float*>(take(static_cast<size_t>(r) * ld * 4));
+  char* vec_end = reinterpret_cast<char*>(q.D[1]) + a256(static_cast<size_t>(r) * ld * 4);
+  q.split = s->split ? 1 : 0;
+  if (s->split) {
+    q.xs[0] = reinterpret_cast<float2*>(take(static_cast<size_t>(r) * ld * 8));
+    q.xs[1] = reinterpret_cast<float2*>(take(static_cast<size_t>(r) * ld * 8));
+    vec_end = reinterpret_cast<char*>(q.xs[1]) + a256(static_cast<size_t>(r) * ld * 8);
+    q.rexp = reinterpret_cast<int*>(take(static_cast<size_t>(ld) * 4));
+  }
   // vectors start at zero so every padding entry is 0 (X0 = 0 is the start vector)
-  const size_t vec_bytes = static_cast<size_t>((reinterpret_cast<char*>(q.D[1]) - reinterpret_cast<char*>(B))) +
-                           a256(static_cast<size_t>(r) * ld * 4);
+  const size_t vec_bytes = static_cast<size_t>(vec_end - reinterpret_cast<char*>(B));
   cudaMemsetAsync(B, 0, vec_bytes, s->stream);
   if (rq->generate) {
     int64_t blocks = std::min<int64_t>(n, 4096);
@@ -498,6 +585,7 @@ int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out) {
   if (d->max_outer > 0) s->max_outer = d->max_outer;
   if (d->inner_rtol > 0) s->inner_rtol = static_cast<float>(d->inner_rtol);
   s->max_active = d->max_active;
+  s->split = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) != 0;
   if (cudaMalloc(&s->arena_base, d->budget_bytes) != cudaSuccess) {
     delete s;
     return JACOBI_ERR_OUT_OF_MEMORY;
@@ -521,7 +609,7 @@ static int submit(jacobi_server* s, int64_t n, int64_t r, Request* rq, int64_t* 
     delete rq;
     return JACOBI_ERR_INVALID_ARG;
   }
-  if (request_bytes(n, r, round_up(n, kLdAlign), true) > s->arena.size) {
+  if (request_bytes(n, r, round_up(n, kLdAlign), true, s->split) > s->arena.size) {
     delete rq;
     return JACOBI_ERR_OUT_OF_MEMORY;  // could never be admitted
   }
@@ -609,6 +697,7 @@ int jacobi_server_step(jacobi_server* s, int32_t* active_out, int32_t* pending_o
           for (int64_t c = 0; c < rq->r; ++c) {
             rq->bnorm[static_cast<size_t>(c)] = as_double(st[16 + c]);
             bmax = std::max(bmax, rq->bnorm[static_cast<size_t>(c)]);
+            q.xg[c] = host_split_exponent(st[40 + c]);  // the iterate's scale: max_i |b_ic / a_ii|
           }
           rq->outer = 1;
           rq->st.rel_residual = 1.0;

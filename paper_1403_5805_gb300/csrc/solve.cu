@@ -23,6 +23,7 @@
 #include "device_util.cuh"
 #include "dot.cuh"
 #include "solver.cuh"
+#include "splitfloat.cuh"
 
 namespace jac {
 namespace {
@@ -195,48 +196,10 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
   }
 }
 
-// ---- FP64-accurate row dot products on FP32 units (split-float residual).
-// GB300 issues about 2 FP64 FMA per clock per SM, so an FP64 pass over A is bound by FP64 arithmetic
-// (8 bytes per FMA, ~4.8 TB/s).  The residual only needs FP64-level accuracy, not FP64 instructions:
-// each a_ij (scaled by 2^-e_i, e_i the exponent of the row maximum, so |a| < 1) is split with integer
-// operations into hi = its top 24 significant bits and lo = the next 23, x_j into two rounded FP32
-// words, and the products are accumulated as float-float: the rounding error of hi*hi is recovered
-// exactly with an FMA, the two cross products are added to it, and a two-sum (Knuth) keeps the running
-// sum as an unevaluated pair.  The representation error is below 2^-46 per element; the lane sums
-// leave FP32 as FP64 values scaled back by 2^e_i.
-struct FF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void split_scaled(double a, int sh, float& hi, float& lo) {
-  // branch-free: out-of-range parts (below FP32's normal range relative to the row maximum) become 0
-  const uint32_t hw = static_cast<uint32_t>(__double2hiint(a)), lw = static_cast<uint32_t>(__double2loint(a));
-  const int E = static_cast<int>((hw >> 20) & 0x7FFu) - sh;  // biased exponent of a * 2^-sh
-  const uint32_t sign = hw & 0x80000000u;
-  const int fe = E - 896;                                     // FP32 exponent field of hi
-  const float h = __uint_as_float(sign | (static_cast<uint32_t>(fe) << 23) | (__funnelshift_l(lw, hw, 3) & 0x7FFFFFu));
-  hi = fe > 0 ? h : 0.0f;
-  const uint32_t m23 = (lw >> 6) & 0x7FFFFFu;                 // mantissa bits 28..6: the next 23 bits
-  const float ml = __fsub_rn(__uint_as_float(0x4B000000u | m23), 8388608.0f);  // m23, exactly
-  const float p2 = __uint_as_float(static_cast<uint32_t>(max(E - 942, 0)) << 23);  // 2^(e - 46), or 0
-  lo = __uint_as_float(__float_as_uint(__fmul_rn(ml, p2)) | sign);
-}
-
-__device__ __forceinline__ void ff_fma(FF& s, float ah, float al, float xh, float xl) {
-  const float p = __fmul_rn(ah, xh);
-  const float e = __fmaf_rn(ah, xh, -p);  // exact error of the rounded product
-  const float t = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
-  const float u = __fadd_rn(s.hi, p);  // two-sum of s.hi and p
-  const float v = __fsub_rn(u, s.hi);
-  const float w = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(u, v)), __fsub_rn(p, v));
-  s.hi = u;
-  s.lo = __fadd_rn(s.lo, __fadd_rn(w, t));
-}
-
 // Same schedule as consume_phase<double> (ring items, warp layout, transposed reduction, epilogue),
 // with the split-float arithmetic above.
 template <typename Epi>
-__device__ void consume_phase_split(const Block& B, uint32_t& u, const double* x, int64_t n, int64_t r0,
+__device__ void consume_phase_split(const Block& B, uint32_t& u, const float2* xs, int g, int64_t n, int64_t r0,
                                     int64_t r1, const int* rexp, double (*red)[kConsumerWarps][kRowsPerWarp],
                                     Epi& epi) {
   constexpr int V = 2;
@@ -258,12 +221,13 @@ __device__ void consume_phase_split(const Block& B, uint32_t& u, const double* x
       sh[r] = r < myrows ? __ldg(rexp + row) : 0;
       acc[r] = FF{0.0f, 0.0f};
     }
-    double xv[V], xn[V];
-    if (nch > 0 && co < n) load_x(xv, x + co);
+    // (hi, lo) of x_col and x_col+1; entries past n are zero (the split buffers' padding)
+    float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), xn = xv;
+    if (nch > 0 && co < n) xv = __ldcg(reinterpret_cast<const float4*>(xs + co));
     for (int64_t c = 0; c < nch; ++c) {
       const int64_t col = c * K + co;
       const int64_t ncol = col + K;
-      if (c + 1 < nch && ncol < n) load_x(xn, x + ncol);
+      if (c + 1 < nch && ncol < n) xn = __ldcg(reinterpret_cast<const float4*>(xs + ncol));
       const int s = static_cast<int>(u % kStages);
       const uint32_t par = (u / kStages) & 1u;
       bool ok = (*B.abort == 0);
@@ -271,13 +235,6 @@ __device__ void consume_phase_split(const Block& B, uint32_t& u, const double* x
       if (!ok) {
         raise_abort(B);
       } else if (col < n && myrows > 0) {
-        if (col + V > n) mask_tail(xv, col, n);
-        float xh[V], xl[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-          xh[e] = __double2float_rn(xv[e]);
-          xl[e] = __double2float_rn(xv[e] - static_cast<double>(xh[e]));
-        }
         const bool two = col + 1 < n;  // the straddling segment's padding element is skipped
         const char* base = B.stages + s * kStageBytes + rh * kRowsPerWarp * kRowBytes + co * 8;
 #pragma unroll
@@ -286,24 +243,23 @@ __device__ void consume_phase_split(const Block& B, uint32_t& u, const double* x
             const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
             float ah, al;
             split_scaled(__hiloint2double(static_cast<int>(m.y), static_cast<int>(m.x)), sh[r], ah, al);
-            ff_fma(acc[r], ah, al, xh[0], xl[0]);
+            ff_fma(acc[r], ah, al, xv.x, xv.y);
             if (two) {
               split_scaled(__hiloint2double(static_cast<int>(m.w), static_cast<int>(m.z)), sh[r], ah, al);
-              ff_fma(acc[r], ah, al, xh[1], xl[1]);
+              ff_fma(acc[r], ah, al, xv.z, xv.w);
             }
+            ff_renorm(acc[r]);
           }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.ring->empty[s]);
       ++u;
-      xv[0] = xn[0];
-      xv[1] = xn[1];
+      xv = xn;
     }
     double dv[kRowsPerWarp];
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r)  // back to FP64, scaled by 2^sh (exact)
-      dv[r] = (static_cast<double>(acc[r].hi) + static_cast<double>(acc[r].lo)) *
-              __longlong_as_double(static_cast<long long>(1023 + sh[r]) << 52);
+    for (int r = 0; r < kRowsPerWarp; ++r)  // back to FP64, scaled by 2^(sh + g) (exact)
+      dv[r] = (static_cast<double>(acc[r].hi) + static_cast<double>(acc[r].lo)) * pow2(sh[r]) * pow2(g);
     const double part = transpose_reduce8(dv, lane);
     if ((lane & 3) == 0) red[grp & 1][warp][row_of_lane(lane)] = part;
     named_barrier(1, kConsumers);
@@ -533,7 +489,8 @@ struct ResidEpi {
 
 // Inner sweep on the narrow matrix: delta^(m)_i = c1_i - f_i * sum_j n_ij delta^(m-1)_j (the Section 2
 // update of A delta = r with the stored factor f_i = 1/a_ii (times the E4M3 row scale)), plus the
-// candidate X + delta^(m) in FP64, used if this is the last inner sweep of the outer step.
+// candidate X + delta^(m) in FP64, used if this is the last inner sweep of the outer step (with its
+// two FP32 words when the residual is split-float).
 struct InnerEpi {
   const float* c1;
   const float* rowfac;
@@ -541,6 +498,8 @@ struct InnerEpi {
   float* dn;
   const double* xc;
   double* xalt;
+  float2* xsalt;
+  int g;  // the split words are of x 2^-g
   unsigned long long mchg, mmag;
   float pc, pf, pd;
   double px;
@@ -554,7 +513,9 @@ struct InnerEpi {
     const float v = fmaf(-pf, dot, pc);
     const float old = pd;
     dn[i] = v;
-    xalt[i] = px + static_cast<double>(v);
+    const double xn = px + static_cast<double>(v);
+    xalt[i] = xn;
+    if (xsalt) xsalt[i] = split_x(xn, g);
     mchg = umax(mchg, abs_bits(v - old));
     mmag = umax(mmag, abs_bits(v));
   }
@@ -587,6 +548,7 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
   const bool producer = threadIdx.x >= kConsumers;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TL* Nl = static_cast<const TL*>(p.Nlow);
+  const int xg = p.rexp ? split_exponent(__ldg(p.cmax)) : 0;  // scale of the iterate's split words
 
   uint32_t u = 0;
   uint32_t phase = 0;
@@ -600,6 +562,8 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
     const bool skip_matrix = s_first && p.x0_zero;
     double* xc = xcur ? p.xb : p.xa;
     double* xalt = xcur ? p.xa : p.xb;
+    const float2* xsc = xcur ? p.xsb : p.xsa;
+    float2* xsalt = xcur ? p.xsa : p.xsb;
     float* dc = dcur ? p.db : p.da;
     float* dn = dcur ? p.da : p.db;
     unsigned long long v0 = 0, v1 = 0;
@@ -608,14 +572,14 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
       if (producer) {
         if (!skip_matrix) produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
       } else if (p.rexp && !skip_matrix) {
-        consume_phase_split(B, u, xc, p.n, r0, r1, p.rexp, red64, epi);
+        consume_phase_split(B, u, xsc, xg, p.n, r0, r1, p.rexp, red64, epi);
       } else {
         consume_phase<double>(B, u, xc, p.n, r0, r1, !skip_matrix, red64, epi);
       }
       v0 = epi.mr;
       v1 = epi.mc;
     } else {
-      InnerEpi epi{p.c1, p.rowfac, dc, dn, xc, xalt, 0ull, 0ull, 0.f, 0.f, 0.f, 0.0};
+      InnerEpi epi{p.c1, p.rowfac, dc, dn, xc, xalt, p.rexp ? xsalt : nullptr, xg, 0ull, 0ull, 0.f, 0.f, 0.f, 0.0};
       if (producer) {
         produce_phase<TL>(B, u, Nl, p.ldn, p.n, r0, r1);
       } else {

@@ -71,6 +71,8 @@ struct SolveParams {
   const double* bnorm;    // ||B||_inf (one value)
   double* xa;             // FP64 iterate buffers, length >= round_up(n, 16), zero padding
   double* xb;
+  float2* xsa;            // split-float residual: FP32 (hi, lo) words of xa / xb, else NULL
+  float2* xsb;
   float* c1;              // IR: inner right-hand side D^-1 r
   float* da;              // IR: inner iterate buffers
   float* db;
@@ -86,6 +88,7 @@ struct SolveParams {
   int max_inner;
   float inner_rtol;
   const int* rexp;        // IR: per-row scale exponent; non-NULL selects the split-float FP64 residual
+  const unsigned long long* cmax;  // split: bits of max_i |b_i / a_ii|, the iterate's scale
   uint64_t wait_ns;       // limit of every device-side wait (nanoseconds)
   int test_drop_copy;     // test only: the first ring item is announced but never copied (a wait expires)
 };
@@ -100,14 +103,19 @@ int max_coresident_grid(bool ir, Narrow kind);
 // (row << 8 | code) of a failing row (code 2: zero, 3: non-finite), or all ones if none.
 cudaError_t launch_diag(const double* A, int64_t lda, int64_t n, double* d, double* rinv,
                         unsigned long long* key_out, cudaStream_t s);
-// b (FP64 copy) and ||b||_inf bits into *bnorm_bits (must be zeroed before).
-cudaError_t launch_rhs(const double* B, int64_t n, double* b, unsigned long long* bnorm_bits,
-                       cudaStream_t s);
+// b (FP64 copy), ||b||_inf bits into *bnorm_bits and, unless cmax_bits is NULL, max_i |b_i / a_ii| bits
+// into *cmax_bits (both zeroed before; rinv from launch_diag, may be NULL without cmax_bits).
+cudaError_t launch_rhs(const double* B, int64_t n, const double* rinv, double* b, unsigned long long* bnorm_bits,
+                       unsigned long long* cmax_bits, cudaStream_t s);
 // Narrow copy of the off-diagonal part of A (zero diagonal, zero padding up to ldn) and the FP32
 // per-row factor of the inner sweep.
 // rexp (may be NULL): per row, the exponent e with max_j |a_ij| < 2^e (the split-float residual's scale).
 cudaError_t launch_narrow(Narrow kind, const double* A, int64_t lda, int64_t n, void* Nlow, int64_t ldn,
                           const double* rinv, float* scale, float* rowfac, int* rexp, cudaStream_t s);
+// xs[i] = the two FP32 words of x_i 2^-g for i < n, g = split_exponent(*cmax_bits): the split-float
+// residual's view of a start vector.
+cudaError_t launch_split_x(const double* x, int64_t n, const unsigned long long* cmax_bits, float2* xs,
+                           cudaStream_t s);
 // Zero columns [n, ld) of an n x ld row-major FP64 matrix.
 cudaError_t launch_pad_zero(double* M, int64_t n, int64_t ld, cudaStream_t s);
 // Relative residual ||b - A x||_inf / ||b||_inf (FP64) into *rel_bits (zeroed before) as max bits of

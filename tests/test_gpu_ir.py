@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import synth
+from conftest import f64_narrowing_cases
 
 pytestmark = pytest.mark.gpu
 
@@ -55,6 +56,31 @@ def test_narrow_copy_bit_exact(jac, prec, n):
     else:
         q, sc = oracle.offdiag_e4m3(A)
         np.testing.assert_array_equal(scale, sc)
+        np.testing.assert_array_equal(got, q)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_narrow_copy_of_edge_values(jac, prec):
+    """The setup's FP64 -> FP32 -> narrow rounding on ties, exponent carries, overflow to infinity, FP32
+    subnormals and signed zeros (a matrix of such off-diagonals): codes identical to the oracle's.
+    The E4M3 case uses the values that stay finite in FP32 (its row scale needs a finite maximum)."""
+    x = f64_narrowing_cases(seed=3)
+    if prec == "fp8_ir":
+        with np.errstate(over="ignore"):
+            x = x[np.isfinite(x.astype(np.float32))]
+    n = int(np.ceil(np.sqrt(x.size))) + 1
+    A = np.eye(n)
+    off = ~np.eye(n, dtype=bool)
+    A[off] = np.resize(x, off.sum())
+    s = dev_solver(jac, A, np.ones((n, 1)), precision=prec)
+    got, scale = s.narrow()
+    if prec == "fp32_ir":
+        np.testing.assert_array_equal(got.view(np.uint32), oracle.offdiag_f32(A).view(np.uint32))
+    elif prec == "bf16_ir":
+        np.testing.assert_array_equal(got, oracle.offdiag_bf16(A))
+    else:
+        q, sc = oracle.offdiag_e4m3(A)
+        np.testing.assert_array_equal(scale.view(np.uint32), sc.view(np.uint32))
         np.testing.assert_array_equal(got, q)
 
 

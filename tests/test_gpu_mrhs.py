@@ -118,3 +118,41 @@ def test_fp64_many_rhs_residual_stop(jac):
     ref = oracle.jacobi(A, B, max_iter=2000, tol=1e-10, norm=oracle.NORM_RESID)
     assert (st.status, st.sweeps) == (ref.status, ref.iters)
     assert np.max(np.abs(X.cpu().numpy().T - ref.X)) <= 1e-12 * np.max(np.abs(ref.X))
+
+
+@pytest.mark.parametrize("n,r,gen", [(300, 16, "dom"), (777, 64, "dom"), (1024, 32, "hard"), (1536, 128, "dom")])
+def test_split_residual_many_rhs(jac, n, r, gen):
+    """BF16 refinement with the split-float residual (FP32 units): every column meets 1e-10 by the
+    oracle's FP64 residual, and the reported residual matches it within the split's accuracy."""
+    make = synth.dominant_system if gen == "dom" else synth.hard_system
+    A, B, _ = make(n, 1.1, seed=900 + n, nrhs=r)
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", split_residual=True)
+    X, st = s.solve(max_iter=5000, tol=1e-10)
+    _, rel = oracle.residual(A, B, X.cpu().numpy().T)
+    assert st.status == 0 and rel <= 1e-10, (st.as_dict(), rel)
+    assert abs(st.rel_residual - rel) <= 5e-13 + 1e-3 * rel
+
+
+def test_split_residual_many_rhs_wild_scales(jac):
+    """One residual evaluation of a given X0 (max_outer = 1): rows of A scaled by 2^-300 .. 2^300 and
+    columns of B (so of X) by 2^-200 .. 2^200; the split-float residual equals the oracle's FP64 one
+    within the split's error bound."""
+    import torch
+    n, r = 600, 16
+    A, B, Xs = synth.dominant_system(n, 1.3, seed=93, nrhs=r)
+    rng = np.random.default_rng(5)
+    rows = 2.0 ** rng.integers(-300, 300, n)
+    cols = 2.0 ** rng.integers(-200, 200, r)
+    A = A * rows[:, None]
+    B = B * rows[:, None] * cols[None, :]
+    X0 = Xs * cols[None, :] * (1 + 1e-6 * rng.standard_normal((n, r)))
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", split_residual=True, max_outer=1)
+    X0t = torch.from_numpy(np.ascontiguousarray(X0.T)).cuda()
+    _, st = s.solve(X0=X0t, max_iter=10, tol=1e-300)
+    assert st.outer_steps == 1 and st.sweeps == 0
+    _, rel = oracle.residual(A, B, X0)
+    # the split's error bound: ~2^-46 of sum_j |a_ij x_jc| per row, relative to ||b_c||
+    S = np.max((np.abs(A) @ np.abs(X0)).max(axis=0) / np.abs(B).max(axis=0))
+    assert rel > 1e-9 and abs(st.rel_residual - rel) <= 2.0 ** -44 * S, (st.rel_residual, rel, S)

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from conftest import read_golden
+from conftest import f64_narrowing_cases, read_golden
 
 
 def tnorm_inf(A):
@@ -325,3 +325,17 @@ def test_offdiag_encodings():
     # the row maximum is encoded as the largest finite code, 448 (m / (m / 448) is within an FP32 ulp
     # of 448, far inside E4M3's rounding interval there)
     assert np.all((q & 0x7F).max(axis=1) == 0x7E)
+
+
+def test_f32_narrowing_of_edge_values():
+    """The FP32 narrow copy rounds FP64 -> FP32 to nearest even (ties, exponent carries, overflow to
+    infinity, subnormals, signed zeros), as numpy's conversion does."""
+    x = f64_narrowing_cases()
+    n = int(np.ceil(np.sqrt(x.size))) + 1
+    A = np.eye(n)
+    off = ~np.eye(n, dtype=bool)
+    A[off] = np.resize(x, off.sum())
+    got = oracle.offdiag_f32(A)
+    with np.errstate(over="ignore"):
+        want = np.where(off, A, 0.0).astype(np.float32)
+    np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
