@@ -36,7 +36,7 @@ ESIZE = {"fp64": 8, "fp32_ir": 4, "bf16_ir": 2, "fp8_ir": 1}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 # the solve kernels' translation unit and every header it includes
 SOLVE_SRC = [os.path.join(ROOT, "paper_1403_5805_gb300", "csrc", f)
-             for f in ("solve.cu", "solver.cuh", "dot.cuh", "device_util.cuh")]
+             for f in ("solve.cu", "solver.cuh", "dot.cuh", "device_util.cuh", "splitfloat.cuh")]
 
 
 def dist_env():
@@ -292,8 +292,9 @@ def make_batch_inputs(count, seed, n_lo=64, n_hi=1024, f_lo=1.05, f_hi=2.0):
 
 def run_batch(args, jac, torch, dev):
     """4096 independent systems (n log-uniform in [64, 1024], f uniform in [1.05, 2.0]): one persistent
-    work-queue kernel per solve, replayed from a CUDA graph, FP32 storage with FP64 refinement against
-    the plain FP64 batched path, both to a 1e-10 relative residual; launch shapes from the autotuner."""
+    work-queue kernel per solve, replayed from a CUDA graph, FP32 storage with FP64 refinement (FP64-FMA
+    or split-float residuals) against the plain FP64 batched path, all to a 1e-10 relative residual;
+    launch shapes from the autotuner."""
     import synth
     from paper_1403_5805_gb300 import autotune
     count = args.batch_count
@@ -303,10 +304,11 @@ def run_batch(args, jac, torch, dev):
     sum_n2 = float(np.sum(ns.astype(np.float64) ** 2))
     stream = torch.cuda.current_stream(dev)
     out = {"count": count, "n_range": [64, 1024], "f_range": [1.05, 2.0], "sum_n2": sum_n2}
-    for prec in ("fp32_ir", "fp64"):
-        tuned = autotune.tune_batch(As, Bs, precision=prec, tol=TARGET, use_cache=True)
+    for name in ("fp32_ir", "fp32_ir+split", "fp64"):
+        prec, split = name.replace("+split", ""), name.endswith("+split")
+        tuned = autotune.tune_batch(As, Bs, precision=prec, tol=TARGET, use_cache=True, split_residual=split)
         bs = jac.BatchSolver(As, Bs, precision=prec, rows_per_warp=tuned["rows_per_warp"],
-                             ctas_per_sm=tuned["ctas_per_sm"], inner_rtol=tuned["inner_rtol"])
+                             ctas_per_sm=tuned["ctas_per_sm"], inner_rtol=tuned["inner_rtol"], split_residual=split)
         for _ in range(args.warmup):
             bs.solve_async(args.max_iter, TARGET)
         torch.cuda.synchronize(dev)
@@ -330,15 +332,17 @@ def run_batch(args, jac, torch, dev):
             # setup pass (read A, write the FP32 copy) + FP64 residual passes + FP32 inner sweeps
             alg = float(np.sum((8.0 + 4.0) * n2 + np.maximum(outer - 1, 0) * 8.0 * n2 + sweeps * 4.0 * n2))
             worst = float(max(x.rel_residual for x in st))
-        out[prec] = {"solves_per_s": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 4),
+        out[name] = {"solves_per_s": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 4),
                      "converged": ok, "mean_sweeps": round(float(sweeps.mean()), 3),
                      "worst_rel_residual": worst, "algorithmic_gbs": round(alg / (ms * 1e-3) / 1e9, 1),
                      "grid": bs.grid, "tuned": {k: tuned[k] for k in ("rows_per_warp", "ctas_per_sm", "inner_rtol",
                                                                       "cached")}}
         if prec != "fp64":
-            out[prec]["mean_outer_steps"] = round(float(np.mean([x.outer_steps for x in st])), 3)
+            out[name]["mean_outer_steps"] = round(float(np.mean([x.outer_steps for x in st])), 3)
         bs.close()
     out["mixed_vs_fp64_solves_ratio"] = round(out["fp32_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
+    out["mixed_split_vs_fp64_solves_ratio"] = round(
+        out["fp32_ir+split"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     return out
 
 

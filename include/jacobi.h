@@ -233,7 +233,7 @@ typedef struct jacobi_batch_desc {
   int32_t ctas_per_sm;        /* cap on resident CTAs per SM (0: as many as fit) */
   int32_t max_outer;          /* IR: cap on residual evaluations per system (0: 30) */
   int32_t max_inner;          /* IR: cap on inner sweeps per outer step (0: 1000) */
-  int32_t reserved;
+  int32_t flags;              /* JACOBI_FLAG_SPLIT_RESIDUAL: split-float residuals (IR; see jacobi_desc) */
   double inner_rtol;          /* IR: inner stop, max|change| <= inner_rtol * max|delta| (0: 2^-14) */
   void* workspace;            /* device, >= jacobi_batch_workspace_size bytes, 256-byte aligned; NULL:
                                  the library allocates it */

@@ -69,10 +69,10 @@ def _time(fn, reps: int) -> float:
 
 
 def tune_batch(As, Bs, precision: str = "fp32_ir", max_iter: int = 5000, tol: float = 1e-10, reps: int = 3,
-               use_cache: bool = True, workspace=None) -> dict:
+               use_cache: bool = True, workspace=None, split_residual: bool = False) -> dict:
     """Best ``{rows_per_warp, ctas_per_sm, inner_rtol, ms}`` for this batch."""
     from .binding import BatchSolver
-    key = _signature("batch", precision, [a.shape[0] for a in As])
+    key = _signature("batch", precision + ("+split" if split_residual else ""), [a.shape[0] for a in As])
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
@@ -84,7 +84,7 @@ def tune_batch(As, Bs, precision: str = "fp32_ir", max_iter: int = 5000, tol: fl
         for cps in (0, 2, 1):
             for rt in rtols:
                 bs = BatchSolver(As, Bs, precision=precision, rows_per_warp=rpw, ctas_per_sm=cps, inner_rtol=rt,
-                                 workspace=workspace)
+                                 workspace=workspace, split_residual=split_residual)
                 workspace = bs.workspace
                 ms = _time(lambda: bs.solve_async(max_iter, tol), reps)
                 ok = all(s.status == 0 for s in bs.stats())

@@ -54,7 +54,7 @@ class JacobiBatchDesc(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64), ("n", ctypes.c_void_p), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
                 ("X", ctypes.c_void_p), ("precision", ctypes.c_int32), ("rows_per_warp", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("workspace", ctypes.c_void_p),
+                ("flags", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
 
 
@@ -314,7 +314,8 @@ class BatchSolver:
     kernel per solve, replayed from a captured CUDA graph."""
 
     def __init__(self, As, Bs, precision: str = "fp32_ir", rows_per_warp: int = 0, ctas_per_sm: int = 0,
-                 max_outer: int = 0, max_inner: int = 0, inner_rtol: float = 0.0, stream=None, workspace=None):
+                 max_outer: int = 0, max_inner: int = 0, inner_rtol: float = 0.0, stream=None, workspace=None,
+                 split_residual: bool = False):
         import torch
         lib = load()
         if len(As) != len(Bs) or not As:
@@ -339,6 +340,7 @@ class BatchSolver:
         d.precision = PRECISIONS[precision]
         d.rows_per_warp, d.ctas_per_sm = rows_per_warp, ctas_per_sm
         d.max_outer, d.max_inner, d.inner_rtol = max_outer, max_inner, inner_rtol
+        d.flags = FLAG_SPLIT_RESIDUAL if split_residual else 0
         d.stream = self.stream.cuda_stream
         nbytes = ctypes.c_size_t(0)
         _check(lib.jacobi_batch_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_batch_workspace_size")

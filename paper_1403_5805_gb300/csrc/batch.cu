@@ -25,6 +25,7 @@
 #include "device_util.cuh"
 #include "dot.cuh"
 #include "solver.cuh"
+#include "splitfloat.cuh"
 
 namespace jac {
 namespace {
@@ -43,6 +44,7 @@ struct BatchSys {
   double* rinv;     // 1 / a_ii
   float* rowfac;    // (float) (1 / a_ii)
   float* c1;        // inner right-hand side
+  int* rexp;        // split-float residual: per-row scale exponents (mixed modes)
   int64_t index;    // position in the caller's arrays
 };
 
@@ -131,6 +133,57 @@ __device__ __forceinline__ double rows_fp64(const double* __restrict__ A, int64_
   return TR<RPW, 16, double>::run(acc, lane);
 }
 
+// The same dot products with the split-float arithmetic of splitfloat.cuh: each a_ij split (row scale
+// 2^-e_i) as it is read, x as its two FP32 words in shared memory, float-float lane sums scaled back by
+// 2^e_i before the FP64 transposed reduction (the caller applies x's scale 2^g).
+template <int RPW>
+__device__ __forceinline__ double rows_split(const double* __restrict__ A, int64_t lda, int64_t n, int64_t i0,
+                                             const float2* xs, const int* __restrict__ rexp, int lane) {
+  FF acc[RPW];
+  int sh[RPW];
+  const int rows = static_cast<int>(i64min(RPW, n - i0));
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    acc[r] = FF{0.0f, 0.0f};
+    sh[r] = r < rows ? rexp[i0 + r] : 0;
+  }
+  int64_t j = lane;
+  for (; j + 96 < n; j += 128) {
+    float2 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = xs[j + 32 * u];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+      if (r < rows) {
+        const double* a = A + (i0 + r) * lda + j;
+        double av[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) av[u] = __ldg(a + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float h, l;
+          split_scaled(av[u], sh[r], h, l);
+          ff_fma(acc[r], h, l, x[u].x, x[u].y);
+        }
+        ff_renorm(acc[r]);
+      }
+  }
+  for (; j < n; j += 32) {
+    const float2 x = xs[j];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+      if (r < rows) {
+        float h, l;
+        split_scaled(__ldg(A + (i0 + r) * lda + j), sh[r], h, l);
+        ff_fma(acc[r], h, l, x.x, x.y);
+      }
+  }
+  double dv[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) dv[r] = (static_cast<double>(acc[r].hi) + static_cast<double>(acc[r].lo)) * pow2(sh[r]);
+  return TR<RPW, 16, double>::run(dv, lane);
+}
+
 // Narrow rows (16-byte segments, our own zero-padded copy, written earlier in this kernel: coherent
 // loads) times the shared-memory FP32 vector x (zero beyond n).
 template <typename TL, int RPW>
@@ -183,8 +236,9 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long v, un
   return m;
 }
 
-// kMode: 0 = FP64 Jacobi, 1 = FP32 inner sweeps, 2 = BF16 inner sweeps.
-template <int kMode, int RPW>
+// kMode: 0 = FP64 Jacobi, 1 = FP32 inner sweeps, 2 = BF16 inner sweeps.  kSplit (mixed modes): residuals
+// with the split-float arithmetic instead of FP64 FMAs.
+template <int kMode, int RPW, bool kSplit>
 __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
   using TL = typename std::conditional<kMode == 2, __nv_bfloat16, float>::type;
   extern __shared__ __align__(16) unsigned char bsmem[];
@@ -195,6 +249,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
   double* xs1 = xs0 + p.smem_ld;
   float* ds0 = reinterpret_cast<float*>(xs1 + p.smem_ld);
   float* ds1 = ds0 + p.smem_ld;
+  float2* xss = reinterpret_cast<float2*>(ds1 + p.smem_ld);  // split words of x (split residual only)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (;;) {
@@ -227,17 +282,37 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
       ds0[i] = 0.0f;
       ds1[i] = 0.0f;
     }
+    unsigned long long cm = 0;  // max_i |b_i / a_ii|: the iterate's scale for the split residual
     if (kMode != 0) {
       TL* Nl = static_cast<TL*>(S.Nlow);
-      for (int64_t i = warp; i < n; i += kBWarps)
-        for (int64_t j = lane; j < S.ldn; j += 32)
-          Nl[i * S.ldn + j] = (j < n && j != i) ? encode_narrow<TL>(__ldg(S.A + i * n + j)) : TL(0.0f);
+      for (int64_t i = warp; i < n; i += kBWarps) {
+        unsigned long long mb = 0;
+        for (int64_t j = lane; j < S.ldn; j += 32) {
+          const double a = j < n ? __ldg(S.A + i * n + j) : 0.0;
+          if constexpr (kSplit) {
+            const unsigned long long ab = abs_bits(a);
+            mb = ab > mb ? ab : mb;
+          }
+          Nl[i * S.ldn + j] = (j < n && j != i) ? encode_narrow<TL>(a) : TL(0.0f);
+        }
+        if constexpr (kSplit) {
+          mb = warp_max_u64(mb);
+          if (lane == 0) S.rexp[i] = split_exponent(mb);
+        }
+      }
+      if constexpr (kSplit)
+        for (int64_t i = threadIdx.x; i < n; i += kBThreads) {
+          const unsigned long long cb = abs_bits(S.B[i] * S.rinv[i]);
+          cm = cb > cm ? cb : cm;
+        }
     }
     // first failing row decides (smallest index); stats are combined in the reduction slots
     if (bad) bad = ~bad;  // so that the max picks the smallest key
     const unsigned long long badmax = block_max(bad, sred, 0);
     const unsigned long long bmax_bits = block_max(bm, sred2, 0);
     const double bnorm = __longlong_as_double(static_cast<long long>(bmax_bits));
+    int xg = 0;
+    if constexpr (kSplit) xg = split_exponent(block_max(cm, sred, 1));
     jacobi_stats st{};
     st.rel_residual = __longlong_as_double(0x7FF8000000000000ll);
     int status = kStatusNotConverged;
@@ -288,9 +363,19 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
       for (;;) {
         // residual of the current iterate (no matrix pass while the iterate is the zero start vector)
         const double* xc = cur ? xs1 : xs0;
+        if (kSplit && !first) {
+          for (int64_t i = threadIdx.x; i < p.smem_ld; i += kBThreads) xss[i] = i < n ? split_x(xc[i], xg) : float2{};
+          __syncthreads();
+        }
         unsigned long long mr = 0, mc = 0;
         for (int64_t i0 = static_cast<int64_t>(warp) * RPW; i0 < n; i0 += static_cast<int64_t>(kBWarps) * RPW) {
-          const double dot = first ? 0.0 : rows_fp64<RPW>(S.A, n, n, i0, xc, lane);
+          double dot = 0.0;
+          if (!first) {
+            if constexpr (kSplit)
+              dot = rows_split<RPW>(S.A, n, n, i0, xss, S.rexp, lane) * pow2(xg);
+            else
+              dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane);
+          }
           const int64_t i = i0 + tr_row<RPW>(lane);
           if (tr_owner<RPW>(lane) && i < n) {
             const double r = S.B[i] - dot;
@@ -372,20 +457,20 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
 
 using BatchKernel = void (*)(BatchParams);
 
-template <int M>
+template <int M, bool kSplit>
 BatchKernel pick_rpw(int rpw) {
   switch (rpw) {
-    case 1: return batch_kernel<M, 1>;
-    case 2: return batch_kernel<M, 2>;
-    case 8: return batch_kernel<M, 8>;
-    default: return batch_kernel<M, 4>;
+    case 1: return batch_kernel<M, 1, kSplit>;
+    case 2: return batch_kernel<M, 2, kSplit>;
+    case 8: return batch_kernel<M, 8, kSplit>;
+    default: return batch_kernel<M, 4, kSplit>;
   }
 }
 
-BatchKernel pick_kernel(int precision, int rpw) {
-  if (precision == JACOBI_FP64) return pick_rpw<0>(rpw);
-  if (precision == JACOBI_FP32_IR) return pick_rpw<1>(rpw);
-  return pick_rpw<2>(rpw);
+BatchKernel pick_kernel(int precision, int rpw, bool split) {
+  if (precision == JACOBI_FP64) return pick_rpw<0, false>(rpw);
+  if (precision == JACOBI_FP32_IR) return split ? pick_rpw<1, true>(rpw) : pick_rpw<1, false>(rpw);
+  return split ? pick_rpw<2, true>(rpw) : pick_rpw<2, false>(rpw);
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -399,6 +484,7 @@ struct jacobi_batch {
   int64_t count = 0;
   int precision = JACOBI_FP32_IR;
   int rpw = 4;
+  bool split = false;
   int grid = 0;
   size_t smem = 0;
   int64_t smem_ld = 0;
@@ -442,7 +528,7 @@ BatchLayout batch_layout(const jacobi_batch_desc* d) {
     const int64_t ld = round_up(n, kLdAlign);
     L.per[static_cast<size_t>(k)] = o;
     o = align256(o + static_cast<size_t>(n) * ld * es);  // narrow copy
-    o = align256(o + static_cast<size_t>(ld) * (8 + 8 + 4 + 4));  // d, rinv, rowfac, c1
+    o = align256(o + static_cast<size_t>(ld) * (8 + 8 + 4 + 4 + 4));  // d, rinv, rowfac, c1, rexp
   }
   L.total = o;
   return L;
@@ -484,6 +570,7 @@ int jacobi_batch_create(const jacobi_batch_desc* d, jacobi_batch** out) {
   b->count = d->count;
   b->precision = d->precision;
   b->rpw = d->rows_per_warp ? d->rows_per_warp : 4;
+  b->split = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) && d->precision != JACOBI_FP64;
   b->stream = static_cast<cudaStream_t>(d->stream);
   if (d->max_outer > 0) b->max_outer = d->max_outer;
   if (d->max_inner > 0) b->max_inner = d->max_inner;
@@ -525,6 +612,7 @@ int jacobi_batch_create(const jacobi_batch_desc* d, jacobi_batch** out) {
     s.rinv = s.d + ld;
     s.rowfac = reinterpret_cast<float*>(s.rinv + ld);
     s.c1 = s.rowfac + ld;
+    s.rexp = reinterpret_cast<int*>(s.c1 + ld);
     s.index = k;
     host[q] = s;
   }
@@ -536,8 +624,8 @@ int jacobi_batch_create(const jacobi_batch_desc* d, jacobi_batch** out) {
     return fail(JACOBI_ERR_CUDA);
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(JACOBI_ERR_CUDA);
   b->smem_ld = round_up(nmax, kLdAlign);
-  b->smem = static_cast<size_t>(b->smem_ld) * (2 * sizeof(double) + 2 * sizeof(float));
-  BatchKernel kern = pick_kernel(b->precision, b->rpw);
+  b->smem = static_cast<size_t>(b->smem_ld) * (2 * sizeof(double) + 2 * sizeof(float) + (b->split ? sizeof(float2) : 0));
+  BatchKernel kern = pick_kernel(b->precision, b->rpw, b->split);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(b->smem)) != cudaSuccess)
     return fail(JACOBI_ERR_CUDA);
   int dev = 0, sms = 0, per_sm = 0;
@@ -576,7 +664,7 @@ int jacobi_batch_solve_async(jacobi_batch* b, int64_t max_iter, double tol) {
     p.max_inner = b->max_inner;
     p.inner_rtol = b->inner_rtol;
     p.smem_ld = b->smem_ld;
-    BatchKernel kern = pick_kernel(b->precision, b->rpw);
+    BatchKernel kern = pick_kernel(b->precision, b->rpw, b->split);
     if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return JACOBI_ERR_CUDA;
     cudaMemsetAsync(b->queue, 0, sizeof(unsigned int), b->capture);
     void* args[] = {&p};

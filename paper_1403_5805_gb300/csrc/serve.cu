@@ -20,6 +20,7 @@
 #include <deque>
 #include <map>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "device_util.cuh"
@@ -30,6 +31,8 @@ namespace jac {
 namespace {
 
 constexpr int kSRows = 16;        // rows per work item
+constexpr int kSRhs = 16;         // right-hand sides per request (JACOBI_SERVE_MAX_RHS)
+constexpr int kKC = 256;          // columns of the iterate staged in shared memory per step
 constexpr int kSThreads = 256;    // 8 warps x 2 rows
 constexpr int kStatSlots = 64;    // per request per round: [0,16) |R| or change per column, [16,32) |B|,
                                   // 32 inner change, 33 inner magnitude, 34 bad-diagonal key (~key),
@@ -39,7 +42,7 @@ enum SrvPhase : int { kPhPrep = 0, kPhResid = 1, kPhInner = 2 };
 
 struct SrvReq {
   int64_t n, r, ld;
-  const double* A;   // n x n row-major, row stride n
+  const double* A;   // n x n row-major, row stride ld (rows 128-byte aligned; padding never read)
   float* Nl;         // FP32 copy of the off-diagonal part, row stride ld
   double* d;
   double* rinv;
@@ -70,11 +73,15 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
   return c;
 }
 
+// Block q of the sequence (seed, stream): the four words 4q .. 4q + 3, counter (q, stream, 0).
+__device__ __forceinline__ uint4 philox_block(uint64_t seed, uint32_t stream, uint64_t q) {
+  return philox(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32), stream, 0u),
+                make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+}
+
 // Word w of the sequence (seed, stream): lane w % 4 of the block with counter (w / 4, stream, 0).
 __device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint32_t stream, uint64_t w) {
-  const uint64_t q = w >> 2;
-  const uint4 o = philox(make_uint4(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32), stream, 0u),
-                         make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+  const uint4 o = philox_block(seed, stream, w >> 2);
   switch (w & 3) {
     case 0: return o.x;
     case 1: return o.y;
@@ -85,16 +92,27 @@ __device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint32_t stream, 
 
 __device__ __forceinline__ double signed_unit(uint32_t w) { return static_cast<double>(static_cast<int32_t>(w)) * 0x1p-31; }
 
-// One CTA per row (grid-stride): A row i, its diagonal, and B (all columns, zero padding up to ld).
-__global__ void serve_generate_kernel(int64_t n, int64_t r, int64_t ld, double f, uint64_t seed, double* A,
-                                      double* B) {
+// One CTA per row (grid-stride): A row i (row stride lda), its diagonal, and B (column stride ld).
+__global__ void serve_generate_kernel(int64_t n, int64_t r, int64_t lda, int64_t ld, double f, uint64_t seed,
+                                      double* A, double* B) {
   __shared__ double part[kSThreads / 32];
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     double s = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-      const double a = (j == i) ? 0.0 : signed_unit(philox_word(seed, 0u, static_cast<uint64_t>(i * n + j)));
-      if (j != i) A[i * n + j] = a;
-      s += fabs(a);  // integers times 2^-31 below 2^13: exact in any order
+    // words i n .. i n + n - 1 of stream 0, one Philox block (4 words) per thread and step
+    const uint64_t w0 = static_cast<uint64_t>(i * n), w1 = w0 + static_cast<uint64_t>(n);
+    for (uint64_t q = (w0 >> 2) + threadIdx.x; 4 * q < w1; q += blockDim.x) {
+      const uint4 o = philox_block(seed, 0u, q);
+      const uint32_t words[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint64_t w = 4 * q + e;
+        if (w < w0 || w >= w1) continue;
+        const int64_t j = static_cast<int64_t>(w - w0);
+        if (j == i) continue;
+        const double a = signed_unit(words[e]);
+        A[i * lda + j] = a;
+        s += fabs(a);  // integers times 2^-31 below 2^13: exact in any order
+      }
     }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
@@ -103,7 +121,7 @@ __global__ void serve_generate_kernel(int64_t n, int64_t r, int64_t ld, double f
       double t = 0.0;
       for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
       const double sign = (philox_word(seed, 1u, static_cast<uint64_t>(i)) & 1u) ? -1.0 : 1.0;
-      A[i * n + i] = n > 1 ? f * t * sign : f * sign;
+      A[i * lda + i] = n > 1 ? f * t * sign : f * sign;
     }
     __syncthreads();
     for (int64_t c = threadIdx.x; c < r; c += blockDim.x)
@@ -152,18 +170,37 @@ __device__ __forceinline__ void umax_to(unsigned long long* p, unsigned long lon
 }
 
 // Setup of rows [i0, i0 + 2) handled by one warp: diagonal and reciprocals, FP32 copy of the off-
-// diagonal row, the first inner right-hand side C1 = B / a_ii (the residual of X = 0) and D0 = C1.
+// diagonal row (4 consecutive elements per lane and step: A's rows start 128-byte aligned), the first
+// inner right-hand side C1 = B / a_ii (the residual of X = 0) and D0 = C1.
 __device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
+  const int64_t n = q.n, ld = q.ld;
   for (int rr = 0; rr < 2; ++rr) {
     const int64_t i = i0 + rr;
-    if (i >= q.n) break;
-    const double* Ai = q.A + i * q.n;
+    if (i >= n) break;
+    const double* Ai = q.A + i * ld;
+    float* Ni = q.Nl + i * ld;
     unsigned long long mb = 0;
-    for (int64_t j = lane; j < q.ld; j += 32) {
-      const double a = j < q.n ? Ai[j] : 0.0;
-      const unsigned long long b = abs_bits(a);
-      mb = b > mb ? b : mb;
-      q.Nl[i * q.ld + j] = (j < q.n && j != i) ? __double2float_rn(a) : 0.0f;
+    for (int64_t j = 4 * lane; j < ld; j += 128) {
+      double a[4];
+      if (j + 4 <= n) {
+        const double2 v0 = __ldcs(reinterpret_cast<const double2*>(Ai + j));
+        const double2 v1 = __ldcs(reinterpret_cast<const double2*>(Ai + j + 2));
+        a[0] = v0.x;
+        a[1] = v0.y;
+        a[2] = v1.x;
+        a[3] = v1.y;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) a[e] = j + e < n ? Ai[j + e] : 0.0;
+      }
+      float f[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const unsigned long long bb = abs_bits(a[e]);
+        mb = bb > mb ? bb : mb;
+        f[e] = (j + e < n && j + e != i) ? __double2float_rn(a[e]) : 0.0f;
+      }
+      *reinterpret_cast<float4*>(Ni + j) = make_float4(f[0], f[1], f[2], f[3]);
     }
     if (q.split) {
       mb = warp_max_u64(mb);
@@ -179,134 +216,230 @@ __device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
         atomicMax(q.st + 34, ~((static_cast<unsigned long long>(i) << 8) | (isfinite(a) ? 2ull : 3ull)));
     }
     for (int64_t c = lane; c < q.r; c += 32) {
-      const double b = q.B[c * q.ld + i];
+      const double b = q.B[c * ld + i];
       const float cc = static_cast<float>(b * ri);
-      q.C1[c * q.ld + i] = cc;
-      q.D[0][c * q.ld + i] = cc;
+      q.C1[c * ld + i] = cc;
+      q.D[0][c * ld + i] = cc;
       umax_to(q.st + 16 + c, abs_bits(b));
       umax_to(q.st + 40 + c, abs_bits(b * ri));
     }
   }
 }
 
-// FP64 residual R = B - A X of rows [i0, i0 + 2) for RB >= r columns.
-template <int RB>
-__device__ void resid_rows(const SrvReq& q, int64_t i0, int lane) {
-  double acc[2 * RB];
-#pragma unroll
-  for (int v = 0; v < 2 * RB; ++v) acc[v] = 0.0;
-  const bool has1 = i0 + 1 < q.n;
-  const double* A0 = q.A + i0 * q.n;
-  const double* A1 = has1 ? A0 + q.n : A0;
-  const double* X = q.xsel ? q.X[1] : q.X[0];
-  for (int64_t j = lane; j < q.n; j += 32) {
-    const double a0 = __ldg(A0 + j), a1 = has1 ? __ldg(A1 + j) : 0.0;
-#pragma unroll
-    for (int c = 0; c < RB; ++c)
-      if (c < q.r) {
-        const double x = __ldg(X + c * q.ld + j);
-        acc[c] = fma(a0, x, acc[c]);
-        acc[RB + c] = fma(a1, x, acc[RB + c]);
-      }
-  }
-  const double tot = tr_finish<2 * RB>(TRs<2 * RB, 16, double>::run(acc, lane));
-  const int v = tr_index<2 * RB>(lane);
-  const int64_t i = i0 + v / RB;
-  const int c = v % RB;
-  if ((lane & (32 / (2 * RB) - 1)) == 0 && i < q.n && c < q.r) {
-    const int64_t o = c * q.ld + i;
-    const double R = q.B[o] - tot;
-    const float cc = static_cast<float>(R * q.rinv[i]);
-    q.C1[o] = cc;
-    q.D[0][o] = cc;
-    umax_to(q.st + c, abs_bits(R));
+// Elements j, j + 1 (j even) of a row whose start is 16-byte aligned; entries at or past n are 0 and
+// not loaded.
+__device__ __forceinline__ double2 load_pair(const double* row, int64_t j, int64_t n) {
+  if (j + 1 < n) return __ldcs(reinterpret_cast<const double2*>(row + j));
+  return make_double2(j < n ? row[j] : 0.0, 0.0);
+}
+
+// Shared memory of one round CTA: the staged chunk of the iterate (FP64 X, its split words, or the
+// FP32 inner iterate D; kSRhs columns x kKC entries) and the cross-warp partial sums of the inner sweep.
+struct SrvSmem {
+  union {
+    double x[kSRhs][kKC];
+    float2 xs[kSRhs][kKC];
+    float4 d[kSRhs][kKC / 4];
+  };
+  float part[kSRows / 4][4][kSRhs];
+};
+
+// Stage entries [j0, j0 + kKC) of r columns of a [r][ld] vector block (zero past ld) into shared memory.
+template <typename T>
+__device__ __forceinline__ void stage_cols(const T* __restrict__ v, int64_t r, int64_t ld, int64_t j0,
+                                           T (*dst)[kKC]) {
+  for (int e = threadIdx.x; e < static_cast<int>(r) * kKC; e += kSThreads) {
+    const int c = e / kKC, jj = e % kKC;
+    dst[c][jj] = j0 + jj < ld ? v[c * ld + j0 + jj] : T{};
   }
 }
 
-// The same residual with the split-float arithmetic of splitfloat.cuh (FP32 units): a_ij split with the
-// row's scale as it is read, X from its two FP32 words, float-float lane sums, FP64 across lanes.
-template <int RB>
-__device__ void resid_rows_split(const SrvReq& q, int64_t i0, int lane) {
-  FF acc[2 * RB];
+// Residual R = B - A X of the work item's rows r0 + 2 warp + {0, 1} for RB >= r columns: FP64 FMAs, or
+// (kSplit) the split-float arithmetic of splitfloat.cuh on the FP32 units.  X is staged per CTA in
+// chunks of kKC columns; every warp takes part in the staging, also when its rows are past n.  The FP64
+// form accumulates both rows in one pass; the split form takes one row per pass (its float-float
+// accumulators are twice as wide), staging X once per pass.
+template <int RB, bool kSplit>
+__device__ void resid_item(const SrvReq& q, int64_t r0, int warp, int lane, SrvSmem& sm) {
+  using Acc = typename std::conditional<kSplit, FF, double>::type;
+  constexpr int RP = kSplit ? 1 : 2;  // rows per pass
+  const int64_t n = q.n, ld = q.ld, i0 = r0 + 2 * warp;
+  const int r = static_cast<int>(q.r);
+  for (int pass = 0; pass < 2 / RP; ++pass) {
+    const int64_t ia = i0 + RP * pass;  // first row of this pass
+    const bool has0 = ia < n, has1 = RP == 2 && ia + 1 < n;
+    const double* A0 = q.A + (has0 ? ia : 0) * ld;
+    const double* A1 = q.A + (has1 ? ia + 1 : 0) * ld;
+    const int sh0 = kSplit && has0 ? q.rexp[ia] : 0;
+    Acc acc[RP * RB];
 #pragma unroll
-  for (int v = 0; v < 2 * RB; ++v) acc[v] = FF{0.0f, 0.0f};
-  const bool has1 = i0 + 1 < q.n;
-  const double* A0 = q.A + i0 * q.n;
-  const double* A1 = has1 ? A0 + q.n : A0;
-  const int sh0 = q.rexp[i0], sh1 = has1 ? q.rexp[i0 + 1] : 0;
-  const float2* X = q.xsel ? q.xs[1] : q.xs[0];
-  int since = 0;
-  for (int64_t j = lane; j < q.n; j += 32) {
-    float h0, l0, h1 = 0.0f, l1 = 0.0f;
-    split_scaled(__ldg(A0 + j), sh0, h0, l0);
-    if (has1) split_scaled(__ldg(A1 + j), sh1, h1, l1);
+    for (int v = 0; v < RP * RB; ++v) acc[v] = Acc{};
+    for (int64_t j0 = 0; j0 < n; j0 += kKC) {
+      __syncthreads();  // the previous chunk is consumed
+      if constexpr (kSplit)
+        stage_cols(q.xsel ? q.xs[1] : q.xs[0], r, ld, j0, sm.xs);
+      else
+        stage_cols(q.xsel ? q.X[1] : q.X[0], r, ld, j0, sm.x);
+      __syncthreads();
+      if (has0) {
+        // lane l takes columns 2 l + 64 t (t < kKC / 64) of the chunk: all of its A loads (16 bytes each,
+        // rows are 128-byte aligned) are issued before the arithmetic; columns past n read as 0 (the
+        // row padding is never read)
+        double2 a0v[kKC / 64], a1v[kKC / 64];
 #pragma unroll
-    for (int c = 0; c < RB; ++c)
-      if (c < q.r) {
-        const float2 x = __ldg(X + c * q.ld + j);
-        ff_fma(acc[c], h0, l0, x.x, x.y);
-        ff_fma(acc[RB + c], h1, l1, x.x, x.y);
+        for (int t = 0; t < kKC / 64; ++t) {
+          const int64_t j = j0 + 2 * lane + 64 * t;
+          a0v[t] = load_pair(A0, j, n);
+          a1v[t] = has1 ? load_pair(A1, j, n) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int t = 0; t < kKC / 64; ++t) {
+          const int jp = lane + 32 * t;  // index of the column pair in the chunk
+          if constexpr (kSplit) {
+            float h0, l0, h1, l1;
+            split_scaled(a0v[t].x, sh0, h0, l0);
+            split_scaled(a0v[t].y, sh0, h1, l1);
+#pragma unroll
+            for (int c = 0; c < RB; ++c)
+              if (c < r) {
+                const float4 x = reinterpret_cast<const float4*>(sm.xs[c])[jp];
+                ff_fma(acc[c], h0, l0, x.x, x.y);
+                ff_fma(acc[c], h1, l1, x.z, x.w);
+              }
+          } else {
+#pragma unroll
+            for (int c = 0; c < RB; ++c)
+              if (c < r) {
+                const double2 x = reinterpret_cast<const double2*>(sm.x[c])[jp];
+                acc[c] = fma(a0v[t].y, x.y, fma(a0v[t].x, x.x, acc[c]));
+                acc[RB + c] = fma(a1v[t].y, x.y, fma(a1v[t].x, x.x, acc[RB + c]));
+              }
+          }
+        }
+        if constexpr (kSplit) {
+#pragma unroll
+          for (int v = 0; v < RB; ++v) ff_renorm(acc[v]);
+        }
       }
-    if (++since == 8) {
-      since = 0;
+    }
+    if (!has0) continue;  // warp-uniform; the next pass (if any) has no valid row either
+    // one transposed reduction per row (RB values each), FP64 across lanes
 #pragma unroll
-      for (int v = 0; v < 2 * RB; ++v) ff_renorm(acc[v]);
+    for (int rr = 0; rr < RP; ++rr) {
+      double dv[RB];
+#pragma unroll
+      for (int c = 0; c < RB; ++c) {
+        if constexpr (kSplit)
+          dv[c] = static_cast<double>(acc[rr * RB + c].hi) + static_cast<double>(acc[rr * RB + c].lo);
+        else
+          dv[c] = acc[rr * RB + c];
+      }
+      const double tot = tr_finish<RB>(TRs<RB, 16, double>::run(dv, lane));
+      const int c = tr_index<RB>(lane);
+      const int64_t i = ia + rr;
+      if ((lane & (32 / RB - 1)) == 0 && i < n && c < r) {
+        const int64_t o = c * ld + i;
+        const double dot = kSplit ? tot * pow2(sh0) * pow2(q.xg[c]) : tot;
+        const double R = q.B[o] - dot;
+        const float cc = static_cast<float>(R * q.rinv[i]);
+        q.C1[o] = cc;
+        q.D[0][o] = cc;
+        umax_to(q.st + c, abs_bits(R));
+      }
     }
   }
-  double dv[2 * RB];
-#pragma unroll
-  for (int v = 0; v < 2 * RB; ++v) dv[v] = static_cast<double>(acc[v].hi) + static_cast<double>(acc[v].lo);
-  const double tot = tr_finish<2 * RB>(TRs<2 * RB, 16, double>::run(dv, lane));
-  const int v = tr_index<2 * RB>(lane);
-  const int64_t i = i0 + v / RB;
-  const int c = v % RB;
-  if ((lane & (32 / (2 * RB) - 1)) == 0 && i < q.n && c < q.r) {
-    const int64_t o = c * q.ld + i;
-    const double dot = tot * pow2(v / RB ? sh1 : sh0) * pow2(q.xg[c]);
-    const double R = q.B[o] - dot;
-    const float cc = static_cast<float>(R * q.rinv[i]);
-    q.C1[o] = cc;
-    q.D[0][o] = cc;
-    umax_to(q.st + c, abs_bits(R));
-  }
 }
 
-// FP32 inner sweep of rows [i0, i0 + 2): D_new = C1 - (1/a_ii) N D_cur, X_alt = X_cur + D_new.
-template <int RB>
-__device__ void inner_rows(const SrvReq& q, int64_t i0, int lane) {
-  float acc[2 * RB];
+// FP32 inner sweep of the work item's 16 rows: D_new = C1 - (1/a_ii) N D_cur, X_alt = X_cur + D_new.
+// D_cur is staged per CTA in chunks of kKC columns.  Warps form 16 / RW row groups of RW rows; with RW = 4
+// the two warps of a group take one half of each chunk each and meet in shared memory, so every staged
+// value feeds RW rows (RW = 2 for 16 right-hand sides keeps the accumulators in registers).
+template <int RB, int RW>
+__device__ void inner_item(const SrvReq& q, int64_t r0, int warp, int lane, SrvSmem& sm) {
+  constexpr int KS = RW / 2;               // warps sharing a row group, each on 1 / KS of a chunk
+  constexpr int NG = kSRows / RW;          // row groups
+  constexpr int QPL = kKC / KS / 128;      // float4 quads per lane per chunk
+  static_assert(NG * KS == kSThreads / 32, "one warp per (row group, chunk part)");
+  const int grp = warp % NG, ks = warp / NG;
+  const int64_t n = q.n, ld = q.ld, ib = r0 + RW * grp;
+  float acc[RW][RB];
 #pragma unroll
-  for (int v = 0; v < 2 * RB; ++v) acc[v] = 0.0f;
-  const bool has1 = i0 + 1 < q.n;
-  const float* N0 = q.Nl + i0 * q.ld;
-  const float* N1 = has1 ? N0 + q.ld : N0;
+  for (int rr = 0; rr < RW; ++rr)
+#pragma unroll
+    for (int c = 0; c < RB; ++c) acc[rr][c] = 0.0f;
   const float* Dc = q.dsel ? q.D[1] : q.D[0];
-  for (int64_t j = 4 * lane; j < q.n; j += 128) {
-    const float4 m0 = __ldcg(reinterpret_cast<const float4*>(N0 + j));
-    const float4 m1 = has1 ? __ldcg(reinterpret_cast<const float4*>(N1 + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t j0 = 0; j0 < n; j0 += kKC) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < static_cast<int>(q.r) * (kKC / 4); e += kSThreads) {
+      const int c = e / (kKC / 4), q4 = e % (kKC / 4);
+      const int64_t j = j0 + 4 * q4;  // ld is a multiple of 16: a quad never straddles it
+      sm.d[c][q4] = j < ld ? __ldcg(reinterpret_cast<const float4*>(Dc + c * ld + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
 #pragma unroll
-    for (int c = 0; c < RB; ++c)
-      if (c < q.r) {
-        const float4 x = __ldcg(reinterpret_cast<const float4*>(Dc + c * q.ld + j));
-        acc[c] = fmaf(m0.x, x.x, fmaf(m0.y, x.y, fmaf(m0.z, x.z, fmaf(m0.w, x.w, acc[c]))));
-        acc[RB + c] = fmaf(m1.x, x.x, fmaf(m1.y, x.y, fmaf(m1.z, x.z, fmaf(m1.w, x.w, acc[RB + c]))));
+    for (int qq = 0; qq < QPL; ++qq) {
+      const int q4 = (kKC / KS) * ks / 4 + 32 * qq + lane;
+      const int64_t j = j0 + 4 * q4;
+      if (j < n) {  // the narrow rows are zero-padded up to ld, so the quad at j < ld is safe to read
+        float4 m[RW];
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr)
+          m[rr] = ib + rr < n ? __ldcs(reinterpret_cast<const float4*>(q.Nl + (ib + rr) * ld + j))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < RB; ++c)
+          if (c < q.r) {
+            const float4 x = sm.d[c][q4];
+#pragma unroll
+            for (int rr = 0; rr < RW; ++rr)
+              acc[rr][c] =
+                  fmaf(m[rr].x, x.x, fmaf(m[rr].y, x.y, fmaf(m[rr].z, x.z, fmaf(m[rr].w, x.w, acc[rr][c]))));
+          }
       }
+    }
   }
-  const float tot = tr_finish<2 * RB>(TRs<2 * RB, 16, float>::run(acc, lane));
-  const int v = tr_index<2 * RB>(lane);
-  const int64_t i = i0 + v / RB;
-  const int c = v % RB;
+  // lane sums: RW / 2 transposed reductions of 2 RB values (rows {0, 1}, {2, 3})
+  float tot[RW / 2];
+  int vidx = 0;
+#pragma unroll
+  for (int p = 0; p < RW / 2; ++p) {
+    float w[2 * RB];
+#pragma unroll
+    for (int c = 0; c < RB; ++c) {
+      w[c] = acc[2 * p][c];
+      w[RB + c] = acc[2 * p + 1][c];
+    }
+    tot[p] = tr_finish<2 * RB>(TRs<2 * RB, 16, float>::run(w, lane));
+    vidx = tr_index<2 * RB>(lane);
+  }
+  const bool owner = (lane & (32 / (2 * RB) - 1)) == 0;
+  const int c = vidx % RB, rsub = vidx / RB;
+  if (KS == 2) {
+    if (ks == 1 && owner) {
+#pragma unroll
+      for (int p = 0; p < RW / 2; ++p) sm.part[grp][2 * p + rsub][c] = tot[p];
+    }
+    __syncthreads();
+  }
   unsigned long long chg = 0, mag = 0;
-  if ((lane & (32 / (2 * RB) - 1)) == 0 && i < q.n && c < q.r) {
-    const int64_t o = c * q.ld + i;
-    const float val = fmaf(-q.rowfac[i], tot, q.C1[o]);
-    const float old = Dc[o];
-    (q.dsel ? q.D[0] : q.D[1])[o] = val;
-    const double xn = (q.xsel ? q.X[1] : q.X[0])[o] + static_cast<double>(val);
-    (q.xsel ? q.X[0] : q.X[1])[o] = xn;
-    if (q.split) (q.xsel ? q.xs[0] : q.xs[1])[o] = split_x(xn, q.xg[c]);
-    chg = abs_bits(val - old);
-    mag = abs_bits(val);
+  if (ks == 0 && owner && c < q.r) {
+#pragma unroll
+    for (int p = 0; p < RW / 2; ++p) {
+      const int64_t i = ib + 2 * p + rsub;
+      if (i < n) {
+        const float sum = KS == 2 ? tot[p] + sm.part[grp][2 * p + rsub][c] : tot[p];
+        const int64_t o = c * ld + i;
+        const float val = fmaf(-q.rowfac[i], sum, q.C1[o]);
+        const float old = Dc[o];
+        (q.dsel ? q.D[0] : q.D[1])[o] = val;
+        const double xn = (q.xsel ? q.X[1] : q.X[0])[o] + static_cast<double>(val);
+        (q.xsel ? q.X[0] : q.X[1])[o] = xn;
+        if (q.split) (q.xsel ? q.xs[0] : q.xs[1])[o] = split_x(xn, q.xg[c]);
+        const unsigned long long cb = abs_bits(val - old), mb = abs_bits(val);
+        chg = cb > chg ? cb : chg;
+        mag = mb > mag ? mb : mag;
+      }
+    }
   }
   chg = warp_max_u64(chg);
   mag = warp_max_u64(mag);
@@ -317,18 +450,20 @@ __device__ void inner_rows(const SrvReq& q, int64_t i0, int lane) {
 }
 
 template <int RB>
-__device__ __forceinline__ void run_item(const SrvReq& q, int64_t i0, int lane) {
+__device__ __forceinline__ void run_item(const SrvReq& q, int64_t r0, int warp, int lane, SrvSmem& sm) {
   if (q.phase == kPhResid) {
     if (q.split)
-      resid_rows_split<RB>(q, i0, lane);
+      resid_item<RB, true>(q, r0, warp, lane, sm);
     else
-      resid_rows<RB>(q, i0, lane);
-  } else
-    inner_rows<RB>(q, i0, lane);
+      resid_item<RB, false>(q, r0, warp, lane, sm);
+  } else {
+    inner_item<RB, RB == 16 ? 2 : 4>(q, r0, warp, lane, sm);
+  }
 }
 
-__global__ void __launch_bounds__(kSThreads) serve_round_kernel(const SrvReq* __restrict__ reqs, int nreq,
-                                                                const int64_t* __restrict__ first, int64_t items) {
+__global__ void __launch_bounds__(kSThreads, 2) serve_round_kernel(const SrvReq* __restrict__ reqs, int nreq,
+                                                                   const int64_t* __restrict__ first, int64_t items) {
+  __shared__ SrvSmem sm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     int lo = 0, hi = nreq - 1;  // request owning this item: last k with first[k] <= it
@@ -340,19 +475,20 @@ __global__ void __launch_bounds__(kSThreads) serve_round_kernel(const SrvReq* __
         hi = mid - 1;
     }
     const SrvReq& q = reqs[lo];  // fields read on demand (L1); dynamic indexing stays off the stack
-    const int64_t i0 = (it - first[lo]) * kSRows + 2 * warp;
-    if (i0 >= q.n) continue;  // warp-uniform
+    const int64_t r0 = (it - first[lo]) * kSRows;  // CTA-uniform
     if (q.phase == kPhPrep) {
-      prep_rows(q, i0, lane);
+      const int64_t i0 = r0 + 2 * warp;
+      if (i0 < q.n) prep_rows(q, i0, lane);
       continue;
     }
     switch (q.rb) {
-      case 1: run_item<1>(q, i0, lane); break;
-      case 2: run_item<2>(q, i0, lane); break;
-      case 4: run_item<4>(q, i0, lane); break;
-      case 8: run_item<8>(q, i0, lane); break;
-      default: run_item<16>(q, i0, lane); break;
+      case 1: run_item<1>(q, r0, warp, lane, sm); break;
+      case 2: run_item<2>(q, r0, warp, lane, sm); break;
+      case 4: run_item<4>(q, r0, warp, lane, sm); break;
+      case 8: run_item<8>(q, r0, warp, lane, sm); break;
+      default: run_item<16>(q, r0, warp, lane, sm); break;
     }
+    __syncthreads();  // the next item restages shared memory
   }
 }
 
@@ -421,7 +557,7 @@ struct Request {
 
 size_t request_bytes(int64_t n, int64_t r, int64_t ld, bool own_A, bool split) {
   size_t b = 0;
-  if (own_A) b += a256(static_cast<size_t>(n) * n * 8);
+  if (own_A) b += a256(static_cast<size_t>(n) * ld * 8);    // A, rows padded to ld (128-byte aligned)
   b += a256(static_cast<size_t>(n) * ld * 4);                // Nl
   b += 2 * a256(static_cast<size_t>(ld) * 8) + a256(static_cast<size_t>(ld) * 4);  // d, rinv, rowfac
   b += 3 * a256(static_cast<size_t>(r) * ld * 8);             // B, X0, X1
@@ -498,7 +634,7 @@ int rbucket(int64_t r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 
 
 // Admit one request: carve its arena block, lay out its buffers, fill A and B, set phase PREP.
 bool admit(jacobi_server* s, Request* rq) {
-  const bool own_A = true;  // A always lives in the arena (copied or generated), row stride n
+  const bool own_A = true;  // A always lives in the arena (copied or generated), row stride ld
   rq->ld = round_up(rq->n, kLdAlign);
   rq->bytes = request_bytes(rq->n, rq->r, rq->ld, own_A, s->split);
   if (!s->arena.alloc(rq->bytes, &rq->off)) return false;
@@ -514,7 +650,7 @@ bool admit(jacobi_server* s, Request* rq) {
     return at;
   };
   const int64_t n = rq->n, r = rq->r, ld = rq->ld;
-  double* A = reinterpret_cast<double*>(take(static_cast<size_t>(n) * n * 8));
+  double* A = reinterpret_cast<double*>(take(static_cast<size_t>(n) * ld * 8));
   q.A = A;
   q.Nl = reinterpret_cast<float*>(take(static_cast<size_t>(n) * ld * 4));
   q.d = reinterpret_cast<double*>(take(static_cast<size_t>(ld) * 8));
@@ -540,10 +676,10 @@ bool admit(jacobi_server* s, Request* rq) {
   cudaMemsetAsync(B, 0, vec_bytes, s->stream);
   if (rq->generate) {
     int64_t blocks = std::min<int64_t>(n, 4096);
-    serve_generate_kernel<<<static_cast<unsigned>(blocks), kSThreads, 0, s->stream>>>(n, r, ld, rq->f, rq->seed, A,
-                                                                                       B);
+    serve_generate_kernel<<<static_cast<unsigned>(blocks), kSThreads, 0, s->stream>>>(n, r, ld, ld, rq->f, rq->seed,
+                                                                                       A, B);
   } else {
-    cudaMemcpyAsync(A, rq->A_in, static_cast<size_t>(n) * n * 8, cudaMemcpyDefault, s->stream);
+    cudaMemcpy2DAsync(A, ld * 8, rq->A_in, n * 8, n * 8, n, cudaMemcpyDefault, s->stream);
     cudaMemcpy2DAsync(B, ld * 8, rq->B_in, n * 8, n * 8, r, cudaMemcpyDefault, s->stream);
   }
   q.phase = kPhPrep;
@@ -798,7 +934,7 @@ int jacobi_generate_request(int64_t n, int64_t r, double f, uint64_t seed, doubl
   if (n < 1 || r < 1 || !A || !B || ldb < n || !(f > 0.0)) return JACOBI_ERR_INVALID_ARG;
   const int64_t blocks = std::min<int64_t>(n, 4096);
   serve_generate_kernel<<<static_cast<unsigned>(blocks), kSThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      n, r, ldb, f, seed, A, B);
+      n, r, n, ldb, f, seed, A, B);
   return cudaGetLastError() == cudaSuccess ? JACOBI_OK : JACOBI_ERR_CUDA;
 }
 
