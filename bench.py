@@ -304,7 +304,7 @@ def run_batch(args, jac, torch, dev):
     sum_n2 = float(np.sum(ns.astype(np.float64) ** 2))
     stream = torch.cuda.current_stream(dev)
     out = {"count": count, "n_range": [64, 1024], "f_range": [1.05, 2.0], "sum_n2": sum_n2}
-    for name in ("fp32_ir", "fp32_ir+split", "fp64"):
+    for name in ("fp32_ir", "fp32_ir+split", "bf16_ir", "fp64"):
         prec, split = name.replace("+split", ""), name.endswith("+split")
         tuned = autotune.tune_batch(As, Bs, precision=prec, tol=TARGET, use_cache=True, split_residual=split)
         bs = jac.BatchSolver(As, Bs, precision=prec, rows_per_warp=tuned["rows_per_warp"],
@@ -329,8 +329,9 @@ def run_batch(args, jac, torch, dev):
             worst = float(max(x.final_delta for x in st))
         else:
             outer = np.array([x.outer_steps for x in st], dtype=np.float64)
-            # setup pass (read A, write the FP32 copy) + FP64 residual passes + FP32 inner sweeps
-            alg = float(np.sum((8.0 + 4.0) * n2 + np.maximum(outer - 1, 0) * 8.0 * n2 + sweeps * 4.0 * n2))
+            # setup pass (read A, write the narrow copy) + FP64 residual passes + narrow inner sweeps
+            es = 2.0 if prec == "bf16_ir" else 4.0
+            alg = float(np.sum((8.0 + es) * n2 + np.maximum(outer - 1, 0) * 8.0 * n2 + sweeps * es * n2))
             worst = float(max(x.rel_residual for x in st))
         out[name] = {"solves_per_s": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 4),
                      "converged": ok, "mean_sweeps": round(float(sweeps.mean()), 3),
@@ -343,6 +344,7 @@ def run_batch(args, jac, torch, dev):
     out["mixed_vs_fp64_solves_ratio"] = round(out["fp32_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     out["mixed_split_vs_fp64_solves_ratio"] = round(
         out["fp32_ir+split"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
+    out["bf16_vs_fp64_solves_ratio"] = round(out["bf16_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     return out
 
 

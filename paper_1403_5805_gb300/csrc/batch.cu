@@ -286,18 +286,15 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
     if (kMode != 0) {
       TL* Nl = static_cast<TL*>(S.Nlow);
       for (int64_t i = warp; i < n; i += kBWarps) {
-        unsigned long long mb = 0;
+        uint32_t mb = 0;
         for (int64_t j = lane; j < S.ldn; j += 32) {
           const double a = j < n ? __ldg(S.A + i * n + j) : 0.0;
-          if constexpr (kSplit) {
-            const unsigned long long ab = abs_bits(a);
-            mb = ab > mb ? ab : mb;
-          }
+          if constexpr (kSplit) mb = max(mb, abs_hi(a));
           Nl[i * S.ldn + j] = (j < n && j != i) ? encode_narrow<TL>(a) : TL(0.0f);
         }
         if constexpr (kSplit) {
-          mb = warp_max_u64(mb);
-          if (lane == 0) S.rexp[i] = split_exponent(mb);
+          mb = __reduce_max_sync(0xffffffffu, mb);
+          if (lane == 0) S.rexp[i] = split_exponent_hi(mb);
         }
       }
       if constexpr (kSplit)

@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
 template <int NC>
 __global__ void __launch_bounds__(kDThreads, 2) mrhs_split_resid_kernel(MrhsDenseParams p) {
   constexpr int kN = 16 * NC;
-  __shared__ float Ah[kDK][kDM + 1], Al[kDK][kDM + 1];
-  __shared__ float Xh[kDK][kN + 1], Xl[kDK][kN + 1];
+  __shared__ float2 As[kDK][kDM + 1];  // (hi, lo) of the split A tile, transposed
+  __shared__ float2 Xs[kDK][kN + 1];   // (hi, lo) of the X tile
   __shared__ int sh_row[kDM], g_col[kN];
   const int tid = threadIdx.x;
   const int tr = tid / 16, tc = tid % 16;
@@ -345,35 +345,27 @@ __global__ void __launch_bounds__(kDThreads, 2) mrhs_split_resid_kernel(MrhsDens
       const double a = (gi < p.n && gk < p.n) ? __ldg(p.A + gi * p.lda + gk) : 0.0;
       float hi, lo;
       split_scaled(a, sh_row[m], hi, lo);
-      Ah[k][m] = hi;
-      Al[k][m] = lo;
+      As[k][m] = make_float2(hi, lo);
     }
     for (int e = tid; e < kDK * kN; e += kDThreads) {
       const int c = e / kDK, k = e % kDK;
       const int64_t gk = k0 + k;
       const float2 v = (gk < p.n && c0 + c < p.r) ? __ldg(p.xs + static_cast<int64_t>(c0 + c) * p.ld + gk)
                                                  : make_float2(0.0f, 0.0f);
-      Xh[k][c] = v.x;
-      Xl[k][c] = v.y;
+      Xs[k][c] = v;
     }
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < kDK; ++k) {
-      float ah[4], al[4], xh[NC], xl[NC];
+      float2 a[4], x[NC];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        ah[u] = Ah[k][tr + 16 * u];
-        al[u] = Al[k][tr + 16 * u];
-      }
+      for (int u = 0; u < 4; ++u) a[u] = As[k][tr + 16 * u];
 #pragma unroll
-      for (int v = 0; v < NC; ++v) {
-        xh[v] = Xh[k][tc + 16 * v];
-        xl[v] = Xl[k][tc + 16 * v];
-      }
+      for (int v = 0; v < NC; ++v) x[v] = Xs[k][tc + 16 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < NC; ++v) ff_fma(acc[u][v], ah[u], al[u], xh[v], xl[v]);
+        for (int v = 0; v < NC; ++v) ff_fma(acc[u][v], a[u].x, a[u].y, x[v].x, x[v].y);
       if ((k & 7) == 7) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)

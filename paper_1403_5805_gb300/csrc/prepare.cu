@@ -144,14 +144,13 @@ __device__ __forceinline__ T block_max(T v, T* sh) {
 // One CTA per row (grid-stride over rows): narrow copy of the off-diagonal part of row i, padding
 // zeroed up to ldn, the row factor of the inner sweep and (if rexp) the row's split-float scale
 // exponent.  Each thread converts 4 consecutive elements per step: two 16-byte loads, one store.
-template <typename TL, bool kScaled>
+template <typename TL, bool kScaled, bool kRexp>
 __global__ void __launch_bounds__(kPrepThreads) narrow_kernel(const double* __restrict__ A, int64_t lda, int64_t n,
                                                               TL* __restrict__ Nl, int64_t ldn,
                                                               const double* __restrict__ rinv,
                                                               float* __restrict__ scale, float* __restrict__ rowfac,
                                                               int* __restrict__ rexp) {
   __shared__ unsigned int shs[32];
-  __shared__ unsigned long long shb[32];
   const int64_t step = 4 * int64_t(blockDim.x);
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const double* row = A + i * lda;
@@ -174,25 +173,24 @@ __global__ void __launch_bounds__(kPrepThreads) narrow_kernel(const double* __re
       if (s == 0.0f) s = 1.0f;
     }
     TL* out = Nl + i * ldn;
-    unsigned long long mb = 0;  // max_j |a_ij| (all j, as IEEE bits)
+    uint32_t mb = 0;  // max_j of the high word of |a_ij| (all j)
 #pragma unroll 2
     for (int64_t j = 4 * int64_t(threadIdx.x); j < ldn; j += step) {
       double a[4];
       float f[4];
       load_quad(row, j, n, a);
-      if (rexp) {
+      if constexpr (kRexp) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const unsigned long long b = abs_bits(a[e]);
-          mb = b > mb ? b : mb;
+          mb = max(mb, abs_hi(a[e]));
         }
       }
       quad_f32(a, j, n, i, f);
       encode_quad<TL>(f, s, out + j);
     }
-    if (rexp) {
-      mb = block_max(mb, shb);
-      if (threadIdx.x == 0) rexp[i] = split_exponent(mb);
+    if constexpr (kRexp) {
+      mb = block_max(mb, shs);
+      if (threadIdx.x == 0) rexp[i] = split_exponent_hi(mb);
     }
     if (threadIdx.x == 0) {
       if (kScaled) scale[i] = s;
@@ -250,23 +248,32 @@ cudaError_t launch_pad_zero(double* M, int64_t n, int64_t ld, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_narrow(Narrow kind, const double* A, int64_t lda, int64_t n, void* Nlow, int64_t ldn,
-                          const double* rinv, float* scale, float* rowfac, int* rexp, cudaStream_t s) {
-  const int blocks = prep_blocks(n, 1);
+template <bool kRexp>
+void narrow_launch(Narrow kind, int blocks, const double* A, int64_t lda, int64_t n, void* Nlow, int64_t ldn,
+                   const double* rinv, float* scale, float* rowfac, int* rexp, cudaStream_t s) {
   switch (kind) {
     case Narrow::F32:
-      narrow_kernel<float, false><<<blocks, kPrepThreads, 0, s>>>(A, lda, n, static_cast<float*>(Nlow), ldn, rinv,
-                                                                  scale, rowfac, rexp);
+      narrow_kernel<float, false, kRexp><<<blocks, kPrepThreads, 0, s>>>(A, lda, n, static_cast<float*>(Nlow), ldn,
+                                                                         rinv, scale, rowfac, rexp);
       break;
     case Narrow::BF16:
-      narrow_kernel<__nv_bfloat16, false><<<blocks, kPrepThreads, 0, s>>>(
+      narrow_kernel<__nv_bfloat16, false, kRexp><<<blocks, kPrepThreads, 0, s>>>(
           A, lda, n, static_cast<__nv_bfloat16*>(Nlow), ldn, rinv, scale, rowfac, rexp);
       break;
     case Narrow::E4M3:
-      narrow_kernel<__nv_fp8_e4m3, true><<<blocks, kPrepThreads, 0, s>>>(
+      narrow_kernel<__nv_fp8_e4m3, true, kRexp><<<blocks, kPrepThreads, 0, s>>>(
           A, lda, n, static_cast<__nv_fp8_e4m3*>(Nlow), ldn, rinv, scale, rowfac, rexp);
       break;
   }
+}
+
+cudaError_t launch_narrow(Narrow kind, const double* A, int64_t lda, int64_t n, void* Nlow, int64_t ldn,
+                          const double* rinv, float* scale, float* rowfac, int* rexp, cudaStream_t s) {
+  const int blocks = prep_blocks(n, 1);
+  if (rexp)
+    narrow_launch<true>(kind, blocks, A, lda, n, Nlow, ldn, rinv, scale, rowfac, rexp, s);
+  else
+    narrow_launch<false>(kind, blocks, A, lda, n, Nlow, ldn, rinv, scale, rowfac, rexp, s);
   return cudaGetLastError();
 }
 

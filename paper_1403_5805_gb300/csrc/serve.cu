@@ -179,7 +179,7 @@ __device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
     if (i >= n) break;
     const double* Ai = q.A + i * ld;
     float* Ni = q.Nl + i * ld;
-    unsigned long long mb = 0;
+    uint32_t mb = 0;  // max_j of the high word of |a_ij|
     for (int64_t j = 4 * lane; j < ld; j += 128) {
       double a[4];
       if (j + 4 <= n) {
@@ -196,15 +196,14 @@ __device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
       float f[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const unsigned long long bb = abs_bits(a[e]);
-        mb = bb > mb ? bb : mb;
+        mb = max(mb, abs_hi(a[e]));
         f[e] = (j + e < n && j + e != i) ? __double2float_rn(a[e]) : 0.0f;
       }
       *reinterpret_cast<float4*>(Ni + j) = make_float4(f[0], f[1], f[2], f[3]);
     }
     if (q.split) {
-      mb = warp_max_u64(mb);
-      if (lane == 0) q.rexp[i] = split_exponent(mb);
+      mb = __reduce_max_sync(0xffffffffu, mb);
+      if (lane == 0) q.rexp[i] = split_exponent_hi(mb);
     }
     const double a = Ai[i];
     const double ri = (a != 0.0 && isfinite(a)) ? __drcp_rn(a) : 0.0;

@@ -69,6 +69,15 @@ __device__ __forceinline__ int split_exponent(unsigned long long bits) {
   return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
 }
 
+// The same exponent from the maximum of the high 32 bits of |v| (sign cleared): the exponent field and
+// the zero / subnormal / non-finite cases sit there, so a 32-bit running maximum suffices.
+__device__ __forceinline__ uint32_t abs_hi(double v) {
+  return static_cast<uint32_t>(__double2hiint(v)) & 0x7FFFFFFFu;
+}
+__device__ __forceinline__ int split_exponent_hi(uint32_t hi_bits) {
+  return split_exponent(static_cast<unsigned long long>(hi_bits) << 32);
+}
+
 // x * 2^-g as an unevaluated pair of FP32 words: hi = fl32(x 2^-g), lo = fl32(x 2^-g - hi).
 __device__ __forceinline__ float2 split_x(double x, int g) {
   const double v = x * pow2(-g);
