@@ -176,3 +176,29 @@ def test_split_float_residual_accuracy_with_wild_row_scales(jac):
     assert st.outer_steps == 1 and st.sweeps == 0
     _, rel = oracle.residual(A, B, X0)
     assert abs(st.rel_residual - rel) <= 1e-12 * rel, (st.rel_residual, rel)
+
+
+@pytest.mark.parametrize("prec", ["fp32_ir", "bf16_ir", "fp8_ir"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_resident_inputs_match_device_inputs(jac, prec, pinned):
+    """A and B in host memory (pinned or pageable), copied into the workspace by the setup: the narrow
+    copy and the solution are identical, bit for bit, to those of the same system given in device
+    memory."""
+    import torch
+    n = 1000
+    A, B, _ = synth.dominant_system(n, 1.1, seed=95)
+    Ah = torch.from_numpy(A)
+    Bh = torch.from_numpy(B[:, 0].copy())
+    if pinned:
+        Ah, Bh = Ah.pin_memory(), Bh.pin_memory()
+    sh = jac.DeviceSolver(Ah, Bh, precision=prec, device=torch.device("cuda", 0))
+    sd = dev_solver(jac, A, B, precision=prec)
+    nh, sch = sh.narrow()
+    nd, scd = sd.narrow()
+    np.testing.assert_array_equal(nh, nd)
+    np.testing.assert_array_equal(sch, scd)
+    Xh, sth = sh.solve(max_iter=5000, tol=1e-10)
+    Xd, std = sd.solve(max_iter=5000, tol=1e-10)
+    assert torch.equal(Xh, Xd) and (sth.sweeps, sth.outer_steps) == (std.sweeps, std.outer_steps)
+    _, rel = oracle.residual(A, B, Xh.cpu().numpy())
+    assert sth.status == 0 and rel <= 1e-10
