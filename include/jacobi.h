@@ -151,6 +151,13 @@ typedef struct jacobi_desc {
 /* Test only: the first ring item of each solve is announced to the consumers but never copied, so their
  * bounded wait expires; the solve then returns JACOBI_ERR_TIMEOUT and the context stays usable. */
 #define JACOBI_FLAG_TEST_DROP_COPY 8
+/* Many right-hand sides: retire each column as soon as it meets the stopping test on its own (the
+ * FP64 path: its change norm below tol; the BF16 path: its relative residual at or below tol) instead of
+ * iterating every column until the worst one does.  A retired column keeps the iterate that met the test
+ * (so each column equals the single-right-hand-side solve of that column), and later passes skip it:
+ * the FP64 sweeps and FP64 residual evaluations only touch the columns still active.  Per-column counts
+ * come from jacobi_column_stats. */
+#define JACOBI_FLAG_RETIRE_COLUMNS 16
 
 /* Fill *d with defaults (n = 0 and null pointers: the caller sets those). */
 JACOBI_API void jacobi_desc_init(jacobi_desc* d);
@@ -185,6 +192,12 @@ JACOBI_API int jacobi_last_stats(jacobi_handle* h, jacobi_stats* stats);
 /* Relative residual ||B - A X||_inf / ||B||_inf of a device X (n, ld = n) against the handle's FP64 A and
  * B, computed on the device in FP64 with the handle's streaming kernel; waits for the stream. */
 JACOBI_API int jacobi_residual(jacobi_handle* h, const double* X, double* rel_out);
+
+/* Per-column record of the last solve of a many-right-hand-side handle (host arrays of nrhs entries,
+ * either may be NULL): iters[c] = sweeps (FP64) or residual evaluations (BF16 IR) after which column c
+ * finished (retired, or the solve ended), value[c] = its last change norm (FP64) or relative residual
+ * (BF16 IR).  JACOBI_ERR_INVALID_ARG for a single-right-hand-side handle. */
+JACOBI_API int jacobi_column_stats(jacobi_handle* h, int64_t* iters, double* value);
 
 /* Copy the narrow off-diagonal matrix that the inner sweeps of an IR handle read to host memory:
  * dst_host is row-major n x ld_dst (ld_dst >= n) of the precision's element type (FP32 values, BF16

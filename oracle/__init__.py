@@ -51,6 +51,9 @@ def _load():
                                           ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(_c_i64),
                                           _c_dp, vp]
             lib.oracle_jacobi.restype = ctypes.c_int
+            lib.oracle_block_sor.argtypes = [_c_i64, _c_i64, vp, vp, vp, _c_i64, ctypes.c_double, ctypes.c_int,
+                                             _c_i64, vp, ctypes.c_double, vp, ctypes.POINTER(_c_i64), _c_dp, vp]
+            lib.oracle_block_sor.restype = ctypes.c_int
             lib.oracle_ge.argtypes = [_c_i64, _c_i64, vp, vp, vp]
             lib.oracle_ge.restype = ctypes.c_int
             lib.oracle_residual.argtypes = [_c_i64, _c_i64, vp, vp, vp, vp, _c_dp]
@@ -115,6 +118,34 @@ def jacobi(A, B, X0=None, max_iter: int = 1000, tol: float = 1e-12, norm: int = 
     st = lib.oracle_jacobi(n, r, _ptr(A), _ptr(Bc), None if X0c is None else _ptr(X0c), max_iter,
                            tol, norm, nthreads, _ptr(Xo), ctypes.byref(it), ctypes.byref(de),
                            None if tr is None else _ptr(tr))
+    k = int(it.value)
+    tr_out = None if tr is None else np.ascontiguousarray(tr[:k].transpose(0, 2, 1))
+    return JacobiResult(st, Xo.T.copy(), k, float(de.value), tr_out)
+
+
+def uniform_blocks(n: int, nblocks: int) -> np.ndarray:
+    """Offsets of nblocks consecutive row blocks of near-equal size: s_b = floor(n b / nblocks)."""
+    return np.array([n * b // nblocks for b in range(nblocks + 1)], dtype=np.int64)
+
+
+def block_sor(A, B, X0=None, max_iter: int = 1000, tol: float = 1e-12, norm: int = NORM_INF,
+              blocks=1, omega: float = 1.0, trace: bool = False) -> JacobiResult:
+    """Block-hybrid Gauss-Seidel / SOR (Gauss-Seidel inside consecutive row blocks, Jacobi across them,
+    relaxation omega) on the CPU in FP64.  blocks: a block count (uniform split) or the offsets."""
+    lib = _load()
+    A = _mat(A)
+    n = A.shape[0]
+    Bc = _cols(B, n)
+    r = Bc.shape[0]
+    starts = uniform_blocks(n, int(blocks)) if np.isscalar(blocks) else np.ascontiguousarray(blocks, dtype=np.int64)
+    X0c = None if X0 is None else _cols(X0, n)
+    Xo = np.zeros((r, n))
+    it = _c_i64(0)
+    de = ctypes.c_double(0.0)
+    tr = np.zeros((max_iter, r, n)) if trace else None
+    st = lib.oracle_block_sor(n, r, _ptr(A), _ptr(Bc), None if X0c is None else _ptr(X0c), max_iter, tol, norm,
+                              len(starts) - 1, starts.ctypes.data_as(ctypes.c_void_p), ctypes.c_double(omega),
+                              _ptr(Xo), ctypes.byref(it), ctypes.byref(de), None if tr is None else _ptr(tr))
     k = int(it.value)
     tr_out = None if tr is None else np.ascontiguousarray(tr[:k].transpose(0, 2, 1))
     return JacobiResult(st, Xo.T.copy(), k, float(de.value), tr_out)

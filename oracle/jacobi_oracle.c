@@ -153,6 +153,94 @@ int oracle_jacobi(int64_t n, int64_t nrhs, const double* A, const double* B, con
 }
 
 /*
+ * Block-hybrid Gauss-Seidel / SOR, the relaxed relative of the Section 2 iteration that the paper's
+ * introduction lists among the iterative solvers, in the row-blocked form a parallel machine runs:
+ * the unknowns are split into consecutive row blocks [s_b, s_(b+1)); inside a block the components
+ * are updated in ascending order using the block's newest values, across blocks using the previous
+ * iterate, and each update is relaxed by omega:
+ *   v_i     = ( beta_i - sum_{j != i} alpha_ij xt_j ) / alpha_ii,
+ *             xt_j = x_j^(k) if s_b <= j < i (same block, already updated), else x_j^(k-1)
+ *   x_i^(k) = v_i                                  if omega == 1 (Gauss-Seidel inside blocks)
+ *           = x_i^(k-1) + omega (v_i - x_i^(k-1))  otherwise.
+ * One block per row with omega = 1 is exactly the Jacobi iteration above; a single block is classical
+ * SOR (Gauss-Seidel for omega = 1).  The control flow, the stopping test (strict, on the change between
+ * consecutive iterates, norm 0 or 1 of oracle_jacobi) and the return conventions are those of
+ * oracle_jacobi.  block_start holds nblocks + 1 ascending offsets from 0 to n.
+ */
+int oracle_block_sor(int64_t n, int64_t nrhs, const double* A, const double* B, const double* X0,
+                     int64_t max_iter, double tol, int norm, int64_t nblocks, const int64_t* block_start,
+                     double omega, double* X_out, int64_t* iters_out, double* delta_out, double* trace) {
+  if (n < 1 || nrhs < 1 || !A || !B || !X_out || !iters_out || !delta_out || !block_start) return OR_INVALID_ARG;
+  if (max_iter < 1 || !(tol > 0.0) || (norm != OR_NORM_INF && norm != OR_NORM_2)) return OR_INVALID_ARG;
+  if (nblocks < 1 || block_start[0] != 0 || block_start[nblocks] != n) return OR_INVALID_ARG;
+  for (int64_t b = 0; b < nblocks; ++b)
+    if (block_start[b + 1] < block_start[b]) return OR_INVALID_ARG;
+  if (!(omega > 0.0 && omega < 2.0)) return OR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    double d = A[i * n + i];
+    if (!isfinite(d)) return OR_NONFINITE;
+    if (d == 0.0) return OR_ZERO_DIAGONAL;
+  }
+  size_t len = (size_t)n * (size_t)nrhs;
+  double* Xt = (double*)malloc(len * sizeof(double));
+  double* X = (double*)malloc(len * sizeof(double));
+  if (!Xt || !X) {
+    free(Xt);
+    free(X);
+    return OR_NO_MEMORY;
+  }
+  if (X0)
+    memcpy(Xt, X0, len * sizeof(double));
+  else
+    memset(Xt, 0, len * sizeof(double));
+
+  int status = OR_NOT_CONVERGED;
+  int64_t k;
+  double delta = 0.0;
+  for (k = 1; k <= max_iter; ++k) {
+    for (int64_t b = 0; b < nblocks; ++b) {
+      const int64_t s0 = block_start[b], s1 = block_start[b + 1];
+      for (int64_t i = s0; i < s1; ++i) {
+        for (int64_t c = 0; c < nrhs; ++c) {
+          double s = 0.0;
+          for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double xj = (j >= s0 && j < i) ? X[c * n + j] : Xt[c * n + j];
+            s += A[i * n + j] * xj;
+          }
+          const double v = (B[c * n + i] - s) / A[i * n + i];
+          X[c * n + i] = omega == 1.0 ? v : Xt[c * n + i] + omega * (v - Xt[c * n + i]);
+        }
+      }
+    }
+    if (trace) memcpy(trace + (size_t)(k - 1) * len, X, len * sizeof(double));
+    delta = or_norm_of_change(n, nrhs, A, B, X, Xt, norm);
+    if (!isfinite(delta)) {
+      status = OR_NONFINITE;
+      memcpy(X_out, X, len * sizeof(double));
+      break;
+    }
+    if (delta < tol) {
+      status = OR_OK;
+      memcpy(X_out, X, len * sizeof(double));
+      break;
+    }
+    double* tmp = Xt;
+    Xt = X;
+    X = tmp;
+  }
+  if (status == OR_NOT_CONVERGED) {
+    k = max_iter;
+    memcpy(X_out, Xt, len * sizeof(double));
+  }
+  *iters_out = k;
+  *delta_out = delta;
+  free(Xt);
+  free(X);
+  return status;
+}
+
+/*
  * Gaussian elimination with partial (row) pivoting, then back substitution: the textbook direct
  * solver used to pin the converged Jacobi value on small systems.  Returns -2 on an exactly zero pivot.
  */

@@ -31,11 +31,12 @@ FLAG_COPY_A = 1
 FLAG_SPLIT_RESIDUAL = 2
 FLAG_SHORT_WAITS = 4
 FLAG_TEST_DROP_COPY = 8
+FLAG_RETIRE_COLUMNS = 16
 
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
            "jacobi_desc_init", "jacobi_workspace_size", "jacobi_setup_ex", "jacobi_solve_async",
            "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual", "jacobi_get_narrow",
-           "jacobi_last_trace", "jacobi_solve_fp64_noalloc", "jacobi_batch_workspace_size",
+           "jacobi_last_trace", "jacobi_column_stats", "jacobi_solve_fp64_noalloc", "jacobi_batch_workspace_size",
            "jacobi_batch_create", "jacobi_batch_solve_async", "jacobi_batch_stats", "jacobi_batch_grid",
            "jacobi_batch_destroy", "jacobi_server_create", "jacobi_server_submit", "jacobi_server_submit_generated",
            "jacobi_server_step", "jacobi_server_poll", "jacobi_server_rounds", "jacobi_server_destroy",
@@ -114,6 +115,7 @@ def load() -> ctypes.CDLL:
         lib.jacobi_residual.argtypes = [H, vp, ctypes.POINTER(dbl)]
         lib.jacobi_get_narrow.argtypes = [H, vp, i64, vp]
         lib.jacobi_last_trace.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_column_stats.argtypes = [H, vp, vp]
         lib.jacobi_batch_workspace_size.argtypes = [ctypes.POINTER(JacobiBatchDesc), ctypes.POINTER(ctypes.c_size_t)]
         lib.jacobi_batch_create.argtypes = [ctypes.POINTER(JacobiBatchDesc), ctypes.POINTER(H)]
         lib.jacobi_batch_solve_async.argtypes = [H, i64, dbl]
@@ -133,7 +135,7 @@ def load() -> ctypes.CDLL:
         lib.jacobi_solve_fp64_noalloc.argtypes = [vp, i64, vp, i64, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats), vp]
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
                      "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
-                     "jacobi_get_narrow", "jacobi_last_trace", "jacobi_solve_fp64_noalloc",
+                     "jacobi_get_narrow", "jacobi_last_trace", "jacobi_column_stats", "jacobi_solve_fp64_noalloc",
                      "jacobi_batch_workspace_size", "jacobi_batch_create", "jacobi_batch_solve_async",
                      "jacobi_batch_stats", "jacobi_batch_grid", "jacobi_server_create", "jacobi_server_submit",
                      "jacobi_server_submit_generated", "jacobi_server_step", "jacobi_server_poll",
@@ -381,7 +383,8 @@ class MultiSolver:
     float64 CUDA tensors (row c is right-hand side c, i.e. column-major n x r)."""
 
     def __init__(self, A, B, precision: str = "bf16_ir", stream=None, max_outer: int = 0, max_inner: int = 0,
-                 inner_rtol: float = 0.0, norm: str = "inf", split_residual: bool = False):
+                 inner_rtol: float = 0.0, norm: str = "inf", split_residual: bool = False,
+                 retire_columns: bool = False):
         import torch
         lib = load()
         n = A.shape[0]
@@ -399,7 +402,7 @@ class MultiSolver:
         d.B, d.ldb = B.data_ptr(), B.stride(0)
         d.stream = self.stream.cuda_stream
         d.max_outer, d.max_inner, d.inner_rtol = max_outer, max_inner, inner_rtol
-        d.flags = FLAG_SPLIT_RESIDUAL if split_residual else 0
+        d.flags = (FLAG_SPLIT_RESIDUAL if split_residual else 0) | (FLAG_RETIRE_COLUMNS if retire_columns else 0)
         nbytes = ctypes.c_size_t(0)
         with torch.cuda.device(A.device):
             _check(lib.jacobi_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_workspace_size")
@@ -413,6 +416,14 @@ class MultiSolver:
     def trace(self):
         """Per-phase CUDA-event timeline of the last solve: list of (kind, start_ns, end_ns)."""
         return DeviceSolver.trace(self)
+
+    def column_stats(self):
+        """Per column of the last solve: (iterations after which it finished, its last change norm or
+        relative residual), as numpy arrays."""
+        iters = np.zeros(self.r, dtype=np.int64)
+        vals = np.zeros(self.r, dtype=np.float64)
+        _check(load().jacobi_column_stats(self._h, iters.ctypes.data, vals.ctypes.data), "jacobi_column_stats")
+        return iters, vals
 
     def solve(self, X0=None, max_iter: int = 5000, tol: float = 1e-10, out=None):
         """Returns ``(X, stats)`` with X an (r, n) tensor; raises on error statuses (< 0)."""

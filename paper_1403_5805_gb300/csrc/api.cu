@@ -128,7 +128,7 @@ int validate_desc(const jacobi_desc* d) {
 
 // Extra device buffers of a many-right-hand-side handle (vectors v[c*ld + i]).
 struct MrhsLayout {
-  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, bcol, stats, status, xs, xexp, total;
+  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, bcol, stats, status, xs, xexp, cols, total;
 };
 
 MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
@@ -155,6 +155,7 @@ MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
   M.status = take(16);
   M.xs = take(v8);  // split-float residual: two FP32 words per entry of X
   M.xexp = take(static_cast<size_t>(r) * 4);
+  M.cols = take(static_cast<size_t>(r) * 4);  // active columns (column retirement)
   M.total = o;
   return M;
 }
@@ -182,6 +183,9 @@ struct jacobi_handle {
   int max_inner = 1000;
   float inner_rtol = 0.0f;
   bool split_residual = false;
+  bool retire_columns = false;
+  std::vector<int64_t> col_iters;  // per-column record of the last many-right-hand-side solve
+  std::vector<double> col_value;
   uint64_t wait_ns = 4000000000ull;
   int test_drop_copy = 0;
   template <typename T>
@@ -270,6 +274,7 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   h->inner_rtol = static_cast<float>(
       d->inner_rtol > 0 ? d->inner_rtol : (d->precision == JACOBI_FP8_IR ? 1.0 / 64 : 1.0 / 1024));
   h->split_residual = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) && d->precision != JACOBI_FP64;
+  h->retire_columns = (d->flags & JACOBI_FLAG_RETIRE_COLUMNS) && d->nrhs > 1;
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
   h->test_drop_copy = (d->flags & JACOBI_FLAG_TEST_DROP_COPY) ? 1 : 0;
   if (d->workspace) {
@@ -356,6 +361,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
   double* xa = h->at<double>(h->M.xa);
   double* xb = h->at<double>(h->M.xb);
   unsigned long long* colmax = h->at<unsigned long long>(h->M.colmax);
+  int* dcols = h->at<int>(h->M.cols);
   std::vector<unsigned long long> hc(static_cast<size_t>(r)), hb(static_cast<size_t>(r));
   CK(cudaMemcpyAsync(hb.data(), h->at<char>(h->M.bcol), static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
   if (X0)
@@ -367,37 +373,68 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
     std::memcpy(&v, &u, 8);
     return v;
   };
+  // Active columns (all of them unless retirement is on); a retired column's final iterate goes to X_out
+  // when it retires, the others' at the end.
+  const bool retire = h->retire_columns;
+  std::vector<int> act(static_cast<size_t>(r));
+  for (int64_t c = 0; c < r; ++c) act[static_cast<size_t>(c)] = static_cast<int>(c);
+  h->col_iters.assign(static_cast<size_t>(r), 0);
+  h->col_value.assign(static_cast<size_t>(r), std::nan(""));
+  auto copy_out = [&](int c, const double* x) -> cudaError_t {
+    return cudaMemcpyAsync(X_out + static_cast<int64_t>(c) * n, x + static_cast<int64_t>(c) * ld, n * 8,
+                           cudaMemcpyDefault, s);
+  };
+  auto upload_active = [&]() -> cudaError_t {
+    return cudaMemcpyAsync(dcols, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  };
   jacobi_stats out{};
   out.rel_residual = std::nan("");
   out.status = JACOBI_NOT_CONVERGED;
   double* xc = xa;
   double* xo = xb;
+  bool all_retired = false;
   if (h->precision == JACOBI_FP64) {
+    const int resid = h->norm == JACOBI_NORM_RESID;
     for (int64_t k = 1;; ++k) {
       CK(cudaMemsetAsync(colmax, 0, static_cast<size_t>(r) * 8, s));
-      const int resid = h->norm == JACOBI_NORM_RESID;
+      if (retire) CK(upload_active());
       MrhsDenseParams p{n, r, ld, h->lda64, 1, resid, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
-                        h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax, nullptr, nullptr, nullptr};
+                        h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax, nullptr, nullptr, nullptr,
+                        retire ? dcols : nullptr, static_cast<int64_t>(act.size())};
       CK(launch_mrhs_dense(p, s));
       clk.mark(JACOBI_PHASE_SWEEP64);
       CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      std::swap(xc, xo);  // xc: the iterate this sweep produced
       double delta = 0.0;
-      for (int64_t c = 0; c < r; ++c) {
-        // max-norm change over every entry, or the largest column relative residual of the previous
-        // iterate (max_i |a_ii (x_i^(k) - x_i^(k-1))| / ||b_c||_inf)
+      std::vector<int> keep;
+      for (int c : act) {
+        // max-norm change of the column, or its relative residual of the previous iterate
+        // (max_i |a_ii (x_i^(k) - x_i^(k-1))| / ||b_c||_inf)
         const double v = resid ? bits(hc[static_cast<size_t>(c)]) / bits(hb[static_cast<size_t>(c)])
                                : bits(hc[static_cast<size_t>(c)]);
         delta = (std::isnan(v) || v > delta) ? v : delta;
+        h->col_iters[static_cast<size_t>(c)] = k;
+        h->col_value[static_cast<size_t>(c)] = v;
+        if (retire && v < tol)
+          CK(copy_out(c, xc));
+        else
+          keep.push_back(c);
       }
-      std::swap(xc, xo);
       out.sweeps = k;
       out.final_delta = delta;
       if (!std::isfinite(delta)) {
         out.status = JACOBI_ERR_NONFINITE;
         break;
       }
-      if (delta < tol) {
+      if (retire) {
+        act.swap(keep);
+        if (act.empty()) {
+          out.status = JACOBI_OK;
+          all_retired = true;
+          break;
+        }
+      } else if (delta < tol) {
         out.status = JACOBI_OK;
         break;
       }
@@ -420,8 +457,10 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
         CK(launch_mrhs_init(n, r, ld, h->at<double>(h->M.b), h->at<double>(h->L.rinv), c1, dA, hA, colmax, s));
         clk.mark(JACOBI_PHASE_RESID0);
       } else {
+        if (retire) CK(upload_active());
         MrhsDenseParams p{n, r, ld, h->lda64, 0, 0, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
-                          h->at<double>(h->L.rinv), c1, dA, hA, nullptr, colmax, nullptr, nullptr, nullptr};
+                          h->at<double>(h->L.rinv), c1, dA, hA, nullptr, colmax, nullptr, nullptr, nullptr,
+                          retire ? dcols : nullptr, static_cast<int64_t>(act.size())};
         if (h->split_residual) {
           p.rexp = h->at<int>(h->L.rexp);
           p.xs = h->at<float2>(h->M.xs);
@@ -436,16 +475,36 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
       CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       double rho = 0.0;
-      for (int64_t c = 0; c < r; ++c) {
+      std::vector<int> keep;
+      for (int c : act) {
         const double v = bits(hc[static_cast<size_t>(c)]) / bits(hb[static_cast<size_t>(c)]);
         rho = (std::isnan(v) || v > rho) ? v : rho;
+        h->col_iters[static_cast<size_t>(c)] = outer;
+        h->col_value[static_cast<size_t>(c)] = v;
+        if (retire && v <= tol) {
+          // the residual just measured is that of xc: it is this column's result; its inner
+          // right-hand side and iterates are zeroed so the shared inner sweeps carry it at delta = 0
+          CK(copy_out(c, xc));
+          CK(cudaMemsetAsync(c1 + static_cast<int64_t>(c) * ld, 0, ld * sizeof(float), s));
+          CK(cudaMemsetAsync(dA + static_cast<int64_t>(c) * ld, 0, ld * sizeof(float), s));
+          CK(cudaMemsetAsync(hA + static_cast<int64_t>(c) * ld, 0, ld * sizeof(__nv_bfloat16), s));
+        } else {
+          keep.push_back(c);
+        }
       }
       out.rel_residual = rho;
       if (!std::isfinite(rho)) {
         out.status = JACOBI_ERR_NONFINITE;
         break;
       }
-      if (rho <= tol) {
+      if (retire) {
+        act.swap(keep);
+        if (act.empty()) {
+          out.status = JACOBI_OK;
+          all_retired = true;
+          break;
+        }
+      } else if (rho <= tol) {
         out.status = JACOBI_OK;
         break;
       }
@@ -485,7 +544,12 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
     out.sweeps = inner_total;
     out.outer_steps = outer;
   }
-  CK(cudaMemcpy2DAsync(X_out, n * 8, xc, ld * 8, n * 8, r, cudaMemcpyDefault, s));
+  if (retire) {
+    if (!all_retired)
+      for (int c : act) CK(copy_out(c, xc));
+  } else {
+    CK(cudaMemcpy2DAsync(X_out, n * 8, xc, ld * 8, n * 8, r, cudaMemcpyDefault, s));
+  }
   CK(cudaStreamSynchronize(s));
   clk.flush(h);
   out.converged = out.status == JACOBI_OK;
@@ -659,6 +723,17 @@ int jacobi_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double to
   if (iters_out) *iters_out = local.sweeps;
   if (final_delta_out) *final_delta_out = local.final_delta;
   return local.status;
+}
+
+int jacobi_column_stats(jacobi_handle* h, int64_t* iters, double* value) {
+  if (!h || h->nrhs < 2) return JACOBI_ERR_INVALID_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  const size_t r = static_cast<size_t>(h->nrhs);
+  for (size_t c = 0; c < r; ++c) {
+    if (iters) iters[c] = c < h->col_iters.size() ? h->col_iters[c] : 0;
+    if (value) value[c] = c < h->col_value.size() ? h->col_value[c] : std::nan("");
+  }
+  return JACOBI_OK;
 }
 
 int jacobi_residual(jacobi_handle* h, const double* X, double* rel_out) {

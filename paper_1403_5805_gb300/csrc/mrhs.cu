@@ -235,6 +235,9 @@ constexpr int kDN = 64;   // columns (right-hand sides) per tile
 constexpr int kDK = 32;   // K step
 constexpr int kDThreads = 256;
 
+// Column worked on by tile column c (c < nact).
+__device__ __forceinline__ int col_of(const MrhsDenseParams& p, int c) { return p.cols ? __ldg(p.cols + c) : c; }
+
 // mode 0: residual R = B - A X; writes C1 = R / a_ii (FP32), delta^(1) = C1 (FP32 + BF16), and the
 //         per-column max |R|.
 // mode 1: FP64 Jacobi sweep X^(k) = (B - A X + a_ii x_i) / a_ii; writes X^(k) and the max |change|.
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
     for (int e = tid; e < kDK * kDN; e += kDThreads) {
       const int c = e / kDK, k = e % kDK;
       const int64_t gk = k0 + k;
-      Xs[k][c] = (gk < p.n && c0 + c < p.r) ? p.x[static_cast<int64_t>(c0 + c) * p.ld + gk] : 0.0;
+      Xs[k][c] = (gk < p.n && c0 + c < p.nact) ? p.x[static_cast<int64_t>(col_of(p, c0 + c)) * p.ld + gk] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
@@ -286,8 +289,8 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
     const double di = p.d[i], ri = p.rinv[i];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const int c = c0 + tc + 16 * v;
-      if (c >= p.r) continue;
+      if (c0 + tc + 16 * v >= p.nact) continue;
+      const int c = col_of(p, c0 + tc + 16 * v);
       const int64_t o = static_cast<int64_t>(c) * p.ld + i;
       const double b = p.b[o];
       if (p.mode == 0) {
@@ -309,10 +312,8 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
     }
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int c = c0 + tc + 16 * v;
-    if (c < p.r && mloc[v]) atomicMax(p.colmax + c, mloc[v]);
-  }
+  for (int v = 0; v < 4; ++v)
+    if (c0 + tc + 16 * v < p.nact && mloc[v]) atomicMax(p.colmax + col_of(p, c0 + tc + 16 * v), mloc[v]);
 }
 
 // ------------------------------------------------- split-float residual pass (FP32 units), all r columns
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kDThreads, 2) mrhs_split_resid_kernel(MrhsDens
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kDM;
   const int c0 = blockIdx.y * kN;
   if (tid < kDM) sh_row[tid] = m0 + tid < p.n ? p.rexp[m0 + tid] : 0;
-  if (tid < kN) g_col[tid] = c0 + tid < p.r ? p.xexp[c0 + tid] : 0;
+  if (tid < kN) g_col[tid] = c0 + tid < p.nact ? p.xexp[col_of(p, c0 + tid)] : 0;
   __syncthreads();
   FF acc[4][NC];
 #pragma unroll
@@ -350,8 +351,8 @@ __global__ void __launch_bounds__(kDThreads, 2) mrhs_split_resid_kernel(MrhsDens
     for (int e = tid; e < kDK * kN; e += kDThreads) {
       const int c = e / kDK, k = e % kDK;
       const int64_t gk = k0 + k;
-      const float2 v = (gk < p.n && c0 + c < p.r) ? __ldg(p.xs + static_cast<int64_t>(c0 + c) * p.ld + gk)
-                                                 : make_float2(0.0f, 0.0f);
+      const float2 v = (gk < p.n && c0 + c < p.nact) ? __ldg(p.xs + static_cast<int64_t>(col_of(p, c0 + c)) * p.ld + gk)
+                                                    : make_float2(0.0f, 0.0f);
       Xs[k][c] = v;
     }
     __syncthreads();
@@ -386,8 +387,8 @@ __global__ void __launch_bounds__(kDThreads, 2) mrhs_split_resid_kernel(MrhsDens
     const double si = pow2(sh_row[tr + 16 * u]);
 #pragma unroll
     for (int v = 0; v < NC; ++v) {
-      const int c = c0 + tc + 16 * v;
-      if (c >= p.r) continue;
+      if (c0 + tc + 16 * v >= p.nact) continue;
+      const int c = col_of(p, c0 + tc + 16 * v);
       const int64_t o = static_cast<int64_t>(c) * p.ld + i;
       const double dot =
           (static_cast<double>(acc[u][v].hi) + static_cast<double>(acc[u][v].lo)) * si * pow2(g_col[tc + 16 * v]);
@@ -401,10 +402,8 @@ __global__ void __launch_bounds__(kDThreads, 2) mrhs_split_resid_kernel(MrhsDens
     }
   }
 #pragma unroll
-  for (int v = 0; v < NC; ++v) {
-    const int c = c0 + tc + 16 * v;
-    if (c < p.r && mloc[v]) atomicMax(p.colmax + c, mloc[v]);
-  }
+  for (int v = 0; v < NC; ++v)
+    if (c0 + tc + 16 * v < p.nact && mloc[v]) atomicMax(p.colmax + col_of(p, c0 + tc + 16 * v), mloc[v]);
 }
 
 // One CTA per column: g_c = split exponent of max_i |x_ic|, then xs = the two FP32 words of x 2^-g_c.
@@ -511,9 +510,11 @@ cudaError_t launch_mrhs_sweep(const void* Nlow, const void* dh, const MrhsSweepP
 }
 
 cudaError_t launch_mrhs_dense(const MrhsDenseParams& p, cudaStream_t s) {
+  if (p.nact < 1) return cudaSuccess;
   if (p.xs && p.mode == 0) {
-    const int nc = p.r <= 16 ? 1 : (p.r <= 32 ? 2 : 4);
-    const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM), static_cast<unsigned>((p.r + 16 * nc - 1) / (16 * nc)));
+    const int nc = p.nact <= 16 ? 1 : (p.nact <= 32 ? 2 : 4);
+    const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM),
+                    static_cast<unsigned>((p.nact + 16 * nc - 1) / (16 * nc)));
     if (nc == 1)
       mrhs_split_resid_kernel<1><<<grid, kDThreads, 0, s>>>(p);
     else if (nc == 2)
@@ -522,7 +523,7 @@ cudaError_t launch_mrhs_dense(const MrhsDenseParams& p, cudaStream_t s) {
       mrhs_split_resid_kernel<4><<<grid, kDThreads, 0, s>>>(p);
     return cudaGetLastError();
   }
-  const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM), static_cast<unsigned>((p.r + kDN - 1) / kDN));
+  const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM), static_cast<unsigned>((p.nact + kDN - 1) / kDN));
   mrhs_dense_kernel<<<grid, kDThreads, 0, s>>>(p);
   return cudaGetLastError();
 }

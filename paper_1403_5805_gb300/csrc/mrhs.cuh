@@ -44,6 +44,9 @@ struct MrhsDenseParams {
   const int* rexp;
   const float2* xs;
   const int* xexp;
+  // active columns: tile column c works on column cols[c] (c < nact); NULL cols: all r columns
+  const int* cols;
+  int64_t nact;
 };
 
 bool mrhs_supported_r(int64_t r);

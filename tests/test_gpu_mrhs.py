@@ -156,3 +156,47 @@ def test_split_residual_many_rhs_wild_scales(jac):
     # the split's error bound: ~2^-46 of sum_j |a_ij x_jc| per row, relative to ||b_c||
     S = np.max((np.abs(A) @ np.abs(X0)).max(axis=0) / np.abs(B).max(axis=0))
     assert rel > 1e-9 and abs(st.rel_residual - rel) <= 2.0 ** -44 * S, (st.rel_residual, rel, S)
+
+
+def test_fp64_column_retirement_matches_single_column_solves(jac):
+    """Retiring columns: each column is the single-right-hand-side oracle solve of that column (same
+    sweep count, iterate within 1e-12), whatever the other columns need."""
+    n, r = 300, 6
+    A, B, _ = synth.dominant_system(n, 1.2, seed=620, nrhs=r)
+    B[:, 1] = 0.0      # X = 0 is exact: done after the first sweep
+    B[:, 2] *= 1e-6    # the absolute change test is met sooner
+    B[:, 4] *= 1e3     # and later
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="fp64", retire_columns=True)
+    X, st = s.solve(max_iter=1000, tol=1e-12)
+    iters, vals = s.column_stats()
+    Xh = X.cpu().numpy().T
+    for c in range(r):
+        ref = oracle.jacobi(A, B[:, c], max_iter=1000, tol=1e-12)
+        assert ref.status == 0 and iters[c] == ref.iters, (c, iters[c], ref.iters)
+        assert np.max(np.abs(Xh[:, c] - ref.X[:, 0])) <= 1e-12 * max(np.max(np.abs(ref.X)), 1e-300), c
+    assert st.status == 0 and st.sweeps == iters.max()
+    assert iters[1] == 1 and iters[2] < iters[0] < iters[4]
+
+
+def test_bf16_column_retirement(jac):
+    """Columns whose start vector already meets the target retire at the first residual evaluation and
+    keep X0 bit for bit; the others refine on; every column ends at or below the 1e-10 target."""
+    import torch
+    n, r = 777, 16
+    A, B, Xs = synth.dominant_system(n, 1.1, seed=621, nrhs=r)
+    X0 = np.zeros((n, r))
+    X0[:, ::2] = Xs[:, ::2]
+    At, Bt = dev(A, B)
+    X0t = torch.from_numpy(np.ascontiguousarray(X0.T)).cuda()
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", retire_columns=True)
+    X, st = s.solve(X0=X0t, max_iter=5000, tol=1e-10)
+    iters, vals = s.column_stats()
+    Xh = X.cpu().numpy().T
+    assert st.status == 0
+    assert np.all(iters[::2] == 1) and np.all(iters[1::2] > 1)
+    np.testing.assert_array_equal(Xh[:, ::2], X0[:, ::2])
+    for c in range(r):
+        _, rel = oracle.residual(A, B[:, c], Xh[:, c])
+        assert rel <= 1e-10, (c, rel)
+        assert abs(vals[c] - rel) <= 1e-13 + 1e-3 * rel
