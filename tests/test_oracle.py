@@ -339,3 +339,110 @@ def test_f32_narrowing_of_edge_values():
     with np.errstate(over="ignore"):
         want = np.where(off, A, 0.0).astype(np.float32)
     np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+# ---- block-hybrid Gauss-Seidel / SOR --------------------------------------------------------------
+
+def test_block_sor_with_one_block_per_row_is_jacobi():
+    """Every row its own block, omega = 1: no in-block predecessor, so each component uses the previous
+    iterate only; the iterates equal the Jacobi oracle's bit for bit."""
+    A, B, _ = synth.dominant_system(60, 1.15, seed=31, nrhs=2)
+    j = oracle.jacobi(A, B, max_iter=300, tol=1e-13, trace=True)
+    g = oracle.block_sor(A, B, max_iter=300, tol=1e-13, blocks=60, omega=1.0, trace=True)
+    assert (g.status, g.iters) == (j.status, j.iters)
+    np.testing.assert_array_equal(g.trace, j.trace)
+
+
+@pytest.mark.parametrize("blocks", [1, 3])
+def test_gauss_seidel_on_block_lower_triangular_is_forward_substitution(blocks):
+    """A lower triangular inside each block and zero elsewhere: one Gauss-Seidel sweep is forward
+    substitution (scipy's triangular solve gives the same X); the second sweep changes nothing."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(5)
+    n = 90
+    starts = oracle.uniform_blocks(n, blocks)
+    A = np.zeros((n, n))
+    for b in range(blocks):
+        s0, s1 = starts[b], starts[b + 1]
+        L = np.tril(rng.uniform(-1, 1, (s1 - s0, s1 - s0)), -1)
+        A[s0:s1, s0:s1] = L + np.diag(rng.uniform(2, 3, s1 - s0) * rng.choice([-1, 1], s1 - s0))
+    B = rng.uniform(-1, 1, (n, 1))
+    g = oracle.block_sor(A, B, max_iter=10, tol=1e-300, blocks=blocks, trace=True)
+    want = np.concatenate([scipy_linalg.solve_triangular(A[s0:s1, s0:s1], B[s0:s1], lower=True)
+                           for s0, s1 in zip(starts[:-1], starts[1:])])
+    np.testing.assert_allclose(g.trace[0], want, rtol=1e-14, atol=1e-15)
+    np.testing.assert_array_equal(g.trace[1], g.trace[0])
+
+
+def _tridiagonal(n, diag):
+    return np.diag(np.full(n, diag)) + np.diag(np.full(n - 1, -1.0), 1) + np.diag(np.full(n - 1, -1.0), -1)
+
+
+@pytest.mark.parametrize("omega_kind", ["gauss_seidel", "under", "optimal", "over"])
+def test_sor_iteration_matrix_matches_young_theory(omega_kind):
+    """Classical SOR (one block) on a consistently ordered tridiagonal matrix.  One sweep with B = 0 is
+    the linear map x -> M x, so sweeping the unit vectors gives M column by column; its spectral radius
+    is Young's: mu^2 for Gauss-Seidel; omega - 1 for omega >= omega_opt = 2 / (1 + sqrt(1 - mu^2));
+    ((omega mu + sqrt(omega^2 mu^2 - 4 (omega - 1))) / 2)^2 below it, mu = rho(D^-1 (L + U))."""
+    n = 40
+    A = _tridiagonal(n, 2.2)
+    D = np.diag(np.diag(A))
+    mu = max(abs(np.linalg.eigvals(np.eye(n) - np.linalg.solve(D, A))))
+    w_opt = 2.0 / (1.0 + np.sqrt(1.0 - mu * mu))
+    omega = {"gauss_seidel": 1.0, "under": 0.5 * (1.0 + w_opt), "optimal": w_opt,
+             "over": 0.5 * (w_opt + 2.0)}[omega_kind]
+    if omega >= w_opt:
+        rho = omega - 1.0
+    else:
+        rho = ((omega * mu + np.sqrt(omega * omega * mu * mu - 4.0 * (omega - 1.0))) / 2.0) ** 2
+    g = oracle.block_sor(A, np.zeros((n, n)), X0=np.eye(n), max_iter=1, tol=1e-300, blocks=1, omega=omega,
+                         trace=True)
+    M = g.trace[0]
+    got = max(abs(np.linalg.eigvals(M)))
+    # the optimal omega gives a defective eigenvalue: its numerical eigenvalues spread by ~sqrt(eps)
+    assert abs(got - rho) <= (2e-7 if omega_kind == "optimal" else 1e-10), (omega_kind, got, rho)
+
+
+def test_sor_on_a_diagonal_matrix_is_one_relaxed_step():
+    """A diagonal: v = b / a_ii is exact, so each sweep moves x by omega (v - x): after k sweeps the error
+    is (1 - omega)^k of the start error (closed form)."""
+    rng = np.random.default_rng(9)
+    n = 25
+    d = rng.uniform(1, 2, n) * rng.choice([-1, 1], n)
+    A = np.diag(d)
+    B = rng.uniform(-1, 1, (n, 1))
+    X0 = rng.uniform(-1, 1, (n, 1))
+    xs = B / d[:, None]
+    for omega in (0.7, 1.0, 1.3):
+        g = oracle.block_sor(A, B, X0=X0, max_iter=4, tol=1e-300, blocks=4, omega=omega, trace=True)
+        for k in range(len(g.trace)):  # omega = 1 lands on xs in one sweep and stops after the second
+            np.testing.assert_allclose(g.trace[k], xs + (1 - omega) ** (k + 1) * (X0 - xs), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("blocks,omega", [(1, 1.0), (4, 1.0), (17, 1.0), (1, 1.1), (5, 0.8)])
+def test_block_sor_converges_to_the_ge_solution(blocks, omega):
+    A, B, Xs = synth.dominant_system(120, 1.2, seed=41, nrhs=2)
+    g = oracle.block_sor(A, B, max_iter=500, tol=1e-14, blocks=blocks, omega=omega)
+    _, Xge = oracle.ge(A, B)
+    assert g.status == 0
+    assert np.max(np.abs(g.X - Xge)) <= 1e-12
+
+
+def test_gauss_seidel_beats_jacobi_on_the_hard_generator():
+    """Positive off-diagonals (rho(T) = 1/f): Gauss-Seidel needs a small fraction of Jacobi's sweeps."""
+    A, B, _ = synth.hard_system(300, 1.05, seed=3)
+    j = oracle.jacobi(A, B, max_iter=5000, tol=1e-10)
+    g = oracle.block_sor(A, B, max_iter=5000, tol=1e-10, blocks=1)
+    assert j.status == 0 and g.status == 0
+    assert g.iters * 10 < j.iters, (g.iters, j.iters)
+
+
+def test_block_sor_errors():
+    A = np.eye(4)
+    B = np.ones((4, 1))
+    A[1, 1] = 0.0
+    assert oracle.block_sor(A, B, blocks=2).status == oracle.ZERO_DIAGONAL
+    A[1, 1] = 1.0
+    assert oracle.block_sor(A, B, blocks=2, omega=2.0).status == oracle.INVALID_ARG
+    assert oracle.block_sor(A, B, blocks=np.array([0, 3, 2, 4])).status == oracle.INVALID_ARG
+    assert oracle.block_sor(A, B, blocks=2, norm=oracle.NORM_RESID).status == oracle.INVALID_ARG
