@@ -135,7 +135,21 @@ typedef struct jacobi_desc {
                              (0: 2^-10 for FP32/BF16, 2^-6 for FP8) */
   int32_t max_inner;      /* IR: cap on inner sweeps per outer step (0: 1000) */
   int32_t flags;          /* JACOBI_FLAG_* */
+  int32_t method;         /* jacobi_method (0: the Jacobi iteration) */
+  int32_t reserved;
+  double omega;           /* JACOBI_METHOD_SOR: relaxation factor, 0 < omega < 2 (0: 1, Gauss-Seidel) */
 } jacobi_desc;
+
+/* Iteration of the FP64 single-right-hand-side path.
+ * JACOBI_METHOD_SOR: the Gauss-Seidel / SOR sweep, the relaxed relative of the Section 2 iteration that
+ *   uses each new component as soon as it is computed,
+ *     x_i^(k) = x_i^(k-1) + omega ((beta_i - sum_{j<i} alpha_ij x_j^(k) - sum_{j>i} alpha_ij x_j^(k-1))
+ *               / alpha_ii - x_i^(k-1)),
+ *   run as a chain over the CTAs' row blocks (each block waits for the earlier blocks' new values), so the
+ *   iterates are those of the sequential sweep whatever the grid.  Stopping test, norms (max-norm or
+ *   Euclidean) and return conventions as for the Jacobi iteration.  Requires JACOBI_FP64, one right-hand
+ *   side and n <= 112 * (co-resident CTAs); otherwise JACOBI_ERR_UNSUPPORTED from the setup. */
+typedef enum { JACOBI_METHOD_JACOBI = 0, JACOBI_METHOD_SOR = 1 } jacobi_method;
 
 #define JACOBI_FLAG_COPY_A 1 /* always copy A into the workspace (never borrow it) */
 /* IR precisions (one or many right-hand sides): compute the FP64 residual r = B - A X with split-float

@@ -32,6 +32,7 @@ FLAG_SPLIT_RESIDUAL = 2
 FLAG_SHORT_WAITS = 4
 FLAG_TEST_DROP_COPY = 8
 FLAG_RETIRE_COLUMNS = 16
+METHODS = {"jacobi": 0, "sor": 1}
 
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
            "jacobi_desc_init", "jacobi_workspace_size", "jacobi_setup_ex", "jacobi_solve_async",
@@ -71,7 +72,8 @@ class JacobiDesc(ctypes.Structure):
                 ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p), ("grid", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("max_inner", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("method", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("omega", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -199,7 +201,8 @@ class DeviceSolver:
 
     def __init__(self, A, B, precision: str = "fp64", norm: str = "inf", grid: int = 0, stream=None,
                  copy_a: bool = False, max_outer: int = 0, max_inner: int = 0, inner_rtol: float = 0.0,
-                 workspace=None, device=None, split_residual: bool = False, flags: int = 0):
+                 workspace=None, device=None, split_residual: bool = False, flags: int = 0,
+                 method: str = "jacobi", omega: float = 1.0):
         """A, B: float64 tensors on the GPU (A may be borrowed, see jacobi_desc.A) or on the host (copied
         to the device during setup; pin them for full link bandwidth).  workspace: optional uint8 CUDA
         tensor of at least workspace_size() bytes to reuse across solvers."""
@@ -228,6 +231,8 @@ class DeviceSolver:
         d.stream = self.stream.cuda_stream
         d.grid, d.max_outer, d.max_inner, d.inner_rtol = grid, max_outer, max_inner, inner_rtol
         d.flags = (FLAG_COPY_A if copy_a else 0) | (FLAG_SPLIT_RESIDUAL if split_residual else 0) | flags
+        d.method = METHODS[method]
+        d.omega = omega
         nbytes = ctypes.c_size_t(0)
         with torch.cuda.device(device):
             _check(lib.jacobi_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_workspace_size")

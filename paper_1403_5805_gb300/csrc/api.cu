@@ -4,6 +4,7 @@
 // X^0, the tolerance and the iteration limit L; output X.  All arithmetic runs in the kernels of
 // prepare.cu and solve.cu; this file only validates arguments, lays out device memory and orders the
 // work on the handle's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -11,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "gs.cuh"
 #include "mrhs.cuh"
 #include "solver.cuh"
 
@@ -69,8 +71,8 @@ bool can_borrow(const jacobi_desc* d) {
 // Offsets of every sub-buffer inside one workspace allocation.
 struct Layout {
   int64_t ld;  // padded length of vectors and row stride of owned matrices
-  size_t A64, Nlow, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, ctl, keys, stats,
-      total;
+  size_t A64, Nlow, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, gsflags, ctl, keys,
+      stats, total;
 };
 
 Layout make_layout(int64_t n, int precision, bool copy_A) {
@@ -103,7 +105,8 @@ Layout make_layout(int64_t n, int precision, bool copy_A) {
   L.c1 = take(vf);
   L.da = take(vf);
   L.db = take(vf);
-  L.part = take(2 * kMaxGrid * sizeof(double));
+  L.part = take(3 * kMaxGrid * sizeof(double));  // Euclidean-norm partials: 2 slots (Jacobi), 3 (Gauss-Seidel)
+  L.gsflags = take(kMaxGrid * sizeof(int));  // Gauss-Seidel chain: per-CTA published sweep
   L.ctl = take(sizeof(Ctl));
   L.keys = take(4 * sizeof(unsigned long long));
   L.stats = take(sizeof(jacobi_stats));
@@ -117,6 +120,11 @@ int validate_desc(const jacobi_desc* d) {
   if (d->precision < JACOBI_FP64 || d->precision > JACOBI_FP8_IR) return JACOBI_ERR_INVALID_ARG;
   if (d->norm < JACOBI_NORM_INF || d->norm > JACOBI_NORM_RESID) return JACOBI_ERR_INVALID_ARG;
   if (d->grid < 0 || d->grid > kMaxGrid) return JACOBI_ERR_INVALID_ARG;
+  if (d->method != JACOBI_METHOD_JACOBI && d->method != JACOBI_METHOD_SOR) return JACOBI_ERR_INVALID_ARG;
+  if (d->method == JACOBI_METHOD_SOR) {
+    if (d->omega != 0.0 && !(d->omega > 0.0 && d->omega < 2.0)) return JACOBI_ERR_INVALID_ARG;
+    if (d->precision != JACOBI_FP64 || d->nrhs != 1 || d->norm == JACOBI_NORM_RESID) return JACOBI_ERR_UNSUPPORTED;
+  }
   if (d->nrhs > 1) {
     // many right-hand sides: plain FP64 (max-norm stop) or BF16 inner sweeps on tcgen05
     if (d->precision == JACOBI_FP64 && d->norm == JACOBI_NORM_2) return JACOBI_ERR_UNSUPPORTED;
@@ -184,6 +192,8 @@ struct jacobi_handle {
   float inner_rtol = 0.0f;
   bool split_residual = false;
   bool retire_columns = false;
+  int method = JACOBI_METHOD_JACOBI;
+  double omega = 1.0;
   std::vector<int64_t> col_iters;  // per-column record of the last many-right-hand-side solve
   std::vector<double> col_value;
   uint64_t wait_ns = 4000000000ull;
@@ -255,6 +265,18 @@ int pick_grid(jacobi_handle* h, int requested) {
   return g;
 }
 
+// Grid of the chained Gauss-Seidel kernel: blocks of at least 16 rows where possible, at most
+// kGsMaxRows rows; -1 if n needs more blocks than can be co-resident, 0 on a failed query.
+int pick_gs_grid(int64_t n, int requested) {
+  const int cap = gs_max_grid();
+  if (cap <= 0) return 0;
+  const int64_t need = (n + kGsMaxRows - 1) / kGsMaxRows;
+  if (need > cap || need > kMaxGrid) return -1;
+  int64_t g = requested > 0 ? requested : std::max<int64_t>(1, n / 16);
+  g = std::min<int64_t>({g, static_cast<int64_t>(cap), static_cast<int64_t>(kMaxGrid), n});
+  return static_cast<int>(std::max<int64_t>(g, need));
+}
+
 int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   jacobi_handle* h = new (std::nothrow) jacobi_handle();
   if (!h) return JACOBI_ERR_OUT_OF_MEMORY;
@@ -291,7 +313,14 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
     }
     h->own_ws = true;
   }
-  h->grid = pick_grid(h, d->grid);
+  h->method = d->method;
+  h->omega = d->omega > 0.0 ? d->omega : 1.0;
+  h->grid = h->method == JACOBI_METHOD_SOR ? pick_gs_grid(h->n, d->grid) : pick_grid(h, d->grid);
+  if (h->grid == -1) {
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return JACOBI_ERR_UNSUPPORTED;  // n too large for the chained Gauss-Seidel blocks
+  }
   if (h->grid <= 0) {
     if (h->own_ws) cudaFree(h->ws);
     delete h;
@@ -679,8 +708,33 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
   p.cmax = h->at<unsigned long long>(h->L.cmax);
   p.wait_ns = h->wait_ns;
   p.test_drop_copy = h->test_drop_copy;
-  cudaError_t e = h->precision == JACOBI_FP64 ? launch_fp64_solve(p, h->grid, s)
-                                               : launch_ir_solve(narrow_kind(h->precision), p, h->grid, s);
+  cudaError_t e;
+  if (h->method == JACOBI_METHOD_SOR) {
+    CK(cudaMemsetAsync(h->at<char>(h->L.gsflags), 0, kMaxGrid * sizeof(int), s));
+    GsParams g{};
+    g.n = n;
+    g.A = h->A64;
+    g.lda = h->lda64;
+    g.b = p.b;
+    g.d = p.d;
+    g.rinv = p.rinv;
+    g.xa = p.xa;
+    g.xb = p.xb;
+    g.flags = h->at<int>(h->L.gsflags);
+    g.part = p.part;
+    g.ctl = p.ctl;
+    g.x_out = X_out;
+    g.stats_out = stats_dev;
+    g.max_iter = max_iter;
+    g.tol = tol;
+    g.norm = h->norm;
+    g.omega = h->omega;
+    g.wait_ns = h->wait_ns;
+    e = launch_gs_solve(g, h->grid, s);
+  } else {
+    e = h->precision == JACOBI_FP64 ? launch_fp64_solve(p, h->grid, s)
+                                    : launch_ir_solve(narrow_kind(h->precision), p, h->grid, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");
   return JACOBI_OK;
 }

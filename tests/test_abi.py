@@ -44,4 +44,4 @@ def test_struct_layouts_match_header():
     import paper_1403_5805_gb300 as jac
     # jacobi_stats: 2 x int64, 2 x double, 2 x int32; jacobi_desc: see include/jacobi.h
     assert ctypes.sizeof(jac.JacobiStats) == 40
-    assert ctypes.sizeof(jac.JacobiDesc) == 104
+    assert ctypes.sizeof(jac.JacobiDesc) == 120
