@@ -71,7 +71,7 @@ bool can_borrow(const jacobi_desc* d) {
 // Offsets of every sub-buffer inside one workspace allocation.
 struct Layout {
   int64_t ld;  // padded length of vectors and row stride of owned matrices
-  size_t A64, Nlow, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, gsflags, ctl, keys,
+  size_t A64, Nlow, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, gsflags, gsmbox, ctl, keys,
       stats, total;
 };
 
@@ -107,6 +107,7 @@ Layout make_layout(int64_t n, int precision, bool copy_A) {
   L.db = take(vf);
   L.part = take(3 * kMaxGrid * sizeof(double));  // Euclidean-norm partials: 2 slots (Jacobi), 3 (Gauss-Seidel)
   L.gsflags = take(kMaxGrid * sizeof(int));  // Gauss-Seidel chain: per-CTA published sweep
+  L.gsmbox = take(2 * vd);                    // Gauss-Seidel chain: mailboxes of x^(k), k odd / even
   L.ctl = take(sizeof(Ctl));
   L.keys = take(4 * sizeof(unsigned long long));
   L.stats = take(sizeof(jacobi_stats));
@@ -711,6 +712,7 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
   cudaError_t e;
   if (h->method == JACOBI_METHOD_SOR) {
     CK(cudaMemsetAsync(h->at<char>(h->L.gsflags), 0, kMaxGrid * sizeof(int), s));
+    CK(cudaMemsetAsync(h->at<char>(h->L.gsmbox), 0xFF, 2 * static_cast<size_t>(n) * sizeof(double), s));
     GsParams g{};
     g.n = n;
     g.A = h->A64;
@@ -721,6 +723,7 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
     g.xa = p.xa;
     g.xb = p.xb;
     g.flags = h->at<int>(h->L.gsflags);
+    g.mbox = h->at<unsigned long long>(h->L.gsmbox);
     g.part = p.part;
     g.ctl = p.ctl;
     g.x_out = X_out;

@@ -4,23 +4,31 @@
 //                                 / alpha_ii - x_i^(k-1) ).
 //
 // The sweep is sequential in i, so it is distributed as a chain over row blocks: CTA c owns rows
-// [r_c, r_(c+1)) and, in sweep k,
-//   1. subtracts from u_i = beta_i the columns after its block (previous iterate) and the strict upper
-//      part of its diagonal block (previous iterate) -- work that needs nobody else;
-//   2. subtracts the columns of every earlier block as soon as that block publishes its new values (a
-//      per-CTA flag set with release semantics after the block's x^(k) is in memory; read with acquire);
-//      the previous block's columns, the last to arrive, come from a tile of A kept in shared memory;
-//   3. solves its block: with M = D + omega L (the block's diagonal and strict lower part),
-//      M x = (1 - omega) D x^(k-1) + omega u, i.e. x = M^-1 w with M^-1 formed once per solve in shared
-//      memory;
-//   4. writes x^(k) for its rows and publishes its flag.
-// So the chain's critical path per block is two shared-memory matrix-vector products (the previous
-// block's contribution and M^-1 w) and one flag hand-off; everything that streams A from HBM runs
-// before the block's turn.
+// [r_c, r_(c+1)).  With M = D + omega L for the block's diagonal and strict lower part, its new values are
+//
+//   x_c^(k) = M^-1 w,   w = (1 - omega) D x_c^(k-1) + omega (u - P x_(c-1)^(k)),
+//   u = beta_c - (strict upper part of the diagonal block) x_c^(k-1) - (columns after the block) x^(k-1)
+//              - (columns of blocks 0 .. c-2) x^(k),
+//
+// where P is the block's rows x the previous block's columns.  Splitting off the last term,
+// x_c^(k) = y + Q x_(c-1)^(k) with y = M^-1 ((1 - omega) D x_c^(k-1) + omega u) and Q = -omega M^-1 P, both
+// M^-1 and Q formed once per solve in shared memory.  So in sweep k CTA c
+//   1. has u without the earlier blocks from the previous iteration (the strict upper part right after
+//      publishing x_c^(k-1), the columns after the block as the later blocks published x^(k-1));
+//   2. subtracts the columns of blocks 0 .. c-2 as each block publishes (a per-CTA flag, release / acquire);
+//   3. forms y;
+//   4. takes x_(c-1)^(k) from a mailbox that block c-1 fills with relaxed stores as soon as it has its values
+//      (the entries start as a NaN pattern no arithmetic produces, so the data is its own flag: no fence
+//      and no second round trip on the chain), empties the mailbox again, and finishes x = y + Q x_(c-1);
+//   5. writes x_c^(k), fills its own mailbox, publishes its flag, and starts sweep k+1's u.
+// The chain's critical path per block is one m x m shared-memory product and one L2 round trip; the streamed
+// products over A from HBM and the triangular solve run while the earlier blocks hold the chain.
 // The result is the sequential Gauss-Seidel / SOR sweep (up to rounding order), whatever the grid.
-// Sweeps overlap: after publishing x^(k), a block starts sweep k+1's columns after it as the later blocks
-// publish, and the stopping test on sweep k is read once the last block has published (no grid barrier).
+// Sweeps overlap: the stopping test on sweep k is read once the last block has published (no grid barrier).
 // Every wait is bounded by %globaltimer; a wait that runs out sets JACOBI_ERR_TIMEOUT for the solve.
+// FP64 issue is the scarce resource here (a couple of lanes per clock per SM), so every product keeps its
+// FP64 adds to the useful ones: rows are split across two threads or reduced by halving exchanges, not by
+// per-row warp butterflies.
 #include "device_util.cuh"
 #include "gs.cuh"
 
@@ -36,6 +44,42 @@ __device__ __forceinline__ int ld_acquire_i32(const int* p) {
 }
 __device__ __forceinline__ void st_release_i32(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Mailbox entry not filled yet: a NaN pattern that no FP64 operation returns (a computed value with these
+// bits, only possible by propagating such a NaN from the start vector, is stored as kNanStandIn instead).
+constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
+constexpr unsigned long long kNanStandIn = 0x7FF8000000000001ull;
+
+// Warp sums of eight per-lane values v[0..7]: lane l receives the total of v[l >> 2].  Halving exchanges
+// across lanes 16, 8 and 4 apart (each lane keeps the half of its values whose row matches its lane bit and
+// adds the partner's copy of them), then a butterfly over the last four lanes: 9 FP64 adds per warp for the
+// eight rows, where eight butterflies would take 40.
+__device__ __forceinline__ double warp_sum8(const double (&v)[8], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  double a[4], b[2];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const double keep = h16 ? v[t + 4] : v[t], give = h16 ? v[t] : v[t + 4];
+    a[t] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const double keep = h8 ? a[t + 2] : a[t], give = h8 ? a[t] : a[t + 2];
+    b[t] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+  }
+  double z = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  return z;
 }
 
 // Pull the block's rows over columns [c0, c1) into L2 ahead of use (one prefetch per 128-byte line).
@@ -61,45 +105,44 @@ __device__ bool wait_flag(const int* flag, int k, const int* status, uint64_t li
   return true;
 }
 
-// u[i] -= sum_{j in [c0, c1)} a_(r0+i),j x_j for the block's rows: each warp takes 4 rows at a time,
-// lanes take column pairs (16-byte loads: rows start 16-byte aligned), with a scalar head and tail for
-// odd ends.  x is read through L2 (other CTAs write it during the launch).
+// u[i] -= sum_{j in [c0, c1)} a_(r0+i),j x_j for the block's rows: each warp takes 8 rows at a time, lanes
+// take column pairs (16-byte loads: rows start 16-byte aligned), with a scalar head and tail for odd ends.
+// x is read through L2 (other CTAs write it during the launch).
 __device__ void rows_dot(const GsParams& p, int64_t r0, int m, int64_t c0, int64_t c1, const double* x, double* u,
                          int warp, int lane) {
   if (c1 <= c0) return;
   const int64_t jp = c0 + (c0 & 1);             // first even column
   const int64_t je = jp + ((c1 - jp) & ~int64_t(1));  // end of the pairs
-  for (int i0 = 4 * warp; i0 < m; i0 += 4 * kGsWarps) {
-    const int nr = m - i0 < 4 ? m - i0 : 4;
-    const double* rp[4];
+  for (int i0 = 8 * warp; i0 < m; i0 += 8 * kGsWarps) {
+    const int nr = m - i0 < 8 ? m - i0 : 8;
+    const double* rp[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) rp[q] = p.A + (r0 + i0 + (q < nr ? q : nr - 1)) * p.lda;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < 8; ++q) rp[q] = p.A + (r0 + i0 + (q < nr ? q : nr - 1)) * p.lda;
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (lane == 0) {
       if (c0 & 1) {
         const double xv = __ldcg(x + c0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = fma(__ldg(rp[q] + c0), xv, acc[q]);
+        for (int q = 0; q < 8; ++q) acc[q] = fma(__ldg(rp[q] + c0), xv, acc[q]);
       }
       if (je < c1) {
         const double xv = __ldcg(x + je);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = fma(__ldg(rp[q] + je), xv, acc[q]);
+        for (int q = 0; q < 8; ++q) acc[q] = fma(__ldg(rp[q] + je), xv, acc[q]);
       }
     }
 #pragma unroll 2
     for (int64_t j = jp + 2 * lane; j < je; j += 64) {
       const double2 xv = __ldcg(reinterpret_cast<const double2*>(x + j));
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 8; ++q) {
         const double2 a = __ldg(reinterpret_cast<const double2*>(rp[q] + j));
         acc[q] = fma(a.y, xv.y, fma(a.x, xv.x, acc[q]));
       }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
-    if (lane == 0)
-      for (int q = 0; q < nr; ++q) u[i0 + q] -= acc[q];
+    const double s = warp_sum8(acc, lane);
+    const int q = lane >> 2;
+    if ((lane & 3) == 0 && q < nr) u[i0 + q] -= s;
   }
 }
 
@@ -136,14 +179,14 @@ __device__ __forceinline__ double bits_to_double(unsigned long long v) {
   return __longlong_as_double(static_cast<long long>(v));
 }
 
-__global__ void __launch_bounds__(kGsThreads) gs_solve_kernel(GsParams p) {
+__global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   extern __shared__ double sm[];
   constexpr int P = kGsPitch;
   double* dm = sm;                    // lower with diagonal: (M^-1)_ij; strict upper: a_(r0+i),(r0+j)
-  double* pv = dm + kGsMaxRows * P;   // a_(r0+i),(s+j): this block's rows x the previous block's columns
-  double* xo_b = pv + kGsMaxRows * P; // x^(k-1) of the block
+  double* qm = dm + kGsMaxRows * P;   // Q = -omega M^-1 P, P_ij = a_(r0+i),(s+j) (the previous block's columns)
+  double* xo_b = qm + kGsMaxRows * P; // x^(k-1) of the block
   double* u = xo_b + kGsMaxRows;      // running right-hand side of the block's rows
-  double* w = u + kGsMaxRows;         // M x = w
+  double* w = u + kGsMaxRows;         // (1 - omega) D x^(k-1) + omega u
   double* xn_b = w + kGsMaxRows;      // x^(k) of the block
   double* xp = xn_b + kGsMaxRows;     // x^(k) of the previous block
   __shared__ unsigned long long s_red[kGsWarps];
@@ -155,14 +198,17 @@ __global__ void __launch_bounds__(kGsThreads) gs_solve_kernel(GsParams p) {
   const int64_t sp = c > 0 ? p.n * (c - 1) / G : 0;  // first column of the previous block
   const int m = static_cast<int>(r1 - r0), mp = static_cast<int>(r0 - sp);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the block products run two threads per row (row ri, even or odd columns), on whole warps
+  const int ri = tid >> 1, par = tid & 1;
+  const bool row_ok = ri < m;
   const double om = p.omega;
   if (tid == 0 && c == 0) p.ctl->t_start = global_timer_ns();
 
-  // ---- once per solve: M^-1 for M = D + omega L of the diagonal block (from the block staged in pv),
-  // the block's strict upper part, then the previous block's columns
+  // ---- once per solve: M^-1 for M = D + omega L of the diagonal block (staged in qm first), the block's
+  // strict upper part, then Q from the previous block's columns
   for (int e = tid; e < m * m; e += kGsThreads) {
     const int i = e / m, j = e % m;
-    pv[i * P + j] = p.A[(r0 + i) * p.lda + r0 + j];
+    qm[i * P + j] = p.A[(r0 + i) * p.lda + r0 + j];
   }
   __syncthreads();
   if (tid < m) {
@@ -171,92 +217,116 @@ __global__ void __launch_bounds__(kGsThreads) gs_solve_kernel(GsParams p) {
     dm[t * P + t] = __ldg(p.rinv + r0 + t);
     for (int i = t + 1; i < m; ++i) {
       double s = 0.0;
-      for (int j = t; j < i; ++j) s = fma(pv[i * P + j], dm[j * P + t], s);
+      for (int j = t; j < i; ++j) s = fma(qm[i * P + j], dm[j * P + t], s);
       dm[i * P + t] = -(om * s) * __ldg(p.rinv + r0 + i);
     }
   }
   __syncthreads();
   for (int e = tid; e < m * m; e += kGsThreads) {
     const int i = e / m, j = e % m;
-    if (j > i) dm[i * P + j] = pv[i * P + j];
+    if (j > i) dm[i * P + j] = qm[i * P + j];
   }
   __syncthreads();
   for (int e = tid; e < m * mp; e += kGsThreads) {
     const int i = e / mp, j = e % mp;
-    pv[i * P + j] = p.A[(r0 + i) * p.lda + sp + j];
+    qm[i * P + j] = p.A[(r0 + i) * p.lda + sp + j];
+  }
+  __syncthreads();
+  if (c > 0 && tid < 2 * kGsMaxRows) {
+    // in place, a pair of threads per column, bottom-up: row i of Q needs rows <= i of P only
+    const int j = tid >> 1;
+    const bool col_ok = j < mp;
+    for (int i = m - 1; i >= 0; --i) {
+      double s = 0.0;
+      if (col_ok)
+        for (int t = par; t <= i; t += 2) s = fma(dm[i * P + t], qm[t * P + j], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (col_ok && par == 0) qm[i * P + j] = -om * s;
+    }
   }
   __syncthreads();
 
+  // u_i = beta_i - sum_{j > i in the block} a_ij x_j with the block's own values xs (all threads call it)
+  auto start_u = [&](const double* xs) {
+    double s = 0.0;
+    if (row_ok)
+      for (int j = ri + 1 + par; j < m; j += 2) s = fma(dm[ri * P + j], xs[j], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (row_ok && par == 0) u[ri] = __ldg(p.b + r0 + ri) - s;
+  };
+
   // ---- sweeps.  Iteration k ends with this block's x^(k) published, then already computes the part of
-  // sweep k+1 that needs the previous iterate (the columns after the block, from x^(k) of the later
-  // blocks, taken as they publish), and decides on sweep k once the last block has published it: every
-  // block's change norm is in red[k % 3] / part by then (each block adds its own before publishing, and
-  // the flags are released and acquired in chain order), so every CTA takes the same decision with no
-  // grid barrier, and the next sweep's chain starts as soon as the last block of this one is done.
-  // x^(k) lives in xb for odd k, xa for even k; x^(0) (the start vector) in xa
+  // sweep k+1 that needs the previous iterate (the strict upper part, and the columns after the block from
+  // x^(k) of the later blocks, taken as they publish), and decides on sweep k once the last block has
+  // published it: every block's change norm is in red[k % 3] / part by then (each block adds its own before
+  // publishing, and the flags are released and acquired in chain order), so every CTA takes the same
+  // decision with no grid barrier, and the next sweep's chain starts as soon as the last block of this one
+  // is done.  x^(k) lives in xb for odd k, xa for even k; x^(0) (the start vector) in xa.  The mailbox of
+  // block c for sweep k is mbox[(k & 1) n + r_c ...].
   int64_t k = 1;
   double delta = 0.0;
   int status = kStatusNotConverged;
   if (tid == 0) s_ok = 1;
-  for (int i = tid; i < m; i += kGsThreads) {
-    xo_b[i] = __ldcg(p.xa + r0 + i);
-    u[i] = __ldg(p.b + r0 + i);
-  }
+  for (int i = tid; i < m; i += kGsThreads) xo_b[i] = __ldcg(p.xa + r0 + i);
+  __syncthreads();
+  start_u(xo_b);
   __syncthreads();
   rows_dot(p, r0, m, r1, p.n, p.xa, u, warp, lane);  // sweep 1: the later blocks' x^(0) is the input
   for (;; ++k) {
     double* xn = (k & 1) ? p.xb : p.xa;
-    __syncthreads();
-    // the block's strict upper part, with x^(k-1)
-    for (int i = warp; i < m; i += kGsWarps) {
-      double s = 0.0;
-      for (int j = i + 1 + lane; j < m; j += 32) s = fma(dm[i * P + j], xo_b[j], s);
-      s = warp_sum(s);
-      if (lane == 0) u[i] -= s;
-    }
+    unsigned long long* box = p.mbox + (k & 1) * p.n;
     // the blocks before the previous one, with x^(k), as they are published (in order)
     process_published(p, r0, m, 0, c - 1, static_cast<int>(k), xn, u, warp, lane, &s_e, &s_ok);
-    //    and the previous block's columns from the shared-memory tile
-    if (c > 0) {
-      __syncthreads();
-      if (tid == 0 && s_ok && !wait_flag(p.flags + c - 1, static_cast<int>(k), &p.ctl->status, p.wait_ns)) s_ok = 0;
-      __syncthreads();
-      for (int j = tid; j < mp; j += kGsThreads) xp[j] = __ldcg(xn + sp + j);
-      __syncthreads();
-      for (int i2 = tid; i2 < 2 * kGsMaxRows; i2 += kGsThreads) {  // two threads per row, even / odd columns
-        const int i = i2 >> 1;
-        double s = 0.0;
-        if (i < m)
-          for (int j = i2 & 1; j < mp; j += 2) s = fma(pv[i * P + j], xp[j], s);
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        if (i < m && (i2 & 1) == 0) u[i] -= s;
-      }
-    }
     __syncthreads();
-    // x^(k) = M^-1 w, w = (1 - omega) D x^(k-1) + omega u
     for (int i = tid; i < m; i += kGsThreads)
       w[i] = om == 1.0 ? u[i] : fma(1.0 - om, __ldg(p.d + r0 + i) * xo_b[i], om * u[i]);
     __syncthreads();
+    // y = M^-1 w
+    double x = 0.0;
+    if (row_ok)
+      for (int j = par; j <= ri; j += 2) x = fma(dm[ri * P + j], w[j], x);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    if (c > 0) {
+      // x_(c-1)^(k) from the previous block's mailbox, one entry per thread, emptied again for sweep k+2
+      if (tid < mp) {
+        unsigned long long* e = box + sp + tid;
+        unsigned long long v = ld_relaxed_u64(e);
+        if (v == kEmpty && s_ok) {
+          const uint64_t t0 = global_timer_ns();
+          while ((v = ld_relaxed_u64(e)) == kEmpty) {
+            if (global_timer_ns() - t0 > p.wait_ns) {
+              s_ok = 0;
+              break;
+            }
+          }
+        }
+        xp[tid] = __longlong_as_double(static_cast<long long>(v));
+        st_relaxed_u64(e, kEmpty);
+      }
+      __syncthreads();
+      // x = y + Q x_(c-1)
+      double s = 0.0;
+      if (row_ok)
+        for (int j = par; j < mp; j += 2) s = fma(qm[ri * P + j], xp[j], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      x += s;
+    }
     unsigned long long mx = 0;
     double sq = 0.0;
-    for (int i2 = tid; i2 < 2 * kGsMaxRows; i2 += kGsThreads) {  // two threads per row
-      const int i = i2 >> 1;
-      double x = 0.0;
-      if (i < m)
-        for (int j = i2 & 1; j <= i; j += 2) x = fma(dm[i * P + j], w[j], x);
-      x += __shfl_xor_sync(0xffffffffu, x, 1);
-      if (i < m && (i2 & 1) == 0) {
-        xn_b[i] = x;
-        xn[r0 + i] = x;
-        const double diff = x - xo_b[i];
-        const unsigned long long bb = abs_bits(diff);
-        mx = bb > mx ? bb : mx;
-        sq = fma(diff, diff, sq);
+    if (row_ok && par == 0) {
+      if (c + 1 < G) {  // the next block's input first
+        const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+        st_relaxed_u64(box + r0 + ri, bits == kEmpty ? kNanStandIn : bits);
       }
+      xn_b[ri] = x;
+      xn[r0 + ri] = x;
+      const double diff = x - xo_b[ri];
+      mx = abs_bits(diff);
+      if (p.norm == JACOBI_NORM_2) sq = diff * diff;
     }
     // the block's change norm, then x^(k) published
     mx = warp_max_u64(mx);
-    sq = warp_sum(sq);
+    if (p.norm == JACOBI_NORM_2) sq = warp_sum(sq);
     if (lane == 0) {
       s_red[warp] = mx;
       s_sq[warp] = sq;
@@ -279,11 +349,10 @@ __global__ void __launch_bounds__(kGsThreads) gs_solve_kernel(GsParams p) {
       __threadfence();
       st_release_i32(p.flags + c, static_cast<int>(k));
     }
-    // sweep k+1's columns after the block, from x^(k) of the later blocks as they publish
-    for (int i = tid; i < m; i += kGsThreads) {
-      xo_b[i] = xn_b[i];
-      u[i] = __ldg(p.b + r0 + i);
-    }
+    // sweep k+1: the strict upper part with x^(k) of the block, then the columns after the block from x^(k)
+    // of the later blocks as they publish
+    for (int i = tid; i < m; i += kGsThreads) xo_b[i] = xn_b[i];
+    start_u(xn_b);
     process_published(p, r0, m, c + 1, G, static_cast<int>(k), xn, u, warp, lane, &s_e, &s_ok);
     // decision on sweep k: the last block has published it (waited for above, or this is the last block)
     __syncthreads();

@@ -11,8 +11,8 @@ namespace jac {
 constexpr int kGsThreads = 256;   // 8 warps per CTA
 constexpr int kGsMaxRows = 112;   // rows per CTA block
 constexpr int kGsPitch = kGsMaxRows + 1;  // shared-memory row pitch of the block tiles (odd: no bank clash)
-// Two block tiles (the diagonal block with the inverse of its lower part; this CTA's rows x the previous
-// block's columns) plus five vectors.
+// Two block tiles (the diagonal block with the inverse of its lower part; -omega M^-1 times this CTA's rows
+// x the previous block's columns) plus five vectors.
 constexpr size_t kGsSmem = 2 * sizeof(double) * kGsMaxRows * kGsPitch + 5 * sizeof(double) * kGsMaxRows;
 
 struct GsParams {
@@ -25,6 +25,7 @@ struct GsParams {
   double* xa;           // iterate buffers: x^(k-1) and x^(k) alternate
   double* xb;
   int* flags;           // one per CTA, zeroed before the launch: the last sweep whose block is final
+  unsigned long long* mbox;  // [2][n] mailboxes of x^(k) (k odd / even) for the next block, all bits set before the launch
   double* part;         // [3][kMaxGrid] per-CTA partial sums (Euclidean norm), one slot per sweep mod 3
   Ctl* ctl;
   double* x_out;
