@@ -266,14 +266,16 @@ int pick_grid(jacobi_handle* h, int requested) {
   return g;
 }
 
-// Grid of the chained Gauss-Seidel kernel: blocks of at least 16 rows where possible, at most
-// kGsMaxRows rows; -1 if n needs more blocks than can be co-resident, 0 on a failed query.
+// Grid of the chained Gauss-Seidel kernel: by default the fewest row blocks of at most kGsMaxRows rows
+// (a requested grid is honoured within that bound); -1 if n needs more blocks than can be co-resident,
+// 0 on a failed query.
 int pick_gs_grid(int64_t n, int requested) {
   const int cap = gs_max_grid();
   if (cap <= 0) return 0;
   const int64_t need = (n + kGsMaxRows - 1) / kGsMaxRows;
   if (need > cap || need > kMaxGrid) return -1;
-  int64_t g = requested > 0 ? requested : std::max<int64_t>(1, n / 16);
+  // default: the fewest, largest row blocks (the chain's hand-offs cost more than the block products)
+  int64_t g = requested > 0 ? requested : need;
   g = std::min<int64_t>({g, static_cast<int64_t>(cap), static_cast<int64_t>(kMaxGrid), n});
   return static_cast<int>(std::max<int64_t>(g, need));
 }

@@ -59,25 +59,29 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 constexpr unsigned long long kEmpty = 0xFFFFFFFFFFFFFFFFull;
 constexpr unsigned long long kNanStandIn = 0x7FF8000000000001ull;
 
-// Warp sums of eight per-lane values v[0..7]: lane l receives the total of v[l >> 2].  Halving exchanges
-// across lanes 16, 8 and 4 apart (each lane keeps the half of its values whose row matches its lane bit and
-// adds the partner's copy of them), then a butterfly over the last four lanes: 9 FP64 adds per warp for the
-// eight rows, where eight butterflies would take 40.
-__device__ __forceinline__ double warp_sum8(const double (&v)[8], int lane) {
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-  double a[4], b[2];
+// Warp sums of sixteen per-lane values v[0..15]: lane l receives the total of v[(l >> 1) & 15].  Halving
+// exchanges across lanes 16, 8, 4 and 2 apart (each lane keeps the half of its values whose row matches its
+// lane bit and adds the partner's copy of them), then one across neighbouring lanes: 16 FP64 adds per warp
+// for the sixteen rows, where sixteen butterflies would take 80.
+__device__ __forceinline__ double warp_sum16(const double (&v)[16], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+  double a[8], b[4], d[2];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const double keep = h16 ? v[t + 4] : v[t], give = h16 ? v[t] : v[t + 4];
+  for (int t = 0; t < 8; ++t) {
+    const double keep = h16 ? v[t + 8] : v[t], give = h16 ? v[t] : v[t + 8];
     a[t] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
   }
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const double keep = h8 ? a[t + 2] : a[t], give = h8 ? a[t] : a[t + 2];
+  for (int t = 0; t < 4; ++t) {
+    const double keep = h8 ? a[t + 4] : a[t], give = h8 ? a[t] : a[t + 4];
     b[t] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
   }
-  double z = (h4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h4 ? b[0] : b[1], 4);
-  z += __shfl_xor_sync(0xffffffffu, z, 2);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const double keep = h4 ? b[t + 2] : b[t], give = h4 ? b[t] : b[t + 2];
+    d[t] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+  }
+  double z = (h2 ? d[1] : d[0]) + __shfl_xor_sync(0xffffffffu, h2 ? d[0] : d[1], 2);
   z += __shfl_xor_sync(0xffffffffu, z, 1);
   return z;
 }
@@ -105,52 +109,67 @@ __device__ bool wait_flag(const int* flag, int k, const int* status, uint64_t li
   return true;
 }
 
-// u[i] -= sum_{j in [c0, c1)} a_(r0+i),j x_j for the block's rows: each warp takes 8 rows at a time, lanes
-// take column pairs (16-byte loads: rows start 16-byte aligned), with a scalar head and tail for odd ends.
-// x is read through L2 (other CTAs write it during the launch).
-__device__ void rows_dot(const GsParams& p, int64_t r0, int m, int64_t c0, int64_t c1, const double* x, double* u,
-                         int warp, int lane) {
-  if (c1 <= c0) return;
-  const int64_t jp = c0 + (c0 & 1);             // first even column
-  const int64_t je = jp + ((c1 - jp) & ~int64_t(1));  // end of the pairs
-  for (int i0 = 8 * warp; i0 < m; i0 += 8 * kGsWarps) {
-    const int nr = m - i0 < 8 ? m - i0 : 8;
-    const double* rp[8];
+// Rows of A per warp in the row products (8 warps cover the largest block).
+constexpr int kGsRowsPerWarp = (kGsMaxRows + kGsWarps - 1) / kGsWarps;
+static_assert(kGsRowsPerWarp <= 16, "the row sums are reduced sixteen at a time");
+
+// One step of the row products: kCols columns per lane (j0 + lane + 32 t, t < kCols; those at or past c1
+// predicated off), every load issued before the FMAs.
+template <int kCols>
+__device__ __forceinline__ void rows_step(const double* a, int64_t lda, int nr, int64_t j0, int64_t c1, const double* x,
+                                          double (&acc)[16], int lane) {
+  double xv[kCols], av[kCols][kGsRowsPerWarp];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) rp[q] = p.A + (r0 + i0 + (q < nr ? q : nr - 1)) * p.lda;
-    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (lane == 0) {
-      if (c0 & 1) {
-        const double xv = __ldcg(x + c0);
+  for (int t = 0; t < kCols; ++t) {
+    const int64_t j = j0 + lane + 32 * t;
+    const bool ok = j < c1;
+    xv[t] = ok ? __ldcg(x + j) : 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = fma(__ldg(rp[q] + c0), xv, acc[q]);
-      }
-      if (je < c1) {
-        const double xv = __ldcg(x + je);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = fma(__ldg(rp[q] + je), xv, acc[q]);
-      }
-    }
-#pragma unroll 2
-    for (int64_t j = jp + 2 * lane; j < je; j += 64) {
-      const double2 xv = __ldcg(reinterpret_cast<const double2*>(x + j));
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(rp[q] + j));
-        acc[q] = fma(a.y, xv.y, fma(a.x, xv.x, acc[q]));
-      }
-    }
-    const double s = warp_sum8(acc, lane);
-    const int q = lane >> 2;
-    if ((lane & 3) == 0 && q < nr) u[i0 + q] -= s;
+    for (int q = 0; q < kGsRowsPerWarp; ++q) av[t][q] = ok && q < nr ? __ldg(a + q * lda + j) : 0.0;
   }
+#pragma unroll
+  for (int t = 0; t < kCols; ++t)
+#pragma unroll
+    for (int q = 0; q < kGsRowsPerWarp; ++q)
+      if (q < nr) acc[q] = fma(av[t][q], xv[t], acc[q]);
 }
 
-// u -= the columns of blocks [b0, b1) with x, taking each block once its flag reaches kf (in block order,
-// runs of already-published blocks at once), and pulling the next awaited block into L2 meanwhile.
-// Called by the whole CTA.  A wait that runs out clears *s_ok and skips the rest.
-__device__ void process_published(const GsParams& p, int64_t r0, int m, int b0, int b1, int kf, const double* x,
-                                  double* u, int warp, int lane, int* s_e, int* s_ok) {
+// Row products over A for the warp's rows i0 .. i0+nr-1 (nr <= kGsRowsPerWarp): acc[q] += a_(r0+i0+q),j x_j
+// over the lane's columns j = c0 + lane + 32 t in [c0, c1).  Lanes read 32 consecutive columns of a row
+// (coalesced), up to 128 columns per step with every load of the step issued before its FMAs; the steps are
+// the same for all lanes (the ragged end is predicated) and the last one is only as wide as the columns
+// left, so a block costs one memory latency and few idle FP64 lanes.  The per-lane sums stay in registers
+// across calls and are reduced once per phase (flush_rows), so the FP64 adds of the reduction do not recur
+// per block.  x is read through L2 (other CTAs write it during the launch).
+__device__ __forceinline__ void rows_dot(const GsParams& p, int64_t r0, int i0, int nr, int64_t c0, int64_t c1,
+                                         const double* x, double (&acc)[16], int lane) {
+  if (nr <= 0) return;
+  const double* a = p.A + (r0 + i0) * p.lda;
+  int64_t j0 = c0;
+  for (; c1 - j0 > 96; j0 += 128) rows_step<4>(a, p.lda, nr, j0, c1, x, acc, lane);
+  const int64_t rem = c1 - j0;
+  if (rem > 64)
+    rows_step<3>(a, p.lda, nr, j0, c1, x, acc, lane);
+  else if (rem > 32)
+    rows_step<2>(a, p.lda, nr, j0, c1, x, acc, lane);
+  else if (rem > 0)
+    rows_step<1>(a, p.lda, nr, j0, c1, x, acc, lane);
+}
+
+// u[i0 + q] -= the warp's sums of acc[q] (q < nr), and acc cleared.
+__device__ __forceinline__ void flush_rows(double (&acc)[16], double* u, int i0, int nr, int lane) {
+  const double s = warp_sum16(acc, lane);
+  const int q = (lane >> 1) & 15;
+  if ((lane & 1) == 0 && q < nr) u[i0 + q] -= s;
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+}
+
+// acc += the columns of blocks [b0, b1) with x for the warp's rows, taking each block once its flag reaches kf
+// (in block order, runs of already-published blocks at once), and pulling the next awaited block into L2
+// meanwhile.  Called by the whole CTA.  A wait that runs out clears *s_ok and skips the rest.
+__device__ void process_published(const GsParams& p, int64_t r0, int m, int i0, int nr, int b0, int b1, int kf,
+                                  const double* x, double (&acc)[16], int lane, int* s_e, int* s_ok) {
   const int G = gridDim.x;
   if (b0 < b1) prefetch_rows(p, r0, m, p.n * b0 / G, p.n * (b0 + 1) / G);
   int done = b0;
@@ -170,7 +189,7 @@ __device__ void process_published(const GsParams& p, int64_t r0, int m, int b0, 
     __syncthreads();
     const int e = *s_e;
     if (e < b1) prefetch_rows(p, r0, m, p.n * e / G, p.n * (e + 1) / G);
-    if (*s_ok) rows_dot(p, r0, m, p.n * done / G, p.n * e / G, x, u, warp, lane);
+    if (*s_ok) rows_dot(p, r0, i0, nr, p.n * done / G, p.n * e / G, x, acc, lane);
     done = e;
   }
 }
@@ -201,6 +220,12 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   // the block products run two threads per row (row ri, even or odd columns), on whole warps
   const int ri = tid >> 1, par = tid & 1;
   const bool row_ok = ri < m;
+  // the row products over A: warp w takes rows [w rpw, (w + 1) rpw)
+  const int rpw = (m + kGsWarps - 1) / kGsWarps;
+  const int i0 = warp * rpw, nr = max(0, min(rpw, m - i0));
+  double acc[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
   const double om = p.omega;
   if (tid == 0 && c == 0) p.ctl->t_start = global_timer_ns();
 
@@ -270,13 +295,15 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   for (int i = tid; i < m; i += kGsThreads) xo_b[i] = __ldcg(p.xa + r0 + i);
   __syncthreads();
   start_u(xo_b);
+  rows_dot(p, r0, i0, nr, r1, p.n, p.xa, acc, lane);  // sweep 1: the later blocks' x^(0) is the input
   __syncthreads();
-  rows_dot(p, r0, m, r1, p.n, p.xa, u, warp, lane);  // sweep 1: the later blocks' x^(0) is the input
+  flush_rows(acc, u, i0, nr, lane);
   for (;; ++k) {
     double* xn = (k & 1) ? p.xb : p.xa;
     unsigned long long* box = p.mbox + (k & 1) * p.n;
     // the blocks before the previous one, with x^(k), as they are published (in order)
-    process_published(p, r0, m, 0, c - 1, static_cast<int>(k), xn, u, warp, lane, &s_e, &s_ok);
+    process_published(p, r0, m, i0, nr, 0, c - 1, static_cast<int>(k), xn, acc, lane, &s_e, &s_ok);
+    flush_rows(acc, u, i0, nr, lane);
     __syncthreads();
     for (int i = tid; i < m; i += kGsThreads)
       w[i] = om == 1.0 ? u[i] : fma(1.0 - om, __ldg(p.d + r0 + i) * xo_b[i], om * u[i]);
@@ -336,10 +363,9 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
     if (tid == 0) {
       unsigned long long bm = 0;
       double bs = 0.0;
-      for (int q = 0; q < kGsWarps; ++q) {  // fixed order
-        bm = s_red[q] > bm ? s_red[q] : bm;
-        bs += s_sq[q];
-      }
+      for (int q = 0; q < kGsWarps; ++q) bm = s_red[q] > bm ? s_red[q] : bm;
+      if (p.norm == JACOBI_NORM_2)
+        for (int q = 0; q < kGsWarps; ++q) bs += s_sq[q];  // fixed order
       if (c == 0) p.ctl->red[slot][0] = 0ull;  // the first block of the sweep opens its slot
       if (p.norm == JACOBI_NORM_2)
         p.part[slot * kMaxGrid + c] = bs;
@@ -353,7 +379,9 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
     // of the later blocks as they publish
     for (int i = tid; i < m; i += kGsThreads) xo_b[i] = xn_b[i];
     start_u(xn_b);
-    process_published(p, r0, m, c + 1, G, static_cast<int>(k), xn, u, warp, lane, &s_e, &s_ok);
+    process_published(p, r0, m, i0, nr, c + 1, G, static_cast<int>(k), xn, acc, lane, &s_e, &s_ok);
+    __syncthreads();
+    flush_rows(acc, u, i0, nr, lane);
     // decision on sweep k: the last block has published it (waited for above, or this is the last block)
     __syncthreads();
     if (tid == 0) {
