@@ -33,10 +33,17 @@ sys.path.insert(0, ROOT)
 METRIC = "solves/s at ||AX-B||/||B||<=1e-10 (BF16 inner sweeps + FP64 refinement), n=16384"
 TARGET = 1e-10
 ESIZE = {"fp64": 8, "fp32_ir": 4, "bf16_ir": 2, "fp8_ir": 1}
+PATH_LABEL = {"bf16_ir": "BF16 inner sweeps + FP64 refinement to rel. residual 1e-10",
+              "fp8_ir": "FP8 (E4M3) inner sweeps + FP64 refinement to rel. residual 1e-10",
+              "fp32_ir": "FP32 inner sweeps + FP64 refinement to rel. residual 1e-10",
+              "fp64": "FP64 Jacobi sweeps to max|dx| < 1e-12",
+              "fp64+gs": "FP64 chained Gauss-Seidel sweeps to max|dx| < 1e-12"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-# the solve kernels' translation unit and every header it includes
+# each timed kernel's translation unit and every header it includes (the solve kernels share one)
 SOLVE_SRC = [os.path.join(ROOT, "paper_1403_5805_gb300", "csrc", f)
              for f in ("solve.cu", "solver.cuh", "dot.cuh", "device_util.cuh", "splitfloat.cuh")]
+KERNEL_SRC = {"gs_solve_kernel": [os.path.join(ROOT, "paper_1403_5805_gb300", "csrc", f)
+                                  for f in ("gs.cu", "gs.cuh", "solver.cuh", "device_util.cuh")]}
 
 
 def dist_env():
@@ -54,9 +61,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def src_hash():
+def src_hash(kernel: str = ""):
     h = hashlib.sha256()
-    for path in SOLVE_SRC:
+    for path in KERNEL_SRC.get(kernel, SOLVE_SRC):
         with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -70,7 +77,7 @@ def committed_traffic(kernel: str):
     except OSError:
         return None
     e = t.get(kernel)
-    if not e or e.get("source_sha256_16") != src_hash():
+    if not e or e.get("source_sha256_16") != src_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -192,13 +199,14 @@ def run_ours(args, world, rank, local):
 
     # algorithmic bytes of the dominant kernel (the persistent solve kernel) per launch
     st = main["stats"]
-    es = ESIZE[args.precision]
+    es = ESIZE[args.precision.replace("+gs", "")]
     outer_with_matrix = max(st["outer_steps"] - 1, 0)  # X0 = 0: the first residual needs no matrix pass
     bytes_launch = outer_with_matrix * 8.0 * n * n + st["sweeps"] * es * float(n) * n
     peaks, peak_kind = measured_peaks()
     achieved = bytes_launch / (main["kernel_ms"] * 1e-3) / 1e9
     kname = {"bf16_ir": "ir_solve_kernel<__nv_bfloat16>", "fp8_ir": "ir_solve_kernel<__nv_fp8_e4m3>",
-             "fp32_ir": "ir_solve_kernel<float>", "fp64": "fp64_solve_kernel"}[args.precision]
+             "fp32_ir": "ir_solve_kernel<float>", "fp64": "fp64_solve_kernel",
+             "fp64+gs": "gs_solve_kernel"}[args.precision]
     traffic = committed_traffic(kname)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
@@ -222,16 +230,18 @@ def run_ours(args, world, rank, local):
     many_rhs = None if (args.quick or args.no_mrhs) else run_many_rhs(args, jac, torch, dev)
     serving = None if (args.quick or args.no_serve) else run_serve(args, jac, torch, dev, args.serve_window)
     result = {
-        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.precision == "bf16_ir" else f"solves/s ({PATH_LABEL[args.precision]}), n={n}",
+        "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16_ir" else args.precision,
+        "vs_baseline": None,
+        "dtype": {"bf16_ir": "bf16", "fp64+gs": "fp64"}.get(args.precision, args.precision),
         "data": "synthetic (seeded Philox4x32-10), resident in HBM",
-        "config": {"workload": f"single dense system n={n}, f={f}, 1 RHS, BF16 inner sweeps + FP64 "
-                               f"refinement to rel. residual 1e-10; one step = setup + solve",
+        "config": {"workload": f"single dense system n={n}, f={f}, 1 RHS, {PATH_LABEL[args.precision]}; "
+                               f"one step = setup + solve",
                    "n": n, "dominance": f, "nrhs": 1, "precision": args.precision, "global_batch": world,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (2.15 GB A) larger than the 129 MB L2; no flush"},
-        "gpu_launches": (4 if args.precision != "fp64" else 3) * args.steps,
+        "gpu_launches": (4 if not args.precision.startswith("fp64") else 3) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
         "serving": serving, "hard_generator": hard,
@@ -653,7 +663,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--f", type=float, default=1.05)
-    ap.add_argument("--precision", default="bf16_ir", choices=list(ESIZE))
+    ap.add_argument("--precision", default="bf16_ir", choices=list(ESIZE) + ["fp64+gs"],
+                    help="the timed path; fp64+gs is the chained Gauss-Seidel solve")
     ap.add_argument("--fp64-tol", type=float, default=1e-12, dest="fp64_tol",
                     help="stopping threshold of the plain FP64 path (max-norm change)")
     ap.add_argument("--max-iter", type=int, default=5000, dest="max_iter")
