@@ -54,6 +54,9 @@ def _load():
             lib.oracle_block_sor.argtypes = [_c_i64, _c_i64, vp, vp, vp, _c_i64, ctypes.c_double, ctypes.c_int,
                                              _c_i64, vp, ctypes.c_double, vp, ctypes.POINTER(_c_i64), _c_dp, vp]
             lib.oracle_block_sor.restype = ctypes.c_int
+            lib.oracle_csr_jacobi.argtypes = [_c_i64, vp, vp, vp, vp, vp, _c_i64, ctypes.c_double, ctypes.c_int,
+                                              vp, ctypes.POINTER(_c_i64), _c_dp, vp]
+            lib.oracle_csr_jacobi.restype = ctypes.c_int
             lib.oracle_ge.argtypes = [_c_i64, _c_i64, vp, vp, vp]
             lib.oracle_ge.restype = ctypes.c_int
             lib.oracle_residual.argtypes = [_c_i64, _c_i64, vp, vp, vp, vp, _c_dp]
@@ -149,6 +152,29 @@ def block_sor(A, B, X0=None, max_iter: int = 1000, tol: float = 1e-12, norm: int
     k = int(it.value)
     tr_out = None if tr is None else np.ascontiguousarray(tr[:k].transpose(0, 2, 1))
     return JacobiResult(st, Xo.T.copy(), k, float(de.value), tr_out)
+
+
+def csr_jacobi(row_ptr, col_idx, values, B, X0=None, max_iter: int = 1000, tol: float = 1e-12,
+               norm: int = NORM_INF, trace: bool = False) -> JacobiResult:
+    """Section 2 Jacobi iteration for a sparse A in CSR (int64 row offsets, int32 columns strictly
+    ascending within each row, the diagonal among them), one right-hand side, on the CPU in FP64."""
+    lib = _load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(values, dtype=np.float64)
+    n = rp.size - 1
+    b = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(-1))
+    if b.size != n or ci.size != va.size or n < 1 or rp[-1] != ci.size:
+        raise ValueError("CSR shape mismatch")
+    x0 = None if X0 is None else np.ascontiguousarray(np.asarray(X0, dtype=np.float64).reshape(-1))
+    Xo = np.zeros(n)
+    it = _c_i64(0)
+    de = ctypes.c_double(0.0)
+    tr = np.zeros((max_iter, n)) if trace else None
+    st = lib.oracle_csr_jacobi(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(b), None if x0 is None else _ptr(x0), max_iter,
+                               tol, norm, _ptr(Xo), ctypes.byref(it), ctypes.byref(de), None if tr is None else _ptr(tr))
+    k = int(it.value)
+    return JacobiResult(st, Xo[:, None].copy(), k, float(de.value), None if tr is None else tr[:k, :, None].copy())
 
 
 def ge(A, B) -> tuple[int, np.ndarray]:

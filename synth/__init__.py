@@ -194,3 +194,98 @@ def serving_trace(rate: float, duration: float, seed: int, n_lo: int = 256, n_hi
     f = f_lo + u[:, 3] * (f_hi - f_lo)
     seeds = np.array([system_seed(seed, k) for k in range(len(t))], dtype=np.int64)
     return t, n, r, f, seeds
+
+
+# ---- sparse (PDE-shaped) systems ------------------------------------------------------------------
+
+def _csr_from_coo(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray):
+    """CSR arrays (row_ptr int64, col_idx int32, values float64), columns ascending within each row."""
+    order = np.argsort(rows.astype(np.int64) * n + cols, kind="stable")
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=row_ptr[1:])
+    return row_ptr, cols.astype(np.int32), vals.astype(np.float64)
+
+
+def _planted(seed: int, n: int, nrhs: int, row_ptr, col_idx, values):
+    Xs = signed_unit(random_u32(seed, STREAM_XSTAR, n * nrhs)).reshape(nrhs, n).T.copy()
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    B = np.zeros((n, nrhs))
+    for c in range(nrhs):  # B = A X* (input construction), summed row by row in column order
+        B[:, c] = np.bincount(rows, weights=values * Xs[col_idx, c], minlength=n)
+    return B, Xs
+
+
+def stencil_system(shape, f: float, seed: int, nrhs: int = 1, weights: str = "variable", diag: str = "dominant"):
+    """PDE-shaped sparse system: the 3-point (1-D), 5-point (2-D) or 7-point (3-D) stencil of a diffusion
+    operator on a grid of ``shape`` with Dirichlet boundaries, unknowns numbered in row-major grid order
+    (the Jacobi codes for differential equations that the paper's related work cites).
+
+    Each grid edge e joining unknowns i and j carries a weight ``w_e`` and ``a_ij = a_ji = -w_e``.
+    ``weights="variable"``: ``w_e = 1 + k_e 2**-20`` with ``k_e`` a uniform integer in [0, 2**20) (exact
+    row sums); ``"unit"``: ``w_e = 1``.  ``diag="dominant"``: ``a_ii = f * sum_{j != i} w_ij``, so
+    ``||T||_inf = 1/f`` exactly; ``"constant"``: ``a_ii = f * 2 * len(shape)`` on every row (the screened
+    Poisson operator, whose Jacobi matrix has the grid's sine modes as eigenvectors).  Planted ``X*``
+    uniform [-1, 1) and ``B = A X*``.
+
+    Returns ``(row_ptr, col_idx, values, B, Xs)``: CSR with int64 row offsets, int32 columns strictly
+    ascending within each row (the diagonal included) and FP64 values; B and X* ``(n, nrhs)``."""
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    grid = np.arange(n, dtype=np.int64).reshape(shape)
+    lo_parts, hi_parts = [], []
+    for ax in range(len(shape)):
+        lo_parts.append(np.take(grid, np.arange(shape[ax] - 1), axis=ax).reshape(-1))
+        hi_parts.append(np.take(grid, np.arange(1, shape[ax]), axis=ax).reshape(-1))
+    lo = np.concatenate(lo_parts) if lo_parts else np.zeros(0, np.int64)
+    hi = np.concatenate(hi_parts) if hi_parts else np.zeros(0, np.int64)
+    if weights == "variable":
+        w = 1.0 + (random_u32(seed, STREAM_A, lo.size) >> np.uint32(12)).astype(np.float64) * 2.0 ** -20
+    else:
+        w = np.ones(lo.size)
+    if diag == "dominant":
+        rowsum = np.bincount(lo, weights=w, minlength=n) + np.bincount(hi, weights=w, minlength=n)
+        d = f * rowsum
+        d[rowsum == 0] = f  # an isolated unknown (a grid of one point)
+    else:
+        d = np.full(n, f * 2.0 * len(shape))
+    diag_idx = np.arange(n, dtype=np.int64)
+    row_ptr, col_idx, values = _csr_from_coo(n, np.concatenate([lo, hi, diag_idx]), np.concatenate([hi, lo, diag_idx]),
+                                             np.concatenate([-w, -w, d]))
+    B, Xs = _planted(seed, n, nrhs, row_ptr, col_idx, values)
+    return row_ptr, col_idx, values, B, Xs
+
+
+def random_sparse_system(n: int, f: float, seed: int, max_len: int = 64, nrhs: int = 1):
+    """Irregular sparse system: row i draws ``L_i`` off-diagonal positions (``L_i`` log-uniform in
+    [1, max_len + 1] minus one, so most rows are short, some empty and a few long) at uniform random
+    columns other than i (repeats merged), values ``int32(w) 2**-31`` in [-1, 1), and
+    ``a_ii = f * sum_{j != i} |a_ij| * (+-1)`` (``+-f`` for a row without off-diagonals).
+    Returns ``(row_ptr, col_idx, values, B, Xs)`` as ``stencil_system``."""
+    u = unit(random_u32(seed, STREAM_META, n))
+    L = log_uniform_int(u, 1, max_len + 1) - 1 if n > 1 else np.zeros(n, np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), L)
+    m = rows.size
+    pos = random_u32(seed, STREAM_A, 2 * m).reshape(m, 2) if m else np.zeros((0, 2), np.uint32)
+    cols = pos[:, 0].astype(np.int64) % max(n - 1, 1)
+    cols = cols + (cols >= rows)  # skip the diagonal
+    key, first = np.unique(rows * n + cols, return_index=True)
+    rows, cols = key // n, key % n
+    vals = signed_unit(pos[first, 1])
+    vals[vals == 0.0] = 2.0 ** -31  # keep every stored off-diagonal non-zero
+    rowsum = np.bincount(rows, weights=np.abs(vals), minlength=n)
+    sign = np.where(random_u32(seed, STREAM_SIGN, n) & np.uint32(1), -1.0, 1.0)
+    d = np.where(rowsum > 0, f * rowsum, f) * sign
+    diag_idx = np.arange(n, dtype=np.int64)
+    row_ptr, col_idx, values = _csr_from_coo(n, np.concatenate([rows, diag_idx]), np.concatenate([cols, diag_idx]),
+                                             np.concatenate([vals, d]))
+    B, Xs = _planted(seed, n, nrhs, row_ptr, col_idx, values)
+    return row_ptr, col_idx, values, B, Xs
+
+
+def csr_to_dense(n: int, row_ptr, col_idx, values) -> np.ndarray:
+    """The dense row-major matrix of a CSR one (for the tests)."""
+    A = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    A[rows, col_idx] = values
+    return A

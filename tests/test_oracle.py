@@ -446,3 +446,99 @@ def test_block_sor_errors():
     assert oracle.block_sor(A, B, blocks=2, omega=2.0).status == oracle.INVALID_ARG
     assert oracle.block_sor(A, B, blocks=np.array([0, 3, 2, 4])).status == oracle.INVALID_ARG
     assert oracle.block_sor(A, B, blocks=2, norm=oracle.NORM_RESID).status == oracle.INVALID_ARG
+
+
+# ---- sparse (CSR) Jacobi ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("norm", [oracle.NORM_INF, oracle.NORM_2])
+@pytest.mark.parametrize("kind", ["irregular", "stencil2d"])
+def test_csr_jacobi_equals_the_dense_oracle_bit_for_bit(kind, norm):
+    """On the dense form of the same matrix the dense oracle adds the zero entries too; adding exact zeros
+    leaves an ascending-order FP64 sum unchanged, so every iterate, the sweep count and the final change
+    agree bit for bit (rows without off-diagonals and rows 60 entries long included)."""
+    if kind == "irregular":
+        rp, ci, v, B, _ = synth.random_sparse_system(257, 1.1, seed=21, max_len=60)
+    else:
+        rp, ci, v, B, _ = synth.stencil_system((13, 11), 1.05, seed=22)
+    n = rp.size - 1
+    assert kind != "irregular" or np.diff(rp).min() == 1  # some rows hold only the diagonal
+    A = synth.csr_to_dense(n, rp, ci, v)
+    d = oracle.jacobi(A, B, max_iter=400, tol=1e-13, norm=norm, trace=True)
+    s = oracle.csr_jacobi(rp, ci, v, B, max_iter=400, tol=1e-13, norm=norm, trace=True)
+    assert (s.status, s.iters, s.delta) == (d.status, d.iters, d.delta)
+    np.testing.assert_array_equal(s.trace, d.trace)
+    np.testing.assert_array_equal(s.X, d.X)
+
+
+@pytest.mark.parametrize("shape,modes", [((23,), (3,)), ((15, 12), (2, 5)), ((7, 9, 6), (1, 4, 2))])
+def test_csr_stencil_sine_mode_decays_by_its_eigenvalue(shape, modes):
+    """Screened Poisson stencil with unit weights and the constant diagonal a = 2 f dim: T = G / a with G
+    the grid's adjacency, whose Dirichlet eigenvectors are products of sines,
+    v(i) = prod_d sin(p_d pi (i_d + 1) / (N_d + 1)), eigenvalue sum_d 2 cos(p_d pi / (N_d + 1)).  With
+    B = 0 and X0 = v every sweep multiplies by lambda = that / a (closed form)."""
+    f = 1.3
+    rp, ci, v, _, _ = synth.stencil_system(shape, f, seed=23, weights="unit", diag="constant")
+    axes = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    mode = np.ones(shape)
+    lam = 0.0
+    for ax, N, p in zip(axes, shape, modes):
+        mode = mode * np.sin(p * np.pi * (ax + 1) / (N + 1))
+        lam += 2.0 * np.cos(p * np.pi / (N + 1))
+    lam /= 2.0 * len(shape) * f
+    x0 = mode.reshape(-1)
+    n = x0.size
+    r = oracle.csr_jacobi(rp, ci, v, np.zeros(n), X0=x0, max_iter=6, tol=1e-300, trace=True)
+    for k in range(6):
+        np.testing.assert_allclose(r.trace[k][:, 0], lam ** (k + 1) * x0, rtol=0, atol=1e-14)
+
+
+def test_csr_tridiagonal_converges_to_the_direct_solution():
+    """1-D variable-coefficient diffusion (tridiagonal): the converged iterate is scipy's banded solve."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rp, ci, v, B, Xs = synth.stencil_system((500,), 1.02, seed=24)
+    A = synth.csr_to_dense(500, rp, ci, v)
+    ab = np.zeros((3, 500))
+    ab[0, 1:] = np.diag(A, 1)
+    ab[1] = np.diag(A)
+    ab[2, :-1] = np.diag(A, -1)
+    want = scipy_linalg.solve_banded((1, 1), ab, B[:, 0])
+    r = oracle.csr_jacobi(rp, ci, v, B, max_iter=5000, tol=1e-14)
+    assert r.status == oracle.OK
+    np.testing.assert_allclose(r.X[:, 0], want, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r.X[:, 0], Xs[:, 0], rtol=0, atol=1e-12)
+
+
+def test_stencil_generator_structure():
+    rp, ci, v, B, Xs = synth.stencil_system((6, 5, 4), 1.05, seed=25)
+    n = 120
+    A = synth.csr_to_dense(n, rp, ci, v)
+    np.testing.assert_array_equal(A, A.T)
+    off = A - np.diag(np.diag(A))
+    assert np.max(np.abs(off).sum(axis=1) / np.abs(np.diag(A))) == pytest.approx(1 / 1.05, rel=1e-15)
+    assert np.diff(rp).max() == 7 and np.diff(rp).min() == 4  # interior 7-point rows, corners 3 + 1
+    np.testing.assert_allclose(A @ Xs, B, rtol=0, atol=1e-13)
+
+
+def test_csr_jacobi_errors():
+    rp = np.array([0, 2, 4, 6])
+    ci = np.array([0, 1, 0, 1, 1, 2])
+    v = np.array([4.0, 1.0, 1.0, 4.0, 1.0, 4.0])
+    b = np.ones(3)
+    assert oracle.csr_jacobi(rp, ci, v, b).status == oracle.OK
+    bad = ci.copy()
+    bad[[4, 5]] = [2, 1]  # descending columns
+    assert oracle.csr_jacobi(rp, bad, v, b).status == oracle.INVALID_ARG
+    bad = ci.copy()
+    bad[5] = 1  # repeated column
+    assert oracle.csr_jacobi(rp, bad, v, b).status == oracle.INVALID_ARG
+    bad = ci.copy()
+    bad[5] = 3  # out of range
+    assert oracle.csr_jacobi(rp, bad, v, b).status == oracle.INVALID_ARG
+    assert oracle.csr_jacobi(np.array([0, 2, 1, 6]), ci, v, b).status == oracle.INVALID_ARG
+    missing = np.array([0, 2, 4, 5]), np.array([0, 1, 0, 1, 1]), np.array([4.0, 1.0, 1.0, 4.0, 1.0])
+    assert oracle.csr_jacobi(*missing, b).status == oracle.ZERO_DIAGONAL  # row 2 has no diagonal entry
+    z = v.copy()
+    z[3] = 0.0
+    assert oracle.csr_jacobi(rp, ci, z, b).status == oracle.ZERO_DIAGONAL
+    z[3] = np.inf
+    assert oracle.csr_jacobi(rp, ci, z, b).status == oracle.NONFINITE
