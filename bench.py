@@ -136,6 +136,8 @@ def run_ours(args, world, rank, local):
         return {"section": "many_rhs", **run_many_rhs(args, jac, torch, dev)}
     if args.only == "batch":
         return {"section": "batched", **run_batch(args, jac, torch, dev)}
+    if args.only == "sparse":
+        return {"section": "sparse", **run_sparse(args, jac, torch, dev)}
     if args.only == "serve":
         return {"section": "serving", **run_serve(args, jac, torch, dev, args.serve_seconds)}
     n, f = args.n, args.f
@@ -228,6 +230,7 @@ def run_ours(args, world, rank, local):
     batched = None if (args.quick or args.no_batch) else run_batch(args, jac, torch, dev)
     del At, Bt, A, B  # free the single-system inputs before the large many-right-hand-side workload
     many_rhs = None if (args.quick or args.no_mrhs) else run_many_rhs(args, jac, torch, dev)
+    sparse = None if (args.quick or args.no_sparse) else run_sparse(args, jac, torch, dev)
     serving = None if (args.quick or args.no_serve) else run_serve(args, jac, torch, dev, args.serve_window)
     result = {
         "metric": METRIC if args.precision == "bf16_ir" else f"solves/s ({PATH_LABEL[args.precision]}), n={n}",
@@ -244,6 +247,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": (4 if not args.precision.startswith("fp64") else 3) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
+        "sparse": sparse,
         "serving": serving, "hard_generator": hard,
     }
     if cpu is not None:
@@ -359,6 +363,71 @@ def run_batch(args, jac, torch, dev):
         out["fp32_ir+split"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     out["bf16_vs_fp64_solves_ratio"] = round(out["bf16_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     return out
+
+
+def run_sparse(args, jac, torch, dev):
+    """PDE-shaped sparse workload: the 5-point stencil of a variable-coefficient diffusion operator on an
+    N x N grid (N = --sparse-grid, 4.19 M unknowns by default), f = 1.05 (rho(T) <= 1/1.05), kept as a
+    sliced-ELL copy.  Times a fixed count of sweeps (per-sweep HBM rate against the measured copy rate)
+    and a full solve to max|dx| < 1e-12, and the CPU oracle on a few sweeps."""
+    import synth
+    N = args.sparse_grid
+    rp, ci, v, B, Xs = synth.stencil_system((N, N), 1.05, seed=synth.BASE_SEED + 6)
+    n = B.shape[0]
+    nnz_off = int(rp[-1]) - n
+    stream = torch.cuda.current_stream(dev)
+    t_rp, t_ci, t_v, t_b = (torch.from_numpy(a).to(dev) for a in (rp, ci, v, B[:, 0].copy()))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    s = jac.CsrSolver(t_rp, t_ci, t_v, t_b)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    setup_ms = ev[0].elapsed_time(ev[1])
+    info = s.info()
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def timed(max_iter, tol, reps):
+        for _ in range(2):
+            s.solve_async(None, max_iter, tol, out)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for _ in range(reps):
+            s.solve_async(None, max_iter, tol, out)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        return ev[0].elapsed_time(ev[1]) / reps, s.last_stats()
+
+    K = args.sparse_sweeps
+    ms_fixed, st_fixed = timed(K, 1e-300, 3)
+    tr = s.trace()
+    per = sorted(b - a for a, b in tr[1:])  # the first sweep also holds the launch
+    sweep_us = per[len(per) // 2] / 1e3
+    alg_bytes = 12.0 * nnz_off + 32.0 * n  # values + columns, b, 1/a_ii, x read, x written
+    peaks, kind = measured_peaks()
+    gbs = alg_bytes / (sweep_us * 1e-6) / 1e9
+    ms_solve, st = timed(5000, 1e-12, 3)
+    err = float((out - torch.from_numpy(Xs[:, 0]).to(dev)).abs().max().item())
+    import oracle
+    import time as _t
+    k_cpu = 3
+    t0 = _t.perf_counter()
+    oracle.csr_jacobi(rp, ci, v, B, max_iter=k_cpu, tol=1e-300)
+    cpu_ms_sweep = (_t.perf_counter() - t0) * 1e3 / k_cpu
+    s.close()
+    return {"workload": f"2-D 5-point variable-coefficient diffusion stencil, {N} x {N} grid, f = 1.05, "
+                        f"planted solution; sliced ELL (32-row slices)",
+            "n": n, "nnz": int(rp[-1]), "stored_slots": info["stored_slots"], "grid": info["grid"],
+            "setup_ms": round(setup_ms, 3),
+            "sweeps": {"count": int(st_fixed.sweeps), "ms_total": round(ms_fixed, 4),
+                       "median_sweep_us": round(sweep_us, 2), "algorithmic_bytes_per_sweep": alg_bytes,
+                       "achieved_gbs": round(gbs, 1), "peak_gbs": peaks["hbm_gbs"],
+                       "frac": round(gbs / peaks["hbm_gbs"], 4),
+                       "peak_source": f"{kind} (MEASURED_PEAKS.json hbm_gbs)"},
+            "solve": {"tol": 1e-12, "status": int(st.status), "sweeps": int(st.sweeps), "ms": round(ms_solve, 3),
+                      "solves_per_s": round(1e3 / ms_solve, 3), "err_vs_xstar": err},
+            "cpu_oracle": {"ms_per_sweep": round(cpu_ms_sweep, 1), "cores": 1,
+                           "sample": f"{k_cpu} sweeps of the full system, one thread"},
+            "gpu_vs_cpu_sweep_ratio": round(cpu_ms_sweep * 1e3 / sweep_us, 1)}
 
 
 def run_many_rhs(args, jac, torch, dev):
@@ -681,12 +750,16 @@ def main():
     ap.add_argument("--no-mrhs", action="store_true", dest="no_mrhs")
     ap.add_argument("--no-serve", action="store_true", dest="no_serve")
     ap.add_argument("--no-hard", action="store_true", dest="no_hard")
+    ap.add_argument("--no-sparse", action="store_true", dest="no_sparse")
+    ap.add_argument("--sparse-grid", type=int, default=2048, dest="sparse_grid",
+                    help="side of the 2-D stencil grid of the sparse section")
+    ap.add_argument("--sparse-sweeps", type=int, default=200, dest="sparse_sweeps")
     ap.add_argument("--serve-seconds", type=float, default=60.0, dest="serve_seconds",
                     help="arrival window of --only serve (the full serving configuration)")
     ap.add_argument("--serve-window", type=float, default=5.0, dest="serve_window",
                     help="arrival window of the serving section of the default run")
     ap.add_argument("--serve-fp64-seconds", type=float, default=1.0, dest="serve_fp64_seconds")
-    ap.add_argument("--only", choices=["batch", "mrhs", "serve"], default=None,
+    ap.add_argument("--only", choices=["batch", "mrhs", "serve", "sparse"], default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--mrhs-n", type=int, default=32768, dest="mrhs_n")
     ap.add_argument("--mrhs-steps", type=int, default=3, dest="mrhs_steps")

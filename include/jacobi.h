@@ -386,6 +386,62 @@ JACOBI_API int jacobi_solve_fp64_noalloc(const double* A, int64_t lda, const dou
                                          const double* X0, int64_t max_iter, double tol, double* X_out,
                                          jacobi_stats* stats, void* stream);
 
+/* ------------------------------------------------------------------------------------------------
+ * Sparse A (compressed sparse rows).  The Section 2 iteration for a sparse A, the banded and
+ * PDE-shaped matrices of the Jacobi codes for differential equations that the paper's related work
+ * (Section 1) cites:
+ *   x_i^(k) = ( beta_i - sum_{stored j != i} alpha_ij x_j^(k-1) ) / alpha_ii,
+ * with the same stopping test, iteration count and return convention as the dense FP64 path (strict
+ * `change < tol` after each sweep, the new iterate returned, X^(L) and JACOBI_NOT_CONVERGED at the cap).
+ * FP64, one right-hand side.  Setup copies the matrix into a sliced-ELL layout of its off-diagonal part
+ * (32-row slices, each as wide as its longest row) that the library owns; the caller's arrays may be
+ * freed when setup returns.
+ * ------------------------------------------------------------------------------------------------ */
+
+typedef struct jacobi_csr jacobi_csr;
+
+typedef struct jacobi_csr_desc {
+  int64_t n;               /* unknowns (rows = columns), >= 1 */
+  int64_t nnz;             /* stored entries, row_ptr[n] */
+  const int64_t* row_ptr;  /* n + 1 offsets: row i is entries [row_ptr[i], row_ptr[i+1]); row_ptr[0] = 0 */
+  const int32_t* col_idx;  /* nnz columns, strictly ascending within each row; each row stores its diagonal */
+  const double* values;    /* nnz values */
+  const double* B;         /* n values: the right-hand side */
+  int32_t norm;            /* JACOBI_NORM_INF or JACOBI_NORM_2 */
+  int32_t flags;           /* JACOBI_FLAG_SHORT_WAITS */
+  void* stream;            /* cudaStream_t of every call on the handle (NULL: the legacy default stream) */
+} jacobi_csr_desc;
+
+/* Validate and copy the matrix (host or device pointers; setup blocks until the copy is built).
+ * Errors: JACOBI_ERR_INVALID_ARG for a null pointer, n < 1, nnz < 1, a bad norm, or a malformed structure
+ * (row_ptr[0] != 0 or row_ptr[n] != nnz, a row range that decreases, a column out of [0, n) or columns not
+ * strictly ascending in a row); then, by the first failing row, JACOBI_ERR_ZERO_DIAGONAL (diagonal missing
+ * or zero) or JACOBI_ERR_NONFINITE (non-finite diagonal); JACOBI_ERR_OUT_OF_MEMORY. */
+JACOBI_API int jacobi_csr_setup(const jacobi_csr_desc* d, jacobi_csr** out);
+
+/* Queue one solve on the handle's stream: one persistent kernel runs every sweep and the stopping test.
+ * X0: n values (host or device) or NULL for zeros; X_out: n values (host or device; a host X_out makes
+ * the call wait for the copy).  Read the outcome with jacobi_csr_last_stats. */
+JACOBI_API int jacobi_csr_solve_async(jacobi_csr* h, const double* X0, int64_t max_iter, double tol,
+                                      double* X_out);
+
+/* Synchronous solve: returns the solve's jacobi_status and fills *stats (host) if not NULL. */
+JACOBI_API int jacobi_csr_solve(jacobi_csr* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                                jacobi_stats* stats);
+
+/* Outcome of the last solve (waits for it). */
+JACOBI_API int jacobi_csr_last_stats(jacobi_csr* h, jacobi_stats* stats);
+
+/* Layout facts for byte accounting: slots stored (off-diagonal entries plus slice padding), slices of
+ * 32 rows, and the grid of the sweep kernel.  Any output may be NULL. */
+JACOBI_API int jacobi_csr_info(jacobi_csr* h, int64_t* stored_slots, int64_t* slices, int32_t* grid);
+
+/* End time of each sweep of the last solve, in nanoseconds since the solve started (as
+ * jacobi_last_trace, every sweep of kind JACOBI_PHASE_SWEEP64; at most 512 are recorded). */
+JACOBI_API int jacobi_csr_last_trace(jacobi_csr* h, int64_t* t_end_ns, int32_t cap, int32_t* count);
+
+JACOBI_API void jacobi_csr_destroy(jacobi_csr* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,7 +41,8 @@ EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_stri
            "jacobi_batch_create", "jacobi_batch_solve_async", "jacobi_batch_stats", "jacobi_batch_grid",
            "jacobi_batch_destroy", "jacobi_server_create", "jacobi_server_submit", "jacobi_server_submit_generated",
            "jacobi_server_step", "jacobi_server_poll", "jacobi_server_rounds", "jacobi_server_destroy",
-           "jacobi_generate_request")
+           "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async", "jacobi_csr_solve",
+           "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace", "jacobi_csr_destroy")
 
 
 class JacobiStats(ctypes.Structure):
@@ -78,6 +79,12 @@ class JacobiDesc(ctypes.Structure):
 
 _lock = threading.Lock()
 _lib = None
+
+
+class JacobiCsrDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("norm", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class JacobiError(RuntimeError):
@@ -135,13 +142,22 @@ def load() -> ctypes.CDLL:
         lib.jacobi_server_destroy.restype = None
         lib.jacobi_generate_request.argtypes = [i64, i64, dbl, ctypes.c_uint64, vp, vp, i64, vp]
         lib.jacobi_solve_fp64_noalloc.argtypes = [vp, i64, vp, i64, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats), vp]
+        lib.jacobi_csr_setup.argtypes = [ctypes.POINTER(JacobiCsrDesc), ctypes.POINTER(H)]
+        lib.jacobi_csr_solve_async.argtypes = [H, vp, i64, dbl, vp]
+        lib.jacobi_csr_solve.argtypes = [H, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats)]
+        lib.jacobi_csr_last_stats.argtypes = [H, ctypes.POINTER(JacobiStats)]
+        lib.jacobi_csr_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_csr_last_trace.argtypes = [H, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_csr_destroy.argtypes = [H]
+        lib.jacobi_csr_destroy.restype = None
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
                      "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
                      "jacobi_get_narrow", "jacobi_last_trace", "jacobi_column_stats", "jacobi_solve_fp64_noalloc",
                      "jacobi_batch_workspace_size", "jacobi_batch_create", "jacobi_batch_solve_async",
                      "jacobi_batch_stats", "jacobi_batch_grid", "jacobi_server_create", "jacobi_server_submit",
                      "jacobi_server_submit_generated", "jacobi_server_step", "jacobi_server_poll",
-                     "jacobi_server_rounds", "jacobi_generate_request"):
+                     "jacobi_server_rounds", "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async",
+                     "jacobi_csr_solve", "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -314,6 +330,95 @@ class DeviceSolver:
 
 
 
+# ------------------------------------------------------------------------------- sparse interface
+
+class CsrSolver:
+    """``jacobi_csr_*``: Jacobi for a sparse A in CSR (int64 row offsets, int32 columns strictly ascending in
+    each row with the diagonal stored, float64 values) and one right-hand side.  The arrays may be torch
+    tensors on the GPU or the host, or numpy arrays; setup copies them into the library's sliced-ELL
+    layout, so they may be dropped afterwards."""
+
+    def __init__(self, row_ptr, col_idx, values, B, norm: str = "inf", flags: int = 0, stream=None, device=None):
+        import torch
+        lib = load()
+
+        def as_tensor(a, dtype):
+            t = torch.as_tensor(a)
+            if t.dtype != dtype:
+                raise ValueError(f"expected {dtype}, got {t.dtype}")
+            return t.contiguous()
+
+        rp = as_tensor(row_ptr, torch.int64)
+        ci = as_tensor(col_idx, torch.int32)
+        va = as_tensor(values, torch.float64)
+        b = as_tensor(B, torch.float64).reshape(-1)
+        self.n = rp.numel() - 1
+        if b.numel() != self.n or ci.numel() != va.numel():
+            raise ValueError("CSR shape mismatch")
+        if device is None:
+            device = va.device if va.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        d = JacobiCsrDesc()
+        d.n, d.nnz = self.n, ci.numel()
+        d.row_ptr, d.col_idx, d.values, d.B = rp.data_ptr(), ci.data_ptr(), va.data_ptr(), b.data_ptr()
+        d.norm, d.flags, d.stream = NORMS[norm], flags, self.stream.cuda_stream
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            _check(lib.jacobi_csr_setup(ctypes.byref(d), ctypes.byref(self._h)), "jacobi_csr_setup", False)
+
+    def solve_async(self, X0=None, max_iter: int = 1000, tol: float = 1e-12, out=None):
+        """Queue a solve on the solver's stream; returns ``out`` (n float64 values on the GPU)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        x0 = None if X0 is None else torch.as_tensor(X0).reshape(-1)
+        if x0 is not None and (x0.dtype != torch.float64 or x0.numel() != self.n or not x0.is_contiguous()):
+            raise ValueError("X0 must hold n contiguous float64 values")
+        self._x0 = x0  # alive until the copy is queued
+        _check(load().jacobi_csr_solve_async(self._h, None if x0 is None else x0.data_ptr(), max_iter, tol,
+                                             out.data_ptr()), "jacobi_csr_solve_async")
+        return out
+
+    def last_stats(self) -> JacobiStats:
+        st = JacobiStats()
+        _check(load().jacobi_csr_last_stats(self._h, ctypes.byref(st)), "jacobi_csr_last_stats")
+        return st
+
+    def solve(self, X0=None, max_iter: int = 1000, tol: float = 1e-12, out=None):
+        """Synchronous solve: returns ``(X, stats)``; raises on error statuses (< 0)."""
+        out = self.solve_async(X0, max_iter, tol, out)
+        st = self.last_stats()
+        _check(st.status, "solve")
+        return out, st
+
+    def info(self) -> dict:
+        stored, slices, grid = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+        _check(load().jacobi_csr_info(self._h, ctypes.byref(stored), ctypes.byref(slices), ctypes.byref(grid)),
+               "jacobi_csr_info")
+        return {"stored_slots": stored.value, "slices": slices.value, "grid": grid.value}
+
+    def trace(self):
+        """Device-side end time of every sweep of the last solve: list of (start_ns, end_ns)."""
+        cap = 512
+        t = np.zeros(cap, dtype=np.int64)
+        cnt = ctypes.c_int32(0)
+        _check(load().jacobi_csr_last_trace(self._h, t.ctypes.data, cap, ctypes.byref(cnt)), "jacobi_csr_last_trace")
+        m = min(cap, cnt.value)
+        return [(int(t[i - 1]) if i else 0, int(t[i])) for i in range(m)]
+
+    def close(self):
+        if self._h:
+            load().jacobi_csr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------------------------ batched interface
 
 class BatchSolver:
@@ -464,7 +569,8 @@ def generate_request(n: int, r: int, f: float, seed: int, device=None, stream=No
     A = torch.empty(n, n, dtype=torch.float64, device=device)
     B = torch.zeros(r, n, dtype=torch.float64, device=device)
     _check(load().jacobi_generate_request(n, r, f, seed, A.data_ptr(), B.data_ptr(), n, stream.cuda_stream),
-           "jacobi_generate_request")
+           "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async", "jacobi_csr_solve",
+           "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace", "jacobi_csr_destroy")
     return A, B
 
 

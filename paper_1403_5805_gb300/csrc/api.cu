@@ -9,12 +9,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
 #include "gs.cuh"
 #include "mrhs.cuh"
 #include "solver.cuh"
+#include "sparse.cuh"
 
 using namespace jac;
 
@@ -594,6 +596,169 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
 
 }  // namespace
 
+// ------------------------------------------------------------------------------------------ sparse A
+
+struct jacobi_csr {
+  int device = 0;
+  int64_t n = 0, nslices = 0, stored = 0;
+  int norm = JACOBI_NORM_INF;
+  int grid = 0;
+  uint64_t wait_ns = 4000000000ull;
+  cudaStream_t stream = nullptr;
+  void* mem = nullptr;  // one allocation for everything below
+  int64_t* soff = nullptr;
+  double* sval = nullptr;
+  int32_t* scol = nullptr;
+  double* b = nullptr;
+  double* rinv = nullptr;
+  double* xa = nullptr;
+  double* xb = nullptr;
+  double* xout = nullptr;
+  double* part = nullptr;
+  Ctl* ctl = nullptr;
+};
+
+namespace {
+
+// Device copies of caller arrays that live on the host (device arrays are used in place); freed on exit.
+struct Staged {
+  std::vector<void*> owned;
+  ~Staged() {
+    for (void* p : owned) cudaFree(p);
+  }
+  template <class T>
+  cudaError_t get(const T* src, size_t count, cudaStream_t s, const T** out) {
+    if (is_device_memory(src)) {
+      *out = src;
+      return cudaSuccess;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T) + 16);
+    if (e != cudaSuccess) return e;
+    owned.push_back(p);
+    e = cudaMemcpyAsync(p, src, count * sizeof(T), cudaMemcpyDefault, s);
+    *out = static_cast<const T*>(p);
+    return e;
+  }
+};
+
+int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
+  if (!d || !out || d->n < 1 || d->nnz < 1 || !d->row_ptr || !d->col_idx || !d->values || !d->B)
+    return JACOBI_ERR_INVALID_ARG;
+  if (d->norm != JACOBI_NORM_INF && d->norm != JACOBI_NORM_2) return JACOBI_ERR_INVALID_ARG;
+  if (d->n > (int64_t(1) << 31) - 64) return JACOBI_ERR_INVALID_ARG;  // int32 column indices
+  *out = nullptr;
+  const int64_t n = d->n, nnz = d->nnz;
+  cudaStream_t s = static_cast<cudaStream_t>(d->stream);
+  int64_t ends[2] = {0, 0};
+  CK(cudaMemcpyAsync(&ends[0], d->row_ptr, sizeof(int64_t), cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(&ends[1], d->row_ptr + n, sizeof(int64_t), cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  if (ends[0] != 0 || ends[1] != nnz) return JACOBI_ERR_INVALID_ARG;
+
+  Staged st;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* va = nullptr;
+  CK(st.get(d->row_ptr, static_cast<size_t>(n + 1), s, &rp));
+  CK(st.get(d->col_idx, static_cast<size_t>(nnz), s, &ci));
+  CK(st.get(d->values, static_cast<size_t>(nnz), s, &va));
+  const int64_t nslices = (n + kSliceRows - 1) / kSliceRows, npad = nslices * kSliceRows;
+  // setup scratch: d (n), lens (npad), widths (nslices), key
+  void* scratch = nullptr;
+  const size_t sc_bytes = align_up(n * sizeof(double)) + align_up(npad * sizeof(int32_t)) +
+                          align_up(nslices * sizeof(int32_t)) + align_up(sizeof(unsigned long long));
+  CK(cudaMalloc(&scratch, sc_bytes));
+  st.owned.push_back(scratch);
+  char* sp = static_cast<char*>(scratch);
+  double* dd = reinterpret_cast<double*>(sp);
+  int32_t* lens = reinterpret_cast<int32_t*>(sp + align_up(n * sizeof(double)));
+  int32_t* width = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(lens) + align_up(npad * sizeof(int32_t)));
+  unsigned long long* key =
+      reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(width) + align_up(nslices * sizeof(int32_t)));
+
+  std::unique_ptr<jacobi_csr> h(new (std::nothrow) jacobi_csr());
+  if (!h) return JACOBI_ERR_OUT_OF_MEMORY;
+  cudaGetDevice(&h->device);
+  h->n = n;
+  h->nslices = nslices;
+  h->norm = d->norm;
+  h->stream = s;
+  if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
+
+  // the vectors first (rinv is written by the check pass)
+  const size_t vec = align_up(npad * sizeof(double));
+  const size_t head = align_up((nslices + 1) * sizeof(int64_t)) + 5 * vec + align_up(2 * kMaxGrid * sizeof(double)) +
+                      align_up(sizeof(Ctl));
+  CK(cudaMemsetAsync(lens, 0, npad * sizeof(int32_t), s));
+  CK(cudaMemsetAsync(key, 0xFF, sizeof(unsigned long long), s));
+  double* rinv_tmp = nullptr;
+  CK(cudaMalloc(reinterpret_cast<void**>(&rinv_tmp), npad * sizeof(double)));
+  st.owned.push_back(rinv_tmp);
+  CK(launch_csr_check(n, nnz, rp, ci, va, dd, rinv_tmp, lens, key, s));
+  unsigned long long hkey = 0;
+  CK(cudaMemcpyAsync(&hkey, key, sizeof(hkey), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hkey != ~0ull) {
+    if ((hkey >> 56) == 0) return JACOBI_ERR_INVALID_ARG;
+    return (hkey & 0xFF) == 3 ? JACOBI_ERR_NONFINITE : JACOBI_ERR_ZERO_DIAGONAL;
+  }
+  CK(launch_csr_widths(n, lens, width, s));
+  std::vector<int32_t> hw(static_cast<size_t>(nslices));
+  CK(cudaMemcpyAsync(hw.data(), width, nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int64_t> hoff(static_cast<size_t>(nslices + 1), 0);
+  for (int64_t q = 0; q < nslices; ++q) hoff[q + 1] = hoff[q] + int64_t(kSliceRows) * hw[q];
+  const int64_t stored = hoff[nslices];
+  h->stored = stored;
+  const size_t vbytes = align_up(std::max<int64_t>(stored, 1) * sizeof(double));
+  const size_t cbytes = align_up(std::max<int64_t>(stored, 1) * sizeof(int32_t));
+  cudaError_t e = cudaMalloc(&h->mem, head + vbytes + cbytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(sparse)");
+  char* p = static_cast<char*>(h->mem);
+  auto take = [&p](size_t bytes) {
+    char* at = p;
+    p += bytes;
+    return at;
+  };
+  h->soff = reinterpret_cast<int64_t*>(take(align_up((nslices + 1) * sizeof(int64_t))));
+  h->b = reinterpret_cast<double*>(take(vec));
+  h->rinv = reinterpret_cast<double*>(take(vec));
+  h->xa = reinterpret_cast<double*>(take(vec));
+  h->xb = reinterpret_cast<double*>(take(vec));
+  h->xout = reinterpret_cast<double*>(take(vec));
+  h->part = reinterpret_cast<double*>(take(align_up(2 * kMaxGrid * sizeof(double))));
+  h->ctl = reinterpret_cast<Ctl*>(take(align_up(sizeof(Ctl))));
+  h->sval = reinterpret_cast<double*>(take(vbytes));
+  h->scol = reinterpret_cast<int32_t*>(take(cbytes));
+  jacobi_csr* raw = h.get();
+  auto fail = [&](cudaError_t err, const char* what) {
+    cudaFree(raw->mem);
+    raw->mem = nullptr;
+    return cuda_fail(err, what);
+  };
+#define CSR_CK(call)                                 \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return fail(e_, #call);   \
+  } while (0)
+  CSR_CK(cudaMemsetAsync(h->mem, 0, head, s));
+  CSR_CK(cudaMemcpyAsync(h->soff, hoff.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CSR_CK(cudaMemcpyAsync(h->rinv, rinv_tmp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CSR_CK(cudaMemcpyAsync(h->b, d->B, n * sizeof(double), cudaMemcpyDefault, s));
+  CSR_CK(launch_csr_fill(n, rp, ci, va, h->soff, h->sval, h->scol, s));
+  CSR_CK(cudaStreamSynchronize(s));
+#undef CSR_CK
+  const int cap = csr_max_grid();
+  if (cap <= 0) return fail(cudaGetLastError(), "occupancy query");
+  const int64_t want = (nslices + csr_warps_per_cta() - 1) / csr_warps_per_cta();
+  h->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(cap, want)));
+  *out = h.release();
+  return JACOBI_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void jacobi_desc_init(jacobi_desc* d) {
@@ -883,5 +1048,89 @@ const char* jacobi_status_string(int status) {
 }
 
 const char* jacobi_last_cuda_error(void) { return g_cuda_err; }
+
+
+int jacobi_csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) { return csr_setup(d, out); }
+
+int jacobi_csr_solve_async(jacobi_csr* h, const double* X0, int64_t max_iter, double tol, double* X_out) {
+  if (!h || !X_out || max_iter < 1 || !(tol > 0.0) || !std::isfinite(tol)) return JACOBI_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+  if (X0)
+    CK(cudaMemcpyAsync(h->xa, X0, h->n * sizeof(double), cudaMemcpyDefault, s));
+  else
+    CK(cudaMemsetAsync(h->xa, 0, h->n * sizeof(double), s));
+  CsrParams p{};
+  p.n = h->n;
+  p.nslices = h->nslices;
+  p.soff = h->soff;
+  p.sval = h->sval;
+  p.scol = h->scol;
+  p.b = h->b;
+  p.rinv = h->rinv;
+  p.xa = h->xa;
+  p.xb = h->xb;
+  p.part = h->part;
+  p.ctl = h->ctl;
+  p.x_out = is_device_memory(X_out) ? X_out : h->xout;
+  p.stats_out = nullptr;
+  p.max_iter = max_iter;
+  p.tol = tol;
+  p.norm = h->norm;
+  p.wait_ns = h->wait_ns;
+  cudaError_t e = launch_csr_solve(p, h->grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch (sparse)");
+  if (p.x_out != X_out) CK(cudaMemcpyAsync(X_out, h->xout, h->n * sizeof(double), cudaMemcpyDefault, s));
+  return JACOBI_OK;
+}
+
+int jacobi_csr_last_stats(jacobi_csr* h, jacobi_stats* stats) {
+  if (!h || !stats) return JACOBI_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(stats, &h->ctl->result, sizeof(jacobi_stats), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return JACOBI_OK;
+}
+
+int jacobi_csr_solve(jacobi_csr* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+                     jacobi_stats* stats) {
+  int st = jacobi_csr_solve_async(h, X0, max_iter, tol, X_out);
+  if (st != JACOBI_OK) return st;
+  jacobi_stats local;
+  st = jacobi_csr_last_stats(h, &local);
+  if (st != JACOBI_OK) return st;
+  if (stats) *stats = local;
+  return local.status;
+}
+
+int jacobi_csr_info(jacobi_csr* h, int64_t* stored_slots, int64_t* slices, int32_t* grid) {
+  if (!h) return JACOBI_ERR_INVALID_ARG;
+  if (stored_slots) *stored_slots = h->stored;
+  if (slices) *slices = h->nslices;
+  if (grid) *grid = h->grid;
+  return JACOBI_OK;
+}
+
+int jacobi_csr_last_trace(jacobi_csr* h, int64_t* t_end_ns, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !t_end_ns)) return JACOBI_ERR_INVALID_ARG;
+  Ctl* host = static_cast<Ctl*>(std::malloc(sizeof(Ctl)));
+  if (!host) return JACOBI_ERR_OUT_OF_MEMORY;
+  cudaError_t e = cudaMemcpyAsync(host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    std::free(host);
+    return cuda_fail(e, "trace read");
+  }
+  *count = host->nphase;
+  const int m = host->nphase < cap ? host->nphase : cap;
+  for (int i = 0; i < m; ++i) t_end_ns[i] = static_cast<int64_t>(host->t_end[i] - host->t_start);
+  std::free(host);
+  return JACOBI_OK;
+}
+
+void jacobi_csr_destroy(jacobi_csr* h) {
+  if (!h) return;
+  if (h->mem) cudaFree(h->mem);
+  delete h;
+}
 
 }  // extern "C"
