@@ -402,7 +402,7 @@ def run_sparse(args, jac, torch, dev):
     tr = s.trace()
     per = sorted(b - a for a, b in tr[1:])  # the first sweep also holds the launch
     sweep_us = per[len(per) // 2] / 1e3
-    alg_bytes = 12.0 * nnz_off + 32.0 * n  # values + columns, b, 1/a_ii, x read, x written
+    alg_bytes = 12.0 * nnz_off + 24.0 * n  # T values + columns, C, x read, x written
     peaks, kind = measured_peaks()
     gbs = alg_bytes / (sweep_us * 1e-6) / 1e9
     ms_solve, st = timed(5000, 1e-12, 3)

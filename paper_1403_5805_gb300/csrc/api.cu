@@ -609,8 +609,7 @@ struct jacobi_csr {
   int64_t* soff = nullptr;
   double* sval = nullptr;
   int32_t* scol = nullptr;
-  double* b = nullptr;
-  double* rinv = nullptr;
+  double* c = nullptr;  // C = D^-1 B
   double* xa = nullptr;
   double* xb = nullptr;
   double* xout = nullptr;
@@ -686,16 +685,12 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   h->stream = s;
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
 
-  // the vectors first (rinv is written by the check pass)
   const size_t vec = align_up(npad * sizeof(double));
-  const size_t head = align_up((nslices + 1) * sizeof(int64_t)) + 5 * vec + align_up(2 * kMaxGrid * sizeof(double)) +
+  const size_t head = align_up((nslices + 1) * sizeof(int64_t)) + 4 * vec + align_up(2 * kMaxGrid * sizeof(double)) +
                       align_up(sizeof(Ctl));
   CK(cudaMemsetAsync(lens, 0, npad * sizeof(int32_t), s));
   CK(cudaMemsetAsync(key, 0xFF, sizeof(unsigned long long), s));
-  double* rinv_tmp = nullptr;
-  CK(cudaMalloc(reinterpret_cast<void**>(&rinv_tmp), npad * sizeof(double)));
-  st.owned.push_back(rinv_tmp);
-  CK(launch_csr_check(n, nnz, rp, ci, va, dd, rinv_tmp, lens, key, s));
+  CK(launch_csr_check(n, nnz, rp, ci, va, dd, lens, key, s));
   unsigned long long hkey = 0;
   CK(cudaMemcpyAsync(&hkey, key, sizeof(hkey), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -722,8 +717,7 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
     return at;
   };
   h->soff = reinterpret_cast<int64_t*>(take(align_up((nslices + 1) * sizeof(int64_t))));
-  h->b = reinterpret_cast<double*>(take(vec));
-  h->rinv = reinterpret_cast<double*>(take(vec));
+  h->c = reinterpret_cast<double*>(take(vec));
   h->xa = reinterpret_cast<double*>(take(vec));
   h->xb = reinterpret_cast<double*>(take(vec));
   h->xout = reinterpret_cast<double*>(take(vec));
@@ -744,9 +738,8 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   } while (0)
   CSR_CK(cudaMemsetAsync(h->mem, 0, head, s));
   CSR_CK(cudaMemcpyAsync(h->soff, hoff.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  CSR_CK(cudaMemcpyAsync(h->rinv, rinv_tmp, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CSR_CK(cudaMemcpyAsync(h->b, d->B, n * sizeof(double), cudaMemcpyDefault, s));
-  CSR_CK(launch_csr_fill(n, rp, ci, va, h->soff, h->sval, h->scol, s));
+  CSR_CK(cudaMemcpyAsync(h->c, d->B, n * sizeof(double), cudaMemcpyDefault, s));
+  CSR_CK(launch_csr_fill(n, rp, ci, va, dd, h->soff, h->sval, h->scol, h->c, s));
   CSR_CK(cudaStreamSynchronize(s));
 #undef CSR_CK
   const int cap = csr_max_grid();
@@ -1066,8 +1059,7 @@ int jacobi_csr_solve_async(jacobi_csr* h, const double* X0, int64_t max_iter, do
   p.soff = h->soff;
   p.sval = h->sval;
   p.scol = h->scol;
-  p.b = h->b;
-  p.rinv = h->rinv;
+  p.c = h->c;
   p.xa = h->xa;
   p.xb = h->xb;
   p.part = h->part;

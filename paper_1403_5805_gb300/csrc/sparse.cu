@@ -3,12 +3,14 @@
 //   x_i^(k) = ( beta_i - sum_{stored j != i} alpha_ij x_j^(k-1) ) / alpha_ii,
 //
 // for the banded and PDE-shaped matrices of the Jacobi codes for differential equations that the paper's
-// related work cites.  The caller's CSR arrays are converted once per setup into a sliced-ELL copy of the
-// off-diagonal part: slices of 32 rows, one warp per slice and one row per lane, each slice as wide as
-// its longest row and stored column-major, so that the warp's loads of the t-th entries of its 32 rows
-// are one contiguous 256-byte run.  The diagonal leaves the matrix: the sweep multiplies by the correctly
-// rounded 1 / a_ii, as the dense FP64 path does.  A row's entries keep their ascending column order, so
-// the sum runs in the same order as the oracle's.
+// related work cites.  Setup forms the fixed-point form of Section 2, T = D^-1 (L + U) and C = D^-1 B,
+// i.e. t_ij = -a_ij / a_ii and c_i = b_i / a_ii (IEEE divisions), and keeps T as a sliced-ELL copy:
+// slices of 32 rows, one warp per slice and one row per lane, each slice as wide as its longest row and
+// stored column-major, so that the warp's loads of the t-th entries of its 32 rows are one contiguous
+// 256-byte run.  A sweep is then x_i = c_i + sum_j t_ij x_j: a row of w stored entries costs w FP64 FMAs
+// plus one subtraction for the change, which matters on GB300, whose FP64 issue rate (about 2 per clock
+// per SM) would otherwise bound these short rows as tightly as HBM does.  A row's entries keep their
+// ascending column order, so the sum runs in the same order as the oracle's.
 //
 // One persistent cooperative launch runs the whole solve: per sweep each warp streams its slices (values
 // and columns with the evict-first hint, so the iterate stays in L2 for the gathers), writes x^(k) and
@@ -21,13 +23,12 @@
 namespace jac {
 namespace {
 
-constexpr int kCsrThreads = 1024;
-constexpr int kCsrMinBlocks = 2;  // 64 warps per SM keep enough loads in flight for rows of a few entries
+constexpr int kCsrThreads = 768;
+constexpr int kCsrMinBlocks = 2;  // 48 warps per SM, up to 42 registers each
 constexpr int kCsrWarps = kCsrThreads / 32;
 
 __global__ void csr_check_kernel(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                 const double* __restrict__ val, double* d, double* rinv, int32_t* lens,
-                                 unsigned long long* key) {
+                                 const double* __restrict__ val, double* d, int32_t* lens, unsigned long long* key) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t e0 = rp[i], e1 = rp[i + 1];
@@ -57,7 +58,6 @@ __global__ void csr_check_kernel(int64_t n, int64_t nnz, const int64_t* __restri
         bad = (1ull << 56) | row | 2u;
       } else {
         d[i] = dv;
-        rinv[i] = 1.0 / dv;
         lens[i] = cnt;
       }
     }
@@ -76,21 +76,25 @@ __global__ void csr_widths_kernel(int64_t n, int64_t nslices, const int32_t* __r
 
 __global__ void csr_fill_kernel(int64_t n, int64_t nslices, const int64_t* __restrict__ rp,
                                 const int32_t* __restrict__ ci, const double* __restrict__ val,
-                                const int64_t* __restrict__ soff, double* sval, int32_t* scol) {
+                                const double* __restrict__ d, const int64_t* __restrict__ soff, double* sval,
+                                int32_t* scol, double* c) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t s = i / kSliceRows;
   if (s >= nslices) return;
   const int lane = static_cast<int>(i % kSliceRows);
   const int64_t base = soff[s] + lane, w = (soff[s + 1] - soff[s]) / kSliceRows;
   int64_t t = 0;
-  if (i < n)
+  if (i < n) {
+    const double di = d[i];
     for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
-      const int32_t c = ci[e];
-      if (c == i) continue;
-      sval[base + kSliceRows * t] = val[e];
-      scol[base + kSliceRows * t] = c;
+      const int32_t col = ci[e];
+      if (col == i) continue;
+      sval[base + kSliceRows * t] = -val[e] / di;  // t_ij = -a_ij / a_ii
+      scol[base + kSliceRows * t] = col;
       ++t;
     }
+    c[i] = c[i] / di;  // c_i = b_i / a_ii (c holds b on entry)
+  }
   const int32_t self = static_cast<int32_t>(i < n ? i : n - 1);
   for (; t < w; ++t) {
     sval[base + kSliceRows * t] = 0.0;
@@ -120,18 +124,28 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(C
     unsigned long long mx = 0;
     double sq = 0.0;
     for (int64_t s = gw; s < p.nslices; s += nw) {
-      const int64_t o0 = __ldg(p.soff + s);
-      const int w = static_cast<int>((__ldg(p.soff + s + 1) - o0) / kSliceRows);
+      const int64_t o0 = __ldg(p.soff + s), o1 = __ldg(p.soff + s + 1);
+      const int w = static_cast<int>((o1 - o0) / kSliceRows);
+      // pull the warp's next slice into L2 meanwhile: its values and columns, one 128-byte line per lane
+      if (s + nw < p.nslices) {
+        const int64_t q0 = __ldg(p.soff + s + nw), q1 = __ldg(p.soff + s + nw + 1);
+        const int64_t vl = (q1 - q0) / 16, cl = (q1 - q0) / 32;  // lines of values (8 B) and columns (4 B)
+        for (int64_t l = lane; l < vl + cl; l += 32) {
+          const char* a = l < vl ? reinterpret_cast<const char*>(p.sval + q0) + 128 * l
+                                 : reinterpret_cast<const char*>(p.scol + q0) + 128 * (l - vl);
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+        }
+      }
+      const int64_t i = s * kSliceRows + lane;
+      const bool live = i < p.n;
+      const double xo = live ? __ldcg(xc + i) : 0.0;
       const double* v = p.sval + o0 + lane;
       const int32_t* cc = p.scol + o0 + lane;
-      double acc = 0.0;
+      double x = live ? __ldcs(p.c + i) : 0.0;
 #pragma unroll 4
-      for (int t = 0; t < w; ++t)
-        acc = fma(__ldcs(v + kSliceRows * t), __ldcg(xc + __ldcs(cc + kSliceRows * t)), acc);
-      const int64_t i = s * kSliceRows + lane;
-      if (i < p.n) {
-        const double x = (__ldcs(p.b + i) - acc) * __ldcs(p.rinv + i);
-        const double diff = x - __ldcg(xc + i);
+      for (int t = 0; t < w; ++t) x = fma(__ldcs(v + kSliceRows * t), __ldcg(xc + __ldcs(cc + kSliceRows * t)), x);
+      if (live) {
+        const double diff = x - xo;
         xn[i] = x;
         const unsigned long long bb = abs_bits(diff);
         mx = bb > mx ? bb : mx;
@@ -222,9 +236,8 @@ int blocks_for(int64_t items, int threads) { return static_cast<int>((items + th
 }  // namespace
 
 cudaError_t launch_csr_check(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
-                             const double* val, double* d, double* rinv, int32_t* lens, unsigned long long* key,
-                             cudaStream_t s) {
-  csr_check_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, nnz, row_ptr, col_idx, val, d, rinv, lens, key);
+                             const double* val, double* d, int32_t* lens, unsigned long long* key, cudaStream_t s) {
+  csr_check_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, nnz, row_ptr, col_idx, val, d, lens, key);
   return cudaGetLastError();
 }
 
@@ -235,10 +248,11 @@ cudaError_t launch_csr_widths(int64_t n, const int32_t* lens, int32_t* width, cu
 }
 
 cudaError_t launch_csr_fill(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
-                            const int64_t* soff, double* sval, int32_t* scol, cudaStream_t s) {
+                            const double* d, const int64_t* soff, double* sval, int32_t* scol, double* c,
+                            cudaStream_t s) {
   const int64_t nslices = (n + kSliceRows - 1) / kSliceRows;
-  csr_fill_kernel<<<blocks_for(nslices * kSliceRows, 256), 256, 0, s>>>(n, nslices, row_ptr, col_idx, val, soff, sval,
-                                                                         scol);
+  csr_fill_kernel<<<blocks_for(nslices * kSliceRows, 256), 256, 0, s>>>(n, nslices, row_ptr, col_idx, val, d, soff,
+                                                                         sval, scol, c);
   return cudaGetLastError();
 }
 

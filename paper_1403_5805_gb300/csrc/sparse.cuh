@@ -11,29 +11,29 @@ namespace jac {
 constexpr int kSliceRows = 32;  // rows per slice of the sliced-ELL copy: one warp, one row per lane
 
 // Setup pass 1 (one thread per row) over CSR arrays in device memory: checks the structure and the
-// diagonal, writes d_i, 1/d_i and the row's off-diagonal count.  The first failure by the oracle's order is
+// diagonal, writes d_i = a_ii and the row's off-diagonal count.  The first failure by the oracle's order is
 // left in *key (all ones beforehand) as (class << 56) | (row << 8) | code: class 0 = structure (code 1:
 // row_ptr[0] != 0, a row range that decreases or leaves [0, nnz), a column out of range, or columns not
 // strictly ascending), class 1 = diagonal (code 2: missing or zero, code 3: non-finite).  Only entries
 // inside [0, nnz) are read.
 cudaError_t launch_csr_check(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
-                             const double* val, double* d, double* rinv, int32_t* lens, unsigned long long* key,
-                             cudaStream_t s);
+                             const double* val, double* d, int32_t* lens, unsigned long long* key, cudaStream_t s);
 // Setup pass 2: width[s] = max off-diagonal count over the rows of slice s (one warp per slice).
 cudaError_t launch_csr_widths(int64_t n, const int32_t* lens, int32_t* width, cudaStream_t s);
-// Setup pass 3: the sliced-ELL copy of the off-diagonal entries.  Entry t of row i = 32 s + l sits at
-// soff[s] + 32 t + l (column-major inside the slice, so a warp's loads of one entry index are one 256-byte
-// run); slots past the row's length hold value 0 and the column min(i, n - 1).
+// Setup pass 3: T = D^-1 (L + U) as a sliced-ELL copy, t_ij = -a_ij / a_ii, and C = D^-1 B in place
+// (c holds b on entry).  Entry t of row i = 32 s + l sits at soff[s] + 32 t + l (column-major inside the
+// slice, so a warp's loads of one entry index are one 256-byte run); slots past the row's length hold
+// value 0 and the column min(i, n - 1).
 cudaError_t launch_csr_fill(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
-                            const int64_t* soff, double* sval, int32_t* scol, cudaStream_t s);
+                            const double* d, const int64_t* soff, double* sval, int32_t* scol, double* c,
+                            cudaStream_t s);
 
 struct CsrParams {
   int64_t n, nslices;
   const int64_t* soff;  // nslices + 1 slot offsets (multiples of 32)
-  const double* sval;   // off-diagonal values, sliced ELL
+  const double* sval;   // t_ij = -a_ij / a_ii, sliced ELL
   const int32_t* scol;  // their columns
-  const double* b;
-  const double* rinv;   // 1 / a_ii (correctly rounded)
+  const double* c;      // c_i = b_i / a_ii
   double* xa;           // iterate buffers (length 32 nslices, zero past n): x^(0) in xa, then alternating
   double* xb;
   double* part;         // [2][kMaxGrid] per-CTA partial sums (Euclidean norm)

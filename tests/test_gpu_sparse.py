@@ -68,7 +68,12 @@ def test_sparse_euclidean_norm_and_start_vector(jac):
     X, st = s.solve(X0=gpu(x0), max_iter=2000, tol=1e-11)
     ref = oracle.csr_jacobi(rp, ci, v, B, X0=x0, max_iter=2000, tol=1e-11, norm=oracle.NORM_2)
     assert (st.status, st.sweeps) == (ref.status, ref.iters)
-    assert abs(st.final_delta - ref.delta) <= 1e-9 * ref.delta + 1e-16
+    # delta is the norm of a difference of nearly equal iterates, so it inherits their rounding
+    # differences: the GPU sweep x = c + T x (rounded t_ij and c_i) and the oracle's (b - s) / a_ii differ by a
+    # few ulps of max|x| per component and sweep, at most (w + 2) ulp / (1 - rho) ~ 1e-14 here (w <= 4,
+    # rho <= 1/1.2), and | ||e_k|| - ||e_k'|| | <= ||e_k - e_k'||_2 <= 2 sqrt(n) max_i |x_i - x_i'|
+    n = B.shape[0]
+    assert abs(st.final_delta - ref.delta) <= 2 * np.sqrt(n) * 1e-14
     assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
 
 
