@@ -569,8 +569,7 @@ def generate_request(n: int, r: int, f: float, seed: int, device=None, stream=No
     A = torch.empty(n, n, dtype=torch.float64, device=device)
     B = torch.zeros(r, n, dtype=torch.float64, device=device)
     _check(load().jacobi_generate_request(n, r, f, seed, A.data_ptr(), B.data_ptr(), n, stream.cuda_stream),
-           "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async", "jacobi_csr_solve",
-           "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace", "jacobi_csr_destroy")
+           "jacobi_generate_request")
     return A, B
 
 
