@@ -31,6 +31,7 @@ FLAG_COPY_A = 1
 FLAG_SPLIT_RESIDUAL = 2
 FLAG_SHORT_WAITS = 4
 FLAG_TEST_DROP_COPY = 8
+FLAG_TEST_SKIP_ARRIVAL = 32
 FLAG_RETIRE_COLUMNS = 16
 METHODS = {"jacobi": 0, "sor": 1}
 

@@ -604,6 +604,7 @@ struct jacobi_csr {
   int norm = JACOBI_NORM_INF;
   int grid = 0;
   uint64_t wait_ns = 4000000000ull;
+  int test_skip_arrival = 0;
   cudaStream_t stream = nullptr;
   void* mem = nullptr;  // one allocation for everything below
   int64_t* soff = nullptr;
@@ -684,6 +685,7 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   h->norm = d->norm;
   h->stream = s;
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
+  h->test_skip_arrival = (d->flags & JACOBI_FLAG_TEST_SKIP_ARRIVAL) ? 1 : 0;
 
   const size_t vec = align_up(npad * sizeof(double));
   const size_t head = align_up((nslices + 1) * sizeof(int64_t)) + 4 * vec + align_up(2 * kMaxGrid * sizeof(double)) +
@@ -1069,6 +1071,7 @@ int jacobi_csr_solve_async(jacobi_csr* h, const double* X0, int64_t max_iter, do
   p.max_iter = max_iter;
   p.tol = tol;
   p.norm = h->norm;
+  p.test_skip_arrival = h->test_skip_arrival;
   p.wait_ns = h->wait_ns;
   cudaError_t e = launch_csr_solve(p, h->grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch (sparse)");

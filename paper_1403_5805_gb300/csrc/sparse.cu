@@ -174,7 +174,13 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(C
           atomicMax(&p.ctl->red[slot][0], bm);
         }
         if (blockIdx.x == 0) p.ctl->red[(phase + 1) % 3][0] = 0ull;  // opened before anyone passes the barrier
-        ok = grid_arrive_and_wait(&p.ctl->arrive, &p.ctl->status, (phase + 1) * static_cast<uint32_t>(G), p.wait_ns);
+        if (p.test_skip_arrival && blockIdx.x == 0 && phase == 0) {
+          ok = 0;
+          atomicMin(&p.ctl->status, kStatusTimeout);  // the others leave their wait on the error word
+        } else {
+          ok = grid_arrive_and_wait(&p.ctl->arrive, &p.ctl->status, (phase + 1) * static_cast<uint32_t>(G),
+                                    p.wait_ns);
+        }
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
       __syncwarp();  // the other lanes read after lane 0's acquire of the grid barrier

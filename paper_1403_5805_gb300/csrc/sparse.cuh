@@ -43,6 +43,7 @@ struct CsrParams {
   int64_t max_iter;
   double tol;
   int norm;             // JACOBI_NORM_INF or JACOBI_NORM_2
+  int test_skip_arrival;  // test only: CTA 0 skips the first grid barrier and raises the error word
   uint64_t wait_ns;
 };
 

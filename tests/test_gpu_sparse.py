@@ -39,6 +39,7 @@ def rel_err(x, ref):
 SYSTEMS = {
     "irregular_1000": lambda: synth.random_sparse_system(1000, 1.1, seed=31, max_len=60),
     "irregular_33": lambda: synth.random_sparse_system(33, 1.3, seed=32, max_len=40),
+    "long_rows_2000": lambda: synth.random_sparse_system(2000, 1.05, seed=39, max_len=1500),
     "one_unknown": lambda: synth.random_sparse_system(1, 1.5, seed=33),
     "line_95": lambda: synth.stencil_system((95,), 1.05, seed=34),
     "plane_37x29": lambda: synth.stencil_system((37, 29), 1.05, seed=35),
@@ -137,3 +138,21 @@ def test_sparse_full_size_plane(jac):
     r = np.array([B[i, 0] - v[rp[i]:rp[i + 1]] @ Xh[ci[rp[i]:rp[i + 1]]] for i in rows])
     assert np.max(np.abs(r)) / np.max(np.abs(B)) <= 1e-11
     assert np.max(np.abs(Xh - Xs[:, 0])) <= 1e-10
+
+
+def test_sparse_bounded_wait_expires_and_context_stays_usable(jac):
+    """Failure detection without a GPU fault: CTA 0 skips the first sweep's grid barrier and raises the
+    error word, the other CTAs leave their bounded wait (50 ms at most), the solve reports a timeout, and
+    the next solve on the same context matches the oracle."""
+    rp, ci, v, B, _ = synth.stencil_system((300, 200), 1.1, seed=40)
+    flags = jac.binding.FLAG_SHORT_WAITS | jac.binding.FLAG_TEST_SKIP_ARRIVAL
+    bad = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), flags=flags)
+    assert bad.info()["grid"] > 1
+    with pytest.raises(jac.JacobiError) as e:
+        bad.solve(max_iter=100, tol=1e-12)
+    assert e.value.status == jac.ERR_TIMEOUT
+    good = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]))
+    X, st = good.solve(max_iter=2000, tol=1e-12)
+    ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=2000, tol=1e-12)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters)
+    assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
