@@ -894,6 +894,7 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
     g.tol = tol;
     g.norm = h->norm;
     g.omega = h->omega;
+    g.cmax = h->at<unsigned long long>(h->L.cmax);
     g.wait_ns = h->wait_ns;
     e = launch_gs_solve(g, h->grid, s);
   } else {

@@ -31,6 +31,7 @@
 // per-row warp butterflies.
 #include "device_util.cuh"
 #include "gs.cuh"
+#include "splitfloat.cuh"
 
 namespace jac {
 namespace {
@@ -208,6 +209,9 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   double* w = u + kGsMaxRows;         // (1 - omega) D x^(k-1) + omega u
   double* xn_b = w + kGsMaxRows;      // x^(k) of the block
   double* xp = xn_b + kGsMaxRows;     // x^(k) of the previous block
+  float2* xpf = reinterpret_cast<float2*>(xp + kGsMaxRows);  // the same as float-float pairs at scale 2^-g
+  int* qe = reinterpret_cast<int*>(xpf + kGsMaxRows);        // row scale exponents of Q
+  float2* qf = reinterpret_cast<float2*>(qm);                 // Q as float-float pairs (in place, after setup)
   __shared__ unsigned long long s_red[kGsWarps];
   __shared__ double s_sq[kGsWarps];
   __shared__ int s_e, s_ok, s_next, s_status;
@@ -270,6 +274,30 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
     }
   }
   __syncthreads();
+  // Q as float-float pairs: row i scaled by 2^-qe_i (qe_i the split exponent of max_j |Q_ij|), each entry
+  // split with integer operations into its top 24 and next 23 significant bits, in place
+  if (c > 0) {
+    if (tid < m) {
+      uint32_t mb = 0;
+      for (int j = 0; j < mp; ++j) {
+        const uint32_t h = abs_hi(qm[tid * P + j]);
+        mb = h > mb ? h : mb;
+      }
+      qe[tid] = split_exponent_hi(mb);
+    }
+    __syncthreads();
+    for (int e = tid; e < m * mp; e += kGsThreads) {
+      const int i = e / mp, j = e % mp;
+      float h, l;
+      split_scaled(qm[i * P + j], qe[i], h, l);
+      qf[i * P + j] = make_float2(h, l);
+    }
+    __syncthreads();
+  }
+  // the scale of the float-float split of the previous block's values: x^(k) stays within a modest factor
+  // of max_i |b_i / a_ii| for a convergent iteration; a link whose values reach 2^(g + 100) (or are not
+  // finite) runs in FP64 instead
+  const int g = split_exponent(__ldg(p.cmax));
 
   // u_i = beta_i - sum_{j > i in the block} a_ij x_j with the block's own values xs (all threads call it)
   auto start_u = [&](const double* xs) {
@@ -315,6 +343,7 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
     x += __shfl_xor_sync(0xffffffffu, x, 1);
     if (c > 0) {
       // x_(c-1)^(k) from the previous block's mailbox, one entry per thread, emptied again for sweep k+2
+      int bad = 0;
       if (tid < mp) {
         unsigned long long* e = box + sp + tid;
         unsigned long long v = ld_relaxed_u64(e);
@@ -327,15 +356,40 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
             }
           }
         }
-        xp[tid] = __longlong_as_double(static_cast<long long>(v));
+        const double xv = __longlong_as_double(static_cast<long long>(v));
+        xp[tid] = xv;
+        const int be = static_cast<int>((v >> 52) & 0x7FFu);
+        bad = be == 0x7FF || be - 1023 >= g + 100;
+        float h, l;
+        split_scaled(xv, g, h, l);
+        xpf[tid] = make_float2(h, l);
         st_relaxed_u64(e, kEmpty);
       }
-      __syncthreads();
-      // x = y + Q x_(c-1)
+      const int any_bad = __syncthreads_or(bad);
+      // x = y + Q x_(c-1): on the FP32 units as float-float products (renormalised every 8), the pair's two
+      // halves summed in FP64 and scaled back by 2^(qe_i + g); FP64 when a value is out of range
       double s = 0.0;
-      if (row_ok)
-        for (int j = par; j < mp; j += 2) s = fma(qm[ri * P + j], xp[j], s);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (!any_bad) {
+        FF a{0.0f, 0.0f};
+        if (row_ok)
+          for (int j = par, cnt = 1; j < mp; j += 2, ++cnt) {
+            const float2 q = qf[ri * P + j], xv = xpf[j];
+            ff_fma(a, q.x, q.y, xv.x, xv.y);
+            if ((cnt & 7) == 0) ff_renorm(a);
+          }
+        double d = static_cast<double>(a.hi) + static_cast<double>(a.lo);
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        if (row_ok) s = d * pow2(qe[ri]) * pow2(g);
+      } else {
+        if (row_ok) {
+          const double sc = pow2(qe[ri]);
+          for (int j = par; j < mp; j += 2) {
+            const float2 q = qf[ri * P + j];
+            s = fma((static_cast<double>(q.x) + static_cast<double>(q.y)) * sc, xp[j], s);
+          }
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+      }
       x += s;
     }
     unsigned long long mx = 0;

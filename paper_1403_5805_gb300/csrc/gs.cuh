@@ -12,8 +12,10 @@ constexpr int kGsThreads = 256;   // 8 warps per CTA
 constexpr int kGsMaxRows = 112;   // rows per CTA block
 constexpr int kGsPitch = kGsMaxRows + 1;  // shared-memory row pitch of the block tiles (odd: no bank clash)
 // Two block tiles (the diagonal block with the inverse of its lower part; -omega M^-1 times this CTA's rows
-// x the previous block's columns) plus five vectors.
-constexpr size_t kGsSmem = 2 * sizeof(double) * kGsMaxRows * kGsPitch + 5 * sizeof(double) * kGsMaxRows;
+// x the previous block's columns, as float-float pairs), five FP64 vectors, the previous block's values as
+// float-float pairs and the row scale exponents of Q.
+constexpr size_t kGsSmem = 2 * sizeof(double) * kGsMaxRows * kGsPitch + 5 * sizeof(double) * kGsMaxRows +
+                           kGsMaxRows * (sizeof(float2) + sizeof(int));
 
 struct GsParams {
   int64_t n;
@@ -34,6 +36,7 @@ struct GsParams {
   double tol;
   int norm;             // JACOBI_NORM_INF or JACOBI_NORM_2
   double omega;         // relaxation, 0 < omega < 2 (1: Gauss-Seidel)
+  const unsigned long long* cmax;  // IEEE bits of max_i |b_i / a_ii|: the scale of the float-float split of x
   uint64_t wait_ns;
 };
 

@@ -98,3 +98,18 @@ def test_sor_full_size_hard_generator(jac):
     R = B[rows, 0] - A[rows] @ Xh
     assert np.max(np.abs(R)) / np.max(np.abs(B)) <= 1e-10
     assert np.max(np.abs(Xh - Xs[:, 0])) <= 1e-9
+
+
+def test_sor_far_start_vector_takes_the_fp64_links(jac):
+    """A start vector 1e40 times larger than max |b_i / a_ii| puts the first hand-offs outside the range of
+    the float-float product (values at or above 2^(g + 100)), so those links run in FP64; the iterates still
+    follow the oracle as the iteration contracts back to the solution's scale."""
+    A, B, _ = synth.dominant_system(900, 1.1, seed=80)
+    x0 = 1e40 * np.cos(np.arange(900.0))
+    s = solver(jac, A, B)
+    import torch
+    for k in (1, 2, 5, 12):  # by sweep 12 the values are back inside the float-float range
+        X, st = s.solve(X0=torch.from_numpy(x0).cuda(), max_iter=k, tol=1e-300)
+        ref = oracle.block_sor(A, B, X0=x0[:, None], max_iter=k, tol=1e-300, blocks=1)
+        assert st.sweeps == ref.iters == k
+        assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12, k
