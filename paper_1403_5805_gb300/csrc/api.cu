@@ -250,6 +250,7 @@ int prepare(jacobi_handle* h, const double* A, int64_t lda, const double* B, boo
     CK(launch_narrow(narrow_kind(h->precision), h->A64, h->lda64, n, h->at<void>(h->L.Nlow), h->L.ld,
                      h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac),
                      h->split_residual ? h->at<int>(h->L.rexp) : nullptr, s));
+  if (h->method == JACOBI_METHOD_SOR) CK(launch_gs_row_exponents(h->A64, h->lda64, n, h->at<int>(h->L.rexp), s));
   unsigned long long key = 0;
   CK(cudaMemcpyAsync(&key, keys, sizeof(key), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -895,6 +896,7 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
     g.norm = h->norm;
     g.omega = h->omega;
     g.cmax = h->at<unsigned long long>(h->L.cmax);
+    g.rexp = h->at<int>(h->L.rexp);
     g.wait_ns = h->wait_ns;
     e = launch_gs_solve(g, h->grid, s);
   } else {

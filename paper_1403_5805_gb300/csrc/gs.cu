@@ -87,6 +87,37 @@ __device__ __forceinline__ double warp_sum16(const double (&v)[16], int lane) {
   return z;
 }
 
+// Float-float sum (two-sum of the high words, the low words added to its error, fast renormalisation).
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float hs = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(hs, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(hs, bv)), __fsub_rn(b.hi, bv));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  FF r;
+  r.hi = __fadd_rn(hs, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, hs));
+  return r;
+}
+
+__device__ __forceinline__ FF shfl_ff(FF v, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// warp_sum16 on float-float values (the same halving exchanges, each add a float-float sum on the FP32
+// units): lane l receives the total of v[(l >> 1) & 15].
+__device__ __forceinline__ FF warp_sum16_ff(const FF (&v)[16], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+  FF a[8], b[4], d[2];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) a[t] = ff_add(h16 ? v[t + 8] : v[t], shfl_ff(h16 ? v[t] : v[t + 8], 16));
+#pragma unroll
+  for (int t = 0; t < 4; ++t) b[t] = ff_add(h8 ? a[t + 4] : a[t], shfl_ff(h8 ? a[t] : a[t + 4], 8));
+#pragma unroll
+  for (int t = 0; t < 2; ++t) d[t] = ff_add(h4 ? b[t + 2] : b[t], shfl_ff(h4 ? b[t] : b[t + 2], 4));
+  FF z = ff_add(h2 ? d[1] : d[0], shfl_ff(h2 ? d[0] : d[1], 2));
+  return ff_add(z, shfl_ff(z, 1));
+}
+
 // Pull the block's rows over columns [c0, c1) into L2 ahead of use (one prefetch per 128-byte line).
 __device__ void prefetch_rows(const GsParams& p, int64_t r0, int m, int64_t c0, int64_t c1) {
   if (c1 <= c0) return;
@@ -115,10 +146,14 @@ constexpr int kGsRowsPerWarp = (kGsMaxRows + kGsWarps - 1) / kGsWarps;
 static_assert(kGsRowsPerWarp <= 16, "the row sums are reduced sixteen at a time");
 
 // One step of the row products: kCols columns per lane (j0 + lane + 32 t, t < kCols; those at or past c1
-// predicated off), every load issued before the FMAs.
+// predicated off), every load issued before the arithmetic.  The products run on the FP32 units as
+// float-float: a_ij scaled by 2^-re_i (re_i: split exponent of the row maximum) and x_j by 2^-g, each split
+// with integer operations into its top 24 and next 23 significant bits, the error of hi * hi recovered by
+// an FMA (splitfloat.cuh).  A step whose x values reach 2^(g + 100) (or are not finite) runs in FP64
+// instead and is reduced into u at once.
 template <int kCols>
 __device__ __forceinline__ void rows_step(const double* a, int64_t lda, int nr, int64_t j0, int64_t c1, const double* x,
-                                          double (&acc)[16], int lane) {
+                                          FF (&acc)[16], const int* re, int g, double* u, int lane) {
   double xv[kCols], av[kCols][kGsRowsPerWarp];
 #pragma unroll
   for (int t = 0; t < kCols; ++t) {
@@ -128,49 +163,82 @@ __device__ __forceinline__ void rows_step(const double* a, int64_t lda, int nr, 
 #pragma unroll
     for (int q = 0; q < kGsRowsPerWarp; ++q) av[t][q] = ok && q < nr ? __ldg(a + q * lda + j) : 0.0;
   }
+  bool bad = false;
 #pragma unroll
-  for (int t = 0; t < kCols; ++t)
+  for (int t = 0; t < kCols; ++t) {
+    const int be = (static_cast<uint32_t>(__double2hiint(xv[t])) >> 20) & 0x7FF;
+    bad |= be == 0x7FF || be - 1023 >= g + 100;
+  }
+  if (!__any_sync(0xffffffffu, bad)) {
+    float xh[kCols], xl[kCols];
+#pragma unroll
+    for (int t = 0; t < kCols; ++t) split_scaled(xv[t], g, xh[t], xl[t]);
 #pragma unroll
     for (int q = 0; q < kGsRowsPerWarp; ++q)
-      if (q < nr) acc[q] = fma(av[t][q], xv[t], acc[q]);
+      if (q < nr) {
+        const int sh = re[q];
+#pragma unroll
+        for (int t = 0; t < kCols; ++t) {
+          float ah, al;
+          split_scaled(av[t][q], sh, ah, al);
+          ff_fma(acc[q], ah, al, xh[t], xl[t]);
+        }
+        ff_renorm(acc[q]);
+      }
+  } else {
+    double part[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) part[q] = 0.0;
+#pragma unroll
+    for (int t = 0; t < kCols; ++t)
+#pragma unroll
+      for (int q = 0; q < kGsRowsPerWarp; ++q)
+        if (q < nr) part[q] = fma(av[t][q], xv[t], part[q]);
+    const double sum = warp_sum16(part, lane);
+    const int q = (lane >> 1) & 15;
+    if ((lane & 1) == 0 && q < nr) u[q] -= sum;
+  }
 }
 
 // Row products over A for the warp's rows i0 .. i0+nr-1 (nr <= kGsRowsPerWarp): acc[q] += a_(r0+i0+q),j x_j
 // over the lane's columns j = c0 + lane + 32 t in [c0, c1).  Lanes read 32 consecutive columns of a row
-// (coalesced), up to 128 columns per step with every load of the step issued before its FMAs; the steps are
-// the same for all lanes (the ragged end is predicated) and the last one is only as wide as the columns
-// left, so a block costs one memory latency and few idle FP64 lanes.  The per-lane sums stay in registers
-// across calls and are reduced once per phase (flush_rows), so the FP64 adds of the reduction do not recur
-// per block.  x is read through L2 (other CTAs write it during the launch).
+// (coalesced), up to 128 columns per step with every load of the step issued before its arithmetic; the
+// steps are the same for all lanes (the ragged end is predicated) and the last one is only as wide as the
+// columns left, so a block costs one memory latency and few idle lanes.  The per-lane float-float sums
+// stay in registers across calls and are reduced once per phase (flush_rows).  x is read through L2
+// (other CTAs write it during the launch).  re: the warp's rows' scale exponents; u: the warp's rows of u.
 __device__ __forceinline__ void rows_dot(const GsParams& p, int64_t r0, int i0, int nr, int64_t c0, int64_t c1,
-                                         const double* x, double (&acc)[16], int lane) {
+                                         const double* x, FF (&acc)[16], const int* re, int g, double* u, int lane) {
   if (nr <= 0) return;
   const double* a = p.A + (r0 + i0) * p.lda;
   int64_t j0 = c0;
-  for (; c1 - j0 > 96; j0 += 128) rows_step<4>(a, p.lda, nr, j0, c1, x, acc, lane);
+  for (; c1 - j0 > 96; j0 += 128) rows_step<4>(a, p.lda, nr, j0, c1, x, acc, re, g, u, lane);
   const int64_t rem = c1 - j0;
   if (rem > 64)
-    rows_step<3>(a, p.lda, nr, j0, c1, x, acc, lane);
+    rows_step<3>(a, p.lda, nr, j0, c1, x, acc, re, g, u, lane);
   else if (rem > 32)
-    rows_step<2>(a, p.lda, nr, j0, c1, x, acc, lane);
+    rows_step<2>(a, p.lda, nr, j0, c1, x, acc, re, g, u, lane);
   else if (rem > 0)
-    rows_step<1>(a, p.lda, nr, j0, c1, x, acc, lane);
+    rows_step<1>(a, p.lda, nr, j0, c1, x, acc, re, g, u, lane);
 }
 
-// u[i0 + q] -= the warp's sums of acc[q] (q < nr), and acc cleared.
-__device__ __forceinline__ void flush_rows(double (&acc)[16], double* u, int i0, int nr, int lane) {
-  const double s = warp_sum16(acc, lane);
+// u[q] -= the warp's float-float sums of acc[q] (q < nr), back in FP64 at scale 2^(re_q + g); acc cleared.
+__device__ __forceinline__ void flush_rows(FF (&acc)[16], double* u, const int* re, int g, int nr, int lane) {
+  if (nr <= 0) return;
+  const FF t = warp_sum16_ff(acc, lane);
   const int q = (lane >> 1) & 15;
-  if ((lane & 1) == 0 && q < nr) u[i0 + q] -= s;
+  if ((lane & 1) == 0 && q < nr)
+    u[q] -= (static_cast<double>(t.hi) + static_cast<double>(t.lo)) * pow2(re[q]) * pow2(g);
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  for (int k = 0; k < 16; ++k) acc[k] = FF{0.0f, 0.0f};
 }
 
-// acc += the columns of blocks [b0, b1) with x for the warp's rows, taking each block once its flag reaches kf
+// acc (and u) -= the columns of blocks [b0, b1) with x for the warp's rows, taking each block once its flag reaches kf
 // (in block order, runs of already-published blocks at once), and pulling the next awaited block into L2
 // meanwhile.  Called by the whole CTA.  A wait that runs out clears *s_ok and skips the rest.
 __device__ void process_published(const GsParams& p, int64_t r0, int m, int i0, int nr, int b0, int b1, int kf,
-                                  const double* x, double (&acc)[16], int lane, int* s_e, int* s_ok) {
+                                  const double* x, FF (&acc)[16], const int* re, int g, double* u, int lane, int* s_e,
+                                  int* s_ok) {
   const int G = gridDim.x;
   if (b0 < b1) prefetch_rows(p, r0, m, p.n * b0 / G, p.n * (b0 + 1) / G);
   int done = b0;
@@ -190,7 +258,7 @@ __device__ void process_published(const GsParams& p, int64_t r0, int m, int i0, 
     __syncthreads();
     const int e = *s_e;
     if (e < b1) prefetch_rows(p, r0, m, p.n * e / G, p.n * (e + 1) / G);
-    if (*s_ok) rows_dot(p, r0, i0, nr, p.n * done / G, p.n * e / G, x, acc, lane);
+    if (*s_ok) rows_dot(p, r0, i0, nr, p.n * done / G, p.n * e / G, x, acc, re, g, u, lane);
     done = e;
   }
 }
@@ -211,6 +279,7 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   double* xp = xn_b + kGsMaxRows;     // x^(k) of the previous block
   float2* xpf = reinterpret_cast<float2*>(xp + kGsMaxRows);  // the same as float-float pairs at scale 2^-g
   int* qe = reinterpret_cast<int*>(xpf + kGsMaxRows);        // row scale exponents of Q
+  int* rex = qe + kGsMaxRows;                                 // row scale exponents of A
   float2* qf = reinterpret_cast<float2*>(qm);                 // Q as float-float pairs (in place, after setup)
   __shared__ unsigned long long s_red[kGsWarps];
   __shared__ double s_sq[kGsWarps];
@@ -227,9 +296,9 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   // the row products over A: warp w takes rows [w rpw, (w + 1) rpw)
   const int rpw = (m + kGsWarps - 1) / kGsWarps;
   const int i0 = warp * rpw, nr = max(0, min(rpw, m - i0));
-  double acc[16];
+  FF acc[16];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  for (int t = 0; t < 16; ++t) acc[t] = FF{0.0f, 0.0f};
   const double om = p.omega;
   if (tid == 0 && c == 0) p.ctl->t_start = global_timer_ns();
 
@@ -298,6 +367,7 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   // of max_i |b_i / a_ii| for a convergent iteration; a link whose values reach 2^(g + 100) (or are not
   // finite) runs in FP64 instead
   const int g = split_exponent(__ldg(p.cmax));
+  for (int i = tid; i < m; i += kGsThreads) rex[i] = __ldg(p.rexp + r0 + i);
 
   // u_i = beta_i - sum_{j > i in the block} a_ij x_j with the block's own values xs (all threads call it)
   auto start_u = [&](const double* xs) {
@@ -323,15 +393,16 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
   for (int i = tid; i < m; i += kGsThreads) xo_b[i] = __ldcg(p.xa + r0 + i);
   __syncthreads();
   start_u(xo_b);
-  rows_dot(p, r0, i0, nr, r1, p.n, p.xa, acc, lane);  // sweep 1: the later blocks' x^(0) is the input
   __syncthreads();
-  flush_rows(acc, u, i0, nr, lane);
+  rows_dot(p, r0, i0, nr, r1, p.n, p.xa, acc, rex + i0, g, u + i0, lane);  // sweep 1: the later blocks' x^(0)
+  flush_rows(acc, u + i0, rex + i0, g, nr, lane);
   for (;; ++k) {
     double* xn = (k & 1) ? p.xb : p.xa;
     unsigned long long* box = p.mbox + (k & 1) * p.n;
     // the blocks before the previous one, with x^(k), as they are published (in order)
-    process_published(p, r0, m, i0, nr, 0, c - 1, static_cast<int>(k), xn, acc, lane, &s_e, &s_ok);
-    flush_rows(acc, u, i0, nr, lane);
+    process_published(p, r0, m, i0, nr, 0, c - 1, static_cast<int>(k), xn, acc, rex + i0, g, u + i0, lane, &s_e,
+                      &s_ok);
+    flush_rows(acc, u + i0, rex + i0, g, nr, lane);
     __syncthreads();
     for (int i = tid; i < m; i += kGsThreads)
       w[i] = om == 1.0 ? u[i] : fma(1.0 - om, __ldg(p.d + r0 + i) * xo_b[i], om * u[i]);
@@ -433,9 +504,10 @@ __global__ void __launch_bounds__(kGsThreads, 1) gs_solve_kernel(GsParams p) {
     // of the later blocks as they publish
     for (int i = tid; i < m; i += kGsThreads) xo_b[i] = xn_b[i];
     start_u(xn_b);
-    process_published(p, r0, m, i0, nr, c + 1, G, static_cast<int>(k), xn, acc, lane, &s_e, &s_ok);
     __syncthreads();
-    flush_rows(acc, u, i0, nr, lane);
+    process_published(p, r0, m, i0, nr, c + 1, G, static_cast<int>(k), xn, acc, rex + i0, g, u + i0, lane, &s_e,
+                      &s_ok);
+    flush_rows(acc, u + i0, rex + i0, g, nr, lane);
     // decision on sweep k: the last block has published it (waited for above, or this is the last block)
     __syncthreads();
     if (tid == 0) {
@@ -500,6 +572,33 @@ cudaError_t launch_gs_solve(const GsParams& p, int grid, cudaStream_t s) {
   void* args[] = {&copy};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(gs_solve_kernel), dim3(grid), dim3(kGsThreads),
                                      args, kGsSmem, s);
+}
+
+namespace {
+// rexp[i] = split exponent of max_j |a_ij| (one CTA per row; 32-bit running maximum of the high words)
+__global__ void gs_row_exponent_kernel(const double* __restrict__ A, int64_t lda, int64_t n, int* rexp) {
+  const int64_t i = blockIdx.x;
+  const double* row = A + i * lda;
+  uint32_t mb = 0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const uint32_t h = abs_hi(__ldcs(row + j));
+    mb = h > mb ? h : mb;
+  }
+  mb = __reduce_max_sync(0xffffffffu, mb);
+  __shared__ uint32_t s_mb[8];
+  if ((threadIdx.x & 31) == 0) s_mb[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) mb = s_mb[w] > mb ? s_mb[w] : mb;
+    mb = s_mb[0] > mb ? s_mb[0] : mb;
+    rexp[i] = split_exponent_hi(mb);
+  }
+}
+}  // namespace
+
+cudaError_t launch_gs_row_exponents(const double* A, int64_t lda, int64_t n, int* rexp, cudaStream_t s) {
+  gs_row_exponent_kernel<<<static_cast<unsigned>(n), 256, 0, s>>>(A, lda, n, rexp);
+  return cudaGetLastError();
 }
 
 int gs_max_grid() {

@@ -13,9 +13,9 @@ constexpr int kGsMaxRows = 112;   // rows per CTA block
 constexpr int kGsPitch = kGsMaxRows + 1;  // shared-memory row pitch of the block tiles (odd: no bank clash)
 // Two block tiles (the diagonal block with the inverse of its lower part; -omega M^-1 times this CTA's rows
 // x the previous block's columns, as float-float pairs), five FP64 vectors, the previous block's values as
-// float-float pairs and the row scale exponents of Q.
+// float-float pairs and the row scale exponents of Q and of A.
 constexpr size_t kGsSmem = 2 * sizeof(double) * kGsMaxRows * kGsPitch + 5 * sizeof(double) * kGsMaxRows +
-                           kGsMaxRows * (sizeof(float2) + sizeof(int));
+                           kGsMaxRows * (sizeof(float2) + 2 * sizeof(int));
 
 struct GsParams {
   int64_t n;
@@ -37,6 +37,7 @@ struct GsParams {
   int norm;             // JACOBI_NORM_INF or JACOBI_NORM_2
   double omega;         // relaxation, 0 < omega < 2 (1: Gauss-Seidel)
   const unsigned long long* cmax;  // IEEE bits of max_i |b_i / a_ii|: the scale of the float-float split of x
+  const int* rexp;      // per row: split exponent of max_j |a_ij| (launch_gs_row_exponents)
   uint64_t wait_ns;
 };
 
@@ -45,5 +46,8 @@ struct GsParams {
 cudaError_t launch_gs_solve(const GsParams& p, int grid, cudaStream_t s);
 // Largest co-resident grid of the kernel (0 on failure).
 int gs_max_grid();
+// rexp[i] = split exponent of max_j |a_ij| (|a_ij| 2^-rexp[i] < 1): the row scales of the float-float row
+// products, computed once per handle.
+cudaError_t launch_gs_row_exponents(const double* A, int64_t lda, int64_t n, int* rexp, cudaStream_t s);
 
 }  // namespace jac
