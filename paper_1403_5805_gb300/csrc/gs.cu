@@ -26,9 +26,12 @@
 // The result is the sequential Gauss-Seidel / SOR sweep (up to rounding order), whatever the grid.
 // Sweeps overlap: the stopping test on sweep k is read once the last block has published (no grid barrier).
 // Every wait is bounded by %globaltimer; a wait that runs out sets JACOBI_ERR_TIMEOUT for the solve.
-// FP64 issue is the scarce resource here (a couple of lanes per clock per SM), so every product keeps its
-// FP64 adds to the useful ones: rows are split across two threads or reduced by halving exchanges, not by
-// per-row warp butterflies.
+// FP64 issue is the scarce resource here (a couple of lanes per clock per SM).  So Q x and the row
+// products over A run on the FP32 units as float-float (splitfloat.cuh): power-of-two scales per row of Q
+// and of A and one per solve for x, integer splits into two FP32 words, error-free products; a step or
+// link whose values leave the scale's range falls back to FP64.  The remaining FP64 products (M^-1 w, the
+// strict upper part) split rows across two threads; reductions use halving exchanges, not per-row warp
+// butterflies.
 #include "device_util.cuh"
 #include "gs.cuh"
 #include "splitfloat.cuh"
