@@ -113,3 +113,29 @@ def test_sor_far_start_vector_takes_the_fp64_links(jac):
         ref = oracle.block_sor(A, B, X0=x0[:, None], max_iter=k, tol=1e-300, blocks=1)
         assert st.sweeps == ref.iters == k
         assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12, k
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_sor_random_configurations(jac, case):
+    """Seeded random mixes of size (ragged against the 112-row blocks), grid, omega, generator and norm:
+    the iterate after 3 sweeps and the converged solve against the oracle."""
+    rng = np.random.default_rng(900 + case)
+    n = int(rng.integers(2, 2400))
+    gen = synth.dominant_system if rng.random() < 0.6 else synth.hard_system
+    f = float(rng.uniform(1.05, 1.5))
+    omega = float(rng.choice([1.0, 1.0, float(rng.uniform(0.6, 1.4))]))
+    norm = "2" if rng.random() < 0.3 else "inf"
+    need = -(-n // 112)
+    grid = int(rng.integers(need, max(need, min(152, n)) + 1)) if rng.random() < 0.5 else 0
+    A, B, _ = gen(n, f, seed=1000 + case)
+    s = solver(jac, A, B, omega=omega, norm=norm, grid=grid)
+    onorm = oracle.NORM_2 if norm == "2" else oracle.NORM_INF
+    X, st = s.solve(max_iter=3, tol=1e-300)
+    ref = oracle.block_sor(A, B, max_iter=3, tol=1e-300, blocks=1, omega=omega, norm=onorm)
+    assert st.sweeps == ref.iters
+    assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12, (n, grid, omega)
+    X, st = s.solve(max_iter=3000, tol=1e-11)
+    ref = oracle.block_sor(A, B, max_iter=3000, tol=1e-11, blocks=1, omega=omega, norm=onorm)
+    assert st.status == ref.status == 0, (n, grid, omega, st.as_dict())
+    assert abs(st.sweeps - ref.iters) <= (1 if norm == "2" else 0), (st.sweeps, ref.iters)
+    assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-11

@@ -156,3 +156,32 @@ def test_sparse_bounded_wait_expires_and_context_stays_usable(jac):
     ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=2000, tol=1e-12)
     assert (st.status, st.sweeps) == (ref.status, ref.iters)
     assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_sparse_random_configurations(jac, case):
+    """Seeded random mixes of stencil shape / irregular rows, size, dominance, norm and start vector: the
+    iterate after 3 sweeps and the converged solve against the oracle."""
+    rng = np.random.default_rng(700 + case)
+    kind = rng.integers(0, 4)
+    f = float(rng.uniform(1.02, 1.5))
+    if kind == 0:
+        rp, ci, v, B, Xs = synth.random_sparse_system(int(rng.integers(1, 5000)), f, seed=800 + case,
+                                                      max_len=int(rng.integers(1, 200)))
+    else:
+        shape = tuple(int(x) for x in rng.integers(1, [4000, 90, 22][kind - 1], size=kind))
+        rp, ci, v, B, Xs = synth.stencil_system(shape, f, seed=800 + case)
+    n = B.shape[0]
+    norm = "2" if rng.random() < 0.3 else "inf"
+    onorm = oracle.NORM_2 if norm == "2" else oracle.NORM_INF
+    x0 = None if rng.random() < 0.5 else rng.uniform(-2, 2, n)
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), norm=norm)
+    X, st = s.solve(X0=None if x0 is None else gpu(x0), max_iter=3, tol=1e-300)
+    ref = oracle.csr_jacobi(rp, ci, v, B, X0=x0, max_iter=3, tol=1e-300, norm=onorm)
+    assert st.sweeps == ref.iters
+    assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12, (n, kind)
+    X, st = s.solve(X0=None if x0 is None else gpu(x0), max_iter=20000, tol=1e-11)
+    ref = oracle.csr_jacobi(rp, ci, v, B, X0=x0, max_iter=20000, tol=1e-11, norm=onorm)
+    assert st.status == ref.status == 0, (n, kind, st.as_dict())
+    assert abs(st.sweeps - ref.iters) <= (1 if norm == "2" else 0), (st.sweeps, ref.iters)
+    assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-11
