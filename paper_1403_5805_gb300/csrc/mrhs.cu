@@ -27,7 +27,14 @@ namespace {
 
 constexpr int kMTile = 128;                 // rows per tile (tcgen05 M)
 constexpr int kKBlock = 64;                 // BF16 elements per 128-byte swizzled row
-constexpr int kMStages = 6;
+constexpr int kMStages = 6;                 // ring depth of the widest blocks (r > 64)
+// Up to 64 right-hand sides a 4-stage ring (97 KB) lets two CTAs share an SM, so the 256 row tiles of
+// n = 32768 are all resident in one wave instead of 1.7 waves of one CTA per SM.
+template <int R>
+struct SweepCfg {
+  static constexpr int kStages = R <= 64 ? 4 : kMStages;
+  static constexpr int kCtasPerSm = R <= 64 ? 2 : 1;
+};
 constexpr int kSweepThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr int kATileBytes = kMTile * kKBlock * 2;  // 16 KB
 
@@ -116,12 +123,13 @@ struct SweepSmem {
 };
 
 template <int R>
-__global__ void __launch_bounds__(kSweepThreads, 1)
+__global__ void __launch_bounds__(kSweepThreads, SweepCfg<R>::kCtasPerSm)
     mrhs_sweep_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       MrhsSweepParams p) {
   constexpr int kBTileBytes = R * kKBlock * 2;
   constexpr int kStageBytes = kATileBytes + kBTileBytes;
   constexpr uint32_t kTmemCols = R < 32 ? 32 : R;
+  constexpr int kStages = SweepCfg<R>::kStages;
   extern __shared__ __align__(1024) unsigned char msmem[];
   __shared__ SweepSmem S;
   unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(msmem) + 1023) & ~uintptr_t(1023));
@@ -130,7 +138,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   const int kb_count = static_cast<int>((p.n + kKBlock - 1) / kKBlock);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kMStages; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
     }
@@ -147,8 +155,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       for (int kb = 0; kb < kb_count; ++kb) {
-        const int s = kb % kMStages;
-        const uint32_t par = ((kb / kMStages) & 1) ^ 1;
+        const int s = kb % kStages;
+        const uint32_t par = ((kb / kStages) & 1) ^ 1;
         if (S.abort || !mbar_wait(&S.empty[s], par) || S.abort) {
           S.abort = 1;
           atomicCAS(p.status, 0, kStatusTimeout);
@@ -164,8 +172,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = mma_idesc(kMTile, R);
       for (int kb = 0; kb < kb_count; ++kb) {
-        const int s = kb % kMStages;
-        if (S.abort || !mbar_wait(&S.full[s], (kb / kMStages) & 1)) {
+        const int s = kb % kStages;
+        if (S.abort || !mbar_wait(&S.full[s], (kb / kStages) & 1)) {
           S.abort = 1;
           atomicCAS(p.status, 0, kStatusTimeout);
           break;
@@ -460,7 +468,7 @@ bool make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, in
 
 template <int R>
 cudaError_t launch_sweep_r(const CUtensorMap& ta, const CUtensorMap& tb, const MrhsSweepParams& p, cudaStream_t s) {
-  constexpr int smem = kMStages * (kATileBytes + R * kKBlock * 2) + 1024;
+  constexpr int smem = SweepCfg<R>::kStages * (kATileBytes + R * kKBlock * 2) + 1024;
   cudaError_t e = cudaFuncSetAttribute(mrhs_sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = static_cast<unsigned>((p.n + kMTile - 1) / kMTile);
