@@ -57,6 +57,8 @@ def _load():
             lib.oracle_csr_jacobi.argtypes = [_c_i64, vp, vp, vp, vp, vp, _c_i64, ctypes.c_double, ctypes.c_int,
                                               vp, ctypes.POINTER(_c_i64), _c_dp, vp]
             lib.oracle_csr_jacobi.restype = ctypes.c_int
+            lib.oracle_csr_residual.argtypes = [_c_i64, vp, vp, vp, vp, vp, vp, _c_dp]
+            lib.oracle_csr_residual.restype = ctypes.c_int
             lib.oracle_ge.argtypes = [_c_i64, _c_i64, vp, vp, vp]
             lib.oracle_ge.restype = ctypes.c_int
             lib.oracle_residual.argtypes = [_c_i64, _c_i64, vp, vp, vp, vp, _c_dp]
@@ -175,6 +177,23 @@ def csr_jacobi(row_ptr, col_idx, values, B, X0=None, max_iter: int = 1000, tol: 
                                tol, norm, _ptr(Xo), ctypes.byref(it), ctypes.byref(de), None if tr is None else _ptr(tr))
     k = int(it.value)
     return JacobiResult(st, Xo[:, None].copy(), k, float(de.value), None if tr is None else tr[:k, :, None].copy())
+
+
+def csr_residual(row_ptr, col_idx, values, B, X) -> tuple[np.ndarray, float]:
+    """r = b - A x for a CSR matrix (FP64, stored entries in column order) and ||r||_inf / ||b||_inf."""
+    lib = _load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(values, dtype=np.float64)
+    n = rp.size - 1
+    b = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(-1))
+    x = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1))
+    if b.size != n or x.size != n:
+        raise ValueError("vector length mismatch")
+    R = np.zeros(n)
+    rel = ctypes.c_double(0.0)
+    lib.oracle_csr_residual(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(b), _ptr(x), _ptr(R), ctypes.byref(rel))
+    return R, float(rel.value)
 
 
 def ge(A, B) -> tuple[int, np.ndarray]:

@@ -420,6 +420,27 @@ int oracle_residual(int64_t n, int64_t nrhs, const double* A, const double* B, c
 }
 
 /*
+ * Residual r = b - A x of a CSR matrix in FP64 (the stored entries of each row in their ascending column
+ * order, the diagonal included), and the relative residual ||r||_inf / ||b||_inf.  r may be NULL.  The
+ * structure is trusted (oracle_csr_jacobi checks it).
+ */
+int oracle_csr_residual(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                        const double* B, const double* X, double* R, double* rel_out) {
+  if (n < 1 || !row_ptr || !B || !X || !rel_out) return OR_INVALID_ARG;
+  double rmax = 0.0, bmax = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s += val[e] * X[col_idx[e]];
+    double r = B[i] - s;
+    if (R) R[i] = r;
+    if (!(fabs(r) <= rmax)) rmax = fabs(r);
+    if (fabs(B[i]) > bmax) bmax = fabs(B[i]);
+  }
+  *rel_out = rmax / bmax;
+  return OR_OK;
+}
+
+/*
  * Fixed-point form of Section 2: A = D - L - U, X = T X + C with T = D^-1 (L + U), C = D^-1 B.
  * With L and U the negated strict triangles of A this is t_ij = -alpha_ij / alpha_ii (j != i),
  * t_ii = 0, c_i = beta_i / alpha_ii, each a single correctly rounded IEEE division.

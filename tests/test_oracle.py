@@ -542,3 +542,17 @@ def test_csr_jacobi_errors():
     assert oracle.csr_jacobi(rp, ci, z, b).status == oracle.ZERO_DIAGONAL
     z[3] = np.inf
     assert oracle.csr_jacobi(rp, ci, z, b).status == oracle.NONFINITE
+
+
+def test_csr_residual_equals_the_dense_residual_bit_for_bit():
+    """The CSR residual sums the stored entries in column order; the dense one adds exact zeros besides,
+    which leaves every FP64 partial sum unchanged: r and the relative residual agree bit for bit."""
+    rp, ci, v, B, Xs = synth.random_sparse_system(300, 1.1, seed=26, max_len=50)
+    A = synth.csr_to_dense(300, rp, ci, v)
+    X = Xs + 1e-3 * np.cos(np.arange(300.0))[:, None]
+    Rd, reld = oracle.residual(A, B, X)
+    Rs, rels = oracle.csr_residual(rp, ci, v, B, X)
+    np.testing.assert_array_equal(Rs, Rd[:, 0])
+    assert rels == reld
+    _, rel0 = oracle.csr_residual(rp, ci, v, B, Xs)
+    assert rel0 <= 1e-15  # the planted solution
