@@ -246,7 +246,7 @@ int oracle_block_sor(int64_t n, int64_t nrhs, const double* A, const double* B, 
  *   x_i^(k) = ( beta_i - sum_{stored j != i} alpha_ij x_j^(k-1) ) / alpha_ii.
  * Row i holds col_idx[row_ptr[i] .. row_ptr[i+1]) (strictly ascending, so the sum runs in ascending j as
  * in oracle_jacobi) and the matching values; its diagonal must be among them.  One right-hand side;
- * stopping norm 0 (max) or 1 (Euclidean).  Validation, in this order: the CSR structure (row_ptr starts
+ * stopping norm 0 (max), 1 (Euclidean) or 2 (relative residual of the previous iterate, as oracle_jacobi).  Validation, in this order: the CSR structure (row_ptr starts
  * at 0 and never decreases, columns in range and strictly ascending) -> -1; then, row by row, a missing or
  * zero diagonal -> -2, a non-finite one -> -3.
  */
@@ -254,7 +254,7 @@ int oracle_csr_jacobi(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                       const double* B, const double* X0, int64_t max_iter, double tol, int norm, double* X_out,
                       int64_t* iters_out, double* delta_out, double* trace) {
   if (n < 1 || !row_ptr || !B || !X_out || !iters_out || !delta_out) return OR_INVALID_ARG;
-  if (max_iter < 1 || !(tol > 0.0) || (norm != OR_NORM_INF && norm != OR_NORM_2)) return OR_INVALID_ARG;
+  if (max_iter < 1 || !(tol > 0.0) || norm < OR_NORM_INF || norm > OR_NORM_RESID) return OR_INVALID_ARG;
   if (row_ptr[0] != 0) return OR_INVALID_ARG;
   for (int64_t i = 0; i < n; ++i) {
     if (row_ptr[i + 1] < row_ptr[i]) return OR_INVALID_ARG;
@@ -308,7 +308,17 @@ int oracle_csr_jacobi(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
       X[i] = (B[i] - s) / diag[i];
     }
     if (trace) memcpy(trace + (size_t)(k - 1) * (size_t)n, X, (size_t)n * sizeof(double));
-    delta = or_norm_of_change(n, 1, NULL, B, X, Xt, norm);
+    if (norm == OR_NORM_RESID) { /* max_i |a_ii (x_i^(k) - x_i^(k-1))| / max_i |b_i|, as or_norm_of_change */
+      double acc = 0.0, bmax = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        double a = fabs(diag[i] * (X[i] - Xt[i]));
+        if (!(a <= acc)) acc = a;
+        if (fabs(B[i]) > bmax) bmax = fabs(B[i]);
+      }
+      delta = acc / bmax;
+    } else {
+      delta = or_norm_of_change(n, 1, NULL, B, X, Xt, norm);
+    }
     if (!isfinite(delta)) {
       status = OR_NONFINITE;
       memcpy(X_out, X, (size_t)n * sizeof(double));

@@ -450,7 +450,7 @@ def test_block_sor_errors():
 
 # ---- sparse (CSR) Jacobi ------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("norm", [oracle.NORM_INF, oracle.NORM_2])
+@pytest.mark.parametrize("norm", [oracle.NORM_INF, oracle.NORM_2, oracle.NORM_RESID])
 @pytest.mark.parametrize("kind", ["irregular", "stencil2d"])
 def test_csr_jacobi_equals_the_dense_oracle_bit_for_bit(kind, norm):
     """On the dense form of the same matrix the dense oracle adds the zero entries too; adding exact zeros
@@ -463,8 +463,9 @@ def test_csr_jacobi_equals_the_dense_oracle_bit_for_bit(kind, norm):
     n = rp.size - 1
     assert kind != "irregular" or np.diff(rp).min() == 1  # some rows hold only the diagonal
     A = synth.csr_to_dense(n, rp, ci, v)
-    d = oracle.jacobi(A, B, max_iter=400, tol=1e-13, norm=norm, trace=True)
-    s = oracle.csr_jacobi(rp, ci, v, B, max_iter=400, tol=1e-13, norm=norm, trace=True)
+    tol = 1e-11 if norm == oracle.NORM_RESID else 1e-13
+    d = oracle.jacobi(A, B, max_iter=400, tol=tol, norm=norm, trace=True)
+    s = oracle.csr_jacobi(rp, ci, v, B, max_iter=400, tol=tol, norm=norm, trace=True)
     assert (s.status, s.iters, s.delta) == (d.status, d.iters, d.delta)
     np.testing.assert_array_equal(s.trace, d.trace)
     np.testing.assert_array_equal(s.X, d.X)
