@@ -407,7 +407,31 @@ def run_sparse(args, jac, torch, dev):
     gbs = alg_bytes / (sweep_us * 1e-6) / 1e9
     ms_solve, st = timed(5000, 1e-12, 3)
     err = float((out - torch.from_numpy(Xs[:, 0]).to(dev)).abs().max().item())
+    s.close()
+    # the same stopping quantity as the refined solves: ||b - A x|| / ||b|| < 1e-10 (of the previous iterate)
+    s = jac.CsrSolver(t_rp, t_ci, t_v, t_b, norm="resid")
+    ms_resid, st_resid = timed(5000, 1e-10, 3)
     import oracle
+    refined = {}
+    for prec in ("bf16_ir", "fp32_ir"):  # the same system, mixed precision, to ||b - A x|| / ||b|| <= 1e-10
+        r = jac.CsrSolver(t_rp, t_ci, t_v, t_b, precision=prec)
+        for _ in range(2):
+            r.solve_async(None, 1, 1e-10, out)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for _ in range(3):
+            r.solve_async(None, 1, 1e-10, out)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        rst = r.last_stats()
+        ms_r = ev[0].elapsed_time(ev[1]) / 3
+        inner = [b - a for (a, b), k in zip(r.trace(), r.kinds()) if k == 3][1:]
+        refined[prec] = {"ms": round(ms_r, 3), "solves_per_s": round(1e3 / ms_r, 3), "status": int(rst.status),
+                         "inner_sweeps": int(rst.sweeps), "outer_steps": int(rst.outer_steps),
+                         "rel_residual_checked": oracle.csr_residual(rp, ci, v, B, out.cpu().numpy())[1],
+                         "median_inner_sweep_us": round(sorted(inner)[len(inner) // 2] / 1e3, 2) if inner else None,
+                         "vs_fp64_same_target": round(ms_resid / ms_r, 2)}
+        r.close()
     import time as _t
     k_cpu = 3
     t0 = _t.perf_counter()
@@ -425,6 +449,10 @@ def run_sparse(args, jac, torch, dev):
                        "peak_source": f"{kind} (MEASURED_PEAKS.json hbm_gbs)"},
             "solve": {"tol": 1e-12, "status": int(st.status), "sweeps": int(st.sweeps), "ms": round(ms_solve, 3),
                       "solves_per_s": round(1e3 / ms_solve, 3), "err_vs_xstar": err},
+            "solve_resid": {"tol": 1e-10, "norm": "relative residual", "status": int(st_resid.status),
+                            "sweeps": int(st_resid.sweeps), "ms": round(ms_resid, 3),
+                            "solves_per_s": round(1e3 / ms_resid, 3)},
+            "refined": refined,
             "cpu_oracle": {"ms_per_sweep": round(cpu_ms_sweep, 1), "cores": 1,
                            "sample": f"{k_cpu} sweeps of the full system, one thread"},
             "gpu_vs_cpu_sweep_ratio": round(cpu_ms_sweep * 1e3 / sweep_us, 1)}

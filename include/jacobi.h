@@ -411,10 +411,24 @@ typedef struct jacobi_csr_desc {
   const int32_t* col_idx;  /* nnz columns, strictly ascending within each row; each row stores its diagonal */
   const double* values;    /* nnz values */
   const double* B;         /* n values: the right-hand side */
-  int32_t norm;            /* JACOBI_NORM_INF or JACOBI_NORM_2 */
+  int32_t norm;            /* JACOBI_FP64: JACOBI_NORM_INF, JACOBI_NORM_2 or JACOBI_NORM_RESID (as jacobi_desc);
+                            * mixed precision: JACOBI_NORM_INF (the relative residual is the test) */
   int32_t flags;           /* JACOBI_FLAG_SHORT_WAITS, JACOBI_FLAG_TEST_SKIP_ARRIVAL */
   void* stream;            /* cudaStream_t of every call on the handle (NULL: the legacy default stream) */
+  int32_t precision;       /* JACOBI_FP64 (0: the plain iteration), JACOBI_FP32_IR or JACOBI_BF16_IR (below) */
+  int32_t max_outer;       /* IR: outer steps after the first residual (0: 60) */
+  int32_t max_inner;       /* IR: inner sweeps per outer step (0: 1000) */
+  int32_t reserved;        /* 0 */
+  double inner_rtol;       /* IR: inner stop at max|delta' - delta| <= inner_rtol max|delta'| (0: 2^-20 for FP32,
+                            * 2^-8 for BF16) */
 } jacobi_csr_desc;
+
+/* Mixed precision (precision = JACOBI_FP32_IR or JACOBI_BF16_IR): the library also keeps T in FP32 or
+ * BF16.  One persistent kernel alternates an FP64 residual, r' = C + T x - x = D^-1 (b - A x), with inner
+ * Jacobi sweeps on the correction, delta <- r' + T_lo delta (FP32 accumulation), until
+ * ||b - A x||_inf / ||b||_inf <= tol (not strict); x += delta in FP64.  The solve reports the relative
+ * residual as final_delta and rel_residual, counts inner sweeps in `sweeps` and residual evaluations in
+ * `outer_steps`.  JACOBI_FP8_IR is JACOBI_ERR_UNSUPPORTED here. */
 
 /* Validate and copy the matrix (host or device pointers; setup blocks until the copy is built).
  * Errors: JACOBI_ERR_INVALID_ARG for a null pointer, n < 1, nnz < 1, a bad norm, or a malformed structure
@@ -440,9 +454,10 @@ JACOBI_API int jacobi_csr_last_stats(jacobi_csr* h, jacobi_stats* stats);
  * 32 rows, and the grid of the sweep kernel.  Any output may be NULL. */
 JACOBI_API int jacobi_csr_info(jacobi_csr* h, int64_t* stored_slots, int64_t* slices, int32_t* grid);
 
-/* End time of each sweep of the last solve, in nanoseconds since the solve started (as
- * jacobi_last_trace, every sweep of kind JACOBI_PHASE_SWEEP64; at most 512 are recorded). */
-JACOBI_API int jacobi_csr_last_trace(jacobi_csr* h, int64_t* t_end_ns, int32_t cap, int32_t* count);
+/* End time of each phase of the last solve, in nanoseconds since the solve started, and its kind, as
+ * jacobi_last_trace: JACOBI_PHASE_SWEEP64 sweeps, or (mixed precision) JACOBI_PHASE_RESID64 residuals and
+ * JACOBI_PHASE_INNER sweeps; at most 512 are recorded, *count is the number of phases run. */
+JACOBI_API int jacobi_csr_last_trace(jacobi_csr* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap, int32_t* count);
 
 JACOBI_API void jacobi_csr_destroy(jacobi_csr* h);
 

@@ -85,7 +85,9 @@ _lib = None
 class JacobiCsrDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
                 ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p), ("B", ctypes.c_void_p),
-                ("norm", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("norm", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("precision", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("inner_rtol", ctypes.c_double)]
 
 
 class JacobiError(RuntimeError):
@@ -148,7 +150,7 @@ def load() -> ctypes.CDLL:
         lib.jacobi_csr_solve.argtypes = [H, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats)]
         lib.jacobi_csr_last_stats.argtypes = [H, ctypes.POINTER(JacobiStats)]
         lib.jacobi_csr_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)]
-        lib.jacobi_csr_last_trace.argtypes = [H, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_csr_last_trace.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
         lib.jacobi_csr_destroy.argtypes = [H]
         lib.jacobi_csr_destroy.restype = None
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
@@ -335,11 +337,13 @@ class DeviceSolver:
 
 class CsrSolver:
     """``jacobi_csr_*``: Jacobi for a sparse A in CSR (int64 row offsets, int32 columns strictly ascending in
-    each row with the diagonal stored, float64 values) and one right-hand side.  The arrays may be torch
+    each row with the diagonal stored, float64 values) and one right-hand side; precision "fp64" (the plain
+    iteration) or "fp32_ir" / "bf16_ir" (mixed-precision refinement to a relative residual).  The arrays may be torch
     tensors on the GPU or the host, or numpy arrays; setup copies them into the library's sliced-ELL
     layout, so they may be dropped afterwards."""
 
-    def __init__(self, row_ptr, col_idx, values, B, norm: str = "inf", flags: int = 0, stream=None, device=None):
+    def __init__(self, row_ptr, col_idx, values, B, norm: str = "inf", flags: int = 0, stream=None, device=None,
+                 precision: str = "fp64", inner_rtol: float = 0.0, max_inner: int = 0, max_outer: int = 0):
         import torch
         lib = load()
 
@@ -364,6 +368,9 @@ class CsrSolver:
         d.n, d.nnz = self.n, ci.numel()
         d.row_ptr, d.col_idx, d.values, d.B = rp.data_ptr(), ci.data_ptr(), va.data_ptr(), b.data_ptr()
         d.norm, d.flags, d.stream = NORMS[norm], flags, self.stream.cuda_stream
+        d.precision = PRECISIONS[precision]
+        d.max_outer, d.max_inner, d.inner_rtol = max_outer, max_inner, inner_rtol
+        self.precision = precision
         self._h = ctypes.c_void_p()
         with torch.cuda.device(device):
             _check(lib.jacobi_csr_setup(ctypes.byref(d), ctypes.byref(self._h)), "jacobi_csr_setup", False)
@@ -400,13 +407,23 @@ class CsrSolver:
         return {"stored_slots": stored.value, "slices": slices.value, "grid": grid.value}
 
     def trace(self):
-        """Device-side end time of every sweep of the last solve: list of (start_ns, end_ns)."""
+        """Device-side end time of every phase of the last solve: list of (start_ns, end_ns)."""
+        t, _ = self._trace()
+        return [(int(t[i - 1]) if i else 0, int(t[i])) for i in range(len(t))]
+
+    def kinds(self):
+        """Kind (JACOBI_PHASE_*) of every phase of the last solve, in the order of trace()."""
+        return [int(k) for k in self._trace()[1]]
+
+    def _trace(self):
         cap = 512
         t = np.zeros(cap, dtype=np.int64)
+        k = np.zeros(cap, dtype=np.int32)
         cnt = ctypes.c_int32(0)
-        _check(load().jacobi_csr_last_trace(self._h, t.ctypes.data, cap, ctypes.byref(cnt)), "jacobi_csr_last_trace")
+        _check(load().jacobi_csr_last_trace(self._h, t.ctypes.data, k.ctypes.data, cap, ctypes.byref(cnt)),
+               "jacobi_csr_last_trace")
         m = min(cap, cnt.value)
-        return [(int(t[i - 1]) if i else 0, int(t[i])) for i in range(m)]
+        return t[:m], k[:m]
 
     def close(self):
         if self._h:

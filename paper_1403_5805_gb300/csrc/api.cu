@@ -617,6 +617,16 @@ struct jacobi_csr {
   double* xout = nullptr;
   double* part = nullptr;
   Ctl* ctl = nullptr;
+  // mixed precision
+  int precision = JACOBI_FP64;
+  int max_outer = 60, max_inner = 1000;
+  float inner_rtol = 0.0f;
+  double bnorm = 0.0;
+  void* tlo = nullptr;
+  double* d = nullptr;
+  float* rf = nullptr;
+  float* da = nullptr;
+  float* db = nullptr;
 };
 
 namespace {
@@ -646,8 +656,14 @@ struct Staged {
 int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   if (!d || !out || d->n < 1 || d->nnz < 1 || !d->row_ptr || !d->col_idx || !d->values || !d->B)
     return JACOBI_ERR_INVALID_ARG;
-  if (d->norm != JACOBI_NORM_INF && d->norm != JACOBI_NORM_2) return JACOBI_ERR_INVALID_ARG;
+  if (d->norm != JACOBI_NORM_INF && d->norm != JACOBI_NORM_2 && d->norm != JACOBI_NORM_RESID)
+    return JACOBI_ERR_INVALID_ARG;
   if (d->n > (int64_t(1) << 31) - 64) return JACOBI_ERR_INVALID_ARG;  // int32 column indices
+  if (d->precision < JACOBI_FP64 || d->precision > JACOBI_FP8_IR || d->max_outer < 0 || d->max_inner < 0 ||
+      !(d->inner_rtol >= 0.0) || d->inner_rtol >= 1.0)
+    return JACOBI_ERR_INVALID_ARG;
+  if (d->precision == JACOBI_FP8_IR) return JACOBI_ERR_UNSUPPORTED;
+  if (d->precision != JACOBI_FP64 && d->norm != JACOBI_NORM_INF) return JACOBI_ERR_INVALID_ARG;
   *out = nullptr;
   const int64_t n = d->n, nnz = d->nnz;
   cudaStream_t s = static_cast<cudaStream_t>(d->stream);
@@ -687,10 +703,19 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   h->stream = s;
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
   h->test_skip_arrival = (d->flags & JACOBI_FLAG_TEST_SKIP_ARRIVAL) ? 1 : 0;
+  h->precision = d->precision;
+  const bool ir = d->precision != JACOBI_FP64;
+  const bool keep_d = ir || d->norm == JACOBI_NORM_RESID;  // a_ii for the residual norm
+  if (d->max_outer > 0) h->max_outer = d->max_outer;
+  if (d->max_inner > 0) h->max_inner = d->max_inner;
+  h->inner_rtol = d->inner_rtol > 0.0 ? static_cast<float>(d->inner_rtol)
+                                      : (d->precision == JACOBI_BF16_IR ? 0x1p-8f : 0x1p-20f);
 
   const size_t vec = align_up(npad * sizeof(double));
+  const size_t vecf = align_up(npad * sizeof(float));
   const size_t head = align_up((nslices + 1) * sizeof(int64_t)) + 4 * vec + align_up(2 * kMaxGrid * sizeof(double)) +
-                      align_up(sizeof(Ctl));
+                      align_up(sizeof(Ctl)) + align_up(sizeof(unsigned long long)) + (keep_d ? vec : 0) +
+                      (ir ? 3 * vecf : 0);
   CK(cudaMemsetAsync(lens, 0, npad * sizeof(int32_t), s));
   CK(cudaMemsetAsync(key, 0xFF, sizeof(unsigned long long), s));
   CK(launch_csr_check(n, nnz, rp, ci, va, dd, lens, key, s));
@@ -711,7 +736,8 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   h->stored = stored;
   const size_t vbytes = align_up(std::max<int64_t>(stored, 1) * sizeof(double));
   const size_t cbytes = align_up(std::max<int64_t>(stored, 1) * sizeof(int32_t));
-  cudaError_t e = cudaMalloc(&h->mem, head + vbytes + cbytes);
+  const size_t tbytes = ir ? align_up(std::max<int64_t>(stored, 1) * (d->precision == JACOBI_BF16_IR ? 2 : 4)) : 0;
+  cudaError_t e = cudaMalloc(&h->mem, head + vbytes + cbytes + tbytes);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(sparse)");
   char* p = static_cast<char*>(h->mem);
   auto take = [&p](size_t bytes) {
@@ -726,8 +752,16 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   h->xout = reinterpret_cast<double*>(take(vec));
   h->part = reinterpret_cast<double*>(take(align_up(2 * kMaxGrid * sizeof(double))));
   h->ctl = reinterpret_cast<Ctl*>(take(align_up(sizeof(Ctl))));
+  unsigned long long* bmax = reinterpret_cast<unsigned long long*>(take(align_up(sizeof(unsigned long long))));
+  if (keep_d) h->d = reinterpret_cast<double*>(take(vec));
+  if (ir) {
+    h->rf = reinterpret_cast<float*>(take(vecf));
+    h->da = reinterpret_cast<float*>(take(vecf));
+    h->db = reinterpret_cast<float*>(take(vecf));
+  }
   h->sval = reinterpret_cast<double*>(take(vbytes));
   h->scol = reinterpret_cast<int32_t*>(take(cbytes));
+  if (ir) h->tlo = take(tbytes);
   jacobi_csr* raw = h.get();
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(raw->mem);
@@ -742,10 +776,19 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   CSR_CK(cudaMemsetAsync(h->mem, 0, head, s));
   CSR_CK(cudaMemcpyAsync(h->soff, hoff.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CSR_CK(cudaMemcpyAsync(h->c, d->B, n * sizeof(double), cudaMemcpyDefault, s));
-  CSR_CK(launch_csr_fill(n, rp, ci, va, dd, h->soff, h->sval, h->scol, h->c, s));
+  CSR_CK(launch_csr_fill(n, rp, ci, va, dd, h->soff, h->sval, h->scol, h->c, bmax, s));
+  if (keep_d) CSR_CK(cudaMemcpyAsync(h->d, dd, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (ir) {
+    CSR_CK(launch_csr_narrow(d->precision == JACOBI_BF16_IR ? CsrInner::BF16 : CsrInner::F32, h->sval, stored, h->tlo,
+                             s));
+  }
+  unsigned long long hb = 0;
+  CSR_CK(cudaMemcpyAsync(&hb, bmax, sizeof(hb), cudaMemcpyDeviceToHost, s));
   CSR_CK(cudaStreamSynchronize(s));
+  std::memcpy(&h->bnorm, &hb, sizeof(double));
 #undef CSR_CK
-  const int cap = csr_max_grid();
+  const int cap = ir ? csr_ir_max_grid(d->precision == JACOBI_BF16_IR ? CsrInner::BF16 : CsrInner::F32)
+                     : csr_max_grid();
   if (cap <= 0) return fail(cudaGetLastError(), "occupancy query");
   const int64_t want = (nslices + csr_warps_per_cta() - 1) / csr_warps_per_cta();
   h->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(cap, want)));
@@ -1074,9 +1117,25 @@ int jacobi_csr_solve_async(jacobi_csr* h, const double* X0, int64_t max_iter, do
   p.max_iter = max_iter;
   p.tol = tol;
   p.norm = h->norm;
+  p.d = h->d;
+  p.bnorm = h->bnorm;
   p.test_skip_arrival = h->test_skip_arrival;
   p.wait_ns = h->wait_ns;
-  cudaError_t e = launch_csr_solve(p, h->grid, s);
+  cudaError_t e;
+  if (h->precision == JACOBI_FP64) {
+    e = launch_csr_solve(p, h->grid, s);
+  } else {
+    CsrIrParams q{};
+    q.base = p;
+    q.tlo = h->tlo;
+    q.rf = h->rf;
+    q.da = h->da;
+    q.db = h->db;
+    q.inner_rtol = h->inner_rtol;
+    q.max_inner = h->max_inner;
+    q.max_outer = h->max_outer;
+    e = launch_csr_ir_solve(h->precision == JACOBI_BF16_IR ? CsrInner::BF16 : CsrInner::F32, q, h->grid, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch (sparse)");
   if (p.x_out != X_out) CK(cudaMemcpyAsync(X_out, h->xout, h->n * sizeof(double), cudaMemcpyDefault, s));
   return JACOBI_OK;
@@ -1108,8 +1167,8 @@ int jacobi_csr_info(jacobi_csr* h, int64_t* stored_slots, int64_t* slices, int32
   return JACOBI_OK;
 }
 
-int jacobi_csr_last_trace(jacobi_csr* h, int64_t* t_end_ns, int32_t cap, int32_t* count) {
-  if (!h || !count || cap < 0 || (cap > 0 && !t_end_ns)) return JACOBI_ERR_INVALID_ARG;
+int jacobi_csr_last_trace(jacobi_csr* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && (!t_end_ns || !kinds))) return JACOBI_ERR_INVALID_ARG;
   Ctl* host = static_cast<Ctl*>(std::malloc(sizeof(Ctl)));
   if (!host) return JACOBI_ERR_OUT_OF_MEMORY;
   cudaError_t e = cudaMemcpyAsync(host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
@@ -1120,7 +1179,10 @@ int jacobi_csr_last_trace(jacobi_csr* h, int64_t* t_end_ns, int32_t cap, int32_t
   }
   *count = host->nphase;
   const int m = host->nphase < cap ? host->nphase : cap;
-  for (int i = 0; i < m; ++i) t_end_ns[i] = static_cast<int64_t>(host->t_end[i] - host->t_start);
+  for (int i = 0; i < m; ++i) {
+    t_end_ns[i] = static_cast<int64_t>(host->t_end[i] - host->t_start);
+    kinds[i] = host->kind[i];
+  }
   std::free(host);
   return JACOBI_OK;
 }

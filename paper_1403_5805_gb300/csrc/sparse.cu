@@ -17,6 +17,10 @@
 // keeps the change norm; the norm is combined over the grid (an order-free max of IEEE bits, or fixed-order
 // per-CTA partial sums for the Euclidean norm) at the one grid barrier of the sweep, and every CTA takes
 // the same stop decision.  Every wait is bounded by %globaltimer and reports JACOBI_ERR_TIMEOUT.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "device_util.cuh"
 #include "sparse.cuh"
 
@@ -77,7 +81,7 @@ __global__ void csr_widths_kernel(int64_t n, int64_t nslices, const int32_t* __r
 __global__ void csr_fill_kernel(int64_t n, int64_t nslices, const int64_t* __restrict__ rp,
                                 const int32_t* __restrict__ ci, const double* __restrict__ val,
                                 const double* __restrict__ d, const int64_t* __restrict__ soff, double* sval,
-                                int32_t* scol, double* c) {
+                                int32_t* scol, double* c, unsigned long long* bmax) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t s = i / kSliceRows;
   if (s >= nslices) return;
@@ -93,7 +97,9 @@ __global__ void csr_fill_kernel(int64_t n, int64_t nslices, const int64_t* __res
       scol[base + kSliceRows * t] = col;
       ++t;
     }
-    c[i] = c[i] / di;  // c_i = b_i / a_ii (c holds b on entry)
+    const double bi = c[i];
+    atomicMax(bmax, abs_bits(bi));
+    c[i] = bi / di;  // c_i = b_i / a_ii (c holds b on entry)
   }
   const int32_t self = static_cast<int32_t>(i < n ? i : n - 1);
   for (; t < w; ++t) {
@@ -106,6 +112,9 @@ __device__ __forceinline__ double bits_to_double(unsigned long long v) {
   return __longlong_as_double(static_cast<long long>(v));
 }
 
+// kResid: the change norm is max |a_ii (x^(k) - x^(k-1))| / ||b||_inf (JACOBI_NORM_RESID), a separate
+// instantiation so that the other norms' loop carries no extra load.
+template <bool kResid>
 __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(CsrParams p) {
   __shared__ unsigned long long s_mx[kCsrWarps];
   __shared__ double s_sq[kCsrWarps];
@@ -147,7 +156,7 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(C
       if (live) {
         const double diff = x - xo;
         xn[i] = x;
-        const unsigned long long bb = abs_bits(diff);
+        const unsigned long long bb = abs_bits(kResid ? __ldg(p.d + i) * diff : diff);
         mx = bb > mx ? bb : mx;
         if (p.norm == JACOBI_NORM_2) sq = fma(diff, diff, sq);
       }
@@ -191,6 +200,7 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(C
         dk = sqrt(warp_sum(acc));
       } else {
         dk = bits_to_double(__ldcg(&p.ctl->red[slot][0]));
+        if (kResid) dk = dk / p.bnorm;  // ||b - A x^(k-1)|| / ||b||, as the oracle
       }
       if (lane == 0) {
         if (blockIdx.x == 0 && phase < static_cast<uint32_t>(kTraceCap)) {
@@ -237,6 +247,216 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(C
   }
 }
 
+// ------------------------------------------------------------------ mixed-precision refinement
+
+template <class TV>
+__device__ __forceinline__ float to_f32(TV v);
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+template <class TV>
+__global__ void csr_narrow_kernel(const double* __restrict__ sval, int64_t slots, TV* tlo) {
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < slots;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float f = __double2float_rn(sval[e]);
+    if constexpr (sizeof(TV) == 4)
+      tlo[e] = f;
+    else
+      tlo[e] = __float2bfloat16_rn(f);
+  }
+}
+
+// Grid-wide maxima of two per-thread values (IEEE bits of non-negative numbers) through rotating slot
+// phase % 3 and one grid barrier; every thread returns with both maxima.  False on a timeout or another
+// CTA's error.  Phase `phase` is recorded in the device trace with `kind`.
+__device__ bool grid_max2(const CsrParams& p, uint32_t phase, int kind, unsigned long long& m0,
+                          unsigned long long& m1, unsigned long long* s0, unsigned long long* s1, int* s_ok) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  m0 = warp_max_u64(m0);
+  m1 = warp_max_u64(m1);
+  if (lane == 0) {
+    s0[warp] = m0;
+    s1[warp] = m1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b0 = 0, b1 = 0;
+    for (int q = 0; q < kCsrWarps; ++q) {
+      b0 = s0[q] > b0 ? s0[q] : b0;
+      b1 = s1[q] > b1 ? s1[q] : b1;
+    }
+    const int slot = static_cast<int>(phase % 3);
+    if (b0) atomicMax(&p.ctl->red[slot][0], b0);
+    if (b1) atomicMax(&p.ctl->red[slot][1], b1);
+    if (blockIdx.x == 0) {
+      p.ctl->red[(phase + 1) % 3][0] = 0ull;
+      p.ctl->red[(phase + 1) % 3][1] = 0ull;
+    }
+    bool ok;
+    if (p.test_skip_arrival && blockIdx.x == 0 && phase == 0) {
+      ok = false;
+      atomicMin(&p.ctl->status, kStatusTimeout);
+    } else {
+      ok = grid_arrive_and_wait(&p.ctl->arrive, &p.ctl->status, (phase + 1) * gridDim.x, p.wait_ns);
+      if (!ok) atomicMin(&p.ctl->status, kStatusTimeout);
+    }
+    if (blockIdx.x == 0 && phase < static_cast<uint32_t>(kTraceCap)) {
+      p.ctl->t_end[phase] = global_timer_ns();
+      p.ctl->kind[phase] = kind;
+      p.ctl->nphase = static_cast<int>(phase) + 1;
+    }
+    s0[0] = __ldcg(&p.ctl->red[slot][0]);
+    s1[0] = __ldcg(&p.ctl->red[slot][1]);
+    *s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  m0 = s0[0];
+  m1 = s1[0];
+  const bool ok = *s_ok != 0;
+  __syncthreads();  // s0 / s1 are written again by the next call
+  return ok;
+}
+
+// The refinement in one persistent launch.  Outer step: r' = c + T x' - x' with x' = x + delta (the last
+// inner correction, gathered as x_j + delta_j, so no separate update pass), written as the FP32 right-hand
+// side of the inner solve, with max |a_ii r'| / ||b||_inf as the stopping quantity (<= tol).  Inner sweeps:
+// delta^(1) = r', delta^(l+1) = r' + T_lo delta^(l) in FP32, until the change is at most inner_rtol times the
+// magnitude or max_inner sweeps.  Each phase ends with one grid barrier; every CTA takes the same decisions.
+template <class TV>
+__global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrIrParams q) {
+  const CsrParams& p = q.base;
+  __shared__ unsigned long long s0[kCsrWarps], s1[kCsrWarps];
+  __shared__ int s_ok;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = static_cast<int64_t>(blockIdx.x) * kCsrWarps + warp;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * kCsrWarps;
+  const TV* tlo = static_cast<const TV*>(q.tlo);
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->t_start = global_timer_ns();
+
+  uint32_t phase = 0;
+  int outer = 0;
+  int64_t inner_total = 0;
+  double rel = 0.0;
+  int status = kStatusNotConverged;
+  const float* dcur = nullptr;  // correction not yet added to x
+  const double* xc = p.xa;      // x
+  double* xn = p.xb;            // x + delta
+  for (;;) {
+    // ---- FP64 residual of x' = x + delta
+    unsigned long long mr = 0, unused = 0;
+    for (int64_t s = gw; s < p.nslices; s += nw) {
+      const int64_t o0 = __ldg(p.soff + s);
+      const int w = static_cast<int>((__ldg(p.soff + s + 1) - o0) / kSliceRows);
+      const int64_t i = s * kSliceRows + lane;
+      const bool live = i < p.n;
+      double xi = 0.0, acc = 0.0;
+      if (live) {
+        xi = __ldcg(xc + i) + (dcur ? static_cast<double>(__ldcg(dcur + i)) : 0.0);
+        acc = __ldcs(p.c + i);
+      }
+      const double* v = p.sval + o0 + lane;
+      const int32_t* cc = p.scol + o0 + lane;
+#pragma unroll 4
+      for (int t = 0; t < w; ++t) {
+        const int32_t j = __ldcs(cc + kSliceRows * t);
+        const double xj = __ldcg(xc + j) + (dcur ? static_cast<double>(__ldcg(dcur + j)) : 0.0);
+        acc = fma(__ldcs(v + kSliceRows * t), xj, acc);
+      }
+      if (live) {
+        const double r = acc - xi;
+        xn[i] = xi;
+        q.rf[i] = __double2float_rn(r);
+        const unsigned long long b = abs_bits(__ldg(p.d + i) * r);
+        mr = b > mr ? b : mr;
+      }
+    }
+    const bool ok = grid_max2(p, phase++, JACOBI_PHASE_RESID64, mr, unused, s0, s1, &s_ok);
+    rel = bits_to_double(mr) / p.bnorm;
+    if (!ok) {
+      status = kStatusTimeout;
+      break;
+    }
+    if (!isfinite(rel)) {
+      status = kStatusNonfinite;
+      break;
+    }
+    if (rel <= p.tol) {
+      status = kStatusOk;
+      break;
+    }
+    if (outer >= q.max_outer) break;  // NOT_CONVERGED with x'
+    ++outer;
+    xc = xn;
+    xn = xn == p.xa ? p.xb : p.xa;
+    // ---- inner sweeps on the correction, FP32
+    const float* dold = q.rf;
+    float* dnew = q.da;
+    bool timed_out = false;
+    for (int l = 1;; ++l) {
+      unsigned long long mc = 0, mg = 0;
+      for (int64_t s = gw; s < p.nslices; s += nw) {
+        const int64_t o0 = __ldg(p.soff + s);
+        const int w = static_cast<int>((__ldg(p.soff + s + 1) - o0) / kSliceRows);
+        const int64_t i = s * kSliceRows + lane;
+        const bool live = i < p.n;
+        float acc = live ? __ldcg(q.rf + i) : 0.0f;
+        const TV* v = tlo + o0 + lane;
+        const int32_t* cc = p.scol + o0 + lane;
+#pragma unroll 4
+        for (int t = 0; t < w; ++t)
+          acc = fmaf(to_f32<TV>(__ldcs(v + kSliceRows * t)), __ldcg(dold + __ldcs(cc + kSliceRows * t)), acc);
+        if (live) {
+          const float old = __ldcg(dold + i);
+          dnew[i] = acc;
+          const unsigned long long b1 = abs_bits(acc - old), b2 = abs_bits(acc);
+          mc = b1 > mc ? b1 : mc;
+          mg = b2 > mg ? b2 : mg;
+        }
+      }
+      const bool iok = grid_max2(p, phase++, JACOBI_PHASE_INNER, mc, mg, s0, s1, &s_ok);
+      ++inner_total;
+      if (!iok) {
+        timed_out = true;
+        break;
+      }
+      const double ch = bits_to_double(mc), mag = bits_to_double(mg);
+      if (!(ch > static_cast<double>(q.inner_rtol) * mag) || l >= q.max_inner) {  // NaN stops too
+        dcur = dnew;
+        break;
+      }
+      dold = dnew;
+      dnew = dnew == q.da ? q.db : q.da;
+    }
+    if (timed_out) {
+      status = kStatusTimeout;
+      break;
+    }
+  }
+  // x' of the last residual: converged, capped or non-finite alike
+  if (status != kStatusTimeout)
+    for (int64_t s = gw; s < p.nslices; s += nw) {
+      const int64_t i = s * kSliceRows + lane;
+      if (i < p.n) p.x_out[i] = xn[i];
+    }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    jacobi_stats st;
+    st.sweeps = inner_total;
+    st.outer_steps = outer + 1;
+    st.final_delta = rel;
+    st.rel_residual = rel;
+    st.status = status;
+    st.converged = status == kStatusOk;
+    p.ctl->result = st;
+    if (p.stats_out) *p.stats_out = st;
+  }
+}
+
 int blocks_for(int64_t items, int threads) { return static_cast<int>((items + threads - 1) / threads); }
 
 }  // namespace
@@ -255,30 +475,64 @@ cudaError_t launch_csr_widths(int64_t n, const int32_t* lens, int32_t* width, cu
 
 cudaError_t launch_csr_fill(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
                             const double* d, const int64_t* soff, double* sval, int32_t* scol, double* c,
-                            cudaStream_t s) {
+                            unsigned long long* bmax, cudaStream_t s) {
   const int64_t nslices = (n + kSliceRows - 1) / kSliceRows;
   csr_fill_kernel<<<blocks_for(nslices * kSliceRows, 256), 256, 0, s>>>(n, nslices, row_ptr, col_idx, val, d, soff,
-                                                                         sval, scol, c);
+                                                                         sval, scol, c, bmax);
   return cudaGetLastError();
 }
 
 cudaError_t launch_csr_solve(const CsrParams& p, int grid, cudaStream_t s) {
   CsrParams copy = p;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(csr_solve_kernel), dim3(grid), dim3(kCsrThreads),
-                                     args, 0, s);
+  const void* fn = p.norm == JACOBI_NORM_RESID ? reinterpret_cast<const void*>(csr_solve_kernel<true>)
+                                               : reinterpret_cast<const void*>(csr_solve_kernel<false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCsrThreads), args, 0, s);
 }
 
 int csr_max_grid() {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_solve_kernel, kCsrThreads, 0) != cudaSuccess)
+  int per_sm_resid = 0;  // the two instantiations may differ in registers: the smaller grid serves both
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_solve_kernel<false>, kCsrThreads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_resid, csr_solve_kernel<true>, kCsrThreads, 0) !=
+          cudaSuccess)
     return 0;
+  per_sm = per_sm < per_sm_resid ? per_sm : per_sm_resid;
   const int g = per_sm * sms;
   return g < kMaxGrid ? g : kMaxGrid;
 }
 
 int csr_warps_per_cta() { return kCsrWarps; }
+
+cudaError_t launch_csr_narrow(CsrInner kind, const double* sval, int64_t slots, void* tlo, cudaStream_t s) {
+  const int blocks = static_cast<int>(std::min<int64_t>((slots + 255) / 256, 65536));
+  if (slots <= 0) return cudaSuccess;
+  if (kind == CsrInner::F32)
+    csr_narrow_kernel<float><<<blocks, 256, 0, s>>>(sval, slots, static_cast<float*>(tlo));
+  else
+    csr_narrow_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(sval, slots, static_cast<__nv_bfloat16*>(tlo));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_ir_solve(CsrInner kind, const CsrIrParams& p, int grid, cudaStream_t s) {
+  CsrIrParams copy = p;
+  void* args[] = {&copy};
+  const void* fn = kind == CsrInner::F32 ? reinterpret_cast<const void*>(csr_ir_kernel<float>)
+                                         : reinterpret_cast<const void*>(csr_ir_kernel<__nv_bfloat16>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCsrThreads), args, 0, s);
+}
+
+int csr_ir_max_grid(CsrInner kind) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const void* fn = kind == CsrInner::F32 ? reinterpret_cast<const void*>(csr_ir_kernel<float>)
+                                         : reinterpret_cast<const void*>(csr_ir_kernel<__nv_bfloat16>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCsrThreads, 0) != cudaSuccess) return 0;
+  const int g = per_sm * sms;
+  return g < kMaxGrid ? g : kMaxGrid;
+}
 
 }  // namespace jac

@@ -21,12 +21,12 @@ cudaError_t launch_csr_check(int64_t n, int64_t nnz, const int64_t* row_ptr, con
 // Setup pass 2: width[s] = max off-diagonal count over the rows of slice s (one warp per slice).
 cudaError_t launch_csr_widths(int64_t n, const int32_t* lens, int32_t* width, cudaStream_t s);
 // Setup pass 3: T = D^-1 (L + U) as a sliced-ELL copy, t_ij = -a_ij / a_ii, and C = D^-1 B in place
-// (c holds b on entry).  Entry t of row i = 32 s + l sits at soff[s] + 32 t + l (column-major inside the
+// (c holds b on entry); *bmax (zero beforehand) receives the IEEE bits of ||b||_inf.  Entry t of row i = 32 s + l sits at soff[s] + 32 t + l (column-major inside the
 // slice, so a warp's loads of one entry index are one 256-byte run); slots past the row's length hold
 // value 0 and the column min(i, n - 1).
 cudaError_t launch_csr_fill(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
                             const double* d, const int64_t* soff, double* sval, int32_t* scol, double* c,
-                            cudaStream_t s);
+                            unsigned long long* bmax, cudaStream_t s);
 
 struct CsrParams {
   int64_t n, nslices;
@@ -42,13 +42,35 @@ struct CsrParams {
   jacobi_stats* stats_out;
   int64_t max_iter;
   double tol;
-  int norm;             // JACOBI_NORM_INF or JACOBI_NORM_2
+  int norm;             // JACOBI_NORM_INF, JACOBI_NORM_2 or JACOBI_NORM_RESID
+  const double* d;      // a_ii (JACOBI_NORM_RESID)
+  double bnorm;         // ||b||_inf (JACOBI_NORM_RESID)
   int test_skip_arrival;  // test only: CTA 0 skips the first grid barrier and raises the error word
   uint64_t wait_ns;
 };
 
 // One cooperative launch of `grid` CTAs runs the whole solve.
 cudaError_t launch_csr_solve(const CsrParams& p, int grid, cudaStream_t s);
+
+// Mixed-precision refinement of the sparse system: FP64 outer residuals r' = C + T x - x (= D^-1 (b - A x))
+// with the stopping test max_i |a_ii r'_i| / ||b||_inf <= tol, inner Jacobi sweeps on the correction,
+// delta <- r' + T_lo delta, with T stored in the inner type (FP32 or BF16) and FP32 accumulation, x += delta
+// folded into the next residual.  `base` carries the FP64 layout, the iterates, the control block and tol.
+struct CsrIrParams {
+  CsrParams base;       // also a_ii and ||b||_inf (base.d, base.bnorm)
+  const void* tlo;      // T in the inner type, same slots as base.sval
+  float* rf;            // r' of the current outer step
+  float* da;            // inner iterates
+  float* db;
+  float inner_rtol;     // inner stop: max |delta' - delta| <= inner_rtol * max |delta'|
+  int max_inner;        // inner sweeps per outer step
+  int max_outer;        // outer steps (residual evaluations after the first)
+};
+enum class CsrInner : int { F32 = 1, BF16 = 2 };
+// T in the inner type from the FP64 slots (round to nearest).
+cudaError_t launch_csr_narrow(CsrInner kind, const double* sval, int64_t slots, void* tlo, cudaStream_t s);
+cudaError_t launch_csr_ir_solve(CsrInner kind, const CsrIrParams& p, int grid, cudaStream_t s);
+int csr_ir_max_grid(CsrInner kind);
 // Largest co-resident grid of the sweep kernel, capped at kMaxGrid (0 on failure), and its warps per CTA.
 int csr_max_grid();
 int csr_warps_per_cta();

@@ -45,5 +45,5 @@ def test_struct_layouts_match_header():
     # jacobi_stats: 2 x int64, 2 x double, 2 x int32; jacobi_desc: see include/jacobi.h
     assert ctypes.sizeof(jac.JacobiStats) == 40
     assert ctypes.sizeof(jac.JacobiDesc) == 120
-    # jacobi_csr_desc: 2 x int64, 4 pointers, 2 x int32, 1 pointer
-    assert ctypes.sizeof(jac.JacobiCsrDesc) == 64
+    # jacobi_csr_desc: 2 x int64, 4 pointers, 2 x int32, 1 pointer, 4 x int32, 1 double
+    assert ctypes.sizeof(jac.JacobiCsrDesc) == 88

@@ -185,3 +185,71 @@ def test_sparse_random_configurations(jac, case):
     assert st.status == ref.status == 0, (n, kind, st.as_dict())
     assert abs(st.sweeps - ref.iters) <= (1 if norm == "2" else 0), (st.sweeps, ref.iters)
     assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-11
+
+
+# ---- mixed precision: FP32 / BF16 inner sweeps, FP64 refinement -----------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp32_ir", "bf16_ir"])
+@pytest.mark.parametrize("name", ["irregular_1000", "irregular_33", "one_unknown", "line_95", "plane_37x29",
+                                  "box_11x9x7", "long_rows_2000"])
+def test_sparse_ir_meets_the_residual_target(jac, prec, name):
+    """Refined to ||b - A x||_inf / ||b||_inf <= 1e-10, recomputed by the CSR oracle in FP64, and the
+    solve's own reported residual agrees with it."""
+    rp, ci, v, B, Xs = SYSTEMS[name]()
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), precision=prec)
+    X, st = s.solve(max_iter=1, tol=1e-10)
+    _, rel = oracle.csr_residual(rp, ci, v, B, X.cpu().numpy())
+    assert st.status == 0 and rel <= 1e-10, (st.as_dict(), rel)
+    assert abs(st.rel_residual - rel) <= 1e-3 * 1e-10
+    assert st.outer_steps >= 1 and st.sweeps >= st.outer_steps - 1
+
+
+def test_sparse_ir_full_size_plane(jac):
+    """The bench workload in BF16 inner precision: the FP64 residual of every row, checked by the oracle,
+    and the error against the planted solution."""
+    rp, ci, v, B, Xs = synth.stencil_system((2048, 2048), 1.05, seed=synth.BASE_SEED + 6)
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), precision="bf16_ir")
+    X, st = s.solve(max_iter=1, tol=1e-10)
+    Xh = X.cpu().numpy()
+    _, rel = oracle.csr_residual(rp, ci, v, B, Xh)
+    assert st.status == 0 and rel <= 1e-10, (st.as_dict(), rel)
+    assert np.max(np.abs(Xh - Xs[:, 0])) <= 1e-8
+
+
+def test_sparse_ir_cap_errors_and_timeout(jac):
+    import torch
+    rp, ci, v, B, _ = synth.stencil_system((60, 50), 1.05, seed=41)
+    # the outer cap: X is the last refined iterate, NOT_CONVERGED
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), precision="bf16_ir", max_outer=1)
+    out = torch.empty(B.shape[0], dtype=torch.float64, device="cuda")
+    s.solve_async(max_iter=1, tol=1e-14, out=out)
+    st = s.last_stats()
+    _, rel = oracle.csr_residual(rp, ci, v, B, out.cpu().numpy())
+    assert st.status == jac.NOT_CONVERGED and st.outer_steps == 2 and abs(st.rel_residual - rel) <= 1e-6 * rel
+    with pytest.raises(jac.JacobiError) as e:
+        jac.CsrSolver(rp, ci, v, B[:, 0], precision="fp8_ir")
+    assert e.value.status == jac.ERR_UNSUPPORTED
+    with pytest.raises(jac.JacobiError) as e:
+        jac.CsrSolver(rp, ci, v, B[:, 0], precision="fp32_ir", norm="2")
+    assert e.value.status == jac.ERR_INVALID_ARG
+    flags = jac.binding.FLAG_SHORT_WAITS | jac.binding.FLAG_TEST_SKIP_ARRIVAL
+    bad = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), precision="fp32_ir", flags=flags)
+    with pytest.raises(jac.JacobiError) as e:
+        bad.solve(max_iter=1, tol=1e-10)
+    assert e.value.status == jac.ERR_TIMEOUT
+    X, st = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), precision="fp32_ir").solve(max_iter=1, tol=1e-10)
+    assert st.status == 0 and oracle.csr_residual(rp, ci, v, B, X.cpu().numpy())[1] <= 1e-10
+
+
+def test_sparse_residual_norm_stop(jac):
+    """JACOBI_NORM_RESID on the FP64 path: the stop on ||b - A x^(k-1)|| / ||b|| follows the oracle's sweep
+    count; the reported value carries the iterates' few-ulp rounding differences (times a_ii / ||b||)."""
+    rp, ci, v, B, _ = synth.random_sparse_system(1500, 1.05, seed=42, max_len=40)
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), norm="resid")
+    X, st = s.solve(max_iter=5000, tol=1e-10)
+    ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=5000, tol=1e-10, norm=oracle.NORM_RESID)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters)
+    assert abs(st.final_delta - ref.delta) <= 1e-3 * ref.delta
+    assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
+    _, rel = oracle.csr_residual(rp, ci, v, B, X.cpu().numpy())
+    assert rel < 1e-10
