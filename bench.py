@@ -678,18 +678,24 @@ def run_e2e(args, jac, torch, dev, A, B, ws):
             st = pending.last_stats()
         return st
 
-    out = {}
+    # the host link is shared with the machine's other tenants and its rate swings between runs, so each
+    # form is timed in three blocks of `steps` solves and the median block is reported, all blocks beside
+    out, blocks = {}, {}
     for name, pipelined in (("pipelined", True), ("sequential", False)):
         run(max(2, args.warmup), pipelined)
         torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        st = run(steps, pipelined)
-        torch.cuda.synchronize(dev)
-        sec = (time.perf_counter() - t0) / steps
-        out[name] = round(1.0 / sec, 3) if st.status == 0 else 0.0
-    return {"value": out["pipelined"], "unit": "solves/s", "steps": steps,
+        rates = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            st = run(steps, pipelined)
+            torch.cuda.synchronize(dev)
+            sec = (time.perf_counter() - t0) / steps
+            rates.append(round(1.0 / sec, 3) if st.status == 0 else 0.0)
+        blocks[name] = rates
+        out[name] = sorted(rates)[1]
+    return {"value": out["pipelined"], "unit": "solves/s", "steps": 3 * steps,
             "h2d_bytes_per_step": int(8 * n * n + 8 * n), "d2h_bytes_per_step": int(8 * n),
-            "sequential_value": out["sequential"],
+            "sequential_value": out["sequential"], "blocks_solves_per_s": blocks,
             "path": "host pinned A,B -> jacobi_setup_ex (H2D copy into the workspace) -> jacobi_solve_async -> "
                     "X to pinned host; two solvers on two streams, each step's H2D overlapping the previous "
                     "step's solve"}
