@@ -297,6 +297,16 @@ JACOBI_API int jacobi_batch_grid(jacobi_batch* b);
 /* Release the batch (waits for its stream; NULL is a no-op). */
 JACOBI_API void jacobi_batch_destroy(jacobi_batch* b);
 
+/* One call for a whole batch, the batched form of jacobi_solve: create with default tuning on the legacy
+ * default stream, solve every system from X = 0, copy the per-system records into stats (host array
+ * [count], may be NULL) and release.  A, B, X_out: host arrays [count] of device pointers as in
+ * jacobi_batch_desc; precision JACOBI_FP64, JACOBI_FP32_IR or JACOBI_BF16_IR.  Returns the worst outcome
+ * over the systems (an error status, else JACOBI_NOT_CONVERGED if any system hit its cap, else JACOBI_OK),
+ * or the error of the create / solve itself. */
+JACOBI_API int jacobi_batch_solve(int64_t count, const int64_t* n, const double* const* A, const double* const* B,
+                                  double* const* X_out, double tol, int64_t max_iter, int32_t precision,
+                                  jacobi_stats* stats);
+
 /* ------------------------------------------------------------------------------------------------
  * Serving: continuous batching of independent solve requests.
  *
@@ -348,6 +358,12 @@ JACOBI_API int jacobi_server_step(jacobi_server* s, int32_t* active_out, int32_t
  * sweeps, outer_steps = residual evaluations, rel_residual = final max over columns).  Their X_out is
  * complete when this returns. */
 JACOBI_API int jacobi_server_poll(jacobi_server* s, int64_t* ids, jacobi_stats* stats, int32_t cap, int32_t* count);
+
+/* Run rounds until request `id` finishes, then return its status and record (*stats may be NULL); its
+ * X_out is complete.  The request is collected: later polls do not report it.  Other requests that
+ * finish meanwhile stay for jacobi_server_poll.  JACOBI_ERR_INVALID_ARG for an unknown id or one
+ * collected already. */
+JACOBI_API int jacobi_server_wait(jacobi_server* s, int64_t id, jacobi_stats* stats);
 
 /* Rounds run so far. */
 JACOBI_API int jacobi_server_rounds(jacobi_server* s, int64_t* rounds);

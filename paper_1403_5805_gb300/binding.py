@@ -43,7 +43,8 @@ EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_stri
            "jacobi_batch_destroy", "jacobi_server_create", "jacobi_server_submit", "jacobi_server_submit_generated",
            "jacobi_server_step", "jacobi_server_poll", "jacobi_server_rounds", "jacobi_server_destroy",
            "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async", "jacobi_csr_solve",
-           "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace", "jacobi_csr_destroy")
+           "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace", "jacobi_csr_destroy",
+           "jacobi_batch_solve", "jacobi_server_wait")
 
 
 class JacobiStats(ctypes.Structure):
@@ -151,6 +152,8 @@ def load() -> ctypes.CDLL:
         lib.jacobi_csr_last_stats.argtypes = [H, ctypes.POINTER(JacobiStats)]
         lib.jacobi_csr_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)]
         lib.jacobi_csr_last_trace.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_batch_solve.argtypes = [i64, vp, vp, vp, vp, dbl, i64, i32, vp]
+        lib.jacobi_server_wait.argtypes = [H, i64, ctypes.POINTER(JacobiStats)]
         lib.jacobi_csr_destroy.argtypes = [H]
         lib.jacobi_csr_destroy.restype = None
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
@@ -160,7 +163,8 @@ def load() -> ctypes.CDLL:
                      "jacobi_batch_stats", "jacobi_batch_grid", "jacobi_server_create", "jacobi_server_submit",
                      "jacobi_server_submit_generated", "jacobi_server_step", "jacobi_server_poll",
                      "jacobi_server_rounds", "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async",
-                     "jacobi_csr_solve", "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace"):
+                     "jacobi_csr_solve", "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace",
+                     "jacobi_batch_solve", "jacobi_server_wait"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -576,6 +580,22 @@ class MultiSolver:
             pass
 
 
+def batch_solve(As, Bs, Xs, tol: float = 1e-10, max_iter: int = 5000, precision: str = "fp32_ir"):
+    """``jacobi_batch_solve``: one call for a batch (lists of float64 CUDA tensors A_k (n_k, n_k), B_k and
+    outputs X_k (n_k,)).  Returns (worst status, per-system records)."""
+    lib = load()
+    count = len(As)
+    ns = np.array([a.shape[0] for a in As], dtype=np.int64)
+    pa = (ctypes.c_void_p * count)(*[a.data_ptr() for a in As])
+    pb = (ctypes.c_void_p * count)(*[b.data_ptr() for b in Bs])
+    px = (ctypes.c_void_p * count)(*[x.data_ptr() for x in Xs])
+    sts = (JacobiStats * count)()
+    st = lib.jacobi_batch_solve(count, ns.ctypes.data, ctypes.addressof(pa), ctypes.addressof(pb),
+                                ctypes.addressof(px), tol, max_iter, PRECISIONS[precision], ctypes.addressof(sts))
+    _check(st, "jacobi_batch_solve")
+    return st, [sts[k] for k in range(count)]
+
+
 # ------------------------------------------------------------------------------ serving interface
 
 def generate_request(n: int, r: int, f: float, seed: int, device=None, stream=None):
@@ -638,6 +658,13 @@ class Server:
         for rid, _ in out:
             self._keep.pop(rid, None)
         return out
+
+    def wait(self, rid: int) -> JacobiStats:
+        """Run rounds until request ``rid`` finishes; returns its record (the request is collected)."""
+        st = JacobiStats()
+        _check(load().jacobi_server_wait(self._h, rid, ctypes.byref(st)), "jacobi_server_wait")
+        self._keep.pop(rid, None)
+        return st
 
     def rounds(self) -> int:
         r = ctypes.c_int64(0)

@@ -698,4 +698,40 @@ void jacobi_batch_destroy(jacobi_batch* b) {
   delete b;
 }
 
+int jacobi_batch_solve(int64_t count, const int64_t* n, const double* const* A, const double* const* B,
+                       double* const* X_out, double tol, int64_t max_iter, int32_t precision, jacobi_stats* stats) {
+  if (count < 1 || !n || !A || !B || !X_out) return JACOBI_ERR_INVALID_ARG;
+  jacobi_batch_desc d{};
+  d.count = count;
+  d.n = n;
+  d.A = A;
+  d.B = B;
+  d.X = X_out;
+  d.precision = precision;
+  jacobi_batch* b = nullptr;
+  int st = jacobi_batch_create(&d, &b);
+  if (st != JACOBI_OK) return st;
+  std::vector<jacobi_stats> local;
+  jacobi_stats* out = stats;
+  if (!out) {
+    local.resize(static_cast<size_t>(count));
+    out = local.data();
+  }
+  st = jacobi_batch_solve_async(b, max_iter, tol);
+  if (st == JACOBI_OK) st = jacobi_batch_stats(b, out);
+  jacobi_batch_destroy(b);
+  if (st != JACOBI_OK) return st;
+  // the worst outcome over the systems: an error, else a system that hit its cap, else converged
+  int worst = JACOBI_OK;
+  for (int64_t k = 0; k < count; ++k) {
+    const int sk = out[k].status;
+    if (sk < 0) {
+      if (worst >= 0 || sk < worst) worst = sk;  // an error outranks any warning
+    } else if (sk > 0 && worst == JACOBI_OK) {
+      worst = sk;
+    }
+  }
+  return worst;
+}
+
 }  // extern "C"

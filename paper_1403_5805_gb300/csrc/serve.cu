@@ -907,6 +907,27 @@ int jacobi_server_poll(jacobi_server* s, int64_t* ids, jacobi_stats* stats, int3
   return JACOBI_OK;
 }
 
+int jacobi_server_wait(jacobi_server* s, int64_t id, jacobi_stats* stats) {
+  if (!s || id < 1 || id >= s->next_id) return JACOBI_ERR_INVALID_ARG;
+  for (;;) {
+    for (auto it = s->done.begin(); it != s->done.end(); ++it)
+      if (it->first == id) {
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return JACOBI_ERR_CUDA;
+        const jacobi_stats st = it->second;
+        s->done.erase(it);
+        if (stats) *stats = st;
+        return st.status;
+      }
+    bool queued = false;
+    for (const Request* rq : s->pending) queued = queued || rq->id == id;
+    for (const Request* rq : s->active) queued = queued || rq->id == id;
+    if (!queued) return JACOBI_ERR_INVALID_ARG;  // collected already by a poll or an earlier wait
+    int32_t active = 0, pending = 0;
+    const int st = jacobi_server_step(s, &active, &pending);
+    if (st != JACOBI_OK) return st;
+  }
+}
+
 int jacobi_server_rounds(jacobi_server* s, int64_t* rounds) {
   if (!s || !rounds) return JACOBI_ERR_INVALID_ARG;
   *rounds = s->rounds;

@@ -141,3 +141,23 @@ def test_full_size_batch_sampled(jac):
         A, B, _ = synth.dominant_system(int(ns[k]), float(fs[k]), synth.system_seed(synth.BASE_SEED + 2, int(k)))
         _, rel = oracle.residual(A, B, X[k].cpu().numpy())
         assert rel <= 1e-10, (k, rel)
+
+
+def test_one_call_batch_solve_equals_the_handle_path(jac):
+    """jacobi_batch_solve (create, solve, records, release in one call) gives the handle path's results
+    bit for bit, and its return value is the worst per-system outcome."""
+    import torch
+    systems = make_batch(23, 1, 400, 1.05, 2.0, seed=131)
+    As, Bs = to_dev(systems)
+    bs = jac.BatchSolver(As, Bs, precision="fp32_ir")
+    Xh = bs.solve_async(max_iter=5000, tol=1e-10)
+    sh = bs.stats()
+    Xs = [torch.empty(A.shape[0], dtype=torch.float64, device="cuda") for A in As]
+    st, recs = jac.batch_solve(As, Bs, Xs, tol=1e-10, max_iter=5000, precision="fp32_ir")
+    assert st == 0
+    for k in range(len(As)):
+        assert torch.equal(Xs[k], Xh[k]), k
+        assert (recs[k].status, recs[k].sweeps, recs[k].outer_steps) == (sh[k].status, sh[k].sweeps, sh[k].outer_steps)
+    # a cap that most systems hit: the call reports JACOBI_NOT_CONVERGED
+    st, recs = jac.batch_solve(As, Bs, Xs, tol=1e-14, max_iter=2, precision="fp64")
+    assert st == jac.NOT_CONVERGED and any(r.status == jac.NOT_CONVERGED for r in recs)

@@ -127,3 +127,26 @@ def test_bad_request_and_oversized_request(jac):
     with pytest.raises(jac.JacobiError) as e:
         srv.submit_generated(8192, 16, 1.2, 6, torch.zeros(16, 8192, dtype=torch.float64, device="cuda"))
     assert e.value.status == jac.ERR_OUT_OF_MEMORY
+
+
+def test_wait_for_one_request(jac):
+    """jacobi_server_wait runs rounds until the named request is done and collects it; requests that finish
+    meanwhile stay for poll; an unknown or collected id is rejected."""
+    import torch
+    srv = jac.Server(budget_bytes=1 << 30)
+    outs, ids = [], []
+    for k, (n, r) in enumerate([(900, 3), (120, 1), (2500, 8), (64, 2)]):
+        o = torch.zeros(r, n, dtype=torch.float64, device="cuda")
+        ids.append(srv.submit_generated(n, r, 1.2, 500 + k, o))
+        outs.append(o)
+    st = srv.wait(ids[2])
+    A, B = synth.serving_request(2500, 8, 1.2, 502)
+    _, rel = oracle.residual(A, B, outs[2].cpu().numpy().T)
+    assert st.status == 0 and rel <= 1e-10
+    with pytest.raises(jac.JacobiError) as e:
+        srv.wait(ids[2])
+    assert e.value.status == jac.ERR_INVALID_ARG
+    rest = drain(srv)
+    assert set(rest) == {ids[0], ids[1], ids[3]}
+    with pytest.raises(jac.JacobiError):
+        srv.wait(12345)
