@@ -722,9 +722,14 @@ def cpu_baseline(A, B, n, budget_s: float = 12.0):
         if time.perf_counter() - t0 >= budget_s or solves >= 5:
             break
     sec = (time.perf_counter() - t0) / solves
+    # and the plain serial loop: two sweeps of the same system on one core
+    t1 = time.perf_counter()
+    oracle.jacobi(A, B, max_iter=2, tol=1e-300, nthreads=1)
+    single_ms = (time.perf_counter() - t1) * 1e3 / 2
     return {"value": round(1.0 / sec, 4), "unit": "solves/s", "cores": threads, "kind": "oracle",
             "sample": f"{solves} full FP64 oracle solve(s) of the n={n} system (OpenMP rows, "
-                      f"{res.iters} sweeps each, relative-residual stop 1e-10)"}
+                      f"{res.iters} sweeps each, relative-residual stop 1e-10)",
+            "single_core_ms_per_sweep": round(single_ms, 1)}
 
 
 def run_reference(args, world, rank):
