@@ -165,9 +165,10 @@ typedef enum { JACOBI_METHOD_JACOBI = 0, JACOBI_METHOD_SOR = 1 } jacobi_method;
 /* Test only: the first ring item of each solve is announced to the consumers but never copied, so their
  * bounded wait expires; the solve then returns JACOBI_ERR_TIMEOUT and the context stays usable. */
 #define JACOBI_FLAG_TEST_DROP_COPY 8
-/* Test only (sparse handle): CTA 0 never arrives at the grid barrier of the first sweep and raises the
- * error word instead, so the other CTAs leave their bounded wait; the solve returns JACOBI_ERR_TIMEOUT
- * and the context stays usable. */
+/* Test only.  Sparse handle: CTA 0 never arrives at the grid barrier of the first sweep and raises the
+ * error word instead.  Gauss-Seidel handle: block 0 never publishes its first sweep (no flag, no mailbox)
+ * and raises the error word.  Either way the other CTAs leave their bounded waits, the solve returns
+ * JACOBI_ERR_TIMEOUT and the context stays usable. */
 #define JACOBI_FLAG_TEST_SKIP_ARRIVAL 32
 /* Many right-hand sides: retire each column as soon as it meets the stopping test on its own (the
  * FP64 path: its change norm below tol; the BF16 path: its relative residual at or below tol) instead of

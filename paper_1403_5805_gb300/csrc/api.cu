@@ -201,6 +201,7 @@ struct jacobi_handle {
   std::vector<double> col_value;
   uint64_t wait_ns = 4000000000ull;
   int test_drop_copy = 0;
+  int test_skip_arrival = 0;  // Gauss-Seidel test hook (JACOBI_FLAG_TEST_SKIP_ARRIVAL)
   template <typename T>
   T* at(size_t off) const {
     return reinterpret_cast<T*>(ws + off);
@@ -305,6 +306,7 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   h->retire_columns = (d->flags & JACOBI_FLAG_RETIRE_COLUMNS) && d->nrhs > 1;
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
   h->test_drop_copy = (d->flags & JACOBI_FLAG_TEST_DROP_COPY) ? 1 : 0;
+  h->test_skip_arrival = (d->flags & JACOBI_FLAG_TEST_SKIP_ARRIVAL) ? 1 : 0;
   if (d->workspace) {
     if (d->workspace_bytes < h->L.total || reinterpret_cast<uintptr_t>(d->workspace) % kAlign != 0) {
       delete h;
@@ -940,6 +942,7 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
     g.omega = h->omega;
     g.cmax = h->at<unsigned long long>(h->L.cmax);
     g.rexp = h->at<int>(h->L.rexp);
+    g.test_skip_publish = h->test_skip_arrival;
     g.wait_ns = h->wait_ns;
     e = launch_gs_solve(g, h->grid, s);
   } else {

@@ -38,6 +38,7 @@ struct GsParams {
   double omega;         // relaxation, 0 < omega < 2 (1: Gauss-Seidel)
   const unsigned long long* cmax;  // IEEE bits of max_i |b_i / a_ii|: the scale of the float-float split of x
   const int* rexp;      // per row: split exponent of max_j |a_ij| (launch_gs_row_exponents)
+  int test_skip_publish;  // test only: block 0 never publishes sweep 1 and raises the error word
   uint64_t wait_ns;
 };
 

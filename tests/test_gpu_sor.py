@@ -139,3 +139,19 @@ def test_sor_random_configurations(jac, case):
     assert st.status == ref.status == 0, (n, grid, omega, st.as_dict())
     assert abs(st.sweeps - ref.iters) <= (1 if norm == "2" else 0), (st.sweeps, ref.iters)
     assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-11
+
+
+def test_sor_bounded_waits_expire_and_context_stays_usable(jac):
+    """Failure detection without a GPU fault: block 0 never publishes its first sweep and raises the error
+    word; the blocks waiting on its flag leave at once, the one polling its mailbox after its bounded wait
+    (50 ms), the solve reports a timeout, and the next solve on the same context matches the oracle."""
+    A, B, _ = synth.dominant_system(2000, 1.2, seed=81)
+    flags = jac.binding.FLAG_SHORT_WAITS | jac.binding.FLAG_TEST_SKIP_ARRIVAL
+    bad = solver(jac, A, B, flags=flags)
+    with pytest.raises(jac.JacobiError) as e:
+        bad.solve(max_iter=100, tol=1e-12)
+    assert e.value.status == jac.ERR_TIMEOUT
+    X, st = solver(jac, A, B).solve(max_iter=1000, tol=1e-12)
+    ref = oracle.block_sor(A, B, max_iter=1000, tol=1e-12, blocks=1)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters)
+    assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
