@@ -129,8 +129,7 @@ int validate_desc(const jacobi_desc* d) {
     if (d->precision != JACOBI_FP64 || d->nrhs != 1 || d->norm == JACOBI_NORM_RESID) return JACOBI_ERR_UNSUPPORTED;
   }
   if (d->nrhs > 1) {
-    // many right-hand sides: plain FP64 (max-norm stop) or BF16 inner sweeps on tcgen05
-    if (d->precision == JACOBI_FP64 && d->norm == JACOBI_NORM_2) return JACOBI_ERR_UNSUPPORTED;
+    // many right-hand sides: plain FP64 (any stopping norm) or BF16 inner sweeps on tcgen05
     if (d->precision != JACOBI_FP64 && d->precision != JACOBI_BF16_IR) return JACOBI_ERR_UNSUPPORTED;
     if (d->precision == JACOBI_BF16_IR && !mrhs_supported_r(d->nrhs)) return JACOBI_ERR_UNSUPPORTED;
   }
@@ -139,7 +138,7 @@ int validate_desc(const jacobi_desc* d) {
 
 // Extra device buffers of a many-right-hand-side handle (vectors v[c*ld + i]).
 struct MrhsLayout {
-  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, bcol, stats, status, xs, xexp, cols, total;
+  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, colsq, bcol, stats, status, xs, xexp, cols, total;
 };
 
 MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
@@ -161,6 +160,7 @@ MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
   M.dah = take(v2);
   M.dbh = take(v2);
   M.colmax = take(static_cast<size_t>(r) * 8);
+  M.colsq = take(static_cast<size_t>((ld + 63) / 64) * r * 8);  // per 64-row tile and column (Euclidean norm)
   M.bcol = take(static_cast<size_t>(r) * 8);
   M.stats = take(16);
   M.status = take(16);
@@ -432,24 +432,36 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
   bool all_retired = false;
   if (h->precision == JACOBI_FP64) {
     const int resid = h->norm == JACOBI_NORM_RESID;
+    const bool eucl = h->norm == JACOBI_NORM_2;
+    const int64_t tiles = (n + 63) / 64;
+    double* colsq = h->at<double>(h->M.colsq);
+    std::vector<double> hs(eucl ? static_cast<size_t>(tiles * r) : 0);
     for (int64_t k = 1;; ++k) {
       CK(cudaMemsetAsync(colmax, 0, static_cast<size_t>(r) * 8, s));
       if (retire) CK(upload_active());
       MrhsDenseParams p{n, r, ld, h->lda64, 1, resid, h->A64, h->at<double>(h->M.b), xc, h->at<double>(h->L.d),
                         h->at<double>(h->L.rinv), nullptr, nullptr, nullptr, xo, colmax, nullptr, nullptr, nullptr,
-                        retire ? dcols : nullptr, static_cast<int64_t>(act.size())};
+                        retire ? dcols : nullptr, static_cast<int64_t>(act.size()), eucl ? colsq : nullptr};
       CK(launch_mrhs_dense(p, s));
       clk.mark(JACOBI_PHASE_SWEEP64);
       CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
+      if (eucl) CK(cudaMemcpyAsync(hs.data(), colsq, hs.size() * 8, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       std::swap(xc, xo);  // xc: the iterate this sweep produced
       double delta = 0.0;
       std::vector<int> keep;
       for (int c : act) {
-        // max-norm change of the column, or its relative residual of the previous iterate
+        // max-norm change of the column, its Euclidean norm (the tiles' sums added in tile order, Section
+        // 2's criterion), or its relative residual of the previous iterate
         // (max_i |a_ii (x_i^(k) - x_i^(k-1))| / ||b_c||_inf)
-        const double v = resid ? bits(hc[static_cast<size_t>(c)]) / bits(hb[static_cast<size_t>(c)])
-                               : bits(hc[static_cast<size_t>(c)]);
+        double v;
+        if (eucl) {
+          double t = 0.0;
+          for (int64_t q = 0; q < tiles; ++q) t += hs[static_cast<size_t>(q * r + c)];
+          v = std::sqrt(t);
+        } else {
+          v = resid ? bits(hc[static_cast<size_t>(c)]) / bits(hb[static_cast<size_t>(c)]) : bits(hc[static_cast<size_t>(c)]);
+        }
         delta = (std::isnan(v) || v > delta) ? v : delta;
         h->col_iters[static_cast<size_t>(c)] = k;
         h->col_value[static_cast<size_t>(c)] = v;

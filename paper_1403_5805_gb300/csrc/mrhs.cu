@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
     __syncthreads();
   }
   unsigned long long mloc[4] = {0, 0, 0, 0};
+  double sq[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int64_t i = m0 + tr + 16 * u;
@@ -316,7 +317,20 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
         p.xn[o] = xi;
         const unsigned long long bits = abs_bits(p.resid_norm ? di * (xi - xo) : xi - xo);
         mloc[v] = bits > mloc[v] ? bits : mloc[v];
+        sq[v] = fma(xi - xo, xi - xo, sq[v]);  // rows in the order u = 0..3
       }
+    }
+  }
+  if (p.colsq) {
+    // the tile's 16 row groups summed per column in a fixed order (As is free after the last K step)
+    double* part = &As[0][0];  // [16][kDN + 1]
+#pragma unroll
+    for (int v = 0; v < 4; ++v) part[tr * (kDN + 1) + tc + 16 * v] = sq[v];
+    __syncthreads();
+    if (tid < kDN && c0 + tid < p.nact) {
+      double t = 0.0;
+      for (int g = 0; g < 16; ++g) t += part[g * (kDN + 1) + tid];
+      p.colsq[static_cast<int64_t>(blockIdx.x) * p.r + col_of(p, c0 + tid)] = t;
     }
   }
 #pragma unroll

@@ -47,6 +47,9 @@ struct MrhsDenseParams {
   // active columns: tile column c works on column cols[c] (c < nact); NULL cols: all r columns
   const int* cols;
   int64_t nact;
+  // mode 1, Euclidean norm: the sum of squared changes of each 64-row tile and column, written (no
+  // atomics, a fixed summation order) at colsq[tile * r + c]; NULL: the maxima only
+  double* colsq;
 };
 
 bool mrhs_supported_r(int64_t r);

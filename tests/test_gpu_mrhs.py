@@ -200,3 +200,29 @@ def test_bf16_column_retirement(jac):
         _, rel = oracle.residual(A, B[:, c], Xh[:, c])
         assert rel <= 1e-10, (c, rel)
         assert abs(vals[c] - rel) <= 1e-13 + 1e-3 * rel
+
+
+def test_fp64_many_rhs_euclidean_norm(jac):
+    """Section 2's Euclidean stopping test on many right-hand sides: per column the square root of the
+    summed squared changes, the stop on the largest column (as the oracle); with retirement, each column
+    is the single-column oracle solve under the same norm.  Per-column values agree with the oracle's
+    within the few-ulp rounding differences of the iterates (times sqrt(n))."""
+    n, r = 500, 7
+    A, B, _ = synth.dominant_system(n, 1.15, seed=630, nrhs=r)
+    B[:, 3] *= 1e-4
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="fp64", norm="2")
+    X, st = s.solve(max_iter=2000, tol=1e-11)
+    ref = oracle.jacobi(A, B, max_iter=2000, tol=1e-11, norm=oracle.NORM_2)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters)
+    assert np.max(np.abs(X.cpu().numpy().T - ref.X)) <= 1e-12 * np.max(np.abs(ref.X))
+    assert abs(st.final_delta - ref.delta) <= 2 * np.sqrt(n) * 1e-14
+    s = jac.MultiSolver(At, Bt, precision="fp64", norm="2", retire_columns=True)
+    X, st = s.solve(max_iter=2000, tol=1e-11)
+    iters, vals = s.column_stats()
+    Xh = X.cpu().numpy().T
+    for c in range(r):
+        ref = oracle.jacobi(A, B[:, c], max_iter=2000, tol=1e-11, norm=oracle.NORM_2)
+        assert ref.status == 0 and iters[c] == ref.iters, (c, iters[c], ref.iters)
+        assert np.max(np.abs(Xh[:, c] - ref.X[:, 0])) <= 1e-12 * np.max(np.abs(ref.X)), c
+    assert iters[3] < iters[0]

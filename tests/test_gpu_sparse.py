@@ -253,3 +253,33 @@ def test_sparse_residual_norm_stop(jac):
     assert rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
     _, rel = oracle.csr_residual(rp, ci, v, B, X.cpu().numpy())
     assert rel < 1e-10
+
+
+def test_sparse_divergence_follows_the_oracle(jac):
+    """f = 0.9: rho(T) > 1.  At a cap of 200 sweeps both return X^(200) with JACOBI_NOT_CONVERGED; without
+    a cap the iterates overflow and both stop with JACOBI_ERR_NONFINITE, within the few sweeps by which
+    the two forms of the row sum move the overflow."""
+    rp, ci, v, B, _ = synth.stencil_system((40, 30), 0.9, seed=44)
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]))
+    import torch
+    out = torch.empty(B.shape[0], dtype=torch.float64, device="cuda")
+    s.solve_async(max_iter=200, tol=1e-12, out=out)
+    st = s.last_stats()
+    ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=200, tol=1e-12)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters) == (jac.NOT_CONVERGED, 200)
+    assert rel_err(out.cpu().numpy(), ref.X[:, 0]) <= 1e-12
+    ref200 = ref.X[:, 0]
+    s.solve_async(max_iter=20000, tol=1e-12, out=out)
+    st = s.last_stats()
+    ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=20000, tol=1e-12)
+    assert st.status == ref.status == jac.ERR_NONFINITE
+    # The sweep at which the iterate overflows depends on the form of the row sum.  The oracle forms
+    # sum_j a_ij x_j, up to max_i sum_j |a_ij| times ||x||_inf, before dividing by a_ii; the GPU adds
+    # t_ij x_j terms that are already divided.  The two overflow points differ by at most a factor of
+    # that row sum (times |a_ii|, which is at least 1 here) in ||x||, i.e. by log(row sum) / log(growth)
+    # sweeps at the growth per sweep seen in the oracle, plus one sweep either side for rounding.
+    A = synth.csr_to_dense(B.shape[0], rp, ci, v)
+    nxt = oracle.csr_jacobi(rp, ci, v, B, max_iter=201, tol=1e-300).X[:, 0]
+    growth = np.max(np.abs(nxt)) / np.max(np.abs(ref200))
+    window = np.log(np.abs(A).sum(axis=1).max()) / np.log(growth) + 2
+    assert abs(st.sweeps - ref.iters) <= window, (st.sweeps, ref.iters, window)
