@@ -140,6 +140,8 @@ def run_ours(args, world, rank, local):
         return {"section": "sparse", **run_sparse(args, jac, torch, dev)}
     if args.only == "serve":
         return {"section": "serving", **run_serve(args, jac, torch, dev, args.serve_seconds)}
+    if args.only == "small":
+        return {"section": "small_system", **run_small(args, jac, torch, dev)}
     n, f = args.n, args.f
     A, B, Xs = synth.dominant_system(n, f, seed=synth.BASE_SEED + 1)
     At = torch.from_numpy(A).to(dev)
@@ -227,6 +229,7 @@ def run_ours(args, world, rank, local):
     e2e = None if args.no_e2e else run_e2e(args, jac, torch, dev, A, B, ws)
     cpu = cpu_baseline(A, B, n) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     hard = None if (args.quick or args.no_hard) else run_hard(args, jac, torch, dev, ws)
+    small = None if (args.quick or args.no_small) else run_small(args, jac, torch, dev)
     batched = None if (args.quick or args.no_batch) else run_batch(args, jac, torch, dev)
     del At, Bt, A, B  # free the single-system inputs before the large many-right-hand-side workload
     many_rhs = None if (args.quick or args.no_mrhs) else run_many_rhs(args, jac, torch, dev)
@@ -248,7 +251,7 @@ def run_ours(args, world, rank, local):
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
         "sparse": sparse,
-        "serving": serving, "hard_generator": hard,
+        "serving": serving, "hard_generator": hard, "small_system": small,
     }
     if cpu is not None:
         result["cpu_baseline"] = cpu
@@ -640,6 +643,55 @@ def run_hard(args, jac, torch, dev, ws):
     return res
 
 
+def run_small(args, jac, torch, dev):
+    """The small system n = 512 (f = 1.25, tol 1e-12 on max|dx|), on the dominant generator (rho(T) small:
+    ~10 sweeps) and the paper-shaped one (rho(T) = 0.8: ~110 sweeps).  A is 2.1 MB and stays in L2, so a
+    sweep is bound by the grid barrier and the FP64 rate, not HBM: per-sweep time from the device trace,
+    the solve with and without setup, and the rate at which the L2-resident A is swept, for the default
+    grid and smaller ones."""
+    import synth
+    n, f = 512, 1.25
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    res = {"n": n, "dominance": f, "tol": 1e-12, "a_bytes": 8 * n * n}
+    for gen_name, gen, seed in (("dominant", synth.dominant_system, synth.BASE_SEED),
+                                ("paper_shaped", synth.hard_system, synth.BASE_SEED + 7)):
+        A, B, Xs = gen(n, f, seed=seed)
+        At = torch.from_numpy(A).to(dev)
+        Bt = torch.from_numpy(B[:, 0].copy()).to(dev)
+        rows = {}
+        for grid in (0, 16, 38, 76):
+            s = jac.DeviceSolver(At, Bt, precision="fp64", grid=grid)
+            for _ in range(3):
+                s.solve_async(None, 2000, 1e-12, out)
+            torch.cuda.synchronize(dev)
+            reps = 50
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                s.solve_async(None, 2000, 1e-12, out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            solve_us = e0.elapsed_time(e1) * 1e3 / reps
+            st = s.last_stats()
+            tr = [(e - b) for k, b, e in s.trace() if k == 0]
+            sweep_us = (sorted(tr)[len(tr) // 2] / 1e3) if tr else None
+            t0 = time.perf_counter()
+            for _ in range(reps):  # setup + solve through the public API, each waited for
+                s2 = jac.DeviceSolver(At, Bt, precision="fp64", grid=grid)
+                s2.solve_async(None, 2000, 1e-12, out)
+                s2.last_stats()
+            with_setup_us = (time.perf_counter() - t0) * 1e6 / reps
+            rows["auto" if grid == 0 else str(grid)] = {
+                "status": st.status, "sweeps": st.sweeps, "solve_us": round(solve_us, 2),
+                "median_sweep_us": round(sweep_us, 3) if sweep_us else None,
+                "l2_sweep_gbs": round(8.0 * n * n / (sweep_us * 1e3), 1) if sweep_us else None,
+                "solves_per_s": round(1e6 / solve_us, 1), "setup_and_solve_us": round(with_setup_us, 1),
+                "err_vs_xstar": float((out - torch.from_numpy(Xs[:, 0].copy()).to(dev)).abs().max().item())}
+        res[gen_name] = rows
+    return res
+
+
 def run_e2e(args, jac, torch, dev, A, B, ws):
     """Same metric through the public API from pinned host buffers: per step the H2D of A and B, setup,
     solve and the D2H read of X, all inside the timed region.  Two solvers alternate on two CUDA streams
@@ -789,6 +841,7 @@ def main():
     ap.add_argument("--no-mrhs", action="store_true", dest="no_mrhs")
     ap.add_argument("--no-serve", action="store_true", dest="no_serve")
     ap.add_argument("--no-hard", action="store_true", dest="no_hard")
+    ap.add_argument("--no-small", action="store_true", dest="no_small")
     ap.add_argument("--no-sparse", action="store_true", dest="no_sparse")
     ap.add_argument("--sparse-grid", type=int, default=2048, dest="sparse_grid",
                     help="side of the 2-D stencil grid of the sparse section")
@@ -798,7 +851,7 @@ def main():
     ap.add_argument("--serve-window", type=float, default=5.0, dest="serve_window",
                     help="arrival window of the serving section of the default run")
     ap.add_argument("--serve-fp64-seconds", type=float, default=1.0, dest="serve_fp64_seconds")
-    ap.add_argument("--only", choices=["batch", "mrhs", "serve", "sparse"], default=None,
+    ap.add_argument("--only", choices=["batch", "mrhs", "serve", "sparse", "small"], default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--mrhs-n", type=int, default=32768, dest="mrhs_n")
     ap.add_argument("--mrhs-steps", type=int, default=3, dest="mrhs_steps")

@@ -97,6 +97,22 @@ __device__ __forceinline__ void seg_dot(float& acc, uint4 m, const float (&xv)[1
   e4m3x4_fma(acc, m.w, xv + 12);
 }
 
+// One segment of each of a warp's R rows against the same x values.  FP64: every row's first product,
+// then every row's second, so consecutive FMAs are independent (each row's own order is the same as
+// seg_dot's).  Narrow rows: seg_dot row by row (their FP32 chains are short-latency).
+template <int R>
+__device__ __forceinline__ void seg_dot_rows(double (&acc)[R], const uint4 (&m)[R], const double (&xv)[2]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = fma(__hiloint2double(static_cast<int>(m[r].y), static_cast<int>(m[r].x)), xv[0], acc[r]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = fma(__hiloint2double(static_cast<int>(m[r].w), static_cast<int>(m[r].z)), xv[1], acc[r]);
+}
+template <int R, int V>
+__device__ __forceinline__ void seg_dot_rows(float (&acc)[R], const uint4 (&m)[R], const float (&xv)[V]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) seg_dot(acc[r], m[r], xv);
+}
+
 // The segment that straddles the end of a row (columns >= n inside it) may carry row padding that is
 // not guaranteed to be zero or even finite when A is read in place.  x is zeroed there, and for FP64
 // rows the padding element is skipped, not multiplied (NaN * 0 would poison the sum).  The narrow

@@ -25,6 +25,8 @@
 #include "solver.cuh"
 #include "splitfloat.cuh"
 
+#include <type_traits>
+
 namespace jac {
 namespace {
 
@@ -158,7 +160,14 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
       } else if (col < n && myrows > 0) {
         const char* base = B.stages + s * kStageBytes + rh * kRowsPerWarp * kRowBytes +
                            co * static_cast<int>(sizeof(TM));
-        if (col + V <= n) {
+        if (std::is_same<TM, double>::value && col + V <= n && myrows >= kRowsPerWarp) {
+          // full rows of a full group: all loads first, then the rows' products interleaved, so a warp has
+          // kRowsPerWarp independent accumulations in flight (each row's order of operations is unchanged)
+          uint4 m[kRowsPerWarp];
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r) m[r] = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+          seg_dot_rows(acc, m, xv);
+        } else if (col + V <= n) {
 #pragma unroll
           for (int r = 0; r < kRowsPerWarp; ++r)
             if (r < myrows) {
@@ -237,19 +246,39 @@ __device__ void consume_phase_split(const Block& B, uint32_t& u, const float2* x
       } else if (col < n && myrows > 0) {
         const bool two = col + 1 < n;  // the straddling segment's padding element is skipped
         const char* base = B.stages + s * kStageBytes + rh * kRowsPerWarp * kRowBytes + co * 8;
+        if (two && myrows >= kRowsPerWarp) {
+          // full group, both elements: the rows' steps interleaved (each row's order unchanged)
+          uint4 m[kRowsPerWarp];
 #pragma unroll
-        for (int r = 0; r < kRowsPerWarp; ++r)
-          if (r < myrows) {
-            const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
-            float ah, al;
-            split_scaled(__hiloint2double(static_cast<int>(m.y), static_cast<int>(m.x)), sh[r], ah, al);
-            ff_fma(acc[r], ah, al, xv.x, xv.y);
-            if (two) {
-              split_scaled(__hiloint2double(static_cast<int>(m.w), static_cast<int>(m.z)), sh[r], ah, al);
-              ff_fma(acc[r], ah, al, xv.z, xv.w);
+          for (int r = 0; r < kRowsPerWarp; ++r) m[r] = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+          float ah[kRowsPerWarp], al[kRowsPerWarp];
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            split_scaled(__hiloint2double(static_cast<int>(m[r].y), static_cast<int>(m[r].x)), sh[r], ah[r], al[r]);
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r) ff_fma(acc[r], ah[r], al[r], xv.x, xv.y);
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            split_scaled(__hiloint2double(static_cast<int>(m[r].w), static_cast<int>(m[r].z)), sh[r], ah[r], al[r]);
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r) ff_fma(acc[r], ah[r], al[r], xv.z, xv.w);
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r) ff_renorm(acc[r]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < kRowsPerWarp; ++r)
+            if (r < myrows) {
+              const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+              float ah, al;
+              split_scaled(__hiloint2double(static_cast<int>(m.y), static_cast<int>(m.x)), sh[r], ah, al);
+              ff_fma(acc[r], ah, al, xv.x, xv.y);
+              if (two) {
+                split_scaled(__hiloint2double(static_cast<int>(m.w), static_cast<int>(m.z)), sh[r], ah, al);
+                ff_fma(acc[r], ah, al, xv.z, xv.w);
+              }
+              ff_renorm(acc[r]);
             }
-            ff_renorm(acc[r]);
-          }
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.ring->empty[s]);
