@@ -69,15 +69,16 @@ def src_hash(kernel: str = ""):
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+def committed_traffic(kernel: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source and
+    the same system size."""
     try:
         with open(TRAFFIC_FILE) as fh:
             t = json.load(fh)
     except OSError:
         return None
     e = t.get(kernel)
-    if not e or e.get("source_sha256_16") != src_hash(kernel):
+    if not e or e.get("source_sha256_16") != src_hash(kernel) or e.get("n") != n:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -211,7 +212,7 @@ def run_ours(args, world, rank, local):
     kname = {"bf16_ir": "ir_solve_kernel<__nv_bfloat16>", "fp8_ir": "ir_solve_kernel<__nv_fp8_e4m3>",
              "fp32_ir": "ir_solve_kernel<float>", "fp64": "fp64_solve_kernel",
              "fp64+gs": "gs_solve_kernel"}[args.precision]
-    traffic = committed_traffic(kname)
+    traffic = committed_traffic(kname, n)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": bytes_launch, "kernel_ms": round(main["kernel_ms"], 4),
@@ -246,7 +247,8 @@ def run_ours(args, world, rank, local):
                                f"one step = setup + solve",
                    "n": n, "dominance": f, "nrhs": 1, "precision": args.precision, "global_batch": world,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs (2.15 GB A) larger than the 129 MB L2; no flush"},
+                   "l2": f"inputs ({8 * n * n / 1e9:.2f} GB A) larger than the 129 MB L2; no flush"
+                         if 8 * n * n > 129e6 else "A fits in the 129 MB L2 (small case; not the bench workload)"},
         "gpu_launches": (4 if not args.precision.startswith("fp64") else 3) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,

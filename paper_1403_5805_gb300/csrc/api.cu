@@ -229,14 +229,21 @@ int prepare(jacobi_handle* h, const double* A, int64_t lda, const double* B, boo
   }
   unsigned long long* keys = h->at<unsigned long long>(h->L.keys);
   CK(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long), s));       // diagonal-check key
-  CK(cudaMemsetAsync(h->at<char>(h->L.bnorm), 0, sizeof(double), s));   // ||B|| bits
-  CK(cudaMemsetAsync(h->at<char>(h->L.cmax), 0, sizeof(double), s));    // max |b_i / a_ii| bits
   CK(launch_diag(h->A64, h->lda64, n, h->at<double>(h->L.d), h->at<double>(h->L.rinv), keys, s));
   double* b = h->at<double>(h->L.b);
   if (B != b && !is_device_memory(B)) {
     CK(cudaMemcpyAsync(b, B, n * sizeof(double), cudaMemcpyHostToDevice, s));
     B = b;
   }
+  // The diagonal decides the return value, so it is checked before the remaining setup work is queued;
+  // that work (the narrow copy above all) then runs while the caller goes on to launch the solve.  Every
+  // read of caller memory (A and B) is complete at this synchronisation.
+  unsigned long long key = 0;
+  CK(cudaMemcpyAsync(&key, keys, sizeof(key), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (key != ~0ull) return (key & 0xFF) == 2 ? JACOBI_ERR_ZERO_DIAGONAL : JACOBI_ERR_NONFINITE;
+  CK(cudaMemsetAsync(h->at<char>(h->L.bnorm), 0, sizeof(double), s));   // ||B|| bits
+  CK(cudaMemsetAsync(h->at<char>(h->L.cmax), 0, sizeof(double), s));    // max |b_i / a_ii| bits
   CK(launch_rhs(B, n, h->at<double>(h->L.rinv), b, h->at<unsigned long long>(h->L.bnorm),
                 h->at<unsigned long long>(h->L.cmax), s));
   // vectors start zeroed so that every padding entry is 0
@@ -252,10 +259,6 @@ int prepare(jacobi_handle* h, const double* A, int64_t lda, const double* B, boo
                      h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac),
                      h->split_residual ? h->at<int>(h->L.rexp) : nullptr, s));
   if (h->method == JACOBI_METHOD_SOR) CK(launch_gs_row_exponents(h->A64, h->lda64, n, h->at<int>(h->L.rexp), s));
-  unsigned long long key = 0;
-  CK(cudaMemcpyAsync(&key, keys, sizeof(key), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (key != ~0ull) return (key & 0xFF) == 2 ? JACOBI_ERR_ZERO_DIAGONAL : JACOBI_ERR_NONFINITE;
   return JACOBI_OK;
 }
 
