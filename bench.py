@@ -207,6 +207,9 @@ def run_ours(args, world, rank, local):
     es = ESIZE[args.precision.replace("+gs", "")]
     outer_with_matrix = max(st["outer_steps"] - 1, 0)  # X0 = 0: the first residual needs no matrix pass
     bytes_launch = outer_with_matrix * 8.0 * n * n + st["sweeps"] * es * float(n) * n
+    fused = "narrow_inner" in main["phases"]  # that sweep also reads FP64 A (and writes the narrow copy)
+    if fused:
+        bytes_launch += 8.0 * n * n
     peaks, peak_kind = measured_peaks()
     achieved = bytes_launch / (main["kernel_ms"] * 1e-3) / 1e9
     kname = {"bf16_ir": "ir_solve_kernel<__nv_bfloat16>", "fp8_ir": "ir_solve_kernel<__nv_fp8_e4m3>",
@@ -249,7 +252,9 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": f"inputs ({8 * n * n / 1e9:.2f} GB A) larger than the 129 MB L2; no flush"
                          if 8 * n * n > 129e6 else "A fits in the 129 MB L2 (small case; not the bench workload)"},
-        "gpu_launches": (4 if not args.precision.startswith("fp64") else 3) * args.steps,
+        # per step: diagonal check, right-hand side, (narrow copy,) solve; BF16 / FP32 inner sweeps write
+        # their narrow copy inside the solve kernel
+        "gpu_launches": (3 if args.precision.startswith("fp64") or fused else 4) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
         "sparse": sparse,
@@ -264,7 +269,8 @@ def phase_bandwidth(trace, n, prec):
     prec = prec.replace("+split", "").replace("+gs", "")
     """Per-phase-kind mean duration and algorithmic matrix bandwidth from the device-side trace of the
     last solve (each phase streams the whole matrix once: FP64 A, or the narrow copy)."""
-    names = {0: ("sweep64", 8), 1: ("resid64", 8), 2: ("resid0", 0), 3: ("inner", ESIZE.get(prec, 8))}
+    names = {0: ("sweep64", 8), 1: ("resid64", 8), 2: ("resid0", 0), 3: ("inner", ESIZE.get(prec, 8)),
+             4: ("narrow_inner", 8 + ESIZE.get(prec, 8))}  # reads FP64 A, writes the narrow copy
     out = {}
     for kind, (name, es) in names.items():
         d = [(e - b) for k, b, e in trace if k == kind]
@@ -286,6 +292,8 @@ def summarize(r, steps, n, prec):
         bytes_launch = st["sweeps"] * 8.0 * n * n
     else:
         bytes_launch = max(st["outer_steps"] - 1, 0) * 8.0 * n * n + st["sweeps"] * es * float(n) * n
+        if "narrow_inner" in r["phases"]:
+            bytes_launch += 8.0 * n * n
     return {"solves_per_s": round(1e3 / ms, 3), "ms_per_solve": round(ms, 4), "kernel_ms": round(r["kernel_ms"], 4),
             "sweeps": st["sweeps"], "outer_steps": st["outer_steps"], "status": st["status"],
             "rel_residual": r["rel_residual_check"], "err_vs_xstar": r["err_vs_xstar"],

@@ -234,6 +234,8 @@ JACOBI_API int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_ds
 #define JACOBI_PHASE_RESID64 1  /* FP64 residual r = B - A X over A */
 #define JACOBI_PHASE_RESID0 2   /* residual of a zero start vector (r = B, no matrix pass) */
 #define JACOBI_PHASE_INNER 3    /* inner sweep over the narrow copy of A */
+#define JACOBI_PHASE_NARROW_INNER 4 /* first inner sweep of a handle's first solve (BF16 / FP32 inner sweeps):
+                                       reads FP64 A, writes the narrow copy and sweeps over the rounded values */
 JACOBI_API int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap,
                                  int32_t* count);
 

@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": FP64, "fp32_ir": FP32_IR, "bf16_ir": BF16_IR, "fp8_ir": FP
 # jacobi_norm
 NORM_INF, NORM_2, NORM_RESID = 0, 1, 2
 # trace phase kinds (JACOBI_PHASE_*)
-PHASE_SWEEP64, PHASE_RESID64, PHASE_RESID0, PHASE_INNER = 0, 1, 2, 3
+PHASE_SWEEP64, PHASE_RESID64, PHASE_RESID0, PHASE_INNER, PHASE_NARROW_INNER = 0, 1, 2, 3, 4
 NORMS = {"inf": NORM_INF, "2": NORM_2, "resid": NORM_RESID}
 FLAG_COPY_A = 1
 FLAG_SPLIT_RESIDUAL = 2

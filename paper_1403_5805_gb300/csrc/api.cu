@@ -73,8 +73,8 @@ bool can_borrow(const jacobi_desc* d) {
 // Offsets of every sub-buffer inside one workspace allocation.
 struct Layout {
   int64_t ld;  // padded length of vectors and row stride of owned matrices
-  size_t A64, Nlow, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, gsflags, gsmbox, ctl, keys,
-      stats, total;
+  size_t A64, Nlow, nready, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, gsflags,
+      gsmbox, ctl, keys, stats, total;
 };
 
 Layout make_layout(int64_t n, int precision, bool copy_A) {
@@ -91,6 +91,7 @@ Layout make_layout(int64_t n, int precision, bool copy_A) {
   L.A64 = copy_A ? take(static_cast<size_t>(n) * L.ld * sizeof(double)) : 0;
   const size_t ns = narrow_size(precision);
   L.Nlow = ns ? take(static_cast<size_t>(n) * L.ld * ns) : 0;
+  L.nready = take(sizeof(int));  // nonzero once the narrow copy and rowfac hold this handle's A
   L.b = take(vd);
   L.d = take(vd);
   L.rinv = take(vd);
@@ -194,6 +195,7 @@ struct jacobi_handle {
   int max_inner = 1000;
   float inner_rtol = 0.0f;
   bool split_residual = false;
+  bool fuse_narrow = false;  // the narrow copy is written by the first inner sweep of the first solve
   bool retire_columns = false;
   int method = JACOBI_METHOD_JACOBI;
   double omega = 1.0;
@@ -209,6 +211,15 @@ struct jacobi_handle {
 };
 
 namespace {
+
+// The setup pass that writes the narrow copy of A (and rowfac, scale, rexp) and marks it written.
+cudaError_t write_narrow(jacobi_handle* h) {
+  cudaError_t e = launch_narrow(narrow_kind(h->precision), h->A64, h->lda64, h->n, h->at<void>(h->L.Nlow), h->L.ld,
+                                h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac),
+                                h->split_residual ? h->at<int>(h->L.rexp) : nullptr, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->at<char>(h->L.nready), 1, sizeof(int), h->stream);
+  return e;
+}
 
 // Runs the preparation kernels on h's stream.  A and B are device pointers (or, for the host-pointer
 // entry point, A has already been placed in the workspace and B in b).
@@ -254,10 +265,8 @@ int prepare(jacobi_handle* h, const double* A, int64_t lda, const double* B, boo
   CK(cudaMemsetAsync(h->at<char>(h->L.c1), 0, h->L.ld * sizeof(float), s));
   CK(cudaMemsetAsync(h->at<char>(h->L.da), 0, h->L.ld * sizeof(float), s));
   CK(cudaMemsetAsync(h->at<char>(h->L.db), 0, h->L.ld * sizeof(float), s));
-  if (h->precision != JACOBI_FP64)
-    CK(launch_narrow(narrow_kind(h->precision), h->A64, h->lda64, n, h->at<void>(h->L.Nlow), h->L.ld,
-                     h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac),
-                     h->split_residual ? h->at<int>(h->L.rexp) : nullptr, s));
+  CK(cudaMemsetAsync(h->at<char>(h->L.nready), 0, sizeof(int), s));
+  if (h->precision != JACOBI_FP64 && !h->fuse_narrow) CK(write_narrow(h));
   if (h->method == JACOBI_METHOD_SOR) CK(launch_gs_row_exponents(h->A64, h->lda64, n, h->at<int>(h->L.rexp), s));
   return JACOBI_OK;
 }
@@ -307,6 +316,10 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
       d->inner_rtol > 0 ? d->inner_rtol : (d->precision == JACOBI_FP8_IR ? 1.0 / 64 : 1.0 / 1024));
   h->split_residual = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) && d->precision != JACOBI_FP64;
   h->retire_columns = (d->flags & JACOBI_FLAG_RETIRE_COLUMNS) && d->nrhs > 1;
+  // BF16 / FP32 copies need no row scale, so a single-right-hand-side solve can round A while it streams
+  // it for its first inner sweep instead of a separate setup pass over A
+  h->fuse_narrow = d->nrhs == 1 && d->method == JACOBI_METHOD_JACOBI && !h->split_residual &&
+                   (d->precision == JACOBI_BF16_IR || d->precision == JACOBI_FP32_IR);
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
   h->test_drop_copy = (d->flags & JACOBI_FLAG_TEST_DROP_COPY) ? 1 : 0;
   h->test_skip_arrival = (d->flags & JACOBI_FLAG_TEST_SKIP_ARRIVAL) ? 1 : 0;
@@ -905,6 +918,9 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
   p.lda = h->lda64;
   p.Nlow = h->precision != JACOBI_FP64 ? h->at<void>(h->L.Nlow) : nullptr;
   p.ldn = h->L.ld;
+  p.Nlow_w = h->precision != JACOBI_FP64 ? h->at<void>(h->L.Nlow) : nullptr;
+  p.nready = h->fuse_narrow ? h->at<int>(h->L.nready) : nullptr;
+  p.rowfac_w = h->at<float>(h->L.rowfac);
   p.b = h->at<double>(h->L.b);
   p.d = h->at<double>(h->L.d);
   p.rinv = h->at<double>(h->L.rinv);
@@ -1038,6 +1054,12 @@ int jacobi_residual(jacobi_handle* h, const double* X, double* rel_out) {
 int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* scale_host) {
   if (!h || !dst_host || ld_dst < h->n || h->precision == JACOBI_FP64) return JACOBI_ERR_INVALID_ARG;
   const size_t es = narrow_size(h->precision);
+  if (h->fuse_narrow) {  // not written yet if no solve has run an inner sweep: write it now
+    int ready = 0;
+    CK(cudaMemcpyAsync(&ready, h->at<int>(h->L.nready), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (!ready) CK(write_narrow(h));
+  }
   CK(cudaMemcpy2DAsync(dst_host, ld_dst * es, h->at<char>(h->L.Nlow), h->L.ld * es, h->n * es, h->n,
                        cudaMemcpyDeviceToHost, h->stream));
   if (scale_host) {

@@ -62,6 +62,9 @@ __device__ void produce_phase(const Block& B, uint32_t& u, const TM* M, int64_t 
   constexpr int K = chunk_cols<TM>();
   const int lane = threadIdx.x & 31;
   const int64_t nch = (n + K - 1) / K;
+  // order this phase's bulk copies after generic-proxy writes of the matrix seen at the last grid barrier
+  // (the narrow copy written by a fused first inner sweep)
+  fence_proxy_async_global();
   for (int64_t g0 = r0; g0 < r1; g0 += kRows) {
     const int rows = static_cast<int>(i64min(kRows, r1 - g0));
     for (int64_t c = 0; c < nch; ++c) {
@@ -302,6 +305,93 @@ __device__ void consume_phase_split(const Block& B, uint32_t& u, const float2* x
   }
 }
 
+// The narrow copy of two FP64 entries of a row (FP64 -> FP32 -> TL, both to nearest even, the setup's
+// rounding), stored at dst, and the two values as FP32.
+__device__ __forceinline__ float2 store_narrow_pair(__nv_bfloat16* dst, float f0, float f1) {
+  const __nv_bfloat162 q = __floats2bfloat162_rn(f0, f1);
+  *reinterpret_cast<__nv_bfloat162*>(dst) = q;
+  return __bfloat1622float2(q);
+}
+__device__ __forceinline__ float2 store_narrow_pair(float* dst, float f0, float f1) {
+  *reinterpret_cast<float2*>(dst) = make_float2(f0, f1);
+  return make_float2(f0, f1);
+}
+
+// First inner sweep of a solve on a handle whose narrow copy is not written yet: the ring streams FP64 A
+// (items of consume_phase<double>), each lane rounds its two entries of every row to the narrow type,
+// stores them (zero on the diagonal and in the row padding up to ldn), and accumulates the inner-sweep
+// dot product of the rounded values with x in FP32.  The reduction and epilogue are consume_phase's.
+template <typename TL, typename Epi>
+__device__ void consume_phase_narrow(const Block& B, uint32_t& u, const float* x, int64_t n, int64_t r0, int64_t r1,
+                                     TL* N, int64_t ldn, float (*red)[kConsumerWarps][kRowsPerWarp], Epi& epi) {
+  constexpr int K = chunk_cols<double>();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cw = warp % kColWarps, rh = warp / kColWarps;
+  const int co = (cw * 32 + lane) * 2;  // first of this lane's two columns inside a chunk
+  const int64_t nch = (n + K - 1) / K;  // K is a multiple of 16, so the chunks also cover the padding to ldn
+  int grp = 0;
+  for (int64_t g0 = r0; g0 < r1; g0 += kRows, ++grp) {
+    const int rows = static_cast<int>(i64min(kRows, r1 - g0));
+    const int myrows = rows - rh * kRowsPerWarp;
+    if (warp == 0 && lane < rows) epi.prefetch(g0 + lane);
+    const int64_t i0 = g0 + rh * kRowsPerWarp;  // this warp's first row
+    float acc[kRowsPerWarp];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r) acc[r] = 0.0f;
+    // x[col], x[col + 1] (the iterate buffers are zero past n up to their padded length)
+    float2 xv = make_float2(0.f, 0.f), xn = xv;
+    if (nch > 0 && co < n) xv = __ldcg(reinterpret_cast<const float2*>(x + co));
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t col = c * K + co;
+      const int64_t ncol = col + K;
+      xn = make_float2(0.f, 0.f);
+      if (c + 1 < nch && ncol < n) xn = __ldcg(reinterpret_cast<const float2*>(x + ncol));
+      const int s = static_cast<int>(u % kStages);
+      const uint32_t par = (u / kStages) & 1u;
+      bool ok = (*B.abort == 0);
+      if (ok) ok = mbar_wait(&B.ring->full[s], par, B.wait_ns);
+      if (!ok) {
+        raise_abort(B);
+      } else if (col < ldn && myrows > 0) {
+        const char* base = B.stages + s * kStageBytes + rh * kRowsPerWarp * kRowBytes + co * 8;
+#pragma unroll
+        for (int r = 0; r < kRowsPerWarp; ++r)
+          if (r < myrows) {
+            const int64_t i = i0 + r;
+            float f0 = 0.0f, f1 = 0.0f;
+            if (col < n) {  // entries at or past n were not copied into the stage (and may be anything in A)
+              const uint4 m = *reinterpret_cast<const uint4*>(base + r * kRowBytes);
+              if (col != i) f0 = __double2float_rn(__hiloint2double(static_cast<int>(m.y), static_cast<int>(m.x)));
+              if (col + 1 < n && col + 1 != i)
+                f1 = __double2float_rn(__hiloint2double(static_cast<int>(m.w), static_cast<int>(m.z)));
+            }
+            const float2 q = store_narrow_pair(N + i * ldn + col, f0, f1);
+            if (col < n) {
+              acc[r] = fmaf(q.x, xv.x, acc[r]);
+              acc[r] = fmaf(q.y, xv.y, acc[r]);
+            }
+          }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.ring->empty[s]);
+      ++u;
+      xv = xn;
+    }
+    const float part = transpose_reduce8(acc, lane);
+    if ((lane & 3) == 0) red[grp & 1][warp][row_of_lane(lane)] = part;
+    named_barrier(1, kConsumers);
+    if (warp == 0 && lane < rows) {
+      const int half = lane / kRowsPerWarp, r = lane % kRowsPerWarp;
+      float dot = red[grp & 1][half * kColWarps][r];
+#pragma unroll
+      for (int w = 1; w < kColWarps; ++w) dot += red[grp & 1][half * kColWarps + w][r];  // fixed order
+      epi.row(g0 + lane, dot);
+    }
+  }
+  // the narrow copy was written through the generic proxy and is read by bulk copies in later phases
+  fence_proxy_async_global();
+}
+
 // Wait for every bulk copy this producer issued (the last kStages items) before the CTA exits.
 __device__ void drain_ring(const Block& B, uint32_t u_issued) {
   const uint32_t first = u_issued > kStages ? u_issued - kStages : 0;
@@ -523,6 +613,8 @@ struct ResidEpi {
 struct InnerEpi {
   const float* c1;
   const float* rowfac;
+  const double* rinv;  // fused first sweep: the factor is fl32(1/a_ii), written to rowfac_out
+  float* rowfac_out;
   const float* dc;
   float* dn;
   const double* xc;
@@ -534,7 +626,12 @@ struct InnerEpi {
   double px;
   __device__ __forceinline__ void prefetch(int64_t i) {
     pc = c1[i];
-    pf = rowfac[i];
+    if (rinv) {
+      pf = __double2float_rn(rinv[i]);
+      rowfac_out[i] = pf;
+    } else {
+      pf = rowfac[i];
+    }
     pd = dc[i];
     px = xc[i];
   }
@@ -554,11 +651,13 @@ enum Kind : int { kResid = 0, kInner = 1, kDone = 2 };
 
 template <typename TL>
 __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
+  // E4M3 rows need their row scale before any entry is encoded, so that copy is always written by setup
+  constexpr bool kFusable = !std::is_same<TL, __nv_fp8_e4m3>::value;
   extern __shared__ unsigned char smem_raw[];
   __shared__ Ring ring;
   __shared__ double red64[2][kConsumerWarps][kRowsPerWarp];
   __shared__ float red32[2][kConsumerWarps][kRowsPerWarp];
-  __shared__ int s_abort, s_kind, s_xcur, s_dcur, s_first;
+  __shared__ int s_abort, s_kind, s_xcur, s_dcur, s_first, s_fuse;
   char* stages = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
 
   const int G = gridDim.x;
@@ -570,6 +669,9 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
     s_xcur = 0;
     s_dcur = 0;
     s_first = 1;
+    // the narrow copy is still to be written: the first inner sweep writes it (every CTA reads the flag
+    // here, before the grid barrier that precedes CTA 0's update of it)
+    s_fuse = kFusable && p.nready != nullptr && *reinterpret_cast<volatile const int*>(p.nready) == 0;
   }
   init_ring(&ring);
   __syncthreads();
@@ -607,8 +709,21 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
       }
       v0 = epi.mr;
       v1 = epi.mc;
+    } else if (s_fuse) {
+      if constexpr (kFusable) {
+        InnerEpi epi{p.c1, p.rowfac, p.rinv, p.rowfac_w, dc, dn, xc, xalt, p.rexp ? xsalt : nullptr, xg, 0ull, 0ull,
+                     0.f, 0.f, 0.f, 0.0};
+        if (producer) {
+          produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
+        } else {
+          consume_phase_narrow<TL>(B, u, dc, p.n, r0, r1, static_cast<TL*>(p.Nlow_w), p.ldn, red32, epi);
+        }
+        v0 = epi.mchg;
+        v1 = epi.mmag;
+      }
     } else {
-      InnerEpi epi{p.c1, p.rowfac, dc, dn, xc, xalt, p.rexp ? xsalt : nullptr, xg, 0ull, 0ull, 0.f, 0.f, 0.f, 0.0};
+      InnerEpi epi{p.c1, p.rowfac, nullptr, nullptr, dc, dn, xc, xalt, p.rexp ? xsalt : nullptr, xg, 0ull, 0ull,
+                   0.f, 0.f, 0.f, 0.0};
       if (producer) {
         produce_phase<TL>(B, u, Nl, p.ldn, p.n, r0, r1);
       } else {
@@ -626,7 +741,8 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (lane == 0) {
         trace_phase(p.ctl, phase,
-                    kind == kInner ? JACOBI_PHASE_INNER : (skip_matrix ? JACOBI_PHASE_RESID0 : JACOBI_PHASE_RESID64));
+                    kind == kInner ? (s_fuse ? JACOBI_PHASE_NARROW_INNER : JACOBI_PHASE_INNER)
+                                   : (skip_matrix ? JACOBI_PHASE_RESID0 : JACOBI_PHASE_RESID64));
         const double g0v = bits_to_double(ld_cg_u64(&p.ctl->red[phase % 3][0]));
         const double g1v = bits_to_double(ld_cg_u64(&p.ctl->red[phase % 3][1]));
         int next = kDone;
@@ -648,6 +764,10 @@ __global__ void __maxnreg__(kMaxRegs) ir_solve_kernel(SolveParams p) {
             s_dcur = 0;  // delta^(1) was written into da
           }
         } else {
+          if (s_fuse) {  // every CTA passed the barrier after writing its rows of the narrow copy
+            s_fuse = 0;
+            if (blockIdx.x == 0) *reinterpret_cast<volatile int*>(p.nready) = 1;
+          }
           ++inner_total;
           ++inner_step;
           last_change = g0v;

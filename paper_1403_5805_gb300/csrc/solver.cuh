@@ -64,6 +64,9 @@ struct SolveParams {
   int64_t lda;
   const void* Nlow;       // IR: narrow off-diagonal copy, row stride ldn, zero diagonal
   int64_t ldn;
+  void* Nlow_w;           // the same buffer, written by the first inner sweep when *nready == 0
+  int* nready;            // BF16 / FP32 inner sweeps: 0 until the narrow copy and rowfac are written; else NULL
+  float* rowfac_w;        // rowfac, written with the narrow copy
   const double* b;        // n
   const double* d;        // n, a_ii
   const double* rinv;     // n, 1 / a_ii (correctly rounded)
