@@ -161,7 +161,8 @@ MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
   M.dah = take(v2);
   M.dbh = take(v2);
   M.colmax = take(static_cast<size_t>(r) * 8);
-  M.colsq = take(static_cast<size_t>((ld + 63) / 64) * r * 8);  // per 64-row tile and column (Euclidean norm)
+  // Euclidean norm: per row tile of the FP64 dense pass and column
+  M.colsq = take(static_cast<size_t>((ld + kMrhsDenseRows - 1) / kMrhsDenseRows) * r * 8);
   M.bcol = take(static_cast<size_t>(r) * 8);
   M.stats = take(16);
   M.status = take(16);
@@ -449,7 +450,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
   if (h->precision == JACOBI_FP64) {
     const int resid = h->norm == JACOBI_NORM_RESID;
     const bool eucl = h->norm == JACOBI_NORM_2;
-    const int64_t tiles = (n + 63) / 64;
+    const int64_t tiles = (n + kMrhsDenseRows - 1) / kMrhsDenseRows;
     double* colsq = h->at<double>(h->M.colsq);
     std::vector<double> hs(eucl ? static_cast<size_t>(tiles * r) : 0);
     for (int64_t k = 1;; ++k) {

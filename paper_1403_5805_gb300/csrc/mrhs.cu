@@ -246,60 +246,67 @@ constexpr int kDThreads = 256;
 // Column worked on by tile column c (c < nact).
 __device__ __forceinline__ int col_of(const MrhsDenseParams& p, int c) { return p.cols ? __ldg(p.cols + c) : c; }
 
+// FP64 dense pass tiles: 32 rows x 64 columns per block, so that the 1024 row tiles of n = 32768 spread
+// over the SMs within a few percent (64-row tiles left a quarter of the SMs with 4 blocks and the rest
+// with 3, and the FP64 pipes of the busier SMs set the time).
+constexpr int kFM = kMrhsDenseRows;
+constexpr int kFN = 64;
+constexpr int kFK = 32;
+
 // mode 0: residual R = B - A X; writes C1 = R / a_ii (FP32), delta^(1) = C1 (FP32 + BF16), and the
 //         per-column max |R|.
 // mode 1: FP64 Jacobi sweep X^(k) = (B - A X + a_ii x_i) / a_ii; writes X^(k) and the max |change|.
 __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p) {
-  __shared__ double As[kDK][kDM + 1];
-  __shared__ double Xs[kDK][kDN + 1];
+  __shared__ double As[kFK][kFM + 1];
+  __shared__ double Xs[kFK][kFN + 1];
   const int tid = threadIdx.x;
-  const int tr = tid / 16, tc = tid % 16;  // 16 x 16 threads, each 4 rows x 4 columns
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kDM;
-  const int c0 = blockIdx.y * kDN;
-  double acc[4][4];
+  const int tr = tid / 32, tc = tid % 32;  // 8 x 32 threads, each 4 rows (tr + 8u) x 2 columns (tc + 32v)
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kFM;
+  const int c0 = blockIdx.y * kFN;
+  double acc[4][2];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  for (int64_t k0 = 0; k0 < p.n; k0 += kDK) {
-    // A tile: kDM rows x kDK columns (row-major A), stored transposed As[k][m]
-    for (int e = tid; e < kDM * kDK; e += kDThreads) {
-      const int m = e / kDK, k = e % kDK;
+    for (int b = 0; b < 2; ++b) acc[a][b] = 0.0;
+  for (int64_t k0 = 0; k0 < p.n; k0 += kFK) {
+    // A tile: kFM rows x kFK columns (row-major A), stored transposed As[k][m]
+    for (int e = tid; e < kFM * kFK; e += kDThreads) {
+      const int m = e / kFK, k = e % kFK;
       const int64_t gi = m0 + m, gk = k0 + k;
       As[k][m] = (gi < p.n && gk < p.n) ? __ldg(p.A + gi * p.lda + gk) : 0.0;
     }
-    // X tile: kDK rows x kDN columns from the column-major X (x[c*ld + k])
-    for (int e = tid; e < kDK * kDN; e += kDThreads) {
-      const int c = e / kDK, k = e % kDK;
+    // X tile: kFK rows x kFN columns from the column-major X (x[c*ld + k])
+    for (int e = tid; e < kFK * kFN; e += kDThreads) {
+      const int c = e / kFK, k = e % kFK;
       const int64_t gk = k0 + k;
       Xs[k][c] = (gk < p.n && c0 + c < p.nact) ? p.x[static_cast<int64_t>(col_of(p, c0 + c)) * p.ld + gk] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int k = 0; k < kDK; ++k) {
-      double a[4], x[4];
+    for (int k = 0; k < kFK; ++k) {
+      double a[4], x[2];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[k][tr + 16 * u];
+      for (int u = 0; u < 4; ++u) a[u] = As[k][tr + 8 * u];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = Xs[k][tc + 16 * u];
+      for (int v = 0; v < 2; ++v) x[v] = Xs[k][tc + 32 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], x[v], acc[u][v]);
+        for (int v = 0; v < 2; ++v) acc[u][v] = fma(a[u], x[v], acc[u][v]);
     }
     __syncthreads();
   }
-  unsigned long long mloc[4] = {0, 0, 0, 0};
-  double sq[4] = {0.0, 0.0, 0.0, 0.0};
+  unsigned long long mloc[2] = {0, 0};
+  double sq[2] = {0.0, 0.0};
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const int64_t i = m0 + tr + 16 * u;
+    const int64_t i = m0 + tr + 8 * u;
     if (i >= p.n) continue;
     const double di = p.d[i], ri = p.rinv[i];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      if (c0 + tc + 16 * v >= p.nact) continue;
-      const int c = col_of(p, c0 + tc + 16 * v);
+    for (int v = 0; v < 2; ++v) {
+      if (c0 + tc + 32 * v >= p.nact) continue;
+      const int c = col_of(p, c0 + tc + 32 * v);
       const int64_t o = static_cast<int64_t>(c) * p.ld + i;
       const double b = p.b[o];
       if (p.mode == 0) {
@@ -322,20 +329,20 @@ __global__ void __launch_bounds__(kDThreads) mrhs_dense_kernel(MrhsDenseParams p
     }
   }
   if (p.colsq) {
-    // the tile's 16 row groups summed per column in a fixed order (As is free after the last K step)
-    double* part = &As[0][0];  // [16][kDN + 1]
+    // the tile's 8 row groups summed per column in a fixed order (As is free after the last K step)
+    double* part = &As[0][0];  // [8][kFN + 1]
 #pragma unroll
-    for (int v = 0; v < 4; ++v) part[tr * (kDN + 1) + tc + 16 * v] = sq[v];
+    for (int v = 0; v < 2; ++v) part[tr * (kFN + 1) + tc + 32 * v] = sq[v];
     __syncthreads();
-    if (tid < kDN && c0 + tid < p.nact) {
+    if (tid < kFN && c0 + tid < p.nact) {
       double t = 0.0;
-      for (int g = 0; g < 16; ++g) t += part[g * (kDN + 1) + tid];
+      for (int g = 0; g < 8; ++g) t += part[g * (kFN + 1) + tid];
       p.colsq[static_cast<int64_t>(blockIdx.x) * p.r + col_of(p, c0 + tid)] = t;
     }
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v)
-    if (c0 + tc + 16 * v < p.nact && mloc[v]) atomicMax(p.colmax + col_of(p, c0 + tc + 16 * v), mloc[v]);
+  for (int v = 0; v < 2; ++v)
+    if (c0 + tc + 32 * v < p.nact && mloc[v]) atomicMax(p.colmax + col_of(p, c0 + tc + 32 * v), mloc[v]);
 }
 
 // ------------------------------------------------- split-float residual pass (FP32 units), all r columns
@@ -545,7 +552,7 @@ cudaError_t launch_mrhs_dense(const MrhsDenseParams& p, cudaStream_t s) {
       mrhs_split_resid_kernel<4><<<grid, kDThreads, 0, s>>>(p);
     return cudaGetLastError();
   }
-  const dim3 grid(static_cast<unsigned>((p.n + kDM - 1) / kDM), static_cast<unsigned>((p.nact + kDN - 1) / kDN));
+  const dim3 grid(static_cast<unsigned>((p.n + kFM - 1) / kFM), static_cast<unsigned>((p.nact + kFN - 1) / kFN));
   mrhs_dense_kernel<<<grid, kDThreads, 0, s>>>(p);
   return cudaGetLastError();
 }

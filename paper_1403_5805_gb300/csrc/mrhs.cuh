@@ -8,6 +8,9 @@
 
 namespace jac {
 
+// Rows per block of the FP64 dense pass (mrhs_dense_kernel); its Euclidean partials are per such tile.
+constexpr int kMrhsDenseRows = 32;
+
 // One inner sweep for r right-hand sides (vectors stored v[c*ld + i]).
 struct MrhsSweepParams {
   int64_t n, r, ld;
@@ -47,8 +50,8 @@ struct MrhsDenseParams {
   // active columns: tile column c works on column cols[c] (c < nact); NULL cols: all r columns
   const int* cols;
   int64_t nact;
-  // mode 1, Euclidean norm: the sum of squared changes of each 64-row tile and column, written (no
-  // atomics, a fixed summation order) at colsq[tile * r + c]; NULL: the maxima only
+  // mode 1, Euclidean norm: the sum of squared changes of each kMrhsDenseRows-row tile and column, written
+  // (no atomics, a fixed summation order) at colsq[tile * r + c]; NULL: the maxima only
   double* colsq;
 };
 
