@@ -128,7 +128,9 @@ __device__ __forceinline__ int row_of_lane(int lane) {
 // (i - group start); epi.prefetch(i) runs on the same lane when the group starts, so the epilogue's
 // operands arrive while the group streams.  Warp w covers column slice w % kColWarps of every chunk
 // and rows [8 * (w / kColWarps), +8) of the group.  with_matrix == false skips the matrix (dot = 0).
-template <typename TM, typename Epi>
+// kResident: the ring items of this CTA's rows were loaded by an earlier phase and stay in their stages
+// (every item of the phase has its own stage), so there is nothing to wait for and nothing to release.
+template <typename TM, typename Epi, bool kResident = false>
 __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTraits<TM>::X* x, int64_t n,
                               int64_t r0, int64_t r1, bool with_matrix,
                               typename MatTraits<TM>::Acc (*red)[kConsumerWarps][kRowsPerWarp], Epi& epi) {
@@ -157,7 +159,7 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
       const int s = static_cast<int>(u % kStages);
       const uint32_t par = (u / kStages) & 1u;
       bool ok = (*B.abort == 0);
-      if (ok) ok = mbar_wait(&B.ring->full[s], par, B.wait_ns);
+      if (ok && !kResident) ok = mbar_wait(&B.ring->full[s], par, B.wait_ns);
       if (!ok) {
         raise_abort(B);
       } else if (col < n && myrows > 0) {
@@ -188,7 +190,7 @@ __device__ void consume_phase(const Block& B, uint32_t& u, const typename MatTra
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&B.ring->empty[s]);
+      if (lane == 0 && !kResident) mbar_arrive(&B.ring->empty[s]);
       ++u;
 #pragma unroll
       for (int e = 0; e < V; ++e) xv[e] = xn[e];
@@ -500,13 +502,23 @@ __global__ void __maxnreg__(kMaxRegs) fp64_solve_kernel(SolveParams p) {
   uint32_t u = 0;
   int cur = 0;                    // buffer holding X^(k-1): 0 -> xa, 1 -> xb
   int64_t k = 1;
+  // Small systems: when every ring item of this CTA's rows has a stage of its own, the first sweep loads
+  // them and later sweeps reuse them from shared memory (A does not change between sweeps), so a sweep
+  // reads only the iterate from L2.
+  const int64_t items = (r1 - r0 + kRows - 1) / kRows * ((p.n + chunk_cols<double>() - 1) / chunk_cols<double>());
+  const bool resident = items <= kStages;
   double delta = 0.0;
   int status = kStatusNotConverged;
   for (;; ++k) {
     const double* xc = cur ? p.xb : p.xa;
     double* xn = cur ? p.xa : p.xb;
     Fp64SweepEpi epi{p.b, p.d, p.rinv, xc, xn, p.norm, 0ull, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (producer) {
+    if (resident && k > 1) {
+      if (!producer) {
+        uint32_t u0 = 0;  // the stages of the first sweep's items, in the same order
+        consume_phase<double, Fp64SweepEpi, true>(B, u0, xc, p.n, r0, r1, true, red, epi);
+      }
+    } else if (producer) {
       produce_phase<double>(B, u, p.A, p.lda, p.n, r0, r1);
     } else {
       consume_phase<double>(B, u, xc, p.n, r0, r1, true, red, epi);
