@@ -380,9 +380,10 @@ def run_batch(args, jac, torch, dev):
 
 def run_sparse(args, jac, torch, dev):
     """PDE-shaped sparse workload: the 5-point stencil of a variable-coefficient diffusion operator on an
-    N x N grid (N = --sparse-grid, 4.19 M unknowns by default), f = 1.05 (rho(T) <= 1/1.05), kept as a
-    sliced-ELL copy.  Times a fixed count of sweeps (per-sweep HBM rate against the measured copy rate)
-    and a full solve to max|dx| < 1e-12, and the CPU oracle on a few sweeps."""
+    N x N grid (N = --sparse-grid, 4.19 M unknowns by default), f = 1.05 (rho(T) <= 1/1.05), kept in the
+    format setup picks (DIA: the stencil's 4 diagonals, no column array).  Times a fixed count of sweeps
+    (per-sweep HBM rate against the measured copy rate) and a full solve to max|dx| < 1e-12, and the CPU
+    oracle on a few sweeps."""
     import synth
     N = args.sparse_grid
     rp, ci, v, B, Xs = synth.stencil_system((N, N), 1.05, seed=synth.BASE_SEED + 6)
@@ -415,7 +416,8 @@ def run_sparse(args, jac, torch, dev):
     tr = s.trace()
     per = sorted(b - a for a, b in tr[1:])  # the first sweep also holds the launch
     sweep_us = per[len(per) // 2] / 1e3
-    alg_bytes = 12.0 * nnz_off + 24.0 * n  # T values + columns, C, x read, x written
+    # T values (+ int32 columns in sliced ELL; DIA has none), C, x read, x written
+    alg_bytes = (8.0 if info["format"] == "dia" else 12.0) * nnz_off + 24.0 * n
     peaks, kind = measured_peaks()
     gbs = alg_bytes / (sweep_us * 1e-6) / 1e9
     ms_solve, st = timed(5000, 1e-12, 3)
@@ -452,7 +454,10 @@ def run_sparse(args, jac, torch, dev):
     cpu_ms_sweep = (_t.perf_counter() - t0) * 1e3 / k_cpu
     s.close()
     return {"workload": f"2-D 5-point variable-coefficient diffusion stencil, {N} x {N} grid, f = 1.05, "
-                        f"planted solution; sliced ELL (32-row slices)",
+                        f"planted solution; "
+                        + (f"DIA ({info['diagonals']} diagonals, 32-row slices)" if info["format"] == "dia"
+                           else "sliced ELL (32-row slices)"),
+            "format": info["format"],
             "n": n, "nnz": int(rp[-1]), "stored_slots": info["stored_slots"], "grid": info["grid"],
             "setup_ms": round(setup_ms, 3),
             "sweeps": {"count": int(st_fixed.sweeps), "ms_total": round(ms_fixed, 4),

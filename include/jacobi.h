@@ -177,6 +177,8 @@ typedef enum { JACOBI_METHOD_JACOBI = 0, JACOBI_METHOD_SOR = 1 } jacobi_method;
  * the FP64 sweeps and FP64 residual evaluations only touch the columns still active.  Per-column counts
  * come from jacobi_column_stats. */
 #define JACOBI_FLAG_RETIRE_COLUMNS 16
+/* Sparse handle: keep T in sliced ELL even when its entries lie on a few diagonals (see jacobi_csr_format). */
+#define JACOBI_FLAG_CSR_ELL 64
 
 /* Fill *d with defaults (n = 0 and null pointers: the caller sets those). */
 JACOBI_API void jacobi_desc_init(jacobi_desc* d);
@@ -469,9 +471,21 @@ JACOBI_API int jacobi_csr_solve(jacobi_csr* h, const double* X0, int64_t max_ite
 /* Outcome of the last solve (waits for it). */
 JACOBI_API int jacobi_csr_last_stats(jacobi_csr* h, jacobi_stats* stats);
 
-/* Layout facts for byte accounting: slots stored (off-diagonal entries plus slice padding), slices of
- * 32 rows, and the grid of the sweep kernel.  Any output may be NULL. */
+/* Layout facts for byte accounting: slots stored (off-diagonal entries plus slice padding; DIA: diagonals
+ * times n rounded up to whole slices), slices of 32 rows, and the grid of the sweep kernel.  Any output may
+ * be NULL. */
 JACOBI_API int jacobi_csr_info(jacobi_csr* h, int64_t* stored_slots, int64_t* slices, int32_t* grid);
+
+/* Storage of T chosen by setup.  JACOBI_CSR_ELL: sliced ELL (slices of 32 rows, each as wide as its
+ * longest row, values and int32 columns).  JACOBI_CSR_DIA: when every off-diagonal entry lies on one of at
+ * most 16 diagonals j - i = const and the band stores at most 1.25 times the slots of sliced ELL (banded
+ * and stencil matrices), T is kept diagonal by diagonal with no column array, absent entries as zeros,
+ * and the sweep gathers x_{i + offset} contiguously.  The sums run over the same entries in the same
+ * ascending column order either way (the zeros add nothing), so the iterates are the same.  *ndiag: the
+ * number of diagonals (0 for ELL).  Either output may be NULL. */
+#define JACOBI_CSR_ELL 0
+#define JACOBI_CSR_DIA 1
+JACOBI_API int jacobi_csr_format(jacobi_csr* h, int32_t* format, int32_t* ndiag);
 
 /* End time of each phase of the last solve, in nanoseconds since the solve started, and its kind, as
  * jacobi_last_trace: JACOBI_PHASE_SWEEP64 sweeps, or (mixed precision) JACOBI_PHASE_RESID64 residuals and

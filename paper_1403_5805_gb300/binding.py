@@ -32,6 +32,7 @@ FLAG_SPLIT_RESIDUAL = 2
 FLAG_SHORT_WAITS = 4
 FLAG_TEST_DROP_COPY = 8
 FLAG_TEST_SKIP_ARRIVAL = 32
+FLAG_CSR_ELL = 64  # sparse handle: keep sliced ELL even for a banded matrix
 FLAG_RETIRE_COLUMNS = 16
 METHODS = {"jacobi": 0, "sor": 1}
 
@@ -44,7 +45,7 @@ EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_stri
            "jacobi_server_step", "jacobi_server_poll", "jacobi_server_rounds", "jacobi_server_destroy",
            "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async", "jacobi_csr_solve",
            "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace", "jacobi_csr_destroy",
-           "jacobi_batch_solve", "jacobi_server_wait")
+           "jacobi_batch_solve", "jacobi_server_wait", "jacobi_csr_format")
 
 
 class JacobiStats(ctypes.Structure):
@@ -151,6 +152,7 @@ def load() -> ctypes.CDLL:
         lib.jacobi_csr_solve.argtypes = [H, vp, i64, dbl, vp, ctypes.POINTER(JacobiStats)]
         lib.jacobi_csr_last_stats.argtypes = [H, ctypes.POINTER(JacobiStats)]
         lib.jacobi_csr_info.argtypes = [H, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)]
+        lib.jacobi_csr_format.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
         lib.jacobi_csr_last_trace.argtypes = [H, vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
         lib.jacobi_batch_solve.argtypes = [i64, vp, vp, vp, vp, dbl, i64, i32, vp]
         lib.jacobi_server_wait.argtypes = [H, i64, ctypes.POINTER(JacobiStats)]
@@ -164,7 +166,7 @@ def load() -> ctypes.CDLL:
                      "jacobi_server_submit_generated", "jacobi_server_step", "jacobi_server_poll",
                      "jacobi_server_rounds", "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async",
                      "jacobi_csr_solve", "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace",
-                     "jacobi_batch_solve", "jacobi_server_wait"):
+                     "jacobi_batch_solve", "jacobi_server_wait", "jacobi_csr_format"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -343,8 +345,9 @@ class CsrSolver:
     """``jacobi_csr_*``: Jacobi for a sparse A in CSR (int64 row offsets, int32 columns strictly ascending in
     each row with the diagonal stored, float64 values) and one right-hand side; precision "fp64" (the plain
     iteration) or "fp32_ir" / "bf16_ir" (mixed-precision refinement to a relative residual).  The arrays may be torch
-    tensors on the GPU or the host, or numpy arrays; setup copies them into the library's sliced-ELL
-    layout, so they may be dropped afterwards."""
+    tensors on the GPU or the host, or numpy arrays; setup copies them into the library's layout (DIA for a
+    matrix whose entries lie on a few diagonals, else sliced ELL; ``flags=FLAG_CSR_ELL`` forces ELL), so
+    they may be dropped afterwards."""
 
     def __init__(self, row_ptr, col_idx, values, B, norm: str = "inf", flags: int = 0, stream=None, device=None,
                  precision: str = "fp64", inner_rtol: float = 0.0, max_inner: int = 0, max_outer: int = 0):
@@ -408,7 +411,10 @@ class CsrSolver:
         stored, slices, grid = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
         _check(load().jacobi_csr_info(self._h, ctypes.byref(stored), ctypes.byref(slices), ctypes.byref(grid)),
                "jacobi_csr_info")
-        return {"stored_slots": stored.value, "slices": slices.value, "grid": grid.value}
+        fmt, ndiag = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().jacobi_csr_format(self._h, ctypes.byref(fmt), ctypes.byref(ndiag)), "jacobi_csr_format")
+        return {"stored_slots": stored.value, "slices": slices.value, "grid": grid.value,
+                "format": "dia" if fmt.value == 1 else "ell", "diagonals": ndiag.value}
 
     def trace(self):
         """Device-side end time of every phase of the last solve: list of (start_ns, end_ns)."""

@@ -658,6 +658,10 @@ struct jacobi_csr {
   float* rf = nullptr;
   float* da = nullptr;
   float* db = nullptr;
+  // DIA copy (ndiag > 0): ascending offsets j - i, and the zero halo around the gathered vectors
+  int ndiag = 0;
+  int32_t* doff = nullptr;
+  int64_t halo = 0;
 };
 
 namespace {
@@ -763,12 +767,63 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   CK(cudaStreamSynchronize(s));
   std::vector<int64_t> hoff(static_cast<size_t>(nslices + 1), 0);
   for (int64_t q = 0; q < nslices; ++q) hoff[q + 1] = hoff[q] + int64_t(kSliceRows) * hw[q];
-  const int64_t stored = hoff[nslices];
+  const int64_t ell_slots = hoff[nslices];
+  // A banded or stencil matrix, whose entries lie on a few diagonals j - i = const, is kept in DIA form:
+  // no column array, and contiguous gathers.  The candidate offsets come from a sample of rows; a pass
+  // over all entries then confirms that no entry lies off them, and the band must not store many more
+  // slots than sliced ELL would.
+  std::vector<int32_t> offs;
+  if (!(d->flags & JACOBI_FLAG_CSR_ELL)) {
+    std::vector<int64_t> rows = {0, n / 4, n / 3, n / 2, 2 * n / 3, 3 * n / 4, n - 1};
+    bool ok = true;
+    for (int64_t r : rows) {
+      int64_t be[2];
+      CK(cudaMemcpyAsync(be, rp + r, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (be[1] - be[0] > 2 * kMaxDiag + 1) {
+        ok = false;
+        break;
+      }
+      std::vector<int32_t> cols(static_cast<size_t>(be[1] - be[0]));
+      if (!cols.empty()) CK(cudaMemcpyAsync(cols.data(), ci + be[0], cols.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int32_t c : cols)
+        if (c != r && std::find(offs.begin(), offs.end(), static_cast<int32_t>(c - r)) == offs.end())
+          offs.push_back(static_cast<int32_t>(c - r));
+    }
+    std::sort(offs.begin(), offs.end());
+    if (!ok || offs.empty() || offs.size() > static_cast<size_t>(kMaxDiag) ||
+        static_cast<double>(offs.size()) * static_cast<double>(npad) > 1.25 * static_cast<double>(ell_slots))
+      offs.clear();
+    if (!offs.empty()) {  // every entry on a sampled diagonal?  (scratch: the lens array, no longer needed)
+      int32_t* doff_s = lens;
+      int* bad = reinterpret_cast<int*>(lens + kMaxDiag);
+      CK(cudaMemcpyAsync(doff_s, offs.data(), offs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      CK(launch_csr_dia_check(n, rp, ci, doff_s, static_cast<int>(offs.size()), bad, s));
+      int hbad = 0;
+      CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hbad) offs.clear();
+    }
+  }
+  const bool dia = !offs.empty();
+  h->ndiag = static_cast<int>(offs.size());
+  if (dia) {
+    int64_t m = 0;
+    for (int32_t o : offs) m = std::max<int64_t>(m, o < 0 ? -static_cast<int64_t>(o) : o);
+    h->halo = (m + 31) / 32 * 32;
+  }
+  const int64_t stored = dia ? static_cast<int64_t>(offs.size()) * npad : ell_slots;
   h->stored = stored;
   const size_t vbytes = align_up(std::max<int64_t>(stored, 1) * sizeof(double));
-  const size_t cbytes = align_up(std::max<int64_t>(stored, 1) * sizeof(int32_t));
+  const size_t cbytes = dia ? align_up(kMaxDiag * sizeof(int32_t)) : align_up(std::max<int64_t>(stored, 1) * sizeof(int32_t));
   const size_t tbytes = ir ? align_up(std::max<int64_t>(stored, 1) * (d->precision == JACOBI_BF16_IR ? 2 : 4)) : 0;
-  cudaError_t e = cudaMalloc(&h->mem, head + vbytes + cbytes + tbytes);
+  // the gathered vectors (x, and the refinement's r' and delta) with their halo on both sides
+  const size_t vech = align_up((npad + 2 * h->halo) * sizeof(double));
+  const size_t vecfh = align_up((npad + 2 * h->halo) * sizeof(float));
+  const size_t head_h = head + 2 * (vech - vec) + (ir ? 3 * (vecfh - vecf) : 0);
+  cudaError_t e = cudaMalloc(&h->mem, head_h + vbytes + cbytes + tbytes);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(sparse)");
   char* p = static_cast<char*>(h->mem);
   auto take = [&p](size_t bytes) {
@@ -778,20 +833,23 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
   };
   h->soff = reinterpret_cast<int64_t*>(take(align_up((nslices + 1) * sizeof(int64_t))));
   h->c = reinterpret_cast<double*>(take(vec));
-  h->xa = reinterpret_cast<double*>(take(vec));
-  h->xb = reinterpret_cast<double*>(take(vec));
+  h->xa = reinterpret_cast<double*>(take(vech)) + h->halo;
+  h->xb = reinterpret_cast<double*>(take(vech)) + h->halo;
   h->xout = reinterpret_cast<double*>(take(vec));
   h->part = reinterpret_cast<double*>(take(align_up(2 * kMaxGrid * sizeof(double))));
   h->ctl = reinterpret_cast<Ctl*>(take(align_up(sizeof(Ctl))));
   unsigned long long* bmax = reinterpret_cast<unsigned long long*>(take(align_up(sizeof(unsigned long long))));
   if (keep_d) h->d = reinterpret_cast<double*>(take(vec));
   if (ir) {
-    h->rf = reinterpret_cast<float*>(take(vecf));
-    h->da = reinterpret_cast<float*>(take(vecf));
-    h->db = reinterpret_cast<float*>(take(vecf));
+    h->rf = reinterpret_cast<float*>(take(vecfh)) + h->halo;
+    h->da = reinterpret_cast<float*>(take(vecfh)) + h->halo;
+    h->db = reinterpret_cast<float*>(take(vecfh)) + h->halo;
   }
   h->sval = reinterpret_cast<double*>(take(vbytes));
-  h->scol = reinterpret_cast<int32_t*>(take(cbytes));
+  if (dia)
+    h->doff = reinterpret_cast<int32_t*>(take(cbytes));
+  else
+    h->scol = reinterpret_cast<int32_t*>(take(cbytes));
   if (ir) h->tlo = take(tbytes);
   jacobi_csr* raw = h.get();
   auto fail = [&](cudaError_t err, const char* what) {
@@ -804,10 +862,16 @@ int csr_setup(const jacobi_csr_desc* d, jacobi_csr** out) {
     cudaError_t e_ = (call);                         \
     if (e_ != cudaSuccess) return fail(e_, #call);   \
   } while (0)
-  CSR_CK(cudaMemsetAsync(h->mem, 0, head, s));
+  CSR_CK(cudaMemsetAsync(h->mem, 0, head_h, s));
   CSR_CK(cudaMemcpyAsync(h->soff, hoff.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CSR_CK(cudaMemcpyAsync(h->c, d->B, n * sizeof(double), cudaMemcpyDefault, s));
-  CSR_CK(launch_csr_fill(n, rp, ci, va, dd, h->soff, h->sval, h->scol, h->c, bmax, s));
+  if (dia) {
+    CSR_CK(cudaMemcpyAsync(h->doff, offs.data(), offs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CSR_CK(cudaMemsetAsync(h->sval, 0, vbytes, s));
+    CSR_CK(launch_csr_dia_fill(n, rp, ci, va, dd, h->doff, h->ndiag, h->sval, h->c, bmax, s));
+  } else {
+    CSR_CK(launch_csr_fill(n, rp, ci, va, dd, h->soff, h->sval, h->scol, h->c, bmax, s));
+  }
   if (keep_d) CSR_CK(cudaMemcpyAsync(h->d, dd, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (ir) {
     CSR_CK(launch_csr_narrow(d->precision == JACOBI_BF16_IR ? CsrInner::BF16 : CsrInner::F32, h->sval, stored, h->tlo,
@@ -1162,6 +1226,8 @@ int jacobi_csr_solve_async(jacobi_csr* h, const double* X0, int64_t max_iter, do
   p.bnorm = h->bnorm;
   p.test_skip_arrival = h->test_skip_arrival;
   p.wait_ns = h->wait_ns;
+  p.doff = h->doff;
+  p.ndiag = h->ndiag;
   cudaError_t e;
   if (h->precision == JACOBI_FP64) {
     e = launch_csr_solve(p, h->grid, s);
@@ -1205,6 +1271,13 @@ int jacobi_csr_info(jacobi_csr* h, int64_t* stored_slots, int64_t* slices, int32
   if (stored_slots) *stored_slots = h->stored;
   if (slices) *slices = h->nslices;
   if (grid) *grid = h->grid;
+  return JACOBI_OK;
+}
+
+int jacobi_csr_format(jacobi_csr* h, int32_t* format, int32_t* ndiag) {
+  if (!h) return JACOBI_ERR_INVALID_ARG;
+  if (format) *format = h->ndiag > 0 ? JACOBI_CSR_DIA : JACOBI_CSR_ELL;
+  if (ndiag) *ndiag = h->ndiag;
   return JACOBI_OK;
 }
 

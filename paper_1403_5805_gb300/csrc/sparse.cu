@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <initializer_list>
 
 #include "device_util.cuh"
 #include "sparse.cuh"
@@ -108,18 +109,107 @@ __global__ void csr_fill_kernel(int64_t n, int64_t nslices, const int64_t* __res
   }
 }
 
+// DIA setup: every off-diagonal entry's offset j - i must be one of doff[0..ndiag) (else *bad = 1).
+__global__ void csr_dia_check_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const int32_t* __restrict__ doff, int ndiag, int* bad) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+    const int64_t off = static_cast<int64_t>(ci[e]) - i;
+    if (off == 0) continue;
+    bool found = false;
+    for (int t = 0; t < ndiag; ++t) found = found || doff[t] == off;
+    if (!found) {
+      atomicOr(bad, 1);
+      return;
+    }
+  }
+}
+
+// DIA setup: entry t of row i, -a_ij / a_ii for j = i + doff[t], at ((i / 32) * ndiag + t) * 32 + i % 32
+// (dval zeroed beforehand); c_i = b_i / a_ii (c holds b on entry); *bmax receives the IEEE bits of
+// ||b||_inf.
+__global__ void csr_dia_fill_kernel(int64_t n, const int64_t* __restrict__ rp,
+                                    const int32_t* __restrict__ ci, const double* __restrict__ val,
+                                    const double* __restrict__ d, const int32_t* __restrict__ doff, int ndiag,
+                                    double* dval, double* c, unsigned long long* bmax) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double di = d[i];
+  for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+    const int64_t off = static_cast<int64_t>(ci[e]) - i;
+    if (off == 0) continue;
+    for (int t = 0; t < ndiag; ++t)
+      if (doff[t] == off)  // t_ij = -a_ij / a_ii
+        dval[((i / kSliceRows) * ndiag + t) * kSliceRows + i % kSliceRows] = -val[e] / di;
+  }
+  const double bi = c[i];
+  atomicMax(bmax, abs_bits(bi));
+  c[i] = bi / di;
+}
+
 __device__ __forceinline__ double bits_to_double(unsigned long long v) {
   return __longlong_as_double(static_cast<long long>(v));
 }
 
+// Storage formats of T, as accessors of a slice's entries.  Sliced ELL: slice s holds w_s slots per row
+// at soff[s] + 32 t + lane with explicit columns.  Diagonal (DIA): every row has the same ndiag offsets
+// doff[0] < ... < doff[ndiag-1] (j = i + doff[t]; absent entries are zero), entry t of row 32 s + lane at
+// (s * ndiag + t) * 32 + lane (a slice's diagonals contiguous, as an ELL slice of width ndiag), and no
+// column array at all; the gathered vectors carry a zero halo of max |doff| entries on both sides, so
+// i + doff[t] is always a valid index.  In both formats a row's entries run in ascending column order.
+struct EllFmt {
+  __device__ static int width(const CsrParams& p, int64_t s, int64_t& o0) {
+    o0 = __ldg(p.soff + s);
+    return static_cast<int>((__ldg(p.soff + s + 1) - o0) / kSliceRows);
+  }
+  __device__ static int64_t at(const CsrParams&, int64_t o0, int t, int lane) { return o0 + lane + kSliceRows * t; }
+  __device__ static int64_t col(const CsrParams& p, int64_t o0, int t, int lane, int64_t, const int*) {
+    return __ldcs(p.scol + o0 + lane + kSliceRows * t);
+  }
+  // pull slice s's values and columns into L2, one 128-byte line per lane
+  __device__ static void prefetch(const CsrParams& p, int64_t s, int lane) {
+    const int64_t q0 = __ldg(p.soff + s), q1 = __ldg(p.soff + s + 1);
+    const int64_t vl = (q1 - q0) / 16, cl = (q1 - q0) / 32;  // lines of values (8 B) and columns (4 B)
+    for (int64_t l = lane; l < vl + cl; l += 32) {
+      const char* a = l < vl ? reinterpret_cast<const char*>(p.sval + q0) + 128 * l
+                             : reinterpret_cast<const char*>(p.scol + q0) + 128 * (l - vl);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+  }
+};
+struct DiaFmt {
+  __device__ static int width(const CsrParams& p, int64_t s, int64_t& o0) {
+    o0 = s * p.ndiag * kSliceRows;
+    return p.ndiag;
+  }
+  __device__ static int64_t at(const CsrParams&, int64_t o0, int t, int lane) { return o0 + lane + kSliceRows * t; }
+  __device__ static int64_t col(const CsrParams&, int64_t, int t, int, int64_t i, const int* sdoff) {
+    return i + sdoff[t];
+  }
+  __device__ static void prefetch(const CsrParams& p, int64_t s, int lane) {
+    if (lane < 2 * p.ndiag)  // the slice's values: two 128-byte lines of FP64 per diagonal
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(p.sval + s * p.ndiag * kSliceRows) +
+                                                    128 * lane));
+  }
+};
+
+// The offsets of a DIA matrix in shared memory (every thread of the CTA calls it once).
+__device__ __forceinline__ void load_doff(const CsrParams& p, int* sdoff) {
+  if (threadIdx.x < kMaxDiag) sdoff[threadIdx.x] = threadIdx.x < p.ndiag ? p.doff[threadIdx.x] : 0;
+  __syncthreads();
+}
+
 // kResid: the change norm is max |a_ii (x^(k) - x^(k-1))| / ||b||_inf (JACOBI_NORM_RESID), a separate
 // instantiation so that the other norms' loop carries no extra load.
-template <bool kResid>
+template <bool kResid, class F>
 __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(CsrParams p) {
   __shared__ unsigned long long s_mx[kCsrWarps];
   __shared__ double s_sq[kCsrWarps];
   __shared__ int s_next, s_status;
   __shared__ double s_delta;
+  __shared__ int sdoff[kMaxDiag];
+  load_doff(p, sdoff);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * kCsrWarps + warp;
   const int64_t nw = static_cast<int64_t>(gridDim.x) * kCsrWarps;
@@ -133,26 +223,17 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_solve_kernel(C
     unsigned long long mx = 0;
     double sq = 0.0;
     for (int64_t s = gw; s < p.nslices; s += nw) {
-      const int64_t o0 = __ldg(p.soff + s), o1 = __ldg(p.soff + s + 1);
-      const int w = static_cast<int>((o1 - o0) / kSliceRows);
-      // pull the warp's next slice into L2 meanwhile: its values and columns, one 128-byte line per lane
-      if (s + nw < p.nslices) {
-        const int64_t q0 = __ldg(p.soff + s + nw), q1 = __ldg(p.soff + s + nw + 1);
-        const int64_t vl = (q1 - q0) / 16, cl = (q1 - q0) / 32;  // lines of values (8 B) and columns (4 B)
-        for (int64_t l = lane; l < vl + cl; l += 32) {
-          const char* a = l < vl ? reinterpret_cast<const char*>(p.sval + q0) + 128 * l
-                                 : reinterpret_cast<const char*>(p.scol + q0) + 128 * (l - vl);
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-        }
-      }
+      int64_t o0;
+      const int w = F::width(p, s, o0);
+      // pull the warp's next slice into L2 meanwhile
+      if (s + nw < p.nslices) F::prefetch(p, s + nw, lane);
       const int64_t i = s * kSliceRows + lane;
       const bool live = i < p.n;
       const double xo = live ? __ldcg(xc + i) : 0.0;
-      const double* v = p.sval + o0 + lane;
-      const int32_t* cc = p.scol + o0 + lane;
       double x = live ? __ldcs(p.c + i) : 0.0;
 #pragma unroll 4
-      for (int t = 0; t < w; ++t) x = fma(__ldcs(v + kSliceRows * t), __ldcg(xc + __ldcs(cc + kSliceRows * t)), x);
+      for (int t = 0; t < w; ++t)
+        x = fma(__ldcs(p.sval + F::at(p, o0, t, lane)), __ldcg(xc + F::col(p, o0, t, lane, i, sdoff)), x);
       if (live) {
         const double diff = x - xo;
         xn[i] = x;
@@ -328,11 +409,13 @@ __device__ bool grid_max2(const CsrParams& p, uint32_t phase, int kind, unsigned
 // side of the inner solve, with max |a_ii r'| / ||b||_inf as the stopping quantity (<= tol).  Inner sweeps:
 // delta^(1) = r', delta^(l+1) = r' + T_lo delta^(l) in FP32, until the change is at most inner_rtol times the
 // magnitude or max_inner sweeps.  Each phase ends with one grid barrier; every CTA takes the same decisions.
-template <class TV>
+template <class TV, class F>
 __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrIrParams q) {
   const CsrParams& p = q.base;
   __shared__ unsigned long long s0[kCsrWarps], s1[kCsrWarps];
   __shared__ int s_ok;
+  __shared__ int sdoff[kMaxDiag];
+  load_doff(p, sdoff);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * kCsrWarps + warp;
   const int64_t nw = static_cast<int64_t>(gridDim.x) * kCsrWarps;
@@ -351,8 +434,8 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrI
     // ---- FP64 residual of x' = x + delta
     unsigned long long mr = 0, unused = 0;
     for (int64_t s = gw; s < p.nslices; s += nw) {
-      const int64_t o0 = __ldg(p.soff + s);
-      const int w = static_cast<int>((__ldg(p.soff + s + 1) - o0) / kSliceRows);
+      int64_t o0;
+      const int w = F::width(p, s, o0);
       const int64_t i = s * kSliceRows + lane;
       const bool live = i < p.n;
       double xi = 0.0, acc = 0.0;
@@ -360,13 +443,11 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrI
         xi = __ldcg(xc + i) + (dcur ? static_cast<double>(__ldcg(dcur + i)) : 0.0);
         acc = __ldcs(p.c + i);
       }
-      const double* v = p.sval + o0 + lane;
-      const int32_t* cc = p.scol + o0 + lane;
 #pragma unroll 4
       for (int t = 0; t < w; ++t) {
-        const int32_t j = __ldcs(cc + kSliceRows * t);
+        const int64_t j = F::col(p, o0, t, lane, i, sdoff);
         const double xj = __ldcg(xc + j) + (dcur ? static_cast<double>(__ldcg(dcur + j)) : 0.0);
-        acc = fma(__ldcs(v + kSliceRows * t), xj, acc);
+        acc = fma(__ldcs(p.sval + F::at(p, o0, t, lane)), xj, acc);
       }
       if (live) {
         const double r = acc - xi;
@@ -401,16 +482,15 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrI
     for (int l = 1;; ++l) {
       unsigned long long mc = 0, mg = 0;
       for (int64_t s = gw; s < p.nslices; s += nw) {
-        const int64_t o0 = __ldg(p.soff + s);
-        const int w = static_cast<int>((__ldg(p.soff + s + 1) - o0) / kSliceRows);
+        int64_t o0;
+        const int w = F::width(p, s, o0);
         const int64_t i = s * kSliceRows + lane;
         const bool live = i < p.n;
         float acc = live ? __ldcg(q.rf + i) : 0.0f;
-        const TV* v = tlo + o0 + lane;
-        const int32_t* cc = p.scol + o0 + lane;
 #pragma unroll 4
         for (int t = 0; t < w; ++t)
-          acc = fmaf(to_f32<TV>(__ldcs(v + kSliceRows * t)), __ldcg(dold + __ldcs(cc + kSliceRows * t)), acc);
+          acc = fmaf(to_f32<TV>(__ldcs(tlo + F::at(p, o0, t, lane))), __ldcg(dold + F::col(p, o0, t, lane, i, sdoff)),
+                     acc);
         if (live) {
           const float old = __ldcg(dold + i);
           dnew[i] = acc;
@@ -482,26 +562,59 @@ cudaError_t launch_csr_fill(int64_t n, const int64_t* row_ptr, const int32_t* co
   return cudaGetLastError();
 }
 
+cudaError_t launch_csr_dia_check(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const int32_t* doff,
+                                 int ndiag, int* bad, cudaStream_t s) {
+  csr_dia_check_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, row_ptr, col_idx, doff, ndiag, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_dia_fill(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                                const double* d, const int32_t* doff, int ndiag, double* dval, double* c,
+                                unsigned long long* bmax, cudaStream_t s) {
+  csr_dia_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, row_ptr, col_idx, val, d, doff, ndiag, dval, c, bmax);
+  return cudaGetLastError();
+}
+
+namespace {
+const void* solve_fn(bool resid, bool dia) {
+  if (dia)
+    return resid ? reinterpret_cast<const void*>(csr_solve_kernel<true, DiaFmt>)
+                 : reinterpret_cast<const void*>(csr_solve_kernel<false, DiaFmt>);
+  return resid ? reinterpret_cast<const void*>(csr_solve_kernel<true, EllFmt>)
+               : reinterpret_cast<const void*>(csr_solve_kernel<false, EllFmt>);
+}
+const void* ir_fn(CsrInner kind, bool dia) {
+  if (dia)
+    return kind == CsrInner::F32 ? reinterpret_cast<const void*>(csr_ir_kernel<float, DiaFmt>)
+                                 : reinterpret_cast<const void*>(csr_ir_kernel<__nv_bfloat16, DiaFmt>);
+  return kind == CsrInner::F32 ? reinterpret_cast<const void*>(csr_ir_kernel<float, EllFmt>)
+                               : reinterpret_cast<const void*>(csr_ir_kernel<__nv_bfloat16, EllFmt>);
+}
+// Co-resident grid of the kernels in fns (the smallest of their occupancies), capped at kMaxGrid.
+int max_grid_of(std::initializer_list<const void*> fns) {
+  int dev = 0, sms = 0, best = 1 << 30;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  for (const void* fn : fns) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCsrThreads, 0) != cudaSuccess) return 0;
+    best = per_sm < best ? per_sm : best;
+  }
+  const int g = best * sms;
+  return g < kMaxGrid ? g : kMaxGrid;
+}
+}  // namespace
+
 cudaError_t launch_csr_solve(const CsrParams& p, int grid, cudaStream_t s) {
   CsrParams copy = p;
   void* args[] = {&copy};
-  const void* fn = p.norm == JACOBI_NORM_RESID ? reinterpret_cast<const void*>(csr_solve_kernel<true>)
-                                               : reinterpret_cast<const void*>(csr_solve_kernel<false>);
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCsrThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel(solve_fn(p.norm == JACOBI_NORM_RESID, p.ndiag > 0), dim3(grid),
+                                     dim3(kCsrThreads), args, 0, s);
 }
 
 int csr_max_grid() {
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  int per_sm_resid = 0;  // the two instantiations may differ in registers: the smaller grid serves both
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_solve_kernel<false>, kCsrThreads, 0) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_resid, csr_solve_kernel<true>, kCsrThreads, 0) !=
-          cudaSuccess)
-    return 0;
-  per_sm = per_sm < per_sm_resid ? per_sm : per_sm_resid;
-  const int g = per_sm * sms;
-  return g < kMaxGrid ? g : kMaxGrid;
+  // the instantiations may differ in registers: the smallest co-resident grid serves all of them
+  return max_grid_of({solve_fn(false, false), solve_fn(true, false), solve_fn(false, true), solve_fn(true, true)});
 }
 
 int csr_warps_per_cta() { return kCsrWarps; }
@@ -519,20 +632,9 @@ cudaError_t launch_csr_narrow(CsrInner kind, const double* sval, int64_t slots, 
 cudaError_t launch_csr_ir_solve(CsrInner kind, const CsrIrParams& p, int grid, cudaStream_t s) {
   CsrIrParams copy = p;
   void* args[] = {&copy};
-  const void* fn = kind == CsrInner::F32 ? reinterpret_cast<const void*>(csr_ir_kernel<float>)
-                                         : reinterpret_cast<const void*>(csr_ir_kernel<__nv_bfloat16>);
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCsrThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel(ir_fn(kind, p.base.ndiag > 0), dim3(grid), dim3(kCsrThreads), args, 0, s);
 }
 
-int csr_ir_max_grid(CsrInner kind) {
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const void* fn = kind == CsrInner::F32 ? reinterpret_cast<const void*>(csr_ir_kernel<float>)
-                                         : reinterpret_cast<const void*>(csr_ir_kernel<__nv_bfloat16>);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCsrThreads, 0) != cudaSuccess) return 0;
-  const int g = per_sm * sms;
-  return g < kMaxGrid ? g : kMaxGrid;
-}
+int csr_ir_max_grid(CsrInner kind) { return max_grid_of({ir_fn(kind, false), ir_fn(kind, true)}); }
 
 }  // namespace jac

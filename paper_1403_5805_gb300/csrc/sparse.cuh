@@ -9,6 +9,7 @@
 namespace jac {
 
 constexpr int kSliceRows = 32;  // rows per slice of the sliced-ELL copy: one warp, one row per lane
+constexpr int kMaxDiag = 16;    // most diagonals of the DIA copy (more, or a poorly filled band: sliced ELL)
 
 // Setup pass 1 (one thread per row) over CSR arrays in device memory: checks the structure and the
 // diagonal, writes d_i = a_ii and the row's off-diagonal count.  The first failure by the oracle's order is
@@ -27,6 +28,15 @@ cudaError_t launch_csr_widths(int64_t n, const int32_t* lens, int32_t* width, cu
 cudaError_t launch_csr_fill(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
                             const double* d, const int64_t* soff, double* sval, int32_t* scol, double* c,
                             unsigned long long* bmax, cudaStream_t s);
+// DIA alternative to pass 3 for banded and stencil matrices: *bad (zero beforehand) becomes nonzero if
+// some off-diagonal entry's offset j - i is not among doff[0..ndiag); the fill writes entry t of row i at
+// dval[((i / 32) * ndiag + t) * 32 + i % 32] (dval zero beforehand, ndiag times n rounded up to whole
+// slices), and C as pass 3 does.
+cudaError_t launch_csr_dia_check(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const int32_t* doff,
+                                 int ndiag, int* bad, cudaStream_t s);
+cudaError_t launch_csr_dia_fill(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                                const double* d, const int32_t* doff, int ndiag, double* dval, double* c,
+                                unsigned long long* bmax, cudaStream_t s);
 
 struct CsrParams {
   int64_t n, nslices;
@@ -47,6 +57,11 @@ struct CsrParams {
   double bnorm;         // ||b||_inf (JACOBI_NORM_RESID)
   int test_skip_arrival;  // test only: CTA 0 skips the first grid barrier and raises the error word
   uint64_t wait_ns;
+  // DIA copy (ndiag > 0): sval holds entry t of row i (column i + doff[t]) at ((i / 32) * ndiag + t) * 32
+  // + i % 32, doff the ascending offsets j - i; soff and scol are unused, and xa, xb (and the FP32 vectors of the refinement) have a zero
+  // halo of max |doff| entries on both sides.  ndiag == 0: sliced ELL.
+  const int32_t* doff;
+  int ndiag;
 };
 
 // One cooperative launch of `grid` CTAs runs the whole solve.

@@ -125,9 +125,12 @@ def test_sparse_full_size_plane(jac):
     rp, ci, v, B, Xs = synth.stencil_system((2048, 2048), 1.05, seed=synth.BASE_SEED + 6)
     n = B.shape[0]
     s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]))
-    info = s.info()
+    info = s.info()  # the 5-point stencil lies on 4 diagonals: stored diagonal by diagonal
+    assert info["format"] == "dia" and info["diagonals"] == 4
+    assert info["slices"] == n // 32 and info["stored_slots"] == 4 * n
+    ell = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), flags=jac.binding.FLAG_CSR_ELL).info()
     slot_width = (np.diff(rp) - 1).reshape(-1, 32).max(axis=1)  # each slice as wide as its longest row
-    assert info["slices"] == n // 32 and info["stored_slots"] == 32 * int(slot_width.sum())
+    assert ell["format"] == "ell" and ell["stored_slots"] == 32 * int(slot_width.sum())
     X, st = s.solve(max_iter=3, tol=1e-300)
     ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=3, tol=1e-300)
     assert st.sweeps == 3 and rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
@@ -283,3 +286,83 @@ def test_sparse_divergence_follows_the_oracle(jac):
     growth = np.max(np.abs(nxt)) / np.max(np.abs(ref200))
     window = np.log(np.abs(A).sum(axis=1).max()) / np.log(growth) + 2
     assert abs(st.sweeps - ref.iters) <= window, (st.sweeps, ref.iters, window)
+
+
+# ---- storage formats: DIA for entries on a few diagonals, sliced ELL otherwise ----------------------------
+
+def banded_system(n, offsets, f, seed):
+    """Off-diagonals uniform [-1, 1) on the given diagonals (where they fall inside the matrix), a_ii = f *
+    row sum of |a_ij|, planted X* and B = A X*, as CSR."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n))
+    for off in offsets:
+        i = np.arange(max(0, -off), min(n, n - off))
+        A[i, i + off] = rng.uniform(-1, 1, i.size)
+    A[np.arange(n), np.arange(n)] = f * np.abs(A).sum(axis=1) + (np.abs(A).sum(axis=1) == 0)
+    return dense_to_csr(A) + (A,)
+
+
+def dense_to_csr(A):
+    r, c = np.nonzero(A)
+    rp = np.zeros(A.shape[0] + 1, dtype=np.int64)
+    np.add.at(rp, r + 1, 1)
+    rp = np.cumsum(rp)
+    Xs = np.random.default_rng(5).uniform(-1, 1, (A.shape[0], 1))
+    return rp, c.astype(np.int32), A[r, c].copy(), A @ Xs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16_ir", "fp32_ir"])
+@pytest.mark.parametrize("name,ndiag", [("line_95", 2), ("plane_37x29", 4), ("box_11x9x7", 6)])
+def test_dia_and_ell_give_the_same_solves(jac, prec, name, ndiag):
+    """A stencil is kept in DIA form (no column array, contiguous gathers) unless sliced ELL is asked for.
+    The two sum the same entries in the same column order (DIA's absent entries are zeros), so every
+    iterate and the converged result are equal, and both follow the oracle."""
+    rp, ci, v, B, _ = SYSTEMS[name]()
+    dia = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), precision=prec)
+    ell = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]), precision=prec, flags=jac.binding.FLAG_CSR_ELL)
+    assert (dia.info()["format"], dia.info()["diagonals"]) == ("dia", ndiag)
+    assert (ell.info()["format"], ell.info()["diagonals"]) == ("ell", 0)
+    caps = (1, 3, 5000) if prec == "fp64" else (5000,)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    for cap in caps:
+        Xd, sd = dia.solve(max_iter=cap, tol=tol if cap > 10 else 1e-300)
+        Xe, se = ell.solve(max_iter=cap, tol=tol if cap > 10 else 1e-300)
+        assert (sd.status, sd.sweeps, sd.outer_steps) == (se.status, se.sweeps, se.outer_steps)
+        np.testing.assert_array_equal(Xd.cpu().numpy(), Xe.cpu().numpy())
+    if prec == "fp64":
+        ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=5000, tol=1e-12)
+        assert sd.sweeps == ref.iters and rel_err(Xd.cpu().numpy(), ref.X[:, 0]) <= 1e-12
+    else:
+        assert sd.status == 0 and oracle.csr_residual(rp, ci, v, B, Xd.cpu().numpy())[1] <= 1e-10
+
+
+@pytest.mark.parametrize("offsets,fmt", [((-1, 1), "dia"), ((-300, -7, -1, 1, 2, 40, 299), "dia"),
+                                         (tuple(range(-8, 0)) + tuple(range(1, 9)), "dia"),
+                                         (tuple(range(-9, 0)) + tuple(range(1, 9)), "ell")])
+def test_banded_matrices_pick_dia_up_to_16_diagonals(jac, offsets, fmt):
+    n = 1000
+    rp, ci, v, B, A = banded_system(n, offsets, 1.1, seed=len(offsets))
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]))
+    assert s.info()["format"] == fmt
+    for k in (1, 4):
+        X, st = s.solve(max_iter=k, tol=1e-300)
+        ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=k, tol=1e-300)
+        assert st.sweeps == ref.iters and rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
+    X, st = s.solve(max_iter=5000, tol=1e-12)
+    ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=5000, tol=1e-12)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters) and rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
+
+
+def test_an_entry_off_the_sampled_diagonals_keeps_ell(jac):
+    """Setup takes candidate diagonals from a few rows and then checks every entry: one entry elsewhere
+    (in a row it did not sample) keeps the matrix in sliced ELL, and the solve still follows the oracle."""
+    rp0, ci0, v0, B0, _ = synth.stencil_system((40, 33), 1.2, seed=41)
+    A = synth.csr_to_dense(B0.shape[0], rp0, ci0, v0)
+    A[5, 900] = -0.01
+    A[5, 5] += 0.02
+    rp, ci, v, B = dense_to_csr(A)
+    s = jac.CsrSolver(gpu(rp), gpu(ci), gpu(v), gpu(B[:, 0]))
+    assert s.info()["format"] == "ell"
+    X, st = s.solve(max_iter=5000, tol=1e-12)
+    ref = oracle.csr_jacobi(rp, ci, v, B, max_iter=5000, tol=1e-12)
+    assert (st.status, st.sweeps) == (ref.status, ref.iters) and rel_err(X.cpu().numpy(), ref.X[:, 0]) <= 1e-12
