@@ -6,7 +6,9 @@
 //     stores d_i = a_ii and rinv_i = 1/a_ii (one correctly rounded reciprocal per row);
 //   * copies B and takes ||B||_inf;
 //   * for the mixed-precision paths, writes the narrow copy of the off-diagonal part of A (FP32, BF16
-//     or E4M3 with an FP32 scale per row) in one pass over A.
+//     or E4M3 with an FP32 scale per row) in one pass over A: E4M3 and split-float handles, many right-
+//     hand sides, and a copy read out before any solve.  The BF16 / FP32 copies of the other handles are
+//     written by the first inner sweep of their first solve (solve.cu), with the same rounding.
 // Rounding of the narrow copies: a_ij -> FP32 (round to nearest even), then BF16 round to nearest even;
 // for E4M3 the row scale s_i = max_{j != i} |a32_ij| / 448 (FP32 division, s_i = 1 if that is 0) and
 // the code is the saturating round-to-nearest-even E4M3 of a32_ij / s_i (FP32 division).

@@ -3,10 +3,13 @@
 // One cooperative launch runs a whole solve.  Each CTA owns a contiguous block of rows (the paper's
 // row-wise distribution of Section 3.1, here over the SMs of one GPU).  Per sweep it streams its rows
 // of the matrix from HBM exactly once through a shared-memory ring: one producer warp issues 1-D TMA
-// bulk copies (4 KB row segments, 8 rows per ring item) that complete on mbarriers, eight consumer
-// warps read them with 128-bit shared-memory loads and accumulate row dot products against the
-// current iterate (read from L2), reduce them with warp shuffles and a fixed-order cross-warp sum, and
-// apply the component update of Section 2 in the epilogue.  The max-norm change is reduced in the
+// bulk copies (one row segment of a column chunk each, 16 rows per ring item, 4 items of 48 KB) that
+// complete on mbarriers; twelve consumer warps (6 column slices x 2 groups of 8 rows) read them with
+// 128-bit shared-memory loads and accumulate row dot products against the current iterate (read from
+// L2), reduce them with warp shuffles and a fixed-order cross-warp sum, and apply the component update
+// of Section 2 in the epilogue.  When a CTA's rows fit in the ring (small systems), later sweeps reuse
+// them from shared memory.  A handle's first BF16 / FP32 inner sweep streams FP64 A instead and writes
+// the narrow copy as it sweeps.  The max-norm change is reduced in the
 // same epilogue (order-free integer max on the IEEE bits), combined over the grid with one atomic and
 // one grid barrier per sweep, and every CTA takes the same stop decision from it - the stopping test
 // of the Section 2 algorithm with no host round trip.
