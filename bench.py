@@ -221,6 +221,7 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": bytes_launch, "kernel_ms": round(main["kernel_ms"], 4),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
 
+    composite = composite_roofline(main, n, args.precision, peaks, dev, torch)
     paths = {args.precision: summarize(main, args.steps, n, args.precision)}
     if not args.quick:
         for prec in [p for p in ("fp64", "fp64+gs", "fp8_ir", "fp32_ir", "bf16_ir+split", "fp32_ir+split")
@@ -256,7 +257,7 @@ def run_ours(args, world, rank, local):
         # per step: diagonal check, right-hand side, (narrow copy,) solve; BF16 / FP32 inner sweeps write
         # their narrow copy inside the solve kernel
         "gpu_launches": (3 if args.precision.startswith("fp64") or fused else 4) * args.steps,
-        "clocks": main["clocks"], "roofline": roofline, "paths": paths,
+        "clocks": main["clocks"], "roofline": roofline, "roofline_composite": composite, "paths": paths,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
         "sparse": sparse,
         "serving": serving, "hard_generator": hard, "small_system": small,
@@ -264,6 +265,35 @@ def run_ours(args, world, rank, local):
     if cpu is not None:
         result["cpu_baseline"] = cpu
     return result
+
+
+def composite_roofline(r, n, prec, peaks, dev, torch):
+    """Per-phase lower bound of the timed kernel: each FP64 pass (residual or sweep) is held by the larger of
+    its HBM time and its FP64-FMA time (n^2 FMAs at 2 FP64 FMA per clock per SM), every other phase by its
+    HBM time; the sum over the launch's phases against the measured kernel time."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_fma_s = 2.0 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    hbm = peaks["hbm_gbs"] * 1e9
+    es = ESIZE.get(prec.replace("+split", "").replace("+gs", ""), 8)
+    per = {"sweep64": (8.0, True), "resid64": (8.0, True), "resid0": (0.0, False), "inner": (float(es), False),
+           "narrow_inner": (8.0 + es, False)}
+    total, rows = 0.0, {}
+    for name, ph in r["phases"].items():
+        if name not in per:
+            continue
+        bpe, fp64 = per[name]
+        t_hbm = bpe * n * n / hbm
+        t_fma = float(n) * n / fp64_fma_s if fp64 else 0.0
+        t_min = max(t_hbm, t_fma)
+        total += ph["count"] * t_min
+        rows[name] = {"count": ph["count"], "bound": "fp64" if t_fma > t_hbm else "hbm", "min_us": round(t_min * 1e6, 1),
+                      "measured_us": ph["mean_us"], "frac": round(t_min * 1e6 / ph["mean_us"], 3) if ph["mean_us"] else None}
+    kernel_s = r["kernel_ms"] * 1e-3
+    return {"min_ms": round(total * 1e3, 4), "kernel_ms": round(r["kernel_ms"], 4),
+            "frac": round(total / kernel_s, 4) if kernel_s > 0 else None, "phases": rows,
+            "fp64_fma_peak": f"2 FP64 FMA/clock/SM x {sms} SMs x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz = "
+                             f"{fp64_fma_s / 1e9:.0f} GFMA/s (derived; about 1.26 TFLOP/s)",
+            "hbm_peak_gbs": peaks["hbm_gbs"]}
 
 
 def phase_bandwidth(trace, n, prec):
