@@ -424,7 +424,8 @@ def run_sparse(args, jac, torch, dev):
     t_rp, t_ci, t_v, t_b = (torch.from_numpy(a).to(dev) for a in (rp, ci, v, B[:, 0].copy()))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
-    s = jac.CsrSolver(t_rp, t_ci, t_v, t_b)
+    fl = jac.binding.FLAG_CSR_ELL if args.sparse_ell else 0  # --sparse-ell: keep sliced ELL
+    s = jac.CsrSolver(t_rp, t_ci, t_v, t_b, flags=fl)
     ev[1].record(stream)
     torch.cuda.synchronize(dev)
     setup_ms = ev[0].elapsed_time(ev[1])
@@ -455,12 +456,12 @@ def run_sparse(args, jac, torch, dev):
     err = float((out - torch.from_numpy(Xs[:, 0]).to(dev)).abs().max().item())
     s.close()
     # the same stopping quantity as the refined solves: ||b - A x|| / ||b|| < 1e-10 (of the previous iterate)
-    s = jac.CsrSolver(t_rp, t_ci, t_v, t_b, norm="resid")
+    s = jac.CsrSolver(t_rp, t_ci, t_v, t_b, norm="resid", flags=fl)
     ms_resid, st_resid = timed(5000, 1e-10, 3)
     import oracle
     refined = {}
     for prec in ("bf16_ir", "fp32_ir"):  # the same system, mixed precision, to ||b - A x|| / ||b|| <= 1e-10
-        r = jac.CsrSolver(t_rp, t_ci, t_v, t_b, precision=prec)
+        r = jac.CsrSolver(t_rp, t_ci, t_v, t_b, precision=prec, flags=fl)
         for _ in range(2):
             r.solve_async(None, 1, 1e-10, out)
         torch.cuda.synchronize(dev)
@@ -892,6 +893,8 @@ def main():
     ap.add_argument("--sparse-grid", type=int, default=2048, dest="sparse_grid",
                     help="side of the 2-D stencil grid of the sparse section")
     ap.add_argument("--sparse-sweeps", type=int, default=200, dest="sparse_sweeps")
+    ap.add_argument("--sparse-ell", action="store_true", dest="sparse_ell",
+                    help="keep the sparse section's matrix in sliced ELL instead of the DIA form setup picks")
     ap.add_argument("--serve-seconds", type=float, default=60.0, dest="serve_seconds",
                     help="arrival window of --only serve (the full serving configuration)")
     ap.add_argument("--serve-window", type=float, default=5.0, dest="serve_window",
