@@ -195,12 +195,7 @@ def run_ours(args, world, rank, local):
 
     main = timed(args.precision, args.steps, args.warmup, sample_clocks=True)
     ms_step = main["ms_total"] / args.steps
-    ms_max = ms_step
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world / (ms_max * 1e-3)
+    ms_max, value = job_rate(ms_step, world, dev)
 
     # algorithmic bytes of the dominant kernel (the persistent solve kernel) per launch
     st = main["stats"]
@@ -265,6 +260,19 @@ def run_ours(args, world, rank, local):
     if cpu is not None:
         result["cpu_baseline"] = cpu
     return result
+
+
+def job_rate(ms_step, world, device):
+    """Replicas: every rank solves its own system per step, so the job's step time is the slowest rank's
+    (a MAX all-reduce over the process group) and the job's rate is world / that time.  Returns
+    (ms per step, solves per second)."""
+    ms_max = ms_step
+    if world > 1:
+        import torch
+        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return ms_max, world / (ms_max * 1e-3)
 
 
 def composite_roofline(r, n, prec, peaks, dev, torch):

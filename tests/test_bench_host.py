@@ -1,5 +1,5 @@
-"""Host-side logic of bench.py (no GPU): the roofline arithmetic, the use of committed DRAM traffic, and
-the per-phase bandwidth of a device trace."""
+"""Host-side logic of bench.py (no GPU): the roofline arithmetic, the use of committed DRAM traffic, the
+per-phase bandwidth of a device trace, and the job rate of N replicas (two gloo ranks on the CPU)."""
 import json
 import os
 import sys
@@ -90,3 +90,32 @@ def test_phase_bandwidth_from_a_trace():
     assert ph["narrow_inner"]["gbs"] == pytest.approx(10.0 * n * n / 10000.0, rel=1e-3)
     assert ph["resid64"]["gbs"] == pytest.approx(8.0 * n * n / 20000.0, rel=1e-3)
     assert ph["resid0"]["gbs"] is None
+
+
+def _rank_main(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        ms, rate = bench.job_rate(1.5 + rank, world, "cpu")  # rank 1 is the slower replica
+        dist.barrier()
+        out[rank] = (ms, rate)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_job_rate_over_two_gloo_ranks():
+    """bench.py --gpus N runs N replicas; the job's step time is the slowest rank's (MAX all-reduce) and
+    the job's rate N / that time, on every rank.  Two CPU ranks over gloo."""
+    torch = pytest.importorskip("torch")
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    manager = mp.get_context("spawn").Manager()
+    out = manager.dict()
+    mp.start_processes(_rank_main, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
+    assert dict(out) == {0: (2.5, 2 / 2.5e-3), 1: (2.5, 2 / 2.5e-3)}
+    assert bench.job_rate(4.0, 1, "cpu") == (4.0, 250.0)
