@@ -43,7 +43,9 @@ typedef enum jacobi_status {
   JACOBI_ERR_OUT_OF_MEMORY = -4,  /* device allocation failed or workspace too small */
   JACOBI_ERR_CUDA = -5,           /* a CUDA runtime call failed (see jacobi_last_cuda_error) */
   JACOBI_ERR_TIMEOUT = -6,        /* a bounded device-side wait expired; the context stays usable */
-  JACOBI_ERR_UNSUPPORTED = -8     /* valid request this build does not implement (e.g. nrhs > 1 here) */
+  JACOBI_ERR_UNSUPPORTED = -8     /* valid request the library does not implement (e.g. Gauss-Seidel, FP32
+                                     or E4M3 inner sweeps with nrhs > 1; BF16 sweeps for an nrhs other than
+                                     16, 32, 64 or 128) */
 } jacobi_status;
 
 /* Arithmetic of the solve.
@@ -112,7 +114,7 @@ JACOBI_API const char* jacobi_last_cuda_error(void);
 
 typedef struct jacobi_desc {
   int64_t n;              /* system size, >= 1 */
-  int64_t nrhs;           /* right-hand sides; this build supports 1 */
+  int64_t nrhs;           /* right-hand sides, >= 1 (B and X column-major, one column per right-hand side) */
   int32_t precision;      /* jacobi_precision */
   int32_t norm;           /* jacobi_norm (FP64 path only) */
   const double* A;        /* row-major, A[i*lda + j], device or host memory.  Borrowed (read by every
