@@ -116,7 +116,8 @@ typedef struct jacobi_desc {
   int64_t n;              /* system size, >= 1 */
   int64_t nrhs;           /* right-hand sides, >= 1 (B and X column-major, one column per right-hand side) */
   int32_t precision;      /* jacobi_precision */
-  int32_t norm;           /* jacobi_norm (FP64 path only) */
+  int32_t norm;           /* jacobi_norm (FP64 path; with nrhs > 1 each column is tested on its own and
+                             the solve stops when every column has met the test) */
   const double* A;        /* row-major, A[i*lda + j], device or host memory.  Borrowed (read by every
                              solve, so it must stay unchanged and alive until jacobi_destroy) when it is
                              16-byte aligned device memory with n and lda even and JACOBI_FLAG_COPY_A is
