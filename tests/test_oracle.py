@@ -262,6 +262,64 @@ def test_multi_rhs_columns_are_independent():
         np.testing.assert_array_equal(multi.X[:, c], one.X[:, 0])
 
 
+def _per_column_changes(trace, X0, norm):
+    """Per sweep k and column c: the Euclidean length of X^(k) - X^(k-1) (numpy's norm), from a trace."""
+    prev = np.concatenate([X0[None], trace[:-1]])
+    if norm == oracle.NORM_2:
+        return np.linalg.norm(trace - prev, axis=1)
+    raise ValueError(norm)
+
+
+@pytest.mark.parametrize("scales", [(1.0, 1.0, 1.0), (2.0 ** -20, 1.0, 2.0 ** 20), (2.0 ** 30, 2.0 ** -30, 1.0)])
+def test_euclidean_norm_over_several_columns_is_the_largest_column_length(scales):
+    # Section 2 measures the change of one system by its Euclidean length; with several right-hand sides
+    # each column is its own system, so the decisive value is the largest column length.  Equal columns
+    # tell this apart from the length of all columns together (sqrt(3) times larger); columns of very
+    # different magnitude tell it apart from the first, last or smallest column's length.
+    A, B0, _ = synth.dominant_system(24, 1.1, seed=31, nrhs=3)
+    if scales[0] == scales[1] == scales[2]:
+        B0 = np.repeat(B0[:, :1], 3, axis=1)
+    B = B0 * np.array(scales)
+    X0 = np.zeros_like(B)
+    full = oracle.jacobi(A, B, max_iter=60, tol=1e-300, norm=oracle.NORM_2, trace=True)
+    per_col = _per_column_changes(full.trace, X0, oracle.NORM_2)        # (k, c)
+    for k in (1, 2, 5, 17):
+        part = oracle.jacobi(A, B, max_iter=k, tol=1e-300, norm=oracle.NORM_2)
+        want = per_col[k - 1].max()
+        assert abs(part.delta - want) <= 1e-14 * want, (k, part.delta, want)
+    # the stop: the first sweep whose largest column length is below tol (strict)
+    tol = float(np.sort(per_col.max(axis=1))[::-1][12]) * 1.0000001
+    first = int(np.argmax(per_col.max(axis=1) < tol)) + 1
+    stop = oracle.jacobi(A, B, max_iter=60, tol=tol, norm=oracle.NORM_2)
+    assert stop.status == oracle.OK and stop.iters == first
+    np.testing.assert_array_equal(stop.X, full.trace[first - 1])
+    if scales[0] == scales[1] == scales[2]:
+        total = np.sqrt((per_col ** 2).sum(axis=1))
+        assert np.all(total > 1.7 * per_col.max(axis=1))               # the reading is distinguishable
+
+
+def test_residual_norm_over_several_columns_is_the_worst_relative_column():
+    # The residual-norm stop of the previous iterate, per column: ||b_c - A x_c^(k-1)||_inf / ||b_c||_inf
+    # (each column its own system), and the largest of these decides.  Column 2 has the smallest right-hand
+    # side and a start far from its solution, so its relative residual leads; pooling the residuals and
+    # right-hand sides of all columns would give a value about a million times smaller.
+    A, B, _ = synth.dominant_system(30, 1.2, seed=33, nrhs=3)
+    B = B * np.array([2.0 ** 20, 1.0, 2.0 ** -20])
+    X0 = np.zeros_like(B)
+    X0[:, 2] = 2.0 ** -10
+    full = oracle.jacobi(A, B, X0=X0, max_iter=8, tol=1e-300, norm=oracle.NORM_RESID, trace=True)
+    prev = np.concatenate([X0[None], full.trace[:-1]])
+    for k in range(1, full.iters + 1):
+        part = oracle.jacobi(A, B, X0=X0, max_iter=k, tol=1e-300, norm=oracle.NORM_RESID)
+        rels = [oracle.residual(A, B[:, c], prev[k - 1][:, c])[1] for c in range(3)]
+        assert int(np.argmax(rels)) == 2
+        want = max(rels)
+        assert abs(part.delta - want) <= 1e-14 * want, (k, part.delta, rels)
+        R, _ = oracle.residual(A, B, prev[k - 1])
+        pooled = np.abs(R).max() / np.abs(B).max()
+        assert pooled < 1e-3 * want                                    # the pooled reading differs
+
+
 def test_thread_count_does_not_change_results():
     A, B, _ = synth.hard_system(97, 1.1, seed=5, nrhs=2)
     a = oracle.jacobi(A, B, max_iter=40, tol=1e-300, nthreads=1)
