@@ -573,7 +573,7 @@ def run_serve(args, jac, torch, dev, seconds):
     rate = 2000.0
     t, ns, rs, fs, seeds = synth.serving_trace(rate, seconds, seed=synth.BASE_SEED + 4)
     free, _ = torch.cuda.mem_get_info(dev)
-    budget = int(min(100e9, free - 8e9))
+    budget = int(min(args.serve_budget_gb * 1e9, free - 8e9))
 
     def served(split):
         srv = jac.Server(budget_bytes=budget, split_residual=split)
@@ -907,6 +907,9 @@ def main():
                     help="arrival window of --only serve (the full serving configuration)")
     ap.add_argument("--serve-window", type=float, default=5.0, dest="serve_window",
                     help="arrival window of the serving section of the default run")
+    ap.add_argument("--serve-budget-gb", type=float, default=100.0, dest="serve_budget_gb",
+                    help="device-memory budget of the serving arena (the configuration's 100 GB; a few GB "
+                         "for a profiler capture)")
     ap.add_argument("--serve-fp64-seconds", type=float, default=1.0, dest="serve_fp64_seconds")
     ap.add_argument("--only", choices=["batch", "mrhs", "serve", "sparse", "small"], default=None,
                     help="run one secondary workload alone (profiling)")
