@@ -167,6 +167,8 @@ def run_ours(args, world, rank, local):
             ev[1].record(stream)
         return s
 
+    xs_host = {}
+
     def timed(prec, steps, warmup, sample_clocks=False):
         for _ in range(warmup):
             s = one_step(prec)
@@ -190,6 +192,7 @@ def run_ours(args, world, rank, local):
         st = s.last_stats()
         rel = s.residual(out)
         err = float((out - Xs_t).abs().max().item())
+        xs_host[prec] = out.cpu().numpy().copy()  # for the error against the oracle's solution
         return {"ms_total": ms, "kernel_ms": kernel_ms, "stats": st.as_dict(), "rel_residual_check": rel,
                 "err_vs_xstar": err, "clocks": clocks, "phases": phase_bandwidth(s.trace(), n, prec)}
 
@@ -227,7 +230,16 @@ def run_ours(args, world, rank, local):
         fp64_ratio = round(paths[args.precision]["solves_per_s"] / paths["fp64"]["solves_per_s"], 3)
 
     e2e = None if args.no_e2e else run_e2e(args, jac, torch, dev, A, B, ws)
-    cpu = cpu_baseline(A, B, n) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    cpu, x_oracle = (cpu_baseline(A, B, n) if (rank == 0 and world == 1 and not args.no_cpu_baseline)
+                     else (None, None))
+    err_vs_oracle = None
+    if x_oracle is not None:
+        # every path's X against the oracle's FP64 Jacobi solution of the same system (relative max-norm)
+        scale = float(np.max(np.abs(x_oracle)))
+        for prec, x in xs_host.items():
+            if prec in paths:
+                paths[prec]["err_vs_oracle"] = float(np.max(np.abs(x - x_oracle)) / scale)
+        err_vs_oracle = paths[args.precision].get("err_vs_oracle")
     hard = None if (args.quick or args.no_hard) else run_hard(args, jac, torch, dev, ws)
     small = None if (args.quick or args.no_small) else run_small(args, jac, torch, dev)
     batched = None if (args.quick or args.no_batch) else run_batch(args, jac, torch, dev)
@@ -253,6 +265,7 @@ def run_ours(args, world, rank, local):
         # their narrow copy inside the solve kernel
         "gpu_launches": (3 if args.precision.startswith("fp64") or fused else 4) * args.steps,
         "clocks": main["clocks"], "roofline": roofline, "roofline_composite": composite, "paths": paths,
+        "err_vs_oracle": err_vs_oracle,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
         "sparse": sparse,
         "serving": serving, "hard_generator": hard, "small_system": small,
@@ -576,7 +589,7 @@ def run_serve(args, jac, torch, dev, seconds):
     budget = int(min(args.serve_budget_gb * 1e9, free - 8e9))
 
     def served(split):
-        srv = jac.Server(budget_bytes=budget, split_residual=split)
+        srv = jac.Server(budget_bytes=budget, split_residual=split, inner_rtol=args.serve_inner_rtol)
         outs, arrive, lat, stats = {}, {}, {}, {}
         k = 0
         total = len(t)
@@ -622,12 +635,15 @@ def run_serve(args, jac, torch, dev, seconds):
                 "p50_ms": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
                 "max_ms": round(float(L[-1]), 3), "rounds": rounds,
                 "mean_in_system": round(float(np.mean(active_samples)), 1),
+                "mean_outer_steps": round(float(np.mean([v[2] for v in stats.values()])), 2),
+                "mean_inner_sweeps": round(float(np.mean([v[3] for v in stats.values()])), 2),
                 "worst_rel_residual": worst, "sampled_host_residuals_max": max(checked) if checked else None,
                 "budget_gb": round(budget / 1e9, 1),
                 "residual": "split-float (FP32 units)" if split else "FP64"}
 
-    served_fp64_resid = served(False)
-    served_split = served(True)
+    modes = args.serve_modes.split(",")
+    served_fp64_resid = served(False) if "fp64" in modes else None
+    served_split = served(True) if "split" in modes else None
 
     # the plain FP64 path, one request at a time, on the first seconds of the same trace
     m = int(np.searchsorted(t, args.serve_fp64_seconds))
@@ -653,7 +669,8 @@ def run_serve(args, jac, torch, dev, seconds):
             "throughput_per_s": round(m / wall64, 1) if m else None,
             "p50_ms": round(float(np.percentile(L64, 50)), 3) if m else None,
             "p99_ms": round(float(np.percentile(L64, 99)), 3) if m else None}
-    ratio = (lambda a: round(a["throughput_per_s"] / fp64["throughput_per_s"], 2) if fp64["throughput_per_s"] else None)
+    ratio = (lambda a: round(a["throughput_per_s"] / fp64["throughput_per_s"], 2)
+             if (a and fp64["throughput_per_s"]) else None)
     return {"served_fp32_ir": served_fp64_resid, "served_fp32_ir_split_residual": served_split,
             "one_at_a_time_fp64": fp64, "throughput_ratio": ratio(served_fp64_resid),
             "throughput_ratio_split_residual": ratio(served_split)}
@@ -836,7 +853,7 @@ def cpu_baseline(A, B, n, budget_s: float = 12.0):
     return {"value": round(1.0 / sec, 4), "unit": "solves/s", "cores": threads, "kind": "oracle",
             "sample": f"{solves} full FP64 oracle solve(s) of the n={n} system (OpenMP rows, "
                       f"{res.iters} sweeps each, relative-residual stop 1e-10)",
-            "single_core_ms_per_sweep": round(single_ms, 1)}
+            "single_core_ms_per_sweep": round(single_ms, 1)}, res.X[:, 0].copy()
 
 
 def run_reference(args, world, rank):
@@ -910,6 +927,10 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=100.0, dest="serve_budget_gb",
                     help="device-memory budget of the serving arena (the configuration's 100 GB; a few GB "
                          "for a profiler capture)")
+    ap.add_argument("--serve-inner-rtol", type=float, default=0.0, dest="serve_inner_rtol",
+                    help="serving: inner-sweep stop (relative change); 0 = library default")
+    ap.add_argument("--serve-modes", default="fp64,split", dest="serve_modes",
+                    help="serving: which residual forms to run (fp64, split)")
     ap.add_argument("--serve-fp64-seconds", type=float, default=1.0, dest="serve_fp64_seconds")
     ap.add_argument("--only", choices=["batch", "mrhs", "serve", "sparse", "small"], default=None,
                     help="run one secondary workload alone (profiling)")

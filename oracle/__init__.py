@@ -63,6 +63,8 @@ def _load():
             lib.oracle_ge.restype = ctypes.c_int
             lib.oracle_residual.argtypes = [_c_i64, _c_i64, vp, vp, vp, vp, _c_dp]
             lib.oracle_residual.restype = ctypes.c_int
+            lib.oracle_residual_rows.argtypes = [_c_i64, _c_i64, vp, vp, vp, _c_i64, vp, vp]
+            lib.oracle_residual_rows.restype = ctypes.c_int
             lib.oracle_split.argtypes = [_c_i64, _c_i64, vp, vp, vp, vp]
             lib.oracle_split.restype = ctypes.c_int
             lib.oracle_bf16_from_f32.argtypes = [ctypes.c_float]
@@ -218,6 +220,21 @@ def residual(A, B, X) -> tuple[np.ndarray, float]:
     rel = ctypes.c_double(0.0)
     lib.oracle_residual(n, Bc.shape[0], _ptr(A), _ptr(Bc), _ptr(Xc), _ptr(R), ctypes.byref(rel))
     return R.T.copy(), float(rel.value)
+
+
+def residual_rows(A, B, X, rows) -> np.ndarray:
+    """R[t, c] = B[i, c] - sum_j A[i, j] X[j, c] for i = rows[t] (FP64, the same row sums as residual())."""
+    lib = _load()
+    A = _mat(A)
+    n = A.shape[0]
+    Bc = _cols(B, n)
+    Xc = _cols(X, n)
+    rw = np.ascontiguousarray(rows, dtype=np.int64)
+    R = np.zeros((Bc.shape[0], rw.size))
+    st = lib.oracle_residual_rows(n, Bc.shape[0], _ptr(A), _ptr(Bc), _ptr(Xc), rw.size, _ptr(rw), _ptr(R))
+    if st != OK:
+        raise ValueError("invalid rows")
+    return R.T.copy()
 
 
 def split(A, B) -> tuple[int, np.ndarray, np.ndarray]:

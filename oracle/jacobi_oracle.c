@@ -430,6 +430,26 @@ int oracle_residual(int64_t n, int64_t nrhs, const double* A, const double* B, c
 }
 
 /*
+ * The residual of oracle_residual restricted to the listed rows: R[c * nrows + t] = b_ic - sum_j a_ij x_jc
+ * for i = rows[t], with the same ascending-j sum per row, for checking large systems on a sample of rows.
+ */
+int oracle_residual_rows(int64_t n, int64_t nrhs, const double* A, const double* B, const double* X,
+                         int64_t nrows, const int64_t* rows, double* R) {
+  if (n < 1 || nrhs < 1 || nrows < 0 || !A || !B || !X || !R || (nrows > 0 && !rows)) return OR_INVALID_ARG;
+  for (int64_t t = 0; t < nrows; ++t)
+    if (rows[t] < 0 || rows[t] >= n) return OR_INVALID_ARG;
+  for (int64_t c = 0; c < nrhs; ++c) {
+    for (int64_t t = 0; t < nrows; ++t) {
+      int64_t i = rows[t];
+      double s = 0.0;
+      for (int64_t j = 0; j < n; ++j) s += A[i * n + j] * X[c * n + j];
+      R[c * nrows + t] = B[c * n + i] - s;
+    }
+  }
+  return OR_OK;
+}
+
+/*
  * Residual r = b - A x of a CSR matrix in FP64 (the stored entries of each row in their ascending column
  * order, the diagonal included), and the relative residual ||r||_inf / ||b||_inf.  r may be NULL.  The
  * structure is trusted (oracle_csr_jacobi checks it).

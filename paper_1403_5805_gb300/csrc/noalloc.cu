@@ -11,7 +11,10 @@
 // exits.  Every call shares it and it keeps the previous call's contents: whatever must start at zero
 // (the control block, the diagonal-check key, ||B||) is cleared on the stream at the start of each call.
 // Calls whose work overlaps on the GPU (different streams, or different host threads on one device)
-// race on the array; serialise them.
+// race on the array; serialise them.  The array's device address is looked up once per device and kept
+// for the life of the process, so the call must not be used after cudaDeviceReset on that device (the
+// reset unloads the module and the kept address goes stale).
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -84,7 +87,7 @@ extern "C" int jacobi_solve_fp64_noalloc(const double* A, int64_t lda, const dou
                                          jacobi_stats* stats, void* stream) {
   if (!A || !B || !X_out || n < 1 || lda < n) return JACOBI_ERR_INVALID_ARG;
   if (n > JACOBI_NOALLOC_MAX_N) return JACOBI_ERR_INVALID_ARG;
-  if (max_iter < 1 || !(tol > 0.0) || tol > 1.79e308) return JACOBI_ERR_INVALID_ARG;
+  if (max_iter < 1 || !(tol > 0.0) || !std::isfinite(tol)) return JACOBI_ERR_INVALID_ARG;
   // rows are streamed in place by bulk copies: 16-byte aligned rows, and for odd n one padding element
   // per row is read (and ignored)
   if (reinterpret_cast<uintptr_t>(A) % 16 != 0 || lda % 2 != 0 || (n % 2 == 1 && lda == n))

@@ -186,6 +186,16 @@ def test_hard_generator_rate_is_one_over_f():
     assert abs(full.iters - pred) < 0.15 * pred
 
 
+def test_residual_rows_equal_the_full_residual():
+    A, B, Xs = synth.dominant_system(150, 1.1, seed=17, nrhs=4)
+    X = Xs + 1e-7 * np.sin(np.arange(Xs.size)).reshape(Xs.shape)
+    R, _ = oracle.residual(A, B, X)
+    rows = np.array([149, 0, 77, 77, 3])
+    np.testing.assert_array_equal(oracle.residual_rows(A, B, X, rows), R[rows])
+    with pytest.raises(ValueError):
+        oracle.residual_rows(A, B, X, [150])
+
+
 def test_split_fixed_point():
     A, B, Xs = synth.dominant_system(50, 1.25, seed=4, nrhs=2)
     st, T, C = oracle.split(A, B)

@@ -96,3 +96,44 @@ def test_rejects_sizes_beyond_the_limit(jac):
     rc, _, _ = noalloc_solve(jac, torch.from_numpy(A).cuda(), 3, torch.from_numpy(B[:, 0].copy()).cuda(), 4,
                              10, 1e-12)
     assert rc == jac.ERR_INVALID_ARG  # lda < n
+
+
+def test_failed_diagonal_check_leaves_nothing_behind(jac):
+    # A zero (then a non-finite) a_ii must be reported as the regular path reports it, and the next call,
+    # which reuses the same scratch (diagonal-check key, ||B||), must solve as if nothing had failed.
+    import torch
+    n = 300
+    A, B, _ = synth.dominant_system(n, 1.2, seed=41)
+    b = B[:, 0].copy()
+    B_t = torch.from_numpy(b).cuda()
+    for bad, want_rc in ((0.0, jac.ERR_ZERO_DIAGONAL), (float("nan"), jac.ERR_NONFINITE)):
+        Ab = A.copy()
+        Ab[123, 123] = bad
+        rc, _, _ = noalloc_solve(jac, torch.from_numpy(Ab).cuda(), n, B_t, n, 100, 1e-12)
+        assert rc == want_rc
+        want, st_want = regular_solve(jac, A, b, 3000, 1e-12)
+        rc, got, st = noalloc_solve(jac, torch.from_numpy(A).cuda(), n, B_t, n, 3000, 1e-12)
+        assert rc == jac.OK == st_want.status and st.sweeps == st_want.sweeps
+        assert rel(got, want) <= TOL_ITER
+
+
+def test_rejects_host_memory_and_bad_tolerances(jac):
+    import torch
+    n = 64
+    A, B, _ = synth.dominant_system(n, 1.5, seed=5)
+    b = np.ascontiguousarray(B[:, 0])
+    A_t, B_t = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    lib = jac.load()
+    st = jac.JacobiStats()
+    stream = torch.cuda.current_stream().cuda_stream
+    # host (pageable) A: rejected by the pointer check before any device work
+    rc = lib.jacobi_solve_fp64_noalloc(A.ctypes.data, n, B_t.data_ptr(), n, None, 10, 1e-12, out.data_ptr(),
+                                       ctypes.byref(st), stream)
+    assert rc == jac.ERR_INVALID_ARG
+    for tol in (0.0, -1.0, float("inf"), float("nan")):
+        rc, _, _ = noalloc_solve(jac, A_t, n, B_t, n, 10, tol)
+        assert rc == jac.ERR_INVALID_ARG, tol
+    # the largest finite tol is a valid (if useless) bound, as on the regular path: one sweep
+    rc, _, st = noalloc_solve(jac, A_t, n, B_t, n, 10, float(np.finfo(np.float64).max))
+    assert rc == jac.OK and st.sweeps == 1
