@@ -219,7 +219,8 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": bytes_launch, "kernel_ms": round(main["kernel_ms"], 4),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
 
-    composite = composite_roofline(main, n, args.precision, peaks, dev, torch)
+    fma = fma_peaks(jac, torch, dev)
+    composite = composite_roofline(main, n, args.precision, peaks, dev, torch, fma)
     paths = {args.precision: summarize(main, args.steps, n, args.precision)}
     if not args.quick:
         for prec in [p for p in ("fp64", "fp64+gs", "fp8_ir", "fp32_ir", "bf16_ir+split", "fp32_ir+split")
@@ -264,7 +265,8 @@ def run_ours(args, world, rank, local):
         # per step: diagonal check, right-hand side, (narrow copy,) solve; BF16 / FP32 inner sweeps write
         # their narrow copy inside the solve kernel
         "gpu_launches": (3 if args.precision.startswith("fp64") or fused else 4) * args.steps,
-        "clocks": main["clocks"], "roofline": roofline, "roofline_composite": composite, "paths": paths,
+        "clocks": main["clocks"], "roofline": roofline, "roofline_composite": composite, "fma_peaks": fma,
+        "paths": paths,
         "err_vs_oracle": err_vs_oracle,
         "mixed_vs_fp64_solves_ratio": fp64_ratio, "e2e": e2e, "batched": batched, "many_rhs": many_rhs,
         "sparse": sparse,
@@ -288,12 +290,34 @@ def job_rate(ms_step, world, device):
     return ms_max, world / (ms_max * 1e-3)
 
 
-def composite_roofline(r, n, prec, peaks, dev, torch):
-    """Per-phase lower bound of the timed kernel: each FP64 pass (residual or sweep) is held by the larger of
-    its HBM time and its FP64-FMA time (n^2 FMAs at 2 FP64 FMA per clock per SM), every other phase by its
-    HBM time; the sum over the launch's phases against the measured kernel time."""
+def fma_peaks(jac, torch, dev):
+    """FP64 and FP32 FMA rates of this GPU's CUDA cores, measured here (jacobi_measure_fma_rates), beside
+    the rate derived from the unit count (2 FP64 FMA per clock per SM at the maximum SM clock)."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp64_fma_s = 2.0 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    f64, f32 = jac.measure_fma_rates()
+    f64b, f32b = jac.measure_fma_rates()
+    f64, f32 = max(f64, f64b), max(f32, f32b)
+    derived = 2.0 * sms * measured_peaks()[0].get("sm_max_mhz", 2070.0) * 1e6
+    return {"fp64_gfma_s": round(f64 / 1e9, 1), "fp32_gfma_s": round(f32 / 1e9, 1),
+            "fp64_tflops": round(2 * f64 / 1e12, 3), "fp64_fma_per_clk_per_sm_at_max_clock":
+            round(f64 / (sms * measured_peaks()[0].get("sm_max_mhz", 2070.0) * 1e6), 3),
+            "fp64_derived_gfma_s": round(derived / 1e9, 1),
+            "how": "8 independent FMA chains per thread, 8 blocks of 256 threads per SM, CUDA events, best of 2"}
+
+
+def composite_roofline(r, n, prec, peaks, dev, torch, fma=None):
+    """Per-phase lower bound of the timed kernel: each FP64 pass (residual or sweep) is held by the larger of
+    its HBM time and its FP64-FMA time (n^2 FMAs at the measured FP64 FMA rate, else 2 FP64 FMA per clock
+    per SM), every other phase by its HBM time; the sum over the launch's phases against the measured
+    kernel time."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if fma is not None:
+        fp64_fma_s = fma["fp64_gfma_s"] * 1e9
+        src = f"measured: {fma['fp64_gfma_s']:.0f} GFMA/s ({fma['fp64_tflops']:.2f} TFLOP/s, jacobi_measure_fma_rates)"
+    else:
+        fp64_fma_s = 2.0 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        src = (f"derived: 2 FP64 FMA/clock/SM x {sms} SMs x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz = "
+               f"{fp64_fma_s / 1e9:.0f} GFMA/s")
     hbm = peaks["hbm_gbs"] * 1e9
     es = ESIZE.get(prec.replace("+split", "").replace("+gs", ""), 8)
     per = {"sweep64": (8.0, True), "resid64": (8.0, True), "resid0": (0.0, False), "inner": (float(es), False),
@@ -312,9 +336,7 @@ def composite_roofline(r, n, prec, peaks, dev, torch):
     kernel_s = r["kernel_ms"] * 1e-3
     return {"min_ms": round(total * 1e3, 4), "kernel_ms": round(r["kernel_ms"], 4),
             "frac": round(total / kernel_s, 4) if kernel_s > 0 else None, "phases": rows,
-            "fp64_fma_peak": f"2 FP64 FMA/clock/SM x {sms} SMs x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz = "
-                             f"{fp64_fma_s / 1e9:.0f} GFMA/s (derived; about 1.26 TFLOP/s)",
-            "hbm_peak_gbs": peaks["hbm_gbs"]}
+            "fp64_fma_peak": src, "hbm_peak_gbs": peaks["hbm_gbs"]}
 
 
 def phase_bandwidth(trace, n, prec):
@@ -541,8 +563,14 @@ def run_many_rhs(args, jac, torch, dev):
     Xst = torch.from_numpy(np.ascontiguousarray(Xs.T)).to(dev)
     stream = torch.cuda.current_stream(dev)
     out = {"n": n, "nrhs": r, "dominance": 1.1}
-    for prec, steps in (("bf16_ir", args.mrhs_steps), ("bf16_ir+split", args.mrhs_steps), ("fp64", 1)):
-        solver = jac.MultiSolver(At, Bt, precision=prec.replace("+split", ""), split_residual=prec.endswith("+split"))
+    for prec, steps in (("bf16_ir+tc", args.mrhs_steps), ("bf16_ir", args.mrhs_steps),
+                        ("bf16_ir+split", args.mrhs_steps), ("fp64", 1)):
+        torch.cuda.synchronize(dev)
+        t_setup = time.perf_counter()
+        solver = jac.MultiSolver(At, Bt, precision=prec.split("+")[0], split_residual=prec.endswith("+split"),
+                                 tc_residual=prec.endswith("+tc"))
+        torch.cuda.synchronize(dev)
+        setup_ms = (time.perf_counter() - t_setup) * 1e3
         X, st = solver.solve(max_iter=5000, tol=TARGET if prec != "fp64" else args.fp64_tol)  # warm-up
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -554,7 +582,8 @@ def run_many_rhs(args, jac, torch, dev):
         ms = e0.elapsed_time(e1) / steps
         err = (X - Xst).abs().amax(dim=1)
         phases = {}
-        rname = "resid64_split_fp32" if prec.endswith("+split") else "resid64_fp64"
+        rname = ("resid64_split_fp32" if prec.endswith("+split") else
+                 "resid64_tc_digits" if prec.endswith("+tc") else "resid64_fp64")
         for kind, name, es, flop in ((3, "inner_tcgen05_bf16", 2, True), (1, rname, 8, True),
                                      (0, "sweep64_fp64", 8, True)):
             d = [(e - b) for k, b, e in solver.trace() if k == kind]
@@ -563,11 +592,13 @@ def run_many_rhs(args, jac, torch, dev):
                 phases[name] = {"count": len(d), "mean_us": round(mean / 1e3, 1),
                                 "matrix_gbs": round(es * float(n) * n / mean, 1),
                                 "tflops": round(2.0 * n * n * r / mean / 1e3, 2)}
-        out[prec] = {"solves_per_s": round(1e3 / ms, 3), "ms_per_solve": round(ms, 2), "status": st.status,
+        out[prec] = {"solves_per_s": round(1e3 / ms, 3), "ms_per_solve": round(ms, 2), "setup_ms": round(setup_ms, 1),
+                     "status": st.status,
                      "sweeps": st.sweeps, "outer_steps": st.outer_steps, "rel_residual": st.rel_residual,
                      "max_err_vs_xstar_per_rhs": float(err.max().item()), "phases": phases}
         solver.close()
     out["mixed_vs_fp64_solves_ratio"] = round(out["bf16_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
+    out["mixed_tc_vs_fp64_solves_ratio"] = round(out["bf16_ir+tc"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     out["mixed_split_vs_fp64_solves_ratio"] = round(
         out["bf16_ir+split"]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
     return out

@@ -182,6 +182,16 @@ typedef enum { JACOBI_METHOD_JACOBI = 0, JACOBI_METHOD_SOR = 1 } jacobi_method;
 #define JACOBI_FLAG_RETIRE_COLUMNS 16
 /* Sparse handle: keep T in sliced ELL even when its entries lie on a few diagonals (see jacobi_csr_format). */
 #define JACOBI_FLAG_CSR_ELL 64
+/* BF16 inner sweeps with many right-hand sides (nrhs 16, 32, 64 or 128): compute each residual
+ * r = B - A X on the tcgen05 tensor cores with FP64 accuracy instead of FP64 FMAs.  Setup splits the off-
+ * diagonal part of A (each row scaled by a power of two from its largest entry) into 7 balanced base-256
+ * digits stored as BF16 matrices (14 bytes per entry of A in the workspace), and each residual splits X
+ * (each column scaled by its largest entry) the same way; the products of digit pairs whose levels add up
+ * to at most 8 are summed by tcgen05.mma in FP32, exactly (1024-column chunks of integer products of at
+ * most 2^14), the chunk sums in float-float, the diagonal term in FP64.  The representation and dropped-
+ * pair errors are below 2^-50 of sum_j |a_ij| max |x_jc| per entry.  Not with JACOBI_FLAG_SPLIT_RESIDUAL;
+ * JACOBI_ERR_UNSUPPORTED for other precisions or one right-hand side. */
+#define JACOBI_FLAG_TC_RESIDUAL 128
 
 /* Fill *d with defaults (n = 0 and null pointers: the caller sets those). */
 JACOBI_API void jacobi_desc_init(jacobi_desc* d);
@@ -385,6 +395,18 @@ JACOBI_API void jacobi_server_destroy(jacobi_server* s);
  * of stream 5).  Asynchronous on `stream`. */
 JACOBI_API int jacobi_generate_request(int64_t n, int64_t r, double f, uint64_t seed, double* A, double* B,
                                        int64_t ldb, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * Measured arithmetic rates.  The paper has no counterpart: this is the measurement behind the roofline
+ * that FP64 passes over A are held to (one FP64 FMA per 8-byte entry of A), and behind the FP32-unit
+ * bound of the split-float residual.
+ * ------------------------------------------------------------------------------------------------ */
+
+/* Time `iters` iterations of 8 independent FMA chains per thread on every SM of the current device, in
+ * FP64 and then in FP32 (64 times as many iterations), each after an untimed launch, with CUDA events on
+ * `stream` (a cudaStream_t; NULL: legacy default stream).  Writes the FMAs per second of each (host
+ * doubles).  Blocks until done.  JACOBI_ERR_INVALID_ARG for iters < 1 or a NULL output. */
+JACOBI_API int jacobi_measure_fma_rates(int64_t iters, double* fp64_fma_per_s, double* fp32_fma_per_s, void* stream);
 
 /* ------------------------------------------------------------------------------------------------
  * Allocation-free FP64 solve.  The paper has no counterpart to this entry point: it exists for callers

@@ -7,9 +7,9 @@ from .binding import (BF16_IR, ERR_CUDA, ERR_INVALID_ARG, ERR_NONFINITE, ERR_OUT
                       ERR_UNSUPPORTED, ERR_ZERO_DIAGONAL, EXPORTS, FP8_IR, FP32_IR, FP64, LIB_PATH, NORM_2,
                       NORM_INF, NORM_RESID, NOT_CONVERGED, OK, DeviceSolver, HostSolver, JacobiDesc, JacobiError,
                       JacobiStats, load, BatchSolver, JacobiBatchDesc, MultiSolver, Server,
-                      generate_request, CsrSolver, JacobiCsrDesc, batch_solve)
+                      generate_request, CsrSolver, JacobiCsrDesc, batch_solve, measure_fma_rates)
 
-__all__ = ["batch_solve", "CsrSolver", "JacobiCsrDesc", "Server", "generate_request", "MultiSolver", "BatchSolver", "JacobiBatchDesc", "DeviceSolver", "HostSolver", "JacobiDesc", "JacobiError", "JacobiStats", "load", "LIB_PATH", "EXPORTS",
+__all__ = ["measure_fma_rates", "batch_solve", "CsrSolver", "JacobiCsrDesc", "Server", "generate_request", "MultiSolver", "BatchSolver", "JacobiBatchDesc", "DeviceSolver", "HostSolver", "JacobiDesc", "JacobiError", "JacobiStats", "load", "LIB_PATH", "EXPORTS",
            "OK", "NOT_CONVERGED", "ERR_INVALID_ARG", "ERR_ZERO_DIAGONAL", "ERR_NONFINITE", "ERR_OUT_OF_MEMORY",
            "ERR_CUDA", "ERR_TIMEOUT", "ERR_UNSUPPORTED", "FP64", "FP32_IR", "BF16_IR", "FP8_IR", "NORM_INF",
            "NORM_2", "NORM_RESID"]

@@ -34,6 +34,7 @@ FLAG_TEST_DROP_COPY = 8
 FLAG_TEST_SKIP_ARRIVAL = 32
 FLAG_CSR_ELL = 64  # sparse handle: keep sliced ELL even for a banded matrix
 FLAG_RETIRE_COLUMNS = 16
+FLAG_TC_RESIDUAL = 128
 METHODS = {"jacobi": 0, "sor": 1}
 
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
@@ -45,7 +46,7 @@ EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_stri
            "jacobi_server_step", "jacobi_server_poll", "jacobi_server_rounds", "jacobi_server_destroy",
            "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async", "jacobi_csr_solve",
            "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace", "jacobi_csr_destroy",
-           "jacobi_batch_solve", "jacobi_server_wait", "jacobi_csr_format")
+           "jacobi_batch_solve", "jacobi_server_wait", "jacobi_csr_format", "jacobi_measure_fma_rates")
 
 
 class JacobiStats(ctypes.Structure):
@@ -158,6 +159,7 @@ def load() -> ctypes.CDLL:
         lib.jacobi_server_wait.argtypes = [H, i64, ctypes.POINTER(JacobiStats)]
         lib.jacobi_csr_destroy.argtypes = [H]
         lib.jacobi_csr_destroy.restype = None
+        lib.jacobi_measure_fma_rates.argtypes = [i64, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
         for name in ("jacobi_setup", "jacobi_solve", "jacobi_workspace_size", "jacobi_setup_ex",
                      "jacobi_solve_async", "jacobi_solve_ex", "jacobi_last_stats", "jacobi_residual",
                      "jacobi_get_narrow", "jacobi_last_trace", "jacobi_column_stats", "jacobi_solve_fp64_noalloc",
@@ -166,10 +168,20 @@ def load() -> ctypes.CDLL:
                      "jacobi_server_submit_generated", "jacobi_server_step", "jacobi_server_poll",
                      "jacobi_server_rounds", "jacobi_generate_request", "jacobi_csr_setup", "jacobi_csr_solve_async",
                      "jacobi_csr_solve", "jacobi_csr_last_stats", "jacobi_csr_info", "jacobi_csr_last_trace",
-                     "jacobi_batch_solve", "jacobi_server_wait", "jacobi_csr_format"):
+                     "jacobi_batch_solve", "jacobi_server_wait", "jacobi_csr_format", "jacobi_measure_fma_rates"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
+
+
+def measure_fma_rates(iters: int = 200000, stream=None) -> tuple[float, float]:
+    """FP64 and FP32 FMAs per second of the current device's CUDA cores (``jacobi_measure_fma_rates``)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    f64, f32 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().jacobi_measure_fma_rates(iters, ctypes.byref(f64), ctypes.byref(f32), s.cuda_stream),
+           "jacobi_measure_fma_rates", False)
+    return f64.value, f32.value
 
 
 def _check(status: int, where: str, allow_warn: bool = True) -> int:
@@ -522,7 +534,7 @@ class MultiSolver:
 
     def __init__(self, A, B, precision: str = "bf16_ir", stream=None, max_outer: int = 0, max_inner: int = 0,
                  inner_rtol: float = 0.0, norm: str = "inf", split_residual: bool = False,
-                 retire_columns: bool = False):
+                 retire_columns: bool = False, tc_residual: bool = False, flags: int = 0):
         import torch
         lib = load()
         n = A.shape[0]
@@ -540,7 +552,8 @@ class MultiSolver:
         d.B, d.ldb = B.data_ptr(), B.stride(0)
         d.stream = self.stream.cuda_stream
         d.max_outer, d.max_inner, d.inner_rtol = max_outer, max_inner, inner_rtol
-        d.flags = (FLAG_SPLIT_RESIDUAL if split_residual else 0) | (FLAG_RETIRE_COLUMNS if retire_columns else 0)
+        d.flags = ((FLAG_SPLIT_RESIDUAL if split_residual else 0) | (FLAG_RETIRE_COLUMNS if retire_columns else 0)
+                   | (FLAG_TC_RESIDUAL if tc_residual else 0) | flags)
         nbytes = ctypes.c_size_t(0)
         with torch.cuda.device(A.device):
             _check(lib.jacobi_workspace_size(ctypes.byref(d), ctypes.byref(nbytes)), "jacobi_workspace_size")

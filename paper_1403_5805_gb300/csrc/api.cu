@@ -134,15 +134,23 @@ int validate_desc(const jacobi_desc* d) {
     if (d->precision != JACOBI_FP64 && d->precision != JACOBI_BF16_IR) return JACOBI_ERR_UNSUPPORTED;
     if (d->precision == JACOBI_BF16_IR && !mrhs_supported_r(d->nrhs)) return JACOBI_ERR_UNSUPPORTED;
   }
+  if (d->flags & JACOBI_FLAG_TC_RESIDUAL) {
+    if (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) return JACOBI_ERR_INVALID_ARG;
+    if (d->nrhs < 2 || d->precision != JACOBI_BF16_IR || d->method != JACOBI_METHOD_JACOBI)
+      return JACOBI_ERR_UNSUPPORTED;
+  }
   return JACOBI_OK;
 }
 
 // Extra device buffers of a many-right-hand-side handle (vectors v[c*ld + i]).
 struct MrhsLayout {
-  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, colsq, bcol, stats, status, xs, xexp, cols, total;
+  size_t b, xa, xb, c1, da, db, dah, dbh, colmax, colsq, bcol, stats, status, xs, xexp, cols, adig, aexp, xdig,
+      total;
 };
 
-MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
+// tc: the tensor-core residual's digit matrices of A (kOzDigits x nr x ld BF16), row exponents and the
+// digits of X (kOzDigits x r x ld BF16).
+MrhsLayout mrhs_layout(size_t base, int64_t n, int64_t ld, int64_t r, bool tc) {
   MrhsLayout M{};
   size_t o = base;
   auto take = [&o](size_t bytes) {
@@ -169,6 +177,12 @@ MrhsLayout mrhs_layout(size_t base, int64_t ld, int64_t r) {
   M.xs = take(v8);  // split-float residual: two FP32 words per entry of X
   M.xexp = take(static_cast<size_t>(r) * 4);
   M.cols = take(static_cast<size_t>(r) * 4);  // active columns (column retirement)
+  if (tc) {
+    const int64_t nr = oz_padded_rows(n);
+    M.adig = take(static_cast<size_t>(kOzDigits) * nr * ld * 2);
+    M.aexp = take(static_cast<size_t>(nr) * 4);
+    M.xdig = take(static_cast<size_t>(kOzDigits) * r * ld * 2);
+  }
   M.total = o;
   return M;
 }
@@ -196,6 +210,7 @@ struct jacobi_handle {
   int max_inner = 1000;
   float inner_rtol = 0.0f;
   bool split_residual = false;
+  bool tc_residual = false;  // many right-hand sides: residuals on the tensor cores (digit split of A, X)
   bool fuse_narrow = false;  // the narrow copy is written by the first inner sweep of the first solve
   bool retire_columns = false;
   int method = JACOBI_METHOD_JACOBI;
@@ -308,7 +323,8 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   h->L = make_layout(d->n, d->precision, copy_A);
   h->nrhs = d->nrhs;
   if (h->nrhs > 1) {
-    h->M = mrhs_layout(h->L.total, h->L.ld, h->nrhs);
+    h->tc_residual = (d->flags & JACOBI_FLAG_TC_RESIDUAL) != 0;
+    h->M = mrhs_layout(h->L.total, h->n, h->L.ld, h->nrhs, h->tc_residual);
     h->L.total = h->M.total;
   }
   h->max_outer = d->max_outer > 0 ? d->max_outer : 60;
@@ -373,6 +389,8 @@ int mrhs_prepare(jacobi_handle* h, const double* B, int64_t ldb) {
   CK(cudaMemsetAsync(bcol, 0, static_cast<size_t>(r) * 8, s));
   CK(launch_mrhs_init(n, r, ld, b, h->at<double>(h->L.rinv), h->at<float>(h->M.c1), h->at<float>(h->M.da),
                       h->at<__nv_bfloat16>(h->M.dah), bcol, s));
+  if (h->tc_residual)
+    CK(launch_oz_split_a(h->A64, h->lda64, n, ld, h->at<__nv_bfloat16>(h->M.adig), h->at<int>(h->M.aexp), s));
   CK(cudaStreamSynchronize(s));
   return JACOBI_OK;
 }
@@ -533,13 +551,43 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
           p.xexp = h->at<int>(h->M.xexp);
           CK(launch_mrhs_split_x(n, r, ld, xc, h->at<float2>(h->M.xs), h->at<int>(h->M.xexp), s));
         }
-        CK(launch_mrhs_dense(p, s));
+        if (h->tc_residual) {
+          OzResidParams q{};
+          q.n = n;
+          q.r = r;
+          q.ld = ld;
+          q.nr = oz_padded_rows(n);
+          q.aexp = h->at<int>(h->M.aexp);
+          q.xexp = h->at<int>(h->M.xexp);
+          q.x = xc;
+          q.b = h->at<double>(h->M.b);
+          q.d = h->at<double>(h->L.d);
+          q.rinv = h->at<double>(h->L.rinv);
+          q.c1 = c1;
+          q.d1 = dA;
+          q.d1h = hA;
+          q.colmax = colmax;
+          q.cols = retire ? dcols : nullptr;
+          q.nact = static_cast<int64_t>(act.size());
+          q.status = status;
+          q.wait_ns = h->wait_ns;
+          CK(launch_oz_split_x(n, r, ld, xc, h->at<__nv_bfloat16>(h->M.xdig), h->at<int>(h->M.xexp), s));
+          CK(launch_oz_resid(h->at<__nv_bfloat16>(h->M.adig), h->at<__nv_bfloat16>(h->M.xdig), q, s));
+        } else {
+          CK(launch_mrhs_dense(p, s));
+        }
         clk.mark(JACOBI_PHASE_RESID64);
       }
       first = false;
       ++outer;
       CK(cudaMemcpyAsync(hc.data(), colmax, static_cast<size_t>(r) * 8, cudaMemcpyDeviceToHost, s));
+      int rst = 0;
+      if (h->tc_residual) CK(cudaMemcpyAsync(&rst, status, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (rst != 0) {  // a bounded wait of the tensor-core residual expired: its maxima are incomplete
+        out.status = rst;
+        break;
+      }
       double rho = 0.0;
       std::vector<int> keep;
       for (int c : act) {
@@ -906,7 +954,8 @@ void jacobi_desc_init(jacobi_desc* d) {
 int jacobi_workspace_size(const jacobi_desc* d, size_t* bytes) {
   if (!d || !bytes || d->n < 1 || d->nrhs < 1) return JACOBI_ERR_INVALID_ARG;
   const Layout L = make_layout(d->n, d->precision, !can_borrow(d));
-  *bytes = d->nrhs > 1 ? mrhs_layout(L.total, L.ld, d->nrhs).total : L.total;
+  *bytes = d->nrhs > 1 ? mrhs_layout(L.total, d->n, L.ld, d->nrhs, (d->flags & JACOBI_FLAG_TC_RESIDUAL) != 0).total
+                        : L.total;
   return JACOBI_OK;
 }
 

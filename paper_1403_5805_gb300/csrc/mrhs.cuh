@@ -55,6 +55,41 @@ struct MrhsDenseParams {
   double* colsq;
 };
 
+// FP64-accurate residual on the tensor cores (ozaki.cu): A's off-diagonal part and X split into kOzDigits
+// balanced base-256 BF16 digits each; products of digit pairs summed exactly in FP32 chunks.
+constexpr int kOzDigits = 7;
+// Rows of each of A's digit matrices: n rounded up to the 128-row tile.
+int64_t oz_padded_rows(int64_t n);
+
+// Residual pass R = B - A X (all r columns computed; active columns written as mode 0 of the FP64 pass:
+// c1 = R / a_ii, d1 = c1 (FP32, BF16), colmax[c] = max_i |R_ic|).
+struct OzResidParams {
+  int64_t n, r, ld, nr;
+  const int* aexp;          // nr: exponent of each row's off-diagonal maximum (A's digit scale)
+  const int* xexp;          // r: exponent of each column's maximum (X's digit scale)
+  const double* x;          // FP64 iterate x[c*ld + i]
+  const double* b;
+  const double* d;          // a_ii
+  const double* rinv;       // 1 / a_ii
+  float* c1;
+  float* d1;
+  __nv_bfloat16* d1h;
+  unsigned long long* colmax;
+  const int* cols;          // active columns (NULL: all)
+  int64_t nact;
+  int* status;              // set to a timeout code if a bounded wait expires
+  uint64_t wait_ns;
+};
+// dig[(p*nr + i)*ld + j]: digit p of a_ij (j != i), zero elsewhere; aexp[i] as above.  A row-major with
+// 16-byte aligned rows (lda even).
+cudaError_t launch_oz_split_a(const double* A, int64_t lda, int64_t n, int64_t ld, __nv_bfloat16* dig, int* aexp,
+                              cudaStream_t s);
+// xd[(q*r + c)*ld + i]: digit q of x_ic; xexp[c].
+cudaError_t launch_oz_split_x(int64_t n, int64_t r, int64_t ld, const double* x, __nv_bfloat16* xd, int* xexp,
+                              cudaStream_t s);
+cudaError_t launch_oz_resid(const __nv_bfloat16* adig, const __nv_bfloat16* xdig, const OzResidParams& p,
+                            cudaStream_t s);
+
 bool mrhs_supported_r(int64_t r);
 // Encodes the TMA maps of the BF16 matrix (n x n, row pitch ld) and of the BF16 iterate block (r x n,
 // row pitch ld) and launches one sweep.

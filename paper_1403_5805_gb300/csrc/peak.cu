@@ -1,0 +1,75 @@
+// Measured arithmetic rates of this GPU's CUDA cores, the denominators of the FP64-FMA and FP32 bounds
+// that the FP64 sweeps, the FP64 residual passes and the split-float residual are held to.
+//
+// Each thread runs kChains independent FMA chains (x <- x * m + c with |m| < 1, so values stay finite),
+// enough independent work per warp that the issue of the FMA pipe, not its latency, limits the rate.  The
+// grid holds every SM full (kBlocksPerSm blocks of kPeakThreads threads each).  The timed launch follows an
+// untimed one on the same stream; the rate is FMAs / elapsed time of the timed launch (CUDA events).
+#include <cuda_runtime.h>
+
+#include "solver.cuh"
+
+namespace jac {
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kPeakThreads = 256;
+constexpr int kBlocksPerSm = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kPeakThreads) fma_rate_kernel(int64_t iters, T m, T c, T* sink) {
+  T x[kChains];
+#pragma unroll
+  for (int u = 0; u < kChains; ++u) x[u] = static_cast<T>(threadIdx.x + u) * static_cast<T>(1e-3);
+  for (int64_t k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int u = 0; u < kChains; ++u) x[u] = fma(x[u], m, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int u = 0; u < kChains; ++u) s += x[u];
+  if (s == static_cast<T>(-1.5)) sink[0] = s;  // never true; keeps the chains live
+}
+
+template <typename T>
+cudaError_t time_rate(int64_t iters, cudaStream_t s, double* per_s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid = sms * kBlocksPerSm;
+  cudaEvent_t a, b;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return e;
+  }
+  const T m = static_cast<T>(0.999999), c = static_cast<T>(1e-7);
+  fma_rate_kernel<T><<<grid, kPeakThreads, 0, s>>>(iters / 4 + 1, m, c, nullptr);
+  cudaEventRecord(a, s);
+  fma_rate_kernel<T><<<grid, kPeakThreads, 0, s>>>(iters, m, c, nullptr);
+  cudaEventRecord(b, s);
+  e = cudaEventSynchronize(b);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return e;
+  const double fmas = static_cast<double>(grid) * kPeakThreads * kChains * static_cast<double>(iters);
+  *per_s = ms > 0.0f ? fmas / (static_cast<double>(ms) * 1e-3) : 0.0;
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace jac
+
+extern "C" int jacobi_measure_fma_rates(int64_t iters, double* fp64_fma_per_s, double* fp32_fma_per_s,
+                                        void* stream) {
+  if (iters < 1 || !fp64_fma_per_s || !fp32_fma_per_s) return JACOBI_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (jac::time_rate<double>(iters, s, fp64_fma_per_s) != cudaSuccess) return JACOBI_ERR_CUDA;
+  // the FP32 pipe is about 64 times faster: run 64 times the iterations for a comparable duration
+  if (jac::time_rate<float>(iters * 64, s, fp32_fma_per_s) != cudaSuccess) return JACOBI_ERR_CUDA;
+  return JACOBI_OK;
+}

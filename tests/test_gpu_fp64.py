@@ -242,3 +242,11 @@ def test_bounded_wait_expires_and_context_stays_usable(jac, prec):
     else:
         _, rel = oracle.residual(A, B, X.cpu().numpy())
         assert rel <= 1e-10
+
+
+def test_measured_fma_rates_are_plausible(jac):
+    # the measurement behind the FP64-FMA bound of the FP64 passes: GB300's CUDA cores issue FP64 FMAs at a
+    # small fraction of their FP32 rate (nominally about 1.2 TFLOP/s FP64 against tens of TFLOP/s FP32)
+    f64, f32 = jac.measure_fma_rates(iters=20000)
+    assert 1e11 < f64 < 1e13, f64
+    assert f32 > 8 * f64, (f32, f64)

@@ -78,12 +78,14 @@ def test_tcgen05_sweep_product(jac, n, r):
     assert np.all(np.abs(got - want) <= 2e-6 * scale + 1e-12), np.max(np.abs(got - want) / (scale + 1e-300))
 
 
-@pytest.mark.parametrize("n,r,gen", [(300, 16, "dom"), (777, 64, "dom"), (1024, 64, "hard"), (2000, 32, "dom")])
-def test_bf16_refinement_many_rhs(jac, n, r, gen):
+@pytest.mark.parametrize("tc", [False, True], ids=["fp64_resid", "tc_resid"])
+@pytest.mark.parametrize("n,r,gen", [(300, 16, "dom"), (777, 64, "dom"), (1024, 64, "hard"), (2000, 32, "dom"),
+                                     (333, 128, "dom")])
+def test_bf16_refinement_many_rhs(jac, n, r, gen, tc):
     make = synth.dominant_system if gen == "dom" else synth.hard_system
     A, B, Xs = make(n, 1.1, seed=800 + n, nrhs=r)
     At, Bt = dev(A, B)
-    s = jac.MultiSolver(At, Bt, precision="bf16_ir")
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", tc_residual=tc)
     X, st = s.solve(max_iter=5000, tol=1e-10)
     Xh = X.cpu().numpy().T
     _, rel = oracle.residual(A, B, Xh)
@@ -93,19 +95,33 @@ def test_bf16_refinement_many_rhs(jac, n, r, gen):
     assert np.all(err <= 2e-10 * (1 + q) / (1 - q) * np.max(np.abs(Xs))), err.max()
 
 
-def test_full_size_many_rhs_against_the_oracle(jac):
-    """n = 32768, 64 right-hand sides, f = 1.1 (the many-right-hand-side configuration at full size): BF16
-    tcgen05 sweeps with FP64 refinement, compared column by column with the oracle's FP64 Jacobi solve of
-    the same system (all host cores, residual-norm stop 1e-12).  For strictly dominant A,
-    ||A^-1||_inf <= 1 / min_i (|a_ii| - sum_{j!=i} |a_ij|), so two solutions whose residuals are at most
-    1e-10 and 1e-12 of ||b_c|| differ by at most ||A^-1||_inf (1e-10 + 1e-12) ||b_c||_inf in every entry (the
-    oracle stops on its previous iterate's residual; the returned one is closer, as ||T||_inf < 1); a wrong
-    entry anywhere in X fails that.  The residual of every column is also recomputed by the oracle on
-    512 sampled rows."""
+@pytest.fixture(scope="module")
+def full_size_system():
+    """n = 32768, 64 right-hand sides, f = 1.1, and the oracle's FP64 Jacobi solution (all host cores,
+    residual-norm stop 1e-12)."""
     n, r = 32768, 64
     A, B, Xs = synth.dominant_system(n, 1.1, seed=synth.BASE_SEED + 3, nrhs=r)
+    ref = oracle.jacobi(A, B, max_iter=200, tol=1e-12, norm=oracle.NORM_RESID, nthreads=oracle.num_threads())
+    assert ref.status == oracle.OK
+    d = np.abs(np.diag(A))
+    margin = float(np.min(d - (np.abs(A).sum(axis=1) - d)))
+    return A, B, Xs, ref, margin
+
+
+@pytest.mark.parametrize("tc", [False, True], ids=["fp64_resid", "tc_resid"])
+def test_full_size_many_rhs_against_the_oracle(jac, full_size_system, tc):
+    """n = 32768, 64 right-hand sides, f = 1.1 (the many-right-hand-side configuration at full size): BF16
+    tcgen05 sweeps with FP64 refinement (the residual by FP64 FMAs, or on the tensor cores from the digit
+    split), compared column by column with the oracle's FP64 Jacobi solve of the same system.  For strictly
+    dominant A, ||A^-1||_inf <= 1 / min_i (|a_ii| - sum_{j!=i} |a_ij|), so two solutions whose residuals are
+    at most 1e-10 and 1e-12 of ||b_c|| differ by at most ||A^-1||_inf (1e-10 + 1e-12) ||b_c||_inf in every
+    entry (the oracle stops on its previous iterate's residual; the returned one is closer, as
+    ||T||_inf < 1); a wrong entry anywhere in X fails that.  The residual of every column is also recomputed
+    by the oracle on 512 sampled rows."""
+    A, B, Xs, ref, margin = full_size_system
+    n = A.shape[0]
     At, Bt = dev(A, B)
-    s = jac.MultiSolver(At, Bt, precision="bf16_ir")
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", tc_residual=tc)
     X, st = s.solve(max_iter=5000, tol=1e-10)
     assert st.status == 0 and st.rel_residual <= 1e-10
     Xh = X.cpu().numpy().T
@@ -115,16 +131,64 @@ def test_full_size_many_rhs_against_the_oracle(jac):
     R = oracle.residual_rows(A, B, Xh, rows)
     bnorm = np.max(np.abs(B), axis=0)
     assert np.all(np.max(np.abs(R), axis=0) <= 1e-10 * bnorm), (np.max(np.abs(R), axis=0) / bnorm).max()
-    ref = oracle.jacobi(A, B, max_iter=200, tol=1e-12, norm=oracle.NORM_RESID, nthreads=oracle.num_threads())
-    assert ref.status == oracle.OK
-    d = np.abs(np.diag(A))
-    margin = np.min(d - (np.abs(A).sum(axis=1) - d))
-    assert margin > 0
     # (+1e-12 for the rounding of the two FP64 residual evaluations, each ~sqrt(n) eps of ||b_c||)
     bound = (1e-10 + 2e-12) * bnorm / margin                      # per column
     err = np.max(np.abs(Xh - ref.X), axis=0)
     assert np.all(err <= bound), (err / bound).max()
     assert np.max(np.abs(ref.X - Xs)) <= 1e-12 * np.max(bnorm) / margin + 1e-13
+
+
+def _one_residual(jac, A, B, X0, tc):
+    """The per-column relative residuals ||b_c - A x0_c||_inf / ||b_c||_inf of one residual evaluation
+    (max_outer = 1: the solve stops after it)."""
+    import torch
+    At, Bt = dev(A, B)
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", tc_residual=tc, split_residual=not tc, max_outer=1)
+    X0t = torch.from_numpy(np.ascontiguousarray(X0.T)).cuda()
+    _, st = s.solve(X0=X0t, max_iter=10, tol=1e-300)
+    assert st.outer_steps == 1 and st.sweeps == 0
+    _, vals = s.column_stats()
+    return np.asarray(vals)
+
+
+@pytest.mark.parametrize("n,r", [(600, 16), (1000, 32), (517, 64), (300, 128)])
+def test_tc_residual_wild_scales(jac, n, r):
+    """The tensor-core residual (digit split of A and X) of a given X0, rows of A scaled by 2^-300 .. 2^300
+    and columns of B (so of X) by 2^-200 .. 2^200, against the oracle's FP64 residual per column, within
+    2^-44 of max_i sum_j |a_ij x_jc| / ||b_c|| (the split's bound is about 2^-50 of it; the rest is the
+    oracle's own FP64 rounding)."""
+    A, B, Xs = synth.dominant_system(n, 1.3, seed=97 + n, nrhs=r)
+    rng = np.random.default_rng(n)
+    rows = 2.0 ** rng.integers(-300, 300, n)
+    cols = 2.0 ** rng.integers(-200, 200, r)
+    A = A * rows[:, None]
+    B = B * rows[:, None] * cols[None, :]
+    X0 = Xs * cols[None, :] * (1 + 1e-6 * rng.standard_normal((n, r)))
+    got = _one_residual(jac, A, B, X0, tc=True)
+    for c in range(r):
+        _, rel = oracle.residual(A, B[:, c], X0[:, c])
+        S = np.max(np.abs(A) @ np.abs(X0[:, c])) / np.max(np.abs(B[:, c]))
+        assert rel > 1e-9 and abs(got[c] - rel) <= 2.0 ** -44 * S, (c, got[c], rel, S)
+
+
+def test_tc_residual_against_a_near_exact_residual(jac):
+    """Where long double is IEEE quad precision (113-bit significand, as on Arm Linux), the residual of a
+    hard-generator system (all entries of A positive: no cancellation in A x) is formed with exact products
+    and 113-bit sums; the tensor-core residual must be within 2^-50 of max_i sum_j |a_ij x_jc| of it per
+    column.  The BF16 digits are balanced, so a dropped digit or a wrong digit weight shows up far above
+    that bound."""
+    if np.finfo(np.longdouble).nmant < 105:
+        pytest.skip("long double is not quad precision on this host")
+    n, r = 512, 32
+    A, B, Xs = synth.hard_system(n, 1.2, seed=55, nrhs=r)
+    X0 = Xs * (1 + 1e-7 * np.random.default_rng(3).standard_normal((n, r)))
+    got = _one_residual(jac, A, B, X0, tc=True)
+    Al, Bl, Xl = A.astype(np.longdouble), B.astype(np.longdouble), X0.astype(np.longdouble)
+    R = Bl - Al @ Xl
+    for c in range(r):
+        want = float(np.max(np.abs(R[:, c])) / np.max(np.abs(Bl[:, c])))
+        S = float(np.max(np.abs(Al) @ np.abs(Xl[:, c])) / np.max(np.abs(Bl[:, c])))
+        assert abs(got[c] - want) <= 2.0 ** -50 * S, (c, got[c], want, S)
 
 
 def test_fp64_many_rhs_residual_stop(jac):
@@ -196,7 +260,8 @@ def test_fp64_column_retirement_matches_single_column_solves(jac):
     assert iters[1] == 1 and iters[2] < iters[0] < iters[4]
 
 
-def test_bf16_column_retirement(jac):
+@pytest.mark.parametrize("tc", [False, True], ids=["fp64_resid", "tc_resid"])
+def test_bf16_column_retirement(jac, tc):
     """Columns whose start vector already meets the target retire at the first residual evaluation and
     keep X0 bit for bit; the others refine on; every column ends at or below the 1e-10 target."""
     import torch
@@ -206,7 +271,7 @@ def test_bf16_column_retirement(jac):
     X0[:, ::2] = Xs[:, ::2]
     At, Bt = dev(A, B)
     X0t = torch.from_numpy(np.ascontiguousarray(X0.T)).cuda()
-    s = jac.MultiSolver(At, Bt, precision="bf16_ir", retire_columns=True)
+    s = jac.MultiSolver(At, Bt, precision="bf16_ir", retire_columns=True, tc_residual=tc)
     X, st = s.solve(X0=X0t, max_iter=5000, tol=1e-10)
     iters, vals = s.column_stats()
     Xh = X.cpu().numpy().T
