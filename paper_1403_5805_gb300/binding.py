@@ -174,7 +174,7 @@ def load() -> ctypes.CDLL:
         return lib
 
 
-def measure_fma_rates(iters: int = 200000, stream=None) -> tuple[float, float]:
+def measure_fma_rates(iters: int = 20000, stream=None) -> tuple[float, float]:
     """FP64 and FP32 FMAs per second of the current device's CUDA cores (``jacobi_measure_fma_rates``)."""
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()

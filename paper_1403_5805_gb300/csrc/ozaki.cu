@@ -44,8 +44,6 @@ namespace {
 
 constexpr int kOzTile = 128;              // rows per CTA (tcgen05 M)
 constexpr int kOzChunkKB = 16;            // 64-column K blocks per exact FP32 chunk: 1024 columns
-constexpr int kOzStages = 4;
-constexpr int kOzThreads = 192;           // warp 0 TMA, warp 1 MMA, warps 2..5 readout
 constexpr int kOzBufCols = 256;           // tensor-memory columns per accumulator buffer
 constexpr int kOzTmemCols = 2 * kOzBufCols;
 constexpr int kOzATile = kOzTile * kKBlock * 2;  // 16 KB
@@ -183,24 +181,44 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
   lo = __fadd_rn(lo, err);
 }
 
+// Per-CTA column count RC (16, 32 or 64 columns of X) fixes the geometry: the readout warps (one output
+// row per thread and TMEM lane quadrant; with 64 columns two warps per quadrant, 32 columns each), the
+// stage size (A digit tile + 7 X digit blocks of RC rows), the ring depth within 217 KB, and the tensor-
+// memory accumulators: a group's nq * RC columns (at most 448) in one buffer for RC = 64, or two
+// alternating 256-column buffers for RC <= 32 (so that the readout of one chunk overlaps the next).
+template <int RC>
+struct OzCfg {
+  static constexpr int kReadWarps = RC == 64 ? 8 : 4;
+  static constexpr int kThreads = 64 + 32 * kReadWarps;
+  static constexpr int kXBlock = RC * kKBlock * 2;
+  static constexpr int kStage = kOzATile + kOzDigits * kXBlock;
+  static constexpr int kStages = (217 * 1024) / kStage < 4 ? (217 * 1024) / kStage : 4;
+  static constexpr int kBufs = kOzDigits * RC <= kOzBufCols ? 2 : 1;
+  static constexpr int kDigitsPerMma = kOzBufCols / RC < kOzDigits ? kOzBufCols / RC : kOzDigits;
+  static constexpr int kColsPerWarp = RC == 64 ? 32 : RC;
+  static constexpr int kSmem = kStages * kStage + 1024;
+  static_assert(kStages >= 2, "ring needs two stages");
+  static_assert(kOzDigits * RC <= kOzTmemCols, "a group's accumulator fits tensor memory");
+};
+
 struct OzSmem {
-  uint64_t full[kOzStages];
-  uint64_t empty[kOzStages];
+  uint64_t full[4];
+  uint64_t empty[4];
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t done;
   uint32_t tmem;
   volatile int abort;
-  int active[128];  // columns of this CTA that are written (1) or skipped (retired columns)
+  int active[64];  // columns of this CTA that are written (1) or skipped (retired columns)
 };
 
 template <int RC>
-__global__ void __launch_bounds__(kOzThreads, 1)
+__global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
     oz_resid_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                     OzResidParams p) {
-  constexpr int kXBlock = RC * kKBlock * 2;               // one X digit block per stage
-  constexpr int kStage = kOzATile + kOzDigits * kXBlock;  // A digit tile + up to 7 X digit blocks
-  static_assert(kOzDigits * RC <= kOzBufCols, "one group's columns fit one accumulator buffer");
+  using C = OzCfg<RC>;
+  constexpr int S_ = C::kStages;
+  constexpr int NB = C::kBufs;
   extern __shared__ __align__(1024) unsigned char osmem[];
   __shared__ OzSmem S;
   unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(osmem) + 1023) & ~uintptr_t(1023));
@@ -211,13 +229,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int nchunk = (kb_count + kOzChunkKB - 1) / kOzChunkKB;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kOzStages; ++s) {
+    for (int s = 0; s < S_; ++s) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&S.tfull[b], 1);
-      mbar_init(&S.tempty[b], 4);  // one arrival per readout warp
+      mbar_init(&S.tempty[b], C::kReadWarps);  // one arrival per readout warp
     }
     mbar_init(&S.done, 1);
     S.abort = 0;
@@ -243,31 +261,31 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         const int pd = kOzDigits - 1 - gi;  // A digit (0-based); X digits 0 .. gi
         const int nq = gi + 1;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
-          const int s = it % kOzStages;
-          if (S.abort || !mbar_wait(&S.empty[s], ((it / kOzStages) & 1) ^ 1, p.wait_ns) || S.abort) {
+          const int s = it % S_;
+          if (S.abort || !mbar_wait(&S.empty[s], ((it / S_) & 1) ^ 1, p.wait_ns) || S.abort) {
             S.abort = 1;
             atomicCAS(p.status, 0, kStatusTimeout);
             break;
           }
-          unsigned char* st = ring + s * kStage;
-          mbar_arrive_expect_tx(&S.full[s], kOzATile + nq * kXBlock);
+          unsigned char* st = ring + s * C::kStage;
+          mbar_arrive_expect_tx(&S.full[s], kOzATile + nq * C::kXBlock);
           tma_load_2d(st, &tmA, kb * kKBlock, static_cast<int>(pd * p.nr + m0), &S.full[s]);
           for (int q = 0; q < nq; ++q)
-            tma_load_2d(st + kOzATile + q * kXBlock, &tmX, kb * kKBlock, static_cast<int>(q * p.r + c0), &S.full[s]);
+            tma_load_2d(st + kOzATile + q * C::kXBlock, &tmX, kb * kKBlock, static_cast<int>(q * p.r + c0),
+                        &S.full[s]);
         }
       }
       // wait (bounded) for the copies still in flight before the CTA can exit
-      for (int k = it - 1; k >= 0 && k >= it - kOzStages; --k) mbar_wait(&S.full[k % kOzStages], (k / kOzStages) & 1, p.wait_ns);
+      for (int k = it - 1; k >= 0 && k >= it - S_; --k) mbar_wait(&S.full[k % S_], (k / S_) & 1, p.wait_ns);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       int it = 0, t = 0;
       for (int gi = 0; gi < kOzDigits && !S.abort; ++gi) {
         const int nq = gi + 1;
-        const uint32_t idesc = mma_idesc(kOzTile, nq * RC);
         for (int ch = 0; ch < nchunk && !S.abort; ++ch, ++t) {
-          const int b = t & 1;
-          if (!mbar_wait(&S.tempty[b], ((t >> 1) & 1) ^ 1, p.wait_ns) || S.abort) {
+          const int b = t % NB, u = t / NB;
+          if (!mbar_wait(&S.tempty[b], (u & 1) ^ 1, p.wait_ns) || S.abort) {
             S.abort = 1;
             atomicCAS(p.status, 0, kStatusTimeout);
             break;
@@ -276,19 +294,25 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           const uint32_t acc = tmem + static_cast<uint32_t>(b * kOzBufCols);
           const int kb1 = min(kb_count, (ch + 1) * kOzChunkKB);
           for (int kb = ch * kOzChunkKB; kb < kb1; ++kb, ++it) {
-            const int s = it % kOzStages;
-            if (!mbar_wait(&S.full[s], (it / kOzStages) & 1, p.wait_ns) || S.abort) {
+            const int s = it % S_;
+            if (!mbar_wait(&S.full[s], (it / S_) & 1, p.wait_ns) || S.abort) {
               S.abort = 1;
               atomicCAS(p.status, 0, kStatusTimeout);
               break;
             }
             tc_fence_after();
-            const uint32_t a = cvta_smem(ring + s * kStage);
+            const uint32_t a = cvta_smem(ring + s * C::kStage);
             const uint32_t bx = a + kOzATile;
 #pragma unroll
-            for (int k = 0; k < kKBlock / 16; ++k)
-              mma_bf16(acc, sw128_desc(a + 32 * k), sw128_desc(bx + 32 * k), idesc,
-                       (kb != ch * kOzChunkKB || k != 0) ? 1u : 0u);
+            for (int k = 0; k < kKBlock / 16; ++k) {
+              const uint32_t accum = (kb != ch * kOzChunkKB || k != 0) ? 1u : 0u;
+              // at most 256 accumulator columns per instruction: digits [q0, q0 + nd) of X
+              for (int q0 = 0; q0 < nq; q0 += C::kDigitsPerMma) {
+                const int nd = min(C::kDigitsPerMma, nq - q0);
+                mma_bf16(acc + static_cast<uint32_t>(q0 * RC), sw128_desc(a + 32 * k),
+                         sw128_desc(bx + q0 * C::kXBlock + 32 * k), mma_idesc(kOzTile, nd * RC), accum);
+              }
+            }
             mma_commit(&S.empty[s]);
           }
           mma_commit(&S.tfull[b]);
@@ -299,20 +323,23 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       mbar_wait(&S.done, 0, p.wait_ns);
     }
   } else {
-    // readout warps 2..5: warp w owns tensor-memory lanes 32 (w % 4) .. + 31, one output row per thread
+    // readout warps: warp w owns tensor-memory lanes 32 (w % 4) .. + 31 (one output row per thread) and,
+    // with 64 columns, the column half (w - 2) / 4
+    constexpr int CW = C::kColsPerWarp;
     const int qd = warp & 3;
+    const int cw = RC == 64 ? ((warp - 2) >> 2) * 32 : 0;  // first column of this warp
     const int64_t i = m0 + 32 * qd + lane;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * qd) << 16);
-    float hi[RC], lo[RC];
+    float hi[CW], lo[CW];
 #pragma unroll
-    for (int c = 0; c < RC; ++c) hi[c] = lo[c] = 0.0f;
+    for (int c = 0; c < CW; ++c) hi[c] = lo[c] = 0.0f;
     bool ok = true;
     int t = 0;
     for (int gi = 0; gi < kOzDigits && ok; ++gi) {
       const int nq = gi + 1;
       for (int ch = 0; ch < nchunk && ok; ++ch, ++t) {
-        const int b = t & 1;
-        bool got = lane == 0 ? (mbar_wait(&S.tfull[b], (t >> 1) & 1, p.wait_ns) && !S.abort) : false;
+        const int b = t % NB, u = t / NB;
+        bool got = lane == 0 ? (mbar_wait(&S.tfull[b], u & 1, p.wait_ns) && !S.abort) : false;
         got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;  // tcgen05.ld is warp-collective
         if (!got) {
           ok = false;
@@ -321,8 +348,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         tc_fence_after();
         // lowest level first: X digit nq-1 (level pd + nq) down to X digit 0
         for (int q = nq - 1; q >= 0; --q) {
-          const uint32_t col = static_cast<uint32_t>(b * kOzBufCols + q * RC);
-          if constexpr (RC == 32) {
+          const uint32_t col = static_cast<uint32_t>(b * kOzBufCols + q * RC + cw);
+          if constexpr (CW == 32) {
             float v[32];
             tmem_ld32(lane_base + col, v);
 #pragma unroll
@@ -335,7 +362,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           }
         }
 #pragma unroll
-        for (int c = 0; c < RC; ++c) {  // renormalise: |lo| <= ulp(hi) / 2
+        for (int c = 0; c < CW; ++c) {  // renormalise: |lo| <= ulp(hi) / 2
           const float z = __fadd_rn(hi[c], lo[c]);
           lo[c] = __fsub_rn(lo[c], __fsub_rn(z, hi[c]));
           hi[c] = z;
@@ -355,18 +382,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int e = row_ok ? p.aexp[i] : 0;
       const double di = row_ok ? p.d[i] : 0.0, ri = row_ok ? p.rinv[i] : 0.0;
 #pragma unroll
-      for (int c = 0; c < RC; ++c) {
-        const int64_t o = static_cast<int64_t>(c0 + c) * p.ld + i;
+      for (int c = 0; c < CW; ++c) {
+        const int col = c0 + cw + c;
+        const int64_t o = static_cast<int64_t>(col) * p.ld + i;
         unsigned long long bits = 0;
         if (row_ok) {
-          const int g = p.xexp[c0 + c];
+          const int g = p.xexp[col];
           double dot;
           if (e == kExpNonfinite || g == kExpNonfinite)
             dot = __longlong_as_double(0x7FF8000000000000ll);
           else
             dot = scale2(static_cast<double>(hi[c]) + static_cast<double>(lo[c]), e + g + 2 - 16);
           const double r = fma(-di, p.x[o], p.b[o]) - dot;
-          if (S.active[c]) {
+          if (S.active[cw + c]) {
             const float cc = static_cast<float>(r * ri);
             p.c1[o] = cc;
             p.d1[o] = cc;
@@ -374,9 +402,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           }
           bits = abs_bits(r);
         }
-        if (S.active[c]) {  // warp-uniform
+        if (S.active[cw + c]) {  // warp-uniform
           bits = warp_max_u64(bits);
-          if (lane == 0 && bits) atomicMax(p.colmax + c0 + c, bits);
+          if (lane == 0 && bits) atomicMax(p.colmax + col, bits);
         }
       }
     }
@@ -391,11 +419,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
 template <int RC>
 cudaError_t launch_resid_rc(const CUtensorMap& ta, const CUtensorMap& tx, const OzResidParams& p, cudaStream_t s) {
-  constexpr int smem = kOzStages * (kOzATile + kOzDigits * RC * kKBlock * 2) + 1024;
+  constexpr int smem = OzCfg<RC>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(oz_resid_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid(static_cast<unsigned>(p.nr / kOzTile), static_cast<unsigned>(p.r / RC));
-  oz_resid_kernel<RC><<<grid, kOzThreads, smem, s>>>(ta, tx, p);
+  oz_resid_kernel<RC><<<grid, OzCfg<RC>::kThreads, smem, s>>>(ta, tx, p);
   return cudaGetLastError();
 }
 
@@ -419,13 +447,17 @@ cudaError_t launch_oz_split_x(int64_t n, int64_t r, int64_t ld, const double* x,
 
 cudaError_t launch_oz_resid(const __nv_bfloat16* adig, const __nv_bfloat16* xdig, const OzResidParams& p,
                             cudaStream_t s) {
-  if (p.r != 16 && p.r % 32 != 0) return cudaErrorInvalidValue;
+  if (p.r != 16 && p.r != 32 && p.r % 64 != 0) return cudaErrorInvalidValue;
   if (p.nr % kOzTile != 0 || p.ld % 16 != 0) return cudaErrorInvalidValue;
-  const int rc = p.r == 16 ? 16 : 32;
+  const int rc = p.r < 64 ? static_cast<int>(p.r) : 64;
   CUtensorMap ta, tx;
   if (!make_map(&ta, adig, p.n, kOzDigits * p.nr, p.ld, kOzTile)) return cudaErrorInvalidValue;
   if (!make_map(&tx, xdig, p.n, kOzDigits * p.r, p.ld, rc)) return cudaErrorInvalidValue;
-  return rc == 16 ? launch_resid_rc<16>(ta, tx, p, s) : launch_resid_rc<32>(ta, tx, p, s);
+  switch (rc) {
+    case 16: return launch_resid_rc<16>(ta, tx, p, s);
+    case 32: return launch_resid_rc<32>(ta, tx, p, s);
+    default: return launch_resid_rc<64>(ta, tx, p, s);
+  }
 }
 
 }  // namespace jac

@@ -1,10 +1,10 @@
 // Measured arithmetic rates of this GPU's CUDA cores, the denominators of the FP64-FMA and FP32 bounds
 // that the FP64 sweeps, the FP64 residual passes and the split-float residual are held to.
 //
-// Each thread runs kChains independent FMA chains (x <- x * m + c with |m| < 1, so values stay finite),
-// enough independent work per warp that the issue of the FMA pipe, not its latency, limits the rate.  The
-// grid holds every SM full (kBlocksPerSm blocks of kPeakThreads threads each).  The timed launch follows an
-// untimed one on the same stream; the rate is FMAs / elapsed time of the timed launch (CUDA events).
+// Each thread runs CH independent FMA chains (x <- x * m + c with |m| < 1, so values stay finite), so that
+// the issue of the FMA pipe, not its latency, limits the rate; the grid holds every SM with BPS blocks of
+// kPeakThreads threads.  Several (CH, BPS) shapes are timed, each launch after an untimed one on the same
+// stream (CUDA events), and the best rate is reported.
 #include <cuda_runtime.h>
 
 #include "solver.cuh"
@@ -12,32 +12,30 @@
 namespace jac {
 namespace {
 
-constexpr int kChains = 8;
 constexpr int kPeakThreads = 256;
-constexpr int kBlocksPerSm = 8;
 
-template <typename T>
+template <typename T, int CH>
 __global__ void __launch_bounds__(kPeakThreads) fma_rate_kernel(int64_t iters, T m, T c, T* sink) {
-  T x[kChains];
+  T x[CH];
 #pragma unroll
-  for (int u = 0; u < kChains; ++u) x[u] = static_cast<T>(threadIdx.x + u) * static_cast<T>(1e-3);
+  for (int u = 0; u < CH; ++u) x[u] = static_cast<T>(threadIdx.x + u) * static_cast<T>(1e-3);
   for (int64_t k = 0; k < iters; ++k) {
 #pragma unroll
-    for (int u = 0; u < kChains; ++u) x[u] = fma(x[u], m, c);
+    for (int u = 0; u < CH; ++u) x[u] = fma(x[u], m, c);
   }
   T s = 0;
 #pragma unroll
-  for (int u = 0; u < kChains; ++u) s += x[u];
+  for (int u = 0; u < CH; ++u) s += x[u];
   if (s == static_cast<T>(-1.5)) sink[0] = s;  // never true; keeps the chains live
 }
 
-template <typename T>
-cudaError_t time_rate(int64_t iters, cudaStream_t s, double* per_s) {
+template <typename T, int CH>
+cudaError_t time_rate_shape(int64_t iters, int bps, cudaStream_t s, double* per_s) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int grid = sms * kBlocksPerSm;
+  const int grid = sms * bps;
   cudaEvent_t a, b;
   if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
   if ((e = cudaEventCreate(&b)) != cudaSuccess) {
@@ -45,9 +43,9 @@ cudaError_t time_rate(int64_t iters, cudaStream_t s, double* per_s) {
     return e;
   }
   const T m = static_cast<T>(0.999999), c = static_cast<T>(1e-7);
-  fma_rate_kernel<T><<<grid, kPeakThreads, 0, s>>>(iters / 4 + 1, m, c, nullptr);
+  fma_rate_kernel<T, CH><<<grid, kPeakThreads, 0, s>>>(iters / 4 + 1, m, c, nullptr);
   cudaEventRecord(a, s);
-  fma_rate_kernel<T><<<grid, kPeakThreads, 0, s>>>(iters, m, c, nullptr);
+  fma_rate_kernel<T, CH><<<grid, kPeakThreads, 0, s>>>(iters, m, c, nullptr);
   cudaEventRecord(b, s);
   e = cudaEventSynchronize(b);
   float ms = 0.0f;
@@ -56,8 +54,24 @@ cudaError_t time_rate(int64_t iters, cudaStream_t s, double* per_s) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e != cudaSuccess) return e;
-  const double fmas = static_cast<double>(grid) * kPeakThreads * kChains * static_cast<double>(iters);
+  const double fmas = static_cast<double>(grid) * kPeakThreads * CH * static_cast<double>(iters);
   *per_s = ms > 0.0f ? fmas / (static_cast<double>(ms) * 1e-3) : 0.0;
+  return cudaSuccess;
+}
+
+// Best over 4 or 16 chains per thread and 4 or 8 blocks per SM (the same FMA count per thread each time).
+template <typename T>
+cudaError_t time_rate(int64_t iters, cudaStream_t s, double* per_s) {
+  double best = 0.0, r = 0.0;
+  for (int bps : {4, 8}) {
+    cudaError_t e = time_rate_shape<T, 4>(iters * 4, bps, s, &r);
+    if (e != cudaSuccess) return e;
+    best = r > best ? r : best;
+    e = time_rate_shape<T, 16>(iters, bps, s, &r);
+    if (e != cudaSuccess) return e;
+    best = r > best ? r : best;
+  }
+  *per_s = best;
   return cudaSuccess;
 }
 
