@@ -279,7 +279,8 @@ typedef struct jacobi_batch_desc {
                                  stop (strict <); JACOBI_FP32_IR / JACOBI_BF16_IR: FP64 refinement around
                                  narrow inner sweeps, stop at ||B - A X||_inf / ||B||_inf <= tol */
   int32_t rows_per_warp;      /* 1, 2, 4 or 8 rows a warp accumulates at once (0: 4) */
-  int32_t ctas_per_sm;        /* cap on resident CTAs per SM (0: as many as fit) */
+  int32_t ctas_per_sm;        /* cap on resident CTAs per SM (0: as many as fit); 3 or more selects the
+                                 build limited to 64 registers per thread, so that 4 CTAs fit */
   int32_t max_outer;          /* IR: cap on residual evaluations per system (0: 30) */
   int32_t max_inner;          /* IR: cap on inner sweeps per outer step (0: 1000) */
   int32_t flags;              /* JACOBI_FLAG_SPLIT_RESIDUAL: split-float residuals (IR; see jacobi_desc) */

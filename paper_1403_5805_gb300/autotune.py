@@ -6,7 +6,8 @@ Results are cached in a JSON file keyed by the workload signature (device name, 
 count and a histogram of the sizes), so a workload is tuned once per machine.
 
 Tuned knobs
-  batch:  rows per warp (1, 2, 4, 8), resident CTAs per SM (all that fit, 2, 1) and, for the mixed
+  batch:  rows per warp (1, 2, 4, 8), resident CTAs per SM (all that fit, 4 with the register-limited
+          build, 2, 1) and, for the mixed
           precisions, the inner-sweep stopping tolerance.
   single: the inner-sweep stopping tolerance of the mixed precisions.
 """
@@ -81,7 +82,7 @@ def tune_batch(As, Bs, precision: str = "fp32_ir", max_iter: int = 5000, tol: fl
     best = None
     trials = []
     for rpw in (1, 2, 4, 8):
-        for cps in (0, 2, 1):
+        for cps in (0, 4, 2, 1):
             for rt in rtols:
                 bs = BatchSolver(As, Bs, precision=precision, rows_per_warp=rpw, ctas_per_sm=cps, inner_rtol=rt,
                                  workspace=workspace, split_residual=split_residual)

@@ -101,15 +101,55 @@ __device__ __forceinline__ bool tr_owner(int lane) {
   return (lane & (low - 1)) == 0;
 }
 
-// Dot products of FP64 rows [i0, i0 + RPW) of A (row stride lda) with the shared-memory FP64 vector x;
-// 8-byte loads (any row alignment), 4 columns per lane in flight.  Returns the lane's transposed total.
+// Dot products of FP64 rows [i0, i0 + RPW) of A (row stride lda) with the shared-memory FP64 vector x.
+// al16 (rows 16-byte aligned: A aligned and lda even): lane l takes column pairs 2 l + 64 t, two 16-byte
+// loads per row and step; otherwise 8-byte loads of columns l + 32 t (any row alignment).  Either way each
+// lane has 4 columns of every row in flight.  Returns the lane's transposed total.
 template <int RPW>
 __device__ __forceinline__ double rows_fp64(const double* __restrict__ A, int64_t lda, int64_t n, int64_t i0,
-                                            const double* xs, int lane) {
+                                            const double* xs, int lane, bool al16) {
   double acc[RPW];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) acc[r] = 0.0;
   const int rows = static_cast<int>(i64min(RPW, n - i0));
+  if (al16) {
+    int64_t j = 2 * lane;
+    for (; j + 65 < n; j += 128) {
+      const double2 x0 = *reinterpret_cast<const double2*>(xs + j);
+      const double2 x1 = *reinterpret_cast<const double2*>(xs + j + 64);
+      double2 a0[RPW], a1[RPW];
+#pragma unroll
+      for (int r = 0; r < RPW; ++r)
+        if (r < rows) {
+          const double* a = A + (i0 + r) * lda + j;
+          a0[r] = __ldg(reinterpret_cast<const double2*>(a));
+          a1[r] = __ldg(reinterpret_cast<const double2*>(a + 64));
+        }
+#pragma unroll
+      for (int r = 0; r < RPW; ++r)
+        if (r < rows) {
+          acc[r] = fma(a0[r].x, x0.x, acc[r]);
+          acc[r] = fma(a0[r].y, x0.y, acc[r]);
+          acc[r] = fma(a1[r].x, x1.x, acc[r]);
+          acc[r] = fma(a1[r].y, x1.y, acc[r]);
+        }
+    }
+    for (; j < n; j += 64) {
+#pragma unroll
+      for (int r = 0; r < RPW; ++r)
+        if (r < rows) {
+          const double* a = A + (i0 + r) * lda + j;
+          if (j + 1 < n) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(a));
+            acc[r] = fma(v.x, xs[j], acc[r]);
+            acc[r] = fma(v.y, xs[j + 1], acc[r]);
+          } else {
+            acc[r] = fma(__ldg(a), xs[j], acc[r]);
+          }
+        }
+    }
+    return TR<RPW, 16, double>::run(acc, lane);
+  }
   int64_t j = lane;
   for (; j + 96 < n; j += 128) {
     const double x0 = xs[j], x1 = xs[j + 32], x2 = xs[j + 64], x3 = xs[j + 96];
@@ -194,7 +234,38 @@ __device__ __forceinline__ float rows_narrow(const TL* __restrict__ N, int64_t l
 #pragma unroll
   for (int r = 0; r < RPW; ++r) acc[r] = 0.0f;
   const int rows = static_cast<int>(i64min(RPW, n - i0));
-  for (int64_t j = static_cast<int64_t>(lane) * V; j < n; j += 32 * V) {
+  // two 16-byte segments of every row per lane and step (columns j and j + 32 V), loads before FMAs
+  int64_t j = static_cast<int64_t>(lane) * V;
+  for (; j + 32 * V < n; j += 64 * V) {
+    float xv0[V], xv1[V];
+#pragma unroll
+    for (int q = 0; q < V / 4; ++q) {
+      const float4 v0 = *reinterpret_cast<const float4*>(xs + j + 4 * q);
+      const float4 v1 = *reinterpret_cast<const float4*>(xs + j + 32 * V + 4 * q);
+      xv0[4 * q] = v0.x;
+      xv0[4 * q + 1] = v0.y;
+      xv0[4 * q + 2] = v0.z;
+      xv0[4 * q + 3] = v0.w;
+      xv1[4 * q] = v1.x;
+      xv1[4 * q + 1] = v1.y;
+      xv1[4 * q + 2] = v1.z;
+      xv1[4 * q + 3] = v1.w;
+    }
+    uint4 m0[RPW], m1[RPW];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+      if (r < rows) {
+        m0[r] = __ldcg(reinterpret_cast<const uint4*>(N + (i0 + r) * ldn + j));
+        m1[r] = __ldcg(reinterpret_cast<const uint4*>(N + (i0 + r) * ldn + j + 32 * V));
+      }
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+      if (r < rows) {
+        seg_dot(acc[r], m0[r], xv0);
+        seg_dot(acc[r], m1[r], xv1);
+      }
+  }
+  for (; j < n; j += 32 * V) {
     float xv[V];
 #pragma unroll
     for (int q = 0; q < V / 4; ++q) {
@@ -238,8 +309,10 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long v, un
 
 // kMode: 0 = FP64 Jacobi, 1 = FP32 inner sweeps, 2 = BF16 inner sweeps.  kSplit (mixed modes): residuals
 // with the split-float arithmetic instead of FP64 FMAs.
-template <int kMode, int RPW, bool kSplit>
-__global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
+// MINB: CTAs per SM the register allocation must allow (1: as many registers as the compiler wants, about
+// two CTAs per SM; 4: at most 64 registers, four CTAs and 32 warps per SM for more loads in flight).
+template <int kMode, int RPW, bool kSplit, int MINB>
+__global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
   using TL = typename std::conditional<kMode == 2, __nv_bfloat16, float>::type;
   extern __shared__ __align__(16) unsigned char bsmem[];
   __shared__ unsigned long long sred[2][kBWarps];   // phase-parity double buffer
@@ -260,6 +333,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
     if (q >= p.count) break;
     const BatchSys S = p.sys[q];
     const int64_t n = S.n;
+    const bool al16 = (n % 2 == 0) && (reinterpret_cast<uintptr_t>(S.A) % 16 == 0);
 
     // ---- phase 0: diagonal, ||b||, narrow copy (mixed modes); zero start vector
     unsigned long long bad = 0, bm = 0;
@@ -326,7 +400,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
         double* xn = cur ? xs0 : xs1;
         unsigned long long mx = 0;
         for (int64_t i0 = static_cast<int64_t>(warp) * RPW; i0 < n; i0 += static_cast<int64_t>(kBWarps) * RPW) {
-          const double dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane);
+          const double dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane, al16);
           const int64_t i = i0 + tr_row<RPW>(lane);
           if (tr_owner<RPW>(lane) && i < n) {
             const double xo = xc[i];
@@ -371,7 +445,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
             if constexpr (kSplit)
               dot = rows_split<RPW>(S.A, n, n, i0, xss, S.rexp, lane) * pow2(xg);
             else
-              dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane);
+              dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane, al16);
           }
           const int64_t i = i0 + tr_row<RPW>(lane);
           if (tr_owner<RPW>(lane) && i < n) {
@@ -454,20 +528,26 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchParams p) {
 
 using BatchKernel = void (*)(BatchParams);
 
-template <int M, bool kSplit>
+template <int M, bool kSplit, int MINB>
 BatchKernel pick_rpw(int rpw) {
   switch (rpw) {
-    case 1: return batch_kernel<M, 1, kSplit>;
-    case 2: return batch_kernel<M, 2, kSplit>;
-    case 8: return batch_kernel<M, 8, kSplit>;
-    default: return batch_kernel<M, 4, kSplit>;
+    case 1: return batch_kernel<M, 1, kSplit, MINB>;
+    case 2: return batch_kernel<M, 2, kSplit, MINB>;
+    case 8: return batch_kernel<M, 8, kSplit, MINB>;
+    default: return batch_kernel<M, 4, kSplit, MINB>;
   }
 }
 
-BatchKernel pick_kernel(int precision, int rpw, bool split) {
-  if (precision == JACOBI_FP64) return pick_rpw<0, false>(rpw);
-  if (precision == JACOBI_FP32_IR) return split ? pick_rpw<1, true>(rpw) : pick_rpw<1, false>(rpw);
-  return split ? pick_rpw<2, true>(rpw) : pick_rpw<2, false>(rpw);
+template <int MINB>
+BatchKernel pick_occ(int precision, int rpw, bool split) {
+  if (precision == JACOBI_FP64) return pick_rpw<0, false, MINB>(rpw);
+  if (precision == JACOBI_FP32_IR) return split ? pick_rpw<1, true, MINB>(rpw) : pick_rpw<1, false, MINB>(rpw);
+  return split ? pick_rpw<2, true, MINB>(rpw) : pick_rpw<2, false, MINB>(rpw);
+}
+
+// ctas_per_sm >= 3 asks for the register-limited build (four CTAs per SM can be resident).
+BatchKernel pick_kernel(int precision, int rpw, bool split, int ctas_per_sm) {
+  return ctas_per_sm >= 3 ? pick_occ<4>(precision, rpw, split) : pick_occ<1>(precision, rpw, split);
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -481,6 +561,7 @@ struct jacobi_batch {
   int64_t count = 0;
   int precision = JACOBI_FP32_IR;
   int rpw = 4;
+  int cps = 0;  // requested CTAs per SM (0: all that fit)
   bool split = false;
   int grid = 0;
   size_t smem = 0;
@@ -622,7 +703,8 @@ int jacobi_batch_create(const jacobi_batch_desc* d, jacobi_batch** out) {
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(JACOBI_ERR_CUDA);
   b->smem_ld = round_up(nmax, kLdAlign);
   b->smem = static_cast<size_t>(b->smem_ld) * (2 * sizeof(double) + 2 * sizeof(float) + (b->split ? sizeof(float2) : 0));
-  BatchKernel kern = pick_kernel(b->precision, b->rpw, b->split);
+  b->cps = d->ctas_per_sm;
+  BatchKernel kern = pick_kernel(b->precision, b->rpw, b->split, b->cps);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(b->smem)) != cudaSuccess)
     return fail(JACOBI_ERR_CUDA);
   int dev = 0, sms = 0, per_sm = 0;
@@ -661,7 +743,7 @@ int jacobi_batch_solve_async(jacobi_batch* b, int64_t max_iter, double tol) {
     p.max_inner = b->max_inner;
     p.inner_rtol = b->inner_rtol;
     p.smem_ld = b->smem_ld;
-    BatchKernel kern = pick_kernel(b->precision, b->rpw, b->split);
+    BatchKernel kern = pick_kernel(b->precision, b->rpw, b->split, b->cps);
     if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return JACOBI_ERR_CUDA;
     cudaMemsetAsync(b->queue, 0, sizeof(unsigned int), b->capture);
     void* args[] = {&p};
