@@ -619,8 +619,9 @@ def run_serve(args, jac, torch, dev, seconds):
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(min(args.serve_budget_gb * 1e9, free - 8e9))
 
-    def served(split):
-        srv = jac.Server(budget_bytes=budget, split_residual=split, inner_rtol=args.serve_inner_rtol)
+    def served(mode):
+        srv = jac.Server(budget_bytes=budget, split_residual=mode == "split", tc_residual=mode == "tc",
+                         inner_rtol=args.serve_inner_rtol)
         outs, arrive, lat, stats = {}, {}, {}, {}
         k = 0
         total = len(t)
@@ -670,11 +671,13 @@ def run_serve(args, jac, torch, dev, seconds):
                 "mean_inner_sweeps": round(float(np.mean([v[3] for v in stats.values()])), 2),
                 "worst_rel_residual": worst, "sampled_host_residuals_max": max(checked) if checked else None,
                 "budget_gb": round(budget / 1e9, 1),
-                "residual": "split-float (FP32 units)" if split else "FP64"}
+                "residual": {"split": "split-float (FP32 units)", "fp64": "FP64 FMAs",
+                             "tc": "tensor cores, BF16 digit split (FP64-accurate)"}[mode]}
 
     modes = args.serve_modes.split(",")
-    served_fp64_resid = served(False) if "fp64" in modes else None
-    served_split = served(True) if "split" in modes else None
+    served_tc = served("tc") if "tc" in modes else None
+    served_fp64_resid = served("fp64") if "fp64" in modes else None
+    served_split = served("split") if "split" in modes else None
 
     # the plain FP64 path, one request at a time, on the first seconds of the same trace
     m = int(np.searchsorted(t, args.serve_fp64_seconds))
@@ -702,9 +705,10 @@ def run_serve(args, jac, torch, dev, seconds):
             "p99_ms": round(float(np.percentile(L64, 99)), 3) if m else None}
     ratio = (lambda a: round(a["throughput_per_s"] / fp64["throughput_per_s"], 2)
              if (a and fp64["throughput_per_s"]) else None)
-    return {"served_fp32_ir": served_fp64_resid, "served_fp32_ir_split_residual": served_split,
-            "one_at_a_time_fp64": fp64, "throughput_ratio": ratio(served_fp64_resid),
-            "throughput_ratio_split_residual": ratio(served_split)}
+    return {"served_fp32_ir_tc_residual": served_tc, "served_fp32_ir": served_fp64_resid,
+            "served_fp32_ir_split_residual": served_split,
+            "one_at_a_time_fp64": fp64, "throughput_ratio_tc_residual": ratio(served_tc),
+            "throughput_ratio": ratio(served_fp64_resid), "throughput_ratio_split_residual": ratio(served_split)}
 
 
 def run_hard(args, jac, torch, dev, ws):

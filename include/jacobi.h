@@ -190,7 +190,8 @@ typedef enum { JACOBI_METHOD_JACOBI = 0, JACOBI_METHOD_SOR = 1 } jacobi_method;
  * to at most 8 are summed by tcgen05.mma in FP32, exactly (1024-column chunks of integer products of at
  * most 2^14), the chunk sums in float-float, the diagonal term in FP64.  The representation and dropped-
  * pair errors are below 2^-50 of sum_j |a_ij| max |x_jc| per entry.  Not with JACOBI_FLAG_SPLIT_RESIDUAL;
- * JACOBI_ERR_UNSUPPORTED for other precisions or one right-hand side. */
+ * JACOBI_ERR_UNSUPPORTED for other precisions or one right-hand side.  Also a server flag
+ * (jacobi_server_desc.flags), for requests of any size and right-hand-side count. */
 #define JACOBI_FLAG_TC_RESIDUAL 128
 
 /* Fill *d with defaults (n = 0 and null pointers: the caller sets those). */
@@ -351,7 +352,10 @@ typedef struct jacobi_server_desc {
   int32_t max_outer;    /* cap on residual evaluations per request (0: 30) */
   double inner_rtol;    /* inner stop: max|change| <= inner_rtol * max|delta| (0: 2^-10) */
   int32_t max_active;   /* cap on concurrently active requests (0: only the budget limits) */
-  int32_t flags;        /* JACOBI_FLAG_SPLIT_RESIDUAL: split-float residual rounds (see jacobi_desc) */
+  int32_t flags;        /* JACOBI_FLAG_SPLIT_RESIDUAL: split-float residual rounds (see jacobi_desc);
+                           JACOBI_FLAG_TC_RESIDUAL: residual rounds on the tensor cores (every request's A
+                           split into digits at admission, 14 more bytes per entry of A in the arena; the
+                           residual requests of a round run in one grouped launch before the round kernel) */
   void* stream;         /* cudaStream_t of every round (NULL: legacy default stream) */
 } jacobi_server_desc;
 

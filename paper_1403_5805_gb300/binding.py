@@ -634,13 +634,14 @@ class Server:
     """``jacobi_server_*``: continuous batching of independent requests (see include/jacobi.h)."""
 
     def __init__(self, budget_bytes: int, tol: float = 1e-10, max_active: int = 0, inner_rtol: float = 0.0,
-                 max_inner: int = 0, max_outer: int = 0, stream=None, split_residual: bool = False):
+                 max_inner: int = 0, max_outer: int = 0, stream=None, split_residual: bool = False,
+                 tc_residual: bool = False):
         import torch
         lib = load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         d = JacobiServerDesc()
         d.budget_bytes, d.tol, d.max_active = budget_bytes, tol, max_active
-        d.flags = FLAG_SPLIT_RESIDUAL if split_residual else 0
+        d.flags = (FLAG_SPLIT_RESIDUAL if split_residual else 0) | (FLAG_TC_RESIDUAL if tc_residual else 0)
         d.inner_rtol, d.max_inner, d.max_outer = inner_rtol, max_inner, max_outer
         d.stream = self.stream.cuda_stream
         self._h = ctypes.c_void_p()

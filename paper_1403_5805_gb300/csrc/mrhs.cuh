@@ -1,6 +1,7 @@
 // Multi-right-hand-side kernels (mrhs.cu): the tcgen05 BF16 sweep and the FP64 dense pass.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -79,6 +80,9 @@ struct OzResidParams {
   int64_t nact;
   int* status;              // set to a timeout code if a bounded wait expires
   uint64_t wait_ns;
+  // grouped launches only (launch_oz_grouped): where the X split writes X's digits and column exponents
+  __nv_bfloat16* xd;
+  int* xexp_w;
 };
 // dig[(p*nr + i)*ld + j]: digit p of a_ij (j != i), zero elsewhere; aexp[i] as above.  A row-major with
 // 16-byte aligned rows (lda even).
@@ -89,6 +93,15 @@ cudaError_t launch_oz_split_x(int64_t n, int64_t r, int64_t ld, const double* x,
                               cudaStream_t s);
 cudaError_t launch_oz_resid(const __nv_bfloat16* adig, const __nv_bfloat16* xdig, const OzResidParams& p,
                             cudaStream_t s);
+// Grouped residuals of requests with at most kOzServeCols right-hand sides (r <= 16): X's digits laid out
+// [kOzDigits][kOzServeCols][ld] (columns >= r zero), r = kOzServeCols in the params.
+constexpr int kOzServeCols = 16;
+// The two tensor maps of one request (A's digits, X's digits) into maps[0], maps[1].
+bool oz_make_maps(const __nv_bfloat16* adig, const __nv_bfloat16* xdig, int64_t n, int64_t ld, CUtensorMap* maps);
+// One launch splitting X of every request (its columns, the padding columns to zero), then one launch of the
+// residual over all row tiles (first[k]: the first tile of request k, tiles in all); device arrays.
+cudaError_t launch_oz_grouped(const OzResidParams* ps_dev, const CUtensorMap* maps_dev, const int64_t* first_dev,
+                              int nreq, int64_t tiles, cudaStream_t s);
 
 bool mrhs_supported_r(int64_t r);
 // Encodes the TMA maps of the BF16 matrix (n x n, row pitch ld) and of the BF16 iterate block (r x n,

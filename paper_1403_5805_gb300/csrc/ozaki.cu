@@ -212,10 +212,11 @@ struct OzSmem {
   int active[64];  // columns of this CTA that are written (1) or skipped (retired columns)
 };
 
+// The residual of one tile: rows [m0, m0 + 128) and columns [c0, c0 + RC) of X, A's digits through the
+// tensor map *tmA, X's digits through *tmX (kernel parameters or maps in global memory).
 template <int RC>
-__global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
-    oz_resid_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
-                    OzResidParams p) {
+__device__ __forceinline__ void oz_resid_tile(const CUtensorMap* tmA_, const CUtensorMap* tmX_,
+                                              const OzResidParams& p, int64_t m0, int c0) {
   using C = OzCfg<RC>;
   constexpr int S_ = C::kStages;
   constexpr int NB = C::kBufs;
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
   __shared__ OzSmem S;
   unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(osmem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kOzTile;
-  const int c0 = blockIdx.y * RC;
+  const CUtensorMap& tmA = *tmA_;
+  const CUtensorMap& tmX = *tmX_;
   const int kb_count = static_cast<int>((p.n + kKBlock - 1) / kKBlock);
   const int nchunk = (kb_count + kOzChunkKB - 1) / kOzChunkKB;
 
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
         const int col = c0 + cw + c;
         const int64_t o = static_cast<int64_t>(col) * p.ld + i;
         unsigned long long bits = 0;
-        if (row_ok) {
+        if (row_ok && S.active[cw + c]) {
           const int g = p.xexp[col];
           double dot;
           if (e == kExpNonfinite || g == kExpNonfinite)
@@ -394,12 +395,10 @@ __global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
           else
             dot = scale2(static_cast<double>(hi[c]) + static_cast<double>(lo[c]), e + g + 2 - 16);
           const double r = fma(-di, p.x[o], p.b[o]) - dot;
-          if (S.active[cw + c]) {
-            const float cc = static_cast<float>(r * ri);
-            p.c1[o] = cc;
-            p.d1[o] = cc;
-            p.d1h[o] = __float2bfloat16_rn(cc);
-          }
+          const float cc = static_cast<float>(r * ri);
+          p.c1[o] = cc;
+          p.d1[o] = cc;
+          if (p.d1h) p.d1h[o] = __float2bfloat16_rn(cc);
           bits = abs_bits(r);
         }
         if (S.active[cw + c]) {  // warp-uniform
@@ -418,6 +417,62 @@ __global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
 }
 
 template <int RC>
+__global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
+    oz_resid_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
+                    OzResidParams p) {
+  oz_resid_tile<RC>(&tmA, &tmX, p, static_cast<int64_t>(blockIdx.x) * kOzTile, static_cast<int>(blockIdx.y) * RC);
+}
+
+// Many independent residuals in one launch (the serving rounds): CTA b takes row tile b - first[k] of
+// request k (first[k] <= b < first[k + 1]), all of its (at most 16) columns, with the request's two tensor
+// maps at maps[2k] (A's digits) and maps[2k + 1] (X's digits).
+__global__ void __launch_bounds__(OzCfg<16>::kThreads, 1)
+    oz_resid_grouped_kernel(const OzResidParams* __restrict__ ps, const CUtensorMap* __restrict__ maps,
+                            const int64_t* __restrict__ first, int nreq) {
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = nreq - 1;  // last k with first[k] <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (first[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const OzResidParams p = ps[lo];
+  if (threadIdx.x == 0) {
+    // the maps were written through the generic proxy (a host copy): order that before the TMA unit reads them
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + 2 * lo) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + 2 * lo + 1) : "memory");
+  }
+  oz_resid_tile<16>(maps + 2 * lo, maps + 2 * lo + 1, p, (b - first[lo]) * kOzTile, 0);
+}
+
+// The X digits of many residuals: block (c, k) splits column c of request k, whose X has p.nact columns
+// (zero digits for c >= nact, the padding up to kOzServeCols).
+__global__ void oz_split_x_grouped_kernel(const OzResidParams* __restrict__ ps) {
+  __shared__ uint32_t sh[32];
+  const OzResidParams& p = ps[blockIdx.y];
+  const int64_t c = blockIdx.x, n = p.n, ld = p.ld, r = p.nact;
+  const double* col = p.x + c * ld;
+  uint32_t m = 0;
+  if (c < r)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = max(m, abs_hi(col[i]));
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  uint32_t t = 0;
+  for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t = max(t, sh[w]);
+  const int g = oz_exponent(t);
+  if (threadIdx.x == 0) p.xexp_w[c] = g;
+  for (int64_t i = threadIdx.x; i < ld; i += blockDim.x) {
+    int d[kOzDigits];
+    oz_digits(c < r && i < n ? col[i] : 0.0, g, d);
+#pragma unroll
+    for (int q = 0; q < kOzDigits; ++q) p.xd[(q * kOzServeCols + c) * ld + i] = oz_digit_value(d[q], q);
+  }
+}
+
+template <int RC>
 cudaError_t launch_resid_rc(const CUtensorMap& ta, const CUtensorMap& tx, const OzResidParams& p, cudaStream_t s) {
   constexpr int smem = OzCfg<RC>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(oz_resid_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -428,6 +483,26 @@ cudaError_t launch_resid_rc(const CUtensorMap& ta, const CUtensorMap& tx, const 
 }
 
 }  // namespace
+
+bool oz_make_maps(const __nv_bfloat16* adig, const __nv_bfloat16* xdig, int64_t n, int64_t ld, CUtensorMap* maps) {
+  const int64_t nr = oz_padded_rows(n);
+  return make_map(&maps[0], adig, n, kOzDigits * nr, ld, kOzTile) &&
+         make_map(&maps[1], xdig, n, kOzDigits * kOzServeCols, ld, kOzServeCols);
+}
+
+cudaError_t launch_oz_grouped(const OzResidParams* ps_dev, const CUtensorMap* maps_dev, const int64_t* first_dev,
+                              int nreq, int64_t tiles, cudaStream_t s) {
+  if (nreq < 1 || tiles < 1) return cudaSuccess;
+  oz_split_x_grouped_kernel<<<dim3(kOzServeCols, static_cast<unsigned>(nreq)), 256, 0, s>>>(ps_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constexpr int smem = OzCfg<16>::kSmem;
+  e = cudaFuncSetAttribute(oz_resid_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  oz_resid_grouped_kernel<<<static_cast<unsigned>(tiles), OzCfg<16>::kThreads, smem, s>>>(ps_dev, maps_dev,
+                                                                                          first_dev, nreq);
+  return cudaGetLastError();
+}
 
 int64_t oz_padded_rows(int64_t n) { return (n + kOzTile - 1) / kOzTile * kOzTile; }
 

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "mrhs.cuh"
 #include "solver.cuh"
 #include "splitfloat.cuh"
 
@@ -58,6 +59,12 @@ struct SrvReq {
   float2* xs[2];
   int xg[16];
   int phase, xsel, dsel, rb, split;
+  // tensor-core residual (JACOBI_FLAG_TC_RESIDUAL): A's digit matrices and row exponents (written at
+  // admission), X's digits and column exponents (written by each residual round)
+  __nv_bfloat16* adig;
+  int* aexp;
+  __nv_bfloat16* xdig;
+  int* xexp;
 };
 
 // ------------------------------------------------------------------------ Philox4x32-10 (device)
@@ -460,11 +467,20 @@ __device__ __forceinline__ void run_item(const SrvReq& q, int64_t r0, int warp, 
   }
 }
 
+// Work items are handed out by an atomic counter (*queue, zero at launch) in array order; the host orders
+// the requests by the cost of one of their items, heaviest first, so the long items start early and the
+// short ones fill the end of the round.
 __global__ void __launch_bounds__(kSThreads, 2) serve_round_kernel(const SrvReq* __restrict__ reqs, int nreq,
-                                                                   const int64_t* __restrict__ first, int64_t items) {
+                                                                   const int64_t* __restrict__ first, int64_t items,
+                                                                   unsigned long long* queue) {
   __shared__ SrvSmem sm;
+  __shared__ long long s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+  for (;;) {
+    if (threadIdx.x == 0) s_item = static_cast<long long>(atomicAdd(queue, 1ull));
+    __syncthreads();
+    const int64_t it = s_item;
+    if (it >= items) break;
     int lo = 0, hi = nreq - 1;  // request owning this item: last k with first[k] <= it
     while (lo < hi) {
       const int mid = (lo + hi + 1) / 2;
@@ -478,6 +494,7 @@ __global__ void __launch_bounds__(kSThreads, 2) serve_round_kernel(const SrvReq*
     if (q.phase == kPhPrep) {
       const int64_t i0 = r0 + 2 * warp;
       if (i0 < q.n) prep_rows(q, i0, lane);
+      __syncthreads();  // s_item is rewritten by the next claim
       continue;
     }
     switch (q.rb) {
@@ -487,7 +504,7 @@ __global__ void __launch_bounds__(kSThreads, 2) serve_round_kernel(const SrvReq*
       case 8: run_item<8>(q, r0, warp, lane, sm); break;
       default: run_item<16>(q, r0, warp, lane, sm); break;
     }
-    __syncthreads();  // the next item restages shared memory
+    __syncthreads();  // the next item restages shared memory (and s_item)
   }
 }
 
@@ -552,10 +569,17 @@ struct Request {
   int64_t outer = 0, inner_total = 0, inner_step = 0;
   std::vector<double> bnorm;  // ||b_c||_inf per column (from the setup round)
   jacobi_stats st{};
+  CUtensorMap maps[2];        // tensor-core residual: TMA maps of A's and X's digits
+  bool maps_ok = true;
 };
 
-size_t request_bytes(int64_t n, int64_t r, int64_t ld, bool own_A, bool split) {
+size_t request_bytes(int64_t n, int64_t r, int64_t ld, bool own_A, bool split, bool tc) {
   size_t b = 0;
+  if (tc) {
+    const int64_t nr = oz_padded_rows(n);
+    b += a256(static_cast<size_t>(kOzDigits) * nr * ld * 2) + a256(static_cast<size_t>(nr) * 4);
+    b += a256(static_cast<size_t>(kOzDigits) * kOzServeCols * ld * 2) + a256(kOzServeCols * 4);
+  }
   if (own_A) b += a256(static_cast<size_t>(n) * ld * 8);    // A, rows padded to ld (128-byte aligned)
   b += a256(static_cast<size_t>(n) * ld * 4);                // Nl
   b += 2 * a256(static_cast<size_t>(ld) * 8) + a256(static_cast<size_t>(ld) * 4);  // d, rinv, rowfac
@@ -585,6 +609,7 @@ struct jacobi_server {
   float inner_rtol = 1.0f / 1024;
   int max_active = 0;
   bool split = false;
+  bool tc = false;  // residual rounds on the tensor cores (digit split)
   int64_t next_id = 1;
   std::deque<Request*> pending;
   std::vector<Request*> active;
@@ -592,6 +617,17 @@ struct jacobi_server {
   // per-round device / pinned buffers
   SrvReq* d_reqs = nullptr;
   int64_t* d_first = nullptr;
+  unsigned long long* d_queue = nullptr;  // work-item counter of the round kernel
+  // tensor-core residual rounds: per residual request its parameters, its two TMA maps and first tile
+  OzResidParams* d_ozp = nullptr;
+  CUtensorMap* d_maps = nullptr;
+  int64_t* d_ozfirst = nullptr;
+  int* d_cols = nullptr;      // 0 .. kOzServeCols - 1: the active columns of a request are its first r
+  int* d_tcstat = nullptr;    // timeout code of the tensor-core residual
+  OzResidParams* h_ozp = nullptr;
+  CUtensorMap* h_maps = nullptr;
+  int64_t* h_ozfirst = nullptr;
+  int* h_tcstat = nullptr;
   unsigned long long* d_stats = nullptr;
   SrvReq* h_reqs = nullptr;
   int64_t* h_first = nullptr;
@@ -619,6 +655,21 @@ int grow(jacobi_server* s, int need) {
       cudaMallocHost(&s->h_first, sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
       cudaMallocHost(&s->h_stats, sizeof(unsigned long long) * kStatSlots * cap) != cudaSuccess)
     return JACOBI_ERR_OUT_OF_MEMORY;
+  if (s->tc) {
+    cudaFree(s->d_ozp);
+    cudaFree(s->d_maps);
+    cudaFree(s->d_ozfirst);
+    cudaFreeHost(s->h_ozp);
+    cudaFreeHost(s->h_maps);
+    cudaFreeHost(s->h_ozfirst);
+    if (cudaMalloc(&s->d_ozp, sizeof(OzResidParams) * cap) != cudaSuccess ||
+        cudaMalloc(&s->d_maps, sizeof(CUtensorMap) * 2 * cap) != cudaSuccess ||
+        cudaMalloc(&s->d_ozfirst, sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
+        cudaMallocHost(&s->h_ozp, sizeof(OzResidParams) * cap) != cudaSuccess ||
+        cudaMallocHost(&s->h_maps, sizeof(CUtensorMap) * 2 * cap) != cudaSuccess ||
+        cudaMallocHost(&s->h_ozfirst, sizeof(int64_t) * (cap + 1)) != cudaSuccess)
+      return JACOBI_ERR_OUT_OF_MEMORY;
+  }
   s->cap = cap;
   return JACOBI_OK;
 }
@@ -635,7 +686,7 @@ int rbucket(int64_t r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 
 bool admit(jacobi_server* s, Request* rq) {
   const bool own_A = true;  // A always lives in the arena (copied or generated), row stride ld
   rq->ld = round_up(rq->n, kLdAlign);
-  rq->bytes = request_bytes(rq->n, rq->r, rq->ld, own_A, s->split);
+  rq->bytes = request_bytes(rq->n, rq->r, rq->ld, own_A, s->split, s->tc);
   if (!s->arena.alloc(rq->bytes, &rq->off)) return false;
   char* p = s->arena_base + rq->off;
   SrvReq& q = rq->q;
@@ -670,6 +721,13 @@ bool admit(jacobi_server* s, Request* rq) {
     vec_end = reinterpret_cast<char*>(q.xs[1]) + a256(static_cast<size_t>(r) * ld * 8);
     q.rexp = reinterpret_cast<int*>(take(static_cast<size_t>(ld) * 4));
   }
+  if (s->tc) {
+    const int64_t nr = oz_padded_rows(n);
+    q.adig = reinterpret_cast<__nv_bfloat16*>(take(static_cast<size_t>(kOzDigits) * nr * ld * 2));
+    q.aexp = reinterpret_cast<int*>(take(static_cast<size_t>(nr) * 4));
+    q.xdig = reinterpret_cast<__nv_bfloat16*>(take(static_cast<size_t>(kOzDigits) * kOzServeCols * ld * 2));
+    q.xexp = reinterpret_cast<int*>(take(kOzServeCols * 4));
+  }
   // vectors start at zero so every padding entry is 0 (X0 = 0 is the start vector)
   const size_t vec_bytes = static_cast<size_t>(vec_end - reinterpret_cast<char*>(B));
   cudaMemsetAsync(B, 0, vec_bytes, s->stream);
@@ -680,6 +738,11 @@ bool admit(jacobi_server* s, Request* rq) {
   } else {
     cudaMemcpy2DAsync(A, ld * 8, rq->A_in, n * 8, n * 8, n, cudaMemcpyDefault, s->stream);
     cudaMemcpy2DAsync(B, ld * 8, rq->B_in, n * 8, n * 8, r, cudaMemcpyDefault, s->stream);
+  }
+  if (s->tc) {
+    // A's digits for the tensor-core residual rounds, and the TMA maps of both digit blocks
+    launch_oz_split_a(A, ld, n, ld, q.adig, q.aexp, s->stream);
+    rq->maps_ok = oz_make_maps(q.adig, q.xdig, n, ld, rq->maps);
   }
   q.phase = kPhPrep;
   q.xsel = 0;
@@ -721,6 +784,11 @@ int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out) {
   if (d->inner_rtol > 0) s->inner_rtol = static_cast<float>(d->inner_rtol);
   s->max_active = d->max_active;
   s->split = (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) != 0;
+  s->tc = (d->flags & JACOBI_FLAG_TC_RESIDUAL) != 0;
+  if (s->split && s->tc) {
+    delete s;
+    return JACOBI_ERR_INVALID_ARG;
+  }
   if (cudaMalloc(&s->arena_base, d->budget_bytes) != cudaSuccess) {
     delete s;
     return JACOBI_ERR_OUT_OF_MEMORY;
@@ -731,9 +799,19 @@ int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads, 0);
   s->grid = std::max(1, per_sm) * sms;
-  if (grow(s, 64) != JACOBI_OK) {
+  if (grow(s, 64) != JACOBI_OK || cudaMalloc(&s->d_queue, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&s->d_cols, kOzServeCols * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&s->d_tcstat, sizeof(int)) != cudaSuccess || cudaMallocHost(&s->h_tcstat, sizeof(int)) != cudaSuccess) {
     jacobi_server_destroy(s);
     return JACOBI_ERR_OUT_OF_MEMORY;
+  }
+  {
+    int cols[kOzServeCols];
+    for (int c = 0; c < kOzServeCols; ++c) cols[c] = c;
+    if (cudaMemcpy(s->d_cols, cols, sizeof(cols), cudaMemcpyHostToDevice) != cudaSuccess) {
+      jacobi_server_destroy(s);
+      return JACOBI_ERR_CUDA;
+    }
   }
   *out = s;
   return JACOBI_OK;
@@ -744,7 +822,7 @@ static int submit(jacobi_server* s, int64_t n, int64_t r, Request* rq, int64_t* 
     delete rq;
     return JACOBI_ERR_INVALID_ARG;
   }
-  if (request_bytes(n, r, round_up(n, kLdAlign), true, s->split) > s->arena.size) {
+  if (request_bytes(n, r, round_up(n, kLdAlign), true, s->split, s->tc) > s->arena.size) {
     delete rq;
     return JACOBI_ERR_OUT_OF_MEMORY;  // could never be admitted
   }
@@ -791,27 +869,87 @@ int jacobi_server_step(jacobi_server* s, int32_t* active_out, int32_t* pending_o
   const int na = static_cast<int>(s->active.size());
   if (na > 0) {
     if (grow(s, na) != JACOBI_OK) return JACOBI_ERR_OUT_OF_MEMORY;
-    int64_t items = 0;
+    // heaviest item first: an FP64 residual item costs 16 n r_bucket FP64 FMAs, an inner-sweep or setup
+    // item streams 16 n FP32 / FP64 entries (a few FP64-FMA times' worth)
+    auto item_cost = [](const Request* rq) {
+      const double n = static_cast<double>(rq->n);
+      if (rq->q.phase == kPhResid) return n * (rq->q.split ? 0.25 : 1.0) * rq->q.rb;
+      return n * (rq->q.phase == kPhPrep ? 0.5 : 0.25);
+    };
+    std::stable_sort(s->active.begin(), s->active.end(),
+                     [&](const Request* a, const Request* b) { return item_cost(a) > item_cost(b); });
+    int64_t items = 0, tiles = 0;
+    int nres = 0;  // tensor-core residual requests of this round
     for (int k = 0; k < na; ++k) {
       Request* rq = s->active[static_cast<size_t>(k)];
       rq->q.st = s->d_stats + static_cast<size_t>(k) * kStatSlots;
       s->h_reqs[k] = rq->q;
       s->h_first[k] = items;
-      items += (rq->n + kSRows - 1) / kSRows;
+      if (s->tc && rq->q.phase == kPhResid) {
+        // this request's residual runs in the grouped tensor-core launch, not in the round kernel
+        OzResidParams& p = s->h_ozp[nres];
+        p = OzResidParams{};
+        p.n = rq->n;
+        p.r = kOzServeCols;
+        p.ld = rq->ld;
+        p.nr = oz_padded_rows(rq->n);
+        p.aexp = rq->q.aexp;
+        p.xexp = rq->q.xexp;
+        p.x = rq->q.X[rq->q.xsel];
+        p.b = rq->q.B;
+        p.d = rq->q.d;
+        p.rinv = rq->q.rinv;
+        p.c1 = rq->q.C1;
+        p.d1 = rq->q.D[0];
+        p.d1h = nullptr;
+        p.colmax = rq->q.st;
+        p.cols = s->d_cols;
+        p.nact = rq->r;
+        p.status = s->d_tcstat;
+        p.wait_ns = kWaitLimitNs;
+        p.xd = rq->q.xdig;
+        p.xexp_w = rq->q.xexp;
+        s->h_maps[2 * nres] = rq->maps[0];
+        s->h_maps[2 * nres + 1] = rq->maps[1];
+        s->h_ozfirst[nres] = tiles;
+        tiles += p.nr / 128;
+        ++nres;
+      } else {
+        items += (rq->n + kSRows - 1) / kSRows;
+      }
     }
     s->h_first[na] = items;
+    if (s->tc) s->h_ozfirst[nres] = tiles;  // the grouped arrays exist only on a tensor-core-residual server
     if (cudaMemcpyAsync(s->d_reqs, s->h_reqs, sizeof(SrvReq) * na, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(s->d_first, s->h_first, sizeof(int64_t) * (na + 1), cudaMemcpyHostToDevice, s->stream) !=
             cudaSuccess ||
-        cudaMemsetAsync(s->d_stats, 0, sizeof(unsigned long long) * kStatSlots * na, s->stream) != cudaSuccess)
+        cudaMemsetAsync(s->d_stats, 0, sizeof(unsigned long long) * kStatSlots * na, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->d_queue, 0, sizeof(unsigned long long), s->stream) != cudaSuccess)
       return JACOBI_ERR_CUDA;
-    const int grid = static_cast<int>(std::min<int64_t>(items, s->grid));
-    serve_round_kernel<<<grid, kSThreads, 0, s->stream>>>(s->d_reqs, na, s->d_first, items);
-    if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    if (nres > 0) {
+      if (cudaMemsetAsync(s->d_tcstat, 0, sizeof(int), s->stream) != cudaSuccess ||
+          cudaMemcpyAsync(s->d_ozp, s->h_ozp, sizeof(OzResidParams) * nres, cudaMemcpyHostToDevice, s->stream) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(s->d_maps, s->h_maps, sizeof(CUtensorMap) * 2 * nres, cudaMemcpyHostToDevice, s->stream) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(s->d_ozfirst, s->h_ozfirst, sizeof(int64_t) * (nres + 1), cudaMemcpyHostToDevice,
+                          s->stream) != cudaSuccess ||
+          launch_oz_grouped(s->d_ozp, s->d_maps, s->d_ozfirst, nres, tiles, s->stream) != cudaSuccess)
+        return JACOBI_ERR_CUDA;
+    }
+    if (items > 0) {
+      const int grid = static_cast<int>(std::min<int64_t>(items, s->grid));
+      serve_round_kernel<<<grid, kSThreads, 0, s->stream>>>(s->d_reqs, na, s->d_first, items, s->d_queue);
+      if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
+    }
+    *s->h_tcstat = 0;
     if (cudaMemcpyAsync(s->h_stats, s->d_stats, sizeof(unsigned long long) * kStatSlots * na, cudaMemcpyDeviceToHost,
                         s->stream) != cudaSuccess ||
+        (nres > 0 &&
+         cudaMemcpyAsync(s->h_tcstat, s->d_tcstat, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
       return JACOBI_ERR_CUDA;
+    if (*s->h_tcstat != 0) return JACOBI_ERR_TIMEOUT;  // a bounded wait of the residual kernel expired
     ++s->rounds;
     // move every request's state machine (Section 2 control flow per request, plus the refinement)
     std::vector<Request*> still;
@@ -821,7 +959,9 @@ int jacobi_server_step(jacobi_server* s, int32_t* active_out, int32_t* pending_o
       const unsigned long long* st = s->h_stats + static_cast<size_t>(k) * kStatSlots;
       SrvReq& q = rq->q;
       int finish = 1;  // 1: keep going, else the final status
-      if (q.phase == kPhPrep) {
+      if (q.phase == kPhPrep && !rq->maps_ok) {
+        finish = JACOBI_ERR_CUDA;  // the tensor maps of its digits could not be encoded
+      } else if (q.phase == kPhPrep) {
         if (st[34]) {
           const unsigned long long key = ~st[34];
           finish = (key & 0xFF) == 2 ? JACOBI_ERR_ZERO_DIAGONAL : JACOBI_ERR_NONFINITE;
@@ -942,6 +1082,16 @@ void jacobi_server_destroy(jacobi_server* s) {
   cudaFree(s->d_reqs);
   cudaFree(s->d_first);
   cudaFree(s->d_stats);
+  cudaFree(s->d_queue);
+  cudaFree(s->d_ozp);
+  cudaFree(s->d_maps);
+  cudaFree(s->d_ozfirst);
+  cudaFree(s->d_cols);
+  cudaFree(s->d_tcstat);
+  cudaFreeHost(s->h_ozp);
+  cudaFreeHost(s->h_maps);
+  cudaFreeHost(s->h_ozfirst);
+  cudaFreeHost(s->h_tcstat);
   cudaFreeHost(s->h_reqs);
   cudaFreeHost(s->h_first);
   cudaFreeHost(s->h_stats);

@@ -48,12 +48,20 @@ def drain(srv, limit=100000):
     return done
 
 
-@pytest.mark.parametrize("split", [False, True])
-def test_served_requests_reach_target(jac, split):
-    """split: the residual rounds use the split-float arithmetic (FP32 units) instead of FP64 FMAs."""
+RESIDUALS = ["fp64", "split", "tc"]
+
+
+def make_server(jac, budget, residual, **kw):
+    return jac.Server(budget_bytes=budget, split_residual=residual == "split", tc_residual=residual == "tc", **kw)
+
+
+@pytest.mark.parametrize("residual", RESIDUALS)
+def test_served_requests_reach_target(jac, residual):
+    """The residual rounds by FP64 FMAs, by the split-float arithmetic (FP32 units), or on the tensor cores
+    from the digit split of A and X."""
     import torch
     t, ns, rs, fs, seeds = synth.serving_trace(2000, 0.02, seed=4, n_lo=64, n_hi=1500)
-    srv = jac.Server(budget_bytes=2 << 30, split_residual=split)
+    srv = make_server(jac, 2 << 30, residual)
     outs, ids = {}, {}
     for k in range(len(t)):
         out = torch.full((int(rs[k]), int(ns[k])), float("nan"), dtype=torch.float64, device="cuda")
@@ -68,18 +76,18 @@ def test_served_requests_reach_target(jac, split):
         X = outs[rid].cpu().numpy().T
         _, rel = oracle.residual(A, B, X)
         assert st.status == 0 and rel <= 1e-10, (k, ns[k], rs[k], st.as_dict(), rel)
-        assert abs(st.rel_residual - rel) <= (5e-13 if split else 1e-13) + 1e-3 * rel
+        assert abs(st.rel_residual - rel) <= (5e-13 if residual == "split" else 1e-13) + 1e-3 * rel
 
 
-@pytest.mark.parametrize("split", [False, True])
-def test_result_is_the_same_alone_and_in_the_mix(jac, split):
+@pytest.mark.parametrize("residual", RESIDUALS)
+def test_result_is_the_same_alone_and_in_the_mix(jac, residual):
     import torch
     probe = (700, 4, 1.1, 777)
-    alone = jac.Server(budget_bytes=1 << 30, split_residual=split)
+    alone = make_server(jac, 1 << 30, residual)
     xa = torch.zeros(4, 700, dtype=torch.float64, device="cuda")
     alone.submit_generated(*probe, xa)
     drain(alone)
-    mix = jac.Server(budget_bytes=1 << 30, split_residual=split)
+    mix = make_server(jac, 1 << 30, residual)
     xm = torch.zeros(4, 700, dtype=torch.float64, device="cuda")
     others = []
     for k, (n, r) in enumerate([(1200, 16), (64, 1), (333, 7)]):
@@ -150,3 +158,26 @@ def test_wait_for_one_request(jac):
     assert set(rest) == {ids[0], ids[1], ids[3]}
     with pytest.raises(jac.JacobiError):
         srv.wait(12345)
+
+
+def test_tc_residual_rounds_wild_scales(jac):
+    """Requests whose A rows and B columns span 2^-60 .. 2^60 (inside the range of the FP32 copy the inner
+    sweeps read): the tensor-core residual rounds scale each row and column by its own power of two, so every
+    request still meets 1e-10 by the oracle."""
+    import torch
+    rng = np.random.default_rng(8)
+    srv = make_server(jac, 1 << 30, "tc")
+    cases = []
+    for k, (n, r) in enumerate([(257, 3), (640, 16), (100, 1)]):
+        A, B, _ = synth.dominant_system(n, 1.2, seed=70 + k, nrhs=r)
+        rows = 2.0 ** rng.integers(-60, 60, n)
+        cols = 2.0 ** rng.integers(-60, 60, r)
+        A = A * rows[:, None]
+        B = B * rows[:, None] * cols[None, :]
+        out = torch.zeros(r, n, dtype=torch.float64, device="cuda")
+        rid = srv.submit(torch.from_numpy(A).cuda(), torch.from_numpy(np.ascontiguousarray(B.T)).cuda(), out)
+        cases.append((rid, A, B, out))
+    done = drain(srv)
+    for rid, A, B, out in cases:
+        _, rel = oracle.residual(A, B, out.cpu().numpy().T)
+        assert done[rid].status == 0 and rel <= 1e-10, (done[rid].as_dict(), rel)
