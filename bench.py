@@ -143,6 +143,8 @@ def run_ours(args, world, rank, local):
         return {"section": "serving", **run_serve(args, jac, torch, dev, args.serve_seconds)}
     if args.only == "small":
         return {"section": "small_system", **run_small(args, jac, torch, dev)}
+    if args.only == "sym":
+        return {"section": "symmetric", **run_symmetric(args, jac, torch, dev)}
     n, f = args.n, args.f
     A, B, Xs = synth.dominant_system(n, f, seed=synth.BASE_SEED + 1)
     At = torch.from_numpy(A).to(dev)
@@ -247,7 +249,8 @@ def run_ours(args, world, rank, local):
     del At, Bt, A, B  # free the single-system inputs before the large many-right-hand-side workload
     many_rhs = None if (args.quick or args.no_mrhs) else run_many_rhs(args, jac, torch, dev)
     sparse = None if (args.quick or args.no_sparse) else run_sparse(args, jac, torch, dev)
-    serving = None if (args.quick or args.no_serve) else run_serve(args, jac, torch, dev, args.serve_window)
+    serving = None if (args.quick or args.no_serve) else run_serve(args, jac, torch, dev, args.serve_seconds,
+                                                                      args.serve_window)
     result = {
         "metric": METRIC if (args.precision == "bf16_ir" and n == 16384)
         else f"solves/s ({PATH_LABEL[args.precision]}), n={n}",
@@ -410,7 +413,12 @@ def run_batch(args, jac, torch, dev):
     out = {"count": count, "n_range": [64, 1024], "f_range": [1.05, 2.0], "sum_n2": sum_n2}
     for name in ("fp32_ir", "fp32_ir+split", "bf16_ir", "fp64"):
         prec, split = name.replace("+split", ""), name.endswith("+split")
-        tuned = autotune.tune_batch(As, Bs, precision=prec, tol=TARGET, use_cache=True, split_residual=split)
+        if args.batch_tuned:  # a fixed launch shape (profiler captures): rows per warp, CTAs per SM, inner tol
+            rpw, cps, rt = args.batch_tuned.split(",")
+            tuned = {"rows_per_warp": int(rpw), "ctas_per_sm": int(cps), "inner_rtol": 0.0 if prec == "fp64" else float(rt),
+                     "cached": "fixed"}
+        else:
+            tuned = autotune.tune_batch(As, Bs, precision=prec, tol=TARGET, use_cache=True, split_residual=split)
         bs = jac.BatchSolver(As, Bs, precision=prec, rows_per_warp=tuned["rows_per_warp"],
                              ctas_per_sm=tuned["ctas_per_sm"], inner_rtol=tuned["inner_rtol"], split_residual=split)
         for _ in range(args.warmup):
@@ -604,22 +612,73 @@ def run_many_rhs(args, jac, torch, dev):
     return out
 
 
-def run_serve(args, jac, torch, dev, seconds):
-    """Poisson arrivals at 2000 requests/s for `seconds` (n log-uniform in [256, 8192], r uniform in
-    {1..16}, f uniform in [1.05, 1.5], FP64 inputs generated on the device at admission), served with
-    continuous batching under a 100 GB budget to a 1e-10 relative residual, once with FP64 residual
-    rounds and once with split-float ones; latency from each request's scheduled arrival to the moment
-    its result is polled.  Beside them, the same trace's first `serve_fp64_seconds` solved one request at
-    a time by the plain FP64 path."""
+def run_symmetric(args, jac, torch, dev):
+    """A symmetric n = 16384 system (the dominant generator mirrored about the diagonal, f = 1.05), BF16 and
+    FP32 inner sweeps with FP64 refinement to a 1e-10 relative residual: the narrow copy in full (the
+    persistent single-system kernel) against the packed upper tiles of JACOBI_FLAG_SYMMETRIC (half the bytes
+    of every inner sweep).  Per inner sweep: the mean phase time of the trace (kernel time between CUDA
+    events for the packed form: its tile launch and its finish launch) and the bytes of the narrow copy it
+    reads."""
+    import synth
+    n = args.sym_n
+    A, B, Xs = synth.symmetric_system(n, 1.05, seed=synth.BASE_SEED + 7)
+    At = torch.from_numpy(A).to(dev)
+    bt = torch.from_numpy(B[:, 0].copy()).to(dev)
+    out = {"n": n, "dominance": 1.05}
+    for prec, es in (("bf16_ir", 2), ("fp32_ir", 4)):
+        for sym in (False, True):
+            name = prec + ("+sym" if sym else "")
+            s = jac.DeviceSolver(At, bt, precision=prec, symmetric=sym)
+            X, st = s.solve(max_iter=5000, tol=TARGET)  # warm-up (and the fused narrow copy)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            reps = 5
+            for _ in range(reps):
+                X, st = s.solve(max_iter=5000, tol=TARGET, out=X)
+            torch.cuda.synchronize(dev)
+            ms = (time.perf_counter() - t0) * 1e3 / reps
+            tr = s.trace()
+            inner = [(e - b) for k, b, e in tr if k == 3]
+            resid = [(e - b) for k, b, e in tr if k == 1]
+            mean_inner = sum(inner) / len(inner) if inner else None
+            stored = (n * n / 2.0 + 64.0 * n) if sym else float(n) * n   # entries of the narrow copy read per sweep
+            out[name] = {"ms_per_solve": round(ms, 3), "status": st.status, "inner_sweeps": st.sweeps,
+                         "outer_steps": st.outer_steps, "rel_residual": st.rel_residual,
+                         "err_vs_xstar": float((X - torch.from_numpy(Xs[:, 0].copy()).to(dev)).abs().max().item()),
+                         "inner_sweep_us": round(mean_inner / 1e3, 2) if mean_inner else None,
+                         "inner_sweep_gbs": round(es * stored / mean_inner, 1) if mean_inner else None,
+                         "resid64_us": round(sum(resid) / len(resid) / 1e3, 1) if resid else None}
+            s.close()
+        full, half = out[prec]["inner_sweep_us"], out[prec + "+sym"]["inner_sweep_us"]
+        out[prec + "_inner_sweep_speedup"] = round(full / half, 3) if full and half else None
+    return out
+
+
+def run_serve(args, jac, torch, dev, seconds, other_seconds=None):
+    """Poisson arrivals at 2000 requests/s (n log-uniform in [256, 8192], r uniform in {1..16}, f uniform
+    in [1.05, 1.5], FP64 inputs generated on the device at admission), served with continuous batching
+    under a 100 GB budget to a 1e-10 relative residual: with residual rounds on the tensor cores (the
+    FP64-accurate digit split) for `seconds` of arrivals, and with FP64-FMA and split-float residual
+    rounds for `other_seconds` (default: the same); latency from each request's scheduled arrival to the
+    moment its result is polled.  Beside them, the same trace's first `serve_fp64_seconds` solved one
+    request at a time by the plain FP64 path."""
     import time as _time
 
     import synth
     rate = 2000.0
-    t, ns, rs, fs, seeds = synth.serving_trace(rate, seconds, seed=synth.BASE_SEED + 4)
+    other_seconds = seconds if other_seconds is None else other_seconds
+    traces = {}
+
+    def trace(sec):
+        if sec not in traces:
+            traces[sec] = synth.serving_trace(rate, sec, seed=synth.BASE_SEED + 4)
+        return traces[sec]
+
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(min(args.serve_budget_gb * 1e9, free - 8e9))
 
     def served(mode):
+        t, ns, rs, fs, seeds = trace(seconds if mode == "tc" else other_seconds)
         srv = jac.Server(budget_bytes=budget, split_residual=mode == "split", tc_residual=mode == "tc",
                          inner_rtol=args.serve_inner_rtol)
         outs, arrive, lat, stats = {}, {}, {}, {}
@@ -665,7 +724,7 @@ def run_serve(args, jac, torch, dev, seconds):
         return {"offered_rate": rate, "seconds": seconds, "requests": total, "converged": ok,
                 "throughput_per_s": round(total / wall, 1), "wall_s": round(wall, 3),
                 "p50_ms": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
-                "max_ms": round(float(L[-1]), 3), "rounds": rounds,
+                "max_ms": round(float(L[-1]), 3), "rounds": rounds, "arrival_window_s": seconds if mode == "tc" else other_seconds,
                 "mean_in_system": round(float(np.mean(active_samples)), 1),
                 "mean_outer_steps": round(float(np.mean([v[2] for v in stats.values()])), 2),
                 "mean_inner_sweeps": round(float(np.mean([v[3] for v in stats.values()])), 2),
@@ -680,6 +739,7 @@ def run_serve(args, jac, torch, dev, seconds):
     served_split = served("split") if "split" in modes else None
 
     # the plain FP64 path, one request at a time, on the first seconds of the same trace
+    t, ns, rs, fs, seeds = trace(seconds)
     m = int(np.searchsorted(t, args.serve_fp64_seconds))
     lat64 = []
     t0 = _time.perf_counter()
@@ -956,19 +1016,22 @@ def main():
     ap.add_argument("--sparse-ell", action="store_true", dest="sparse_ell",
                     help="keep the sparse section's matrix in sliced ELL instead of the DIA form setup picks")
     ap.add_argument("--serve-seconds", type=float, default=60.0, dest="serve_seconds",
-                    help="arrival window of --only serve (the full serving configuration)")
+                    help="arrival window of the tensor-core-residual server (the serving configuration's 60 s)")
     ap.add_argument("--serve-window", type=float, default=5.0, dest="serve_window",
-                    help="arrival window of the serving section of the default run")
+                    help="arrival window of the FP64-FMA and split-float servers in the default run")
     ap.add_argument("--serve-budget-gb", type=float, default=100.0, dest="serve_budget_gb",
                     help="device-memory budget of the serving arena (the configuration's 100 GB; a few GB "
                          "for a profiler capture)")
     ap.add_argument("--serve-inner-rtol", type=float, default=0.0, dest="serve_inner_rtol",
                     help="serving: inner-sweep stop (relative change); 0 = library default")
-    ap.add_argument("--serve-modes", default="fp64,split", dest="serve_modes",
+    ap.add_argument("--serve-modes", default="tc,fp64,split", dest="serve_modes",
                     help="serving: which residual forms to run (fp64, split)")
     ap.add_argument("--serve-fp64-seconds", type=float, default=1.0, dest="serve_fp64_seconds")
-    ap.add_argument("--only", choices=["batch", "mrhs", "serve", "sparse", "small"], default=None,
+    ap.add_argument("--sym-n", type=int, default=16384, dest="sym_n")
+    ap.add_argument("--only", choices=["batch", "mrhs", "serve", "sparse", "small", "sym"], default=None,
                     help="run one secondary workload alone (profiling)")
+    ap.add_argument("--batch-tuned", default="", dest="batch_tuned",
+                    help="batched section: fixed 'rows_per_warp,ctas_per_sm,inner_rtol' instead of the autotuner")
     ap.add_argument("--mrhs-n", type=int, default=32768, dest="mrhs_n")
     ap.add_argument("--mrhs-steps", type=int, default=3, dest="mrhs_steps")
     ap.add_argument("--batch-count", type=int, default=4096, dest="batch_count")

@@ -193,6 +193,16 @@ typedef enum { JACOBI_METHOD_JACOBI = 0, JACOBI_METHOD_SOR = 1 } jacobi_method;
  * JACOBI_ERR_UNSUPPORTED for other precisions or one right-hand side.  Also a server flag
  * (jacobi_server_desc.flags), for requests of any size and right-hand-side count. */
 #define JACOBI_FLAG_TC_RESIDUAL 128
+/* BF16 / FP32 inner sweeps, one right-hand side: A is symmetric, so the narrow copy of its off-diagonal part
+ * keeps only the 128 x 128 tiles on and above the diagonal (packed), half the bytes of every inner sweep.
+ * Each off-diagonal tile (I, J) gives the row dots of block I and, through a_ji = a_ij, the column dots of
+ * block J in one read; per-row partial sums go to fixed slots that a second launch adds in slot order.  The
+ * lower triangle of A is not read for the narrow copy (the FP64 residual reads all of A, so a non-symmetric
+ * A refines slowly or not at all).  The refinement loop runs on the host (one small device-to-host read per
+ * phase); the per-phase trace (jacobi_last_trace) comes from CUDA events.  Not with the split-float or
+ * tensor-core residual; JACOBI_ERR_UNSUPPORTED for other precisions, several right-hand sides or SOR.
+ * jacobi_get_narrow returns JACOBI_ERR_UNSUPPORTED (the copy is not row-major). */
+#define JACOBI_FLAG_SYMMETRIC 256
 
 /* Fill *d with defaults (n = 0 and null pointers: the caller sets those). */
 JACOBI_API void jacobi_desc_init(jacobi_desc* d);
@@ -252,6 +262,8 @@ JACOBI_API int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_ds
 #define JACOBI_PHASE_INNER 3    /* inner sweep over the narrow copy of A */
 #define JACOBI_PHASE_NARROW_INNER 4 /* first inner sweep of a handle's first solve (BF16 / FP32 inner sweeps):
                                        reads FP64 A, writes the narrow copy and sweeps over the rounded values */
+#define JACOBI_PHASE_HOST_GAP 5     /* host-driven solves (JACOBI_FLAG_SYMMETRIC): the stream's idle time while the
+                                       host reads a phase's result and queues the next; not a phase of work */
 JACOBI_API int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap,
                                  int32_t* count);
 

@@ -35,6 +35,7 @@ FLAG_TEST_SKIP_ARRIVAL = 32
 FLAG_CSR_ELL = 64  # sparse handle: keep sliced ELL even for a banded matrix
 FLAG_RETIRE_COLUMNS = 16
 FLAG_TC_RESIDUAL = 128
+FLAG_SYMMETRIC = 256
 METHODS = {"jacobi": 0, "sor": 1}
 
 EXPORTS = ("jacobi_setup", "jacobi_solve", "jacobi_destroy", "jacobi_status_string", "jacobi_last_cuda_error",
@@ -239,7 +240,7 @@ class DeviceSolver:
     def __init__(self, A, B, precision: str = "fp64", norm: str = "inf", grid: int = 0, stream=None,
                  copy_a: bool = False, max_outer: int = 0, max_inner: int = 0, inner_rtol: float = 0.0,
                  workspace=None, device=None, split_residual: bool = False, flags: int = 0,
-                 method: str = "jacobi", omega: float = 1.0):
+                 method: str = "jacobi", omega: float = 1.0, symmetric: bool = False):
         """A, B: float64 tensors on the GPU (A may be borrowed, see jacobi_desc.A) or on the host (copied
         to the device during setup; pin them for full link bandwidth).  workspace: optional uint8 CUDA
         tensor of at least workspace_size() bytes to reuse across solvers."""
@@ -267,7 +268,8 @@ class DeviceSolver:
         d.B, d.ldb = Bv.data_ptr(), n
         d.stream = self.stream.cuda_stream
         d.grid, d.max_outer, d.max_inner, d.inner_rtol = grid, max_outer, max_inner, inner_rtol
-        d.flags = (FLAG_COPY_A if copy_a else 0) | (FLAG_SPLIT_RESIDUAL if split_residual else 0) | flags
+        d.flags = ((FLAG_COPY_A if copy_a else 0) | (FLAG_SPLIT_RESIDUAL if split_residual else 0)
+                   | (FLAG_SYMMETRIC if symmetric else 0) | flags)
         d.method = METHODS[method]
         d.omega = omega
         nbytes = ctypes.c_size_t(0)

@@ -15,6 +15,7 @@
 
 #include "gs.cuh"
 #include "mrhs.cuh"
+#include "sym.cuh"
 #include "solver.cuh"
 #include "sparse.cuh"
 
@@ -74,10 +75,11 @@ bool can_borrow(const jacobi_desc* d) {
 struct Layout {
   int64_t ld;  // padded length of vectors and row stride of owned matrices
   size_t A64, Nlow, nready, b, d, rinv, bnorm, cmax, rowfac, scale, rexp, xa, xb, xsa, xsb, xout, c1, da, db, part, gsflags,
-      gsmbox, ctl, keys, stats, total;
+      gsmbox, ctl, keys, stats, symP, symstats, total;
 };
 
-Layout make_layout(int64_t n, int precision, bool copy_A) {
+// sym: the narrow copy holds the packed upper tiles of a symmetric A (plus the tile partial sums).
+Layout make_layout(int64_t n, int precision, bool copy_A, bool sym = false) {
   Layout L{};
   L.ld = round_up(n, kLdAlign);
   size_t o = 0;
@@ -90,7 +92,14 @@ Layout make_layout(int64_t n, int precision, bool copy_A) {
   const size_t vf = static_cast<size_t>(L.ld) * sizeof(float);
   L.A64 = copy_A ? take(static_cast<size_t>(n) * L.ld * sizeof(double)) : 0;
   const size_t ns = narrow_size(precision);
-  L.Nlow = ns ? take(static_cast<size_t>(n) * L.ld * ns) : 0;
+  if (sym) {
+    const int64_t nt = sym_tiles_per_side(n);
+    L.Nlow = take(static_cast<size_t>(sym_tile_count(n)) * kSymTile * kSymTile * ns);
+    L.symP = take(static_cast<size_t>(nt) * nt * kSymTile * sizeof(float));
+    L.symstats = take(4 * sizeof(unsigned long long));
+  } else {
+    L.Nlow = ns ? take(static_cast<size_t>(n) * L.ld * ns) : 0;
+  }
   L.nready = take(sizeof(int));  // nonzero once the narrow copy and rowfac hold this handle's A
   L.b = take(vd);
   L.d = take(vd);
@@ -133,6 +142,12 @@ int validate_desc(const jacobi_desc* d) {
     // many right-hand sides: plain FP64 (any stopping norm) or BF16 inner sweeps on tcgen05
     if (d->precision != JACOBI_FP64 && d->precision != JACOBI_BF16_IR) return JACOBI_ERR_UNSUPPORTED;
     if (d->precision == JACOBI_BF16_IR && !mrhs_supported_r(d->nrhs)) return JACOBI_ERR_UNSUPPORTED;
+  }
+  if (d->flags & JACOBI_FLAG_SYMMETRIC) {
+    if (d->flags & (JACOBI_FLAG_SPLIT_RESIDUAL | JACOBI_FLAG_TC_RESIDUAL)) return JACOBI_ERR_INVALID_ARG;
+    if (d->nrhs != 1 || d->method != JACOBI_METHOD_JACOBI ||
+        (d->precision != JACOBI_BF16_IR && d->precision != JACOBI_FP32_IR))
+      return JACOBI_ERR_UNSUPPORTED;
   }
   if (d->flags & JACOBI_FLAG_TC_RESIDUAL) {
     if (d->flags & JACOBI_FLAG_SPLIT_RESIDUAL) return JACOBI_ERR_INVALID_ARG;
@@ -211,6 +226,7 @@ struct jacobi_handle {
   float inner_rtol = 0.0f;
   bool split_residual = false;
   bool tc_residual = false;  // many right-hand sides: residuals on the tensor cores (digit split of A, X)
+  bool symmetric = false;    // symmetric A: packed upper tiles for the narrow inner sweeps (sym.cu)
   bool fuse_narrow = false;  // the narrow copy is written by the first inner sweep of the first solve
   bool retire_columns = false;
   int method = JACOBI_METHOD_JACOBI;
@@ -230,6 +246,12 @@ namespace {
 
 // The setup pass that writes the narrow copy of A (and rowfac, scale, rexp) and marks it written.
 cudaError_t write_narrow(jacobi_handle* h) {
+  if (h->symmetric) {
+    cudaError_t e = launch_sym_pack(narrow_kind(h->precision), h->A64, h->lda64, h->n, h->at<double>(h->L.rinv),
+                                    h->at<void>(h->L.Nlow), h->at<float>(h->L.rowfac), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->at<char>(h->L.nready), 1, sizeof(int), h->stream);
+    return e;
+  }
   cudaError_t e = launch_narrow(narrow_kind(h->precision), h->A64, h->lda64, h->n, h->at<void>(h->L.Nlow), h->L.ld,
                                 h->at<double>(h->L.rinv), h->at<float>(h->L.scale), h->at<float>(h->L.rowfac),
                                 h->split_residual ? h->at<int>(h->L.rexp) : nullptr, h->stream);
@@ -320,7 +342,8 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   h->precision = d->precision;
   h->norm = d->norm;
   h->stream = static_cast<cudaStream_t>(d->stream);
-  h->L = make_layout(d->n, d->precision, copy_A);
+  h->symmetric = (d->flags & JACOBI_FLAG_SYMMETRIC) != 0;
+  h->L = make_layout(d->n, d->precision, copy_A, h->symmetric);
   h->nrhs = d->nrhs;
   if (h->nrhs > 1) {
     h->tc_residual = (d->flags & JACOBI_FLAG_TC_RESIDUAL) != 0;
@@ -335,7 +358,7 @@ int make_handle(const jacobi_desc* d, bool copy_A, jacobi_handle** out) {
   h->retire_columns = (d->flags & JACOBI_FLAG_RETIRE_COLUMNS) && d->nrhs > 1;
   // BF16 / FP32 copies need no row scale, so a single-right-hand-side solve can round A while it streams
   // it for its first inner sweep instead of a separate setup pass over A
-  h->fuse_narrow = d->nrhs == 1 && d->method == JACOBI_METHOD_JACOBI && !h->split_residual &&
+  h->fuse_narrow = d->nrhs == 1 && d->method == JACOBI_METHOD_JACOBI && !h->split_residual && !h->symmetric &&
                    (d->precision == JACOBI_BF16_IR || d->precision == JACOBI_FP32_IR);
   if (d->flags & JACOBI_FLAG_SHORT_WAITS) h->wait_ns = 50000000ull;
   h->test_drop_copy = (d->flags & JACOBI_FLAG_TEST_DROP_COPY) ? 1 : 0;
@@ -674,6 +697,93 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
   return out.status;
 }
 
+// Host-driven refinement for a symmetric A (packed upper tiles for the inner sweeps): the control flow of
+// the single-system mixed-precision kernel (FP64 residual, inner sweeps until the relative change is at
+// most inner_rtol, X + delta, stop at ||B - A X|| / ||B|| <= tol), with one small device-to-host read per
+// phase.  The result record goes where jacobi_last_stats finds it; X_out is device or host memory.
+int sym_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol, double* X_out,
+              jacobi_stats* stats_dev) {
+  cudaStream_t s = h->stream;
+  PhaseClock clk(s);
+  const int64_t n = h->n;
+  double* xc = h->at<double>(h->L.xa);
+  double* xo = h->at<double>(h->L.xb);
+  float* c1 = h->at<float>(h->L.c1);
+  float* dcur = h->at<float>(h->L.da);
+  float* dnew = h->at<float>(h->L.db);
+  unsigned long long* st = h->at<unsigned long long>(h->L.symstats);
+  if (X0)
+    CK(cudaMemcpyAsync(xc, X0, n * sizeof(double), cudaMemcpyDefault, s));
+  else
+    CK(cudaMemsetAsync(xc, 0, n * sizeof(double), s));
+  double bn = 0.0;
+  CK(cudaMemcpyAsync(&bn, h->at<double>(h->L.bnorm), sizeof(bn), cudaMemcpyDeviceToHost, s));
+  auto bits = [](unsigned long long u) {
+    double v;
+    std::memcpy(&v, &u, 8);
+    return v;
+  };
+  jacobi_stats out{};
+  out.rel_residual = std::nan("");
+  out.status = JACOBI_NOT_CONVERGED;
+  int64_t outer = 0, inner_total = 0;
+  bool first = true;
+  for (;;) {
+    clk.mark(JACOBI_PHASE_HOST_GAP);  // the phase's own time starts here, after the host's decision
+    CK(cudaMemsetAsync(st, 0, 2 * sizeof(unsigned long long), s));
+    CK(launch_sym_resid(n, h->A64, h->lda64, (first && !X0) ? nullptr : xc, h->at<double>(h->L.b),
+                        h->at<double>(h->L.rinv), c1, h->at<float>(h->L.da), st, s));
+    clk.mark((first && !X0) ? JACOBI_PHASE_RESID0 : JACOBI_PHASE_RESID64);
+    first = false;
+    unsigned long long hs[2];
+    CK(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ++outer;
+    const double rho = bits(hs[0]) / bn;
+    out.rel_residual = rho;
+    if (!std::isfinite(rho)) {
+      out.status = JACOBI_ERR_NONFINITE;
+      break;
+    }
+    if (rho <= tol) {
+      out.status = JACOBI_OK;
+      break;
+    }
+    if (outer >= h->max_outer || inner_total >= max_iter) break;
+    dcur = h->at<float>(h->L.da);  // the residual wrote delta^(1) = c1 there
+    dnew = h->at<float>(h->L.db);
+    for (int64_t m = 1;; ++m) {
+      clk.mark(JACOBI_PHASE_HOST_GAP);
+      CK(cudaMemsetAsync(st, 0, 2 * sizeof(unsigned long long), s));
+      CK(launch_sym_sweep(narrow_kind(h->precision), h->at<void>(h->L.Nlow), n, dcur, h->at<float>(h->L.symP), c1,
+                          h->at<float>(h->L.rowfac), dnew, xc, xo, st, s));
+      clk.mark(JACOBI_PHASE_INNER);
+      CK(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      ++inner_total;
+      const double chg = bits(hs[0]), mag = bits(hs[1]);
+      out.final_delta = chg;
+      std::swap(dcur, dnew);
+      if (!std::isfinite(chg) || !std::isfinite(mag)) {
+        out.status = JACOBI_ERR_NONFINITE;
+        break;
+      }
+      if (chg <= h->inner_rtol * mag || m >= h->max_inner || inner_total >= max_iter) break;
+    }
+    if (out.status != JACOBI_NOT_CONVERGED) break;
+    std::swap(xc, xo);  // X + delta becomes the current iterate
+  }
+  out.sweeps = inner_total;
+  out.outer_steps = outer;
+  out.converged = out.status == JACOBI_OK;
+  CK(cudaMemcpyAsync(X_out, xc, n * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(&h->at<Ctl>(h->L.ctl)->result, &out, sizeof(out), cudaMemcpyHostToDevice, s));
+  if (stats_dev) CK(cudaMemcpyAsync(stats_dev, &out, sizeof(out), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  clk.flush(h);
+  return JACOBI_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------ sparse A
@@ -953,7 +1063,7 @@ void jacobi_desc_init(jacobi_desc* d) {
 
 int jacobi_workspace_size(const jacobi_desc* d, size_t* bytes) {
   if (!d || !bytes || d->n < 1 || d->nrhs < 1) return JACOBI_ERR_INVALID_ARG;
-  const Layout L = make_layout(d->n, d->precision, !can_borrow(d));
+  const Layout L = make_layout(d->n, d->precision, !can_borrow(d), (d->flags & JACOBI_FLAG_SYMMETRIC) != 0);
   *bytes = d->nrhs > 1 ? mrhs_layout(L.total, d->n, L.ld, d->nrhs, (d->flags & JACOBI_FLAG_TC_RESIDUAL) != 0).total
                         : L.total;
   return JACOBI_OK;
@@ -1016,6 +1126,7 @@ int jacobi_solve_async(jacobi_handle* h, const double* X0, int64_t max_iter, dou
                        jacobi_stats* stats_dev) {
   if (!h || !X_out || max_iter < 1 || !(tol > 0.0) || !std::isfinite(tol)) return JACOBI_ERR_INVALID_ARG;
   if (h->nrhs > 1) return JACOBI_ERR_UNSUPPORTED;  // many right-hand sides: jacobi_solve_ex
+  if (h->symmetric) return sym_solve(h, X0, max_iter, tol, X_out, stats_dev);  // host-driven: returns when done
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
   CK(cudaMemsetAsync(h->at<char>(h->L.ctl), 0, sizeof(Ctl), s));
@@ -1167,6 +1278,7 @@ int jacobi_residual(jacobi_handle* h, const double* X, double* rel_out) {
 
 int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* scale_host) {
   if (!h || !dst_host || ld_dst < h->n || h->precision == JACOBI_FP64) return JACOBI_ERR_INVALID_ARG;
+  if (h->symmetric) return JACOBI_ERR_UNSUPPORTED;  // packed upper tiles, not a row-major copy
   const size_t es = narrow_size(h->precision);
   if (h->fuse_narrow) {  // not written yet if no solve has run an inner sweep: write it now
     int ready = 0;
@@ -1190,7 +1302,7 @@ int jacobi_get_narrow(jacobi_handle* h, void* dst_host, int64_t ld_dst, float* s
 
 int jacobi_last_trace(jacobi_handle* h, int64_t* t_end_ns, int32_t* kinds, int32_t cap, int32_t* count) {
   if (!h || !count || cap < 0 || (cap > 0 && (!t_end_ns || !kinds))) return JACOBI_ERR_INVALID_ARG;
-  if (h->nrhs > 1) {  // host-driven path: CUDA-event timeline
+  if (h->nrhs > 1 || h->symmetric) {  // host-driven path: CUDA-event timeline
     const int32_t m = static_cast<int32_t>(h->htrace_kind.size());
     *count = m;
     for (int32_t i = 0; i < m && i < cap; ++i) {

@@ -132,6 +132,24 @@ def dominant_system(n: int, f: float, seed: int, nrhs: int = 1):
     return A, B, Xs
 
 
+def symmetric_system(n: int, f: float, seed: int, nrhs: int = 1):
+    """Symmetric strictly diagonally dominant system with a planted solution: the off-diagonal entries of
+    row i < j are the dominant generator's, mirrored below the diagonal (a_ji = a_ij), a_ii = f * sum_{j != i}
+    |a_ij| * (+-1), so ||T||_inf = 1/f exactly.  Returns ``(A, B, Xstar)`` as dominant_system."""
+    A = _offdiag(seed, n, signed=True)
+    A = np.triu(A, 1)
+    A = A + A.T                                    # exact: one of the two terms is zero
+    rowsum = np.abs(A).sum(axis=1)                 # exact (integers times 2**-31)
+    sign = np.where(random_u32(seed, STREAM_SIGN, n) & np.uint32(1), -1.0, 1.0)
+    d = f * rowsum * sign
+    if n == 1:
+        d = np.array([f * sign[0]])
+    A[np.arange(n), np.arange(n)] = d
+    Xs = signed_unit(random_u32(seed, STREAM_XSTAR, n * nrhs)).reshape(nrhs, n).T.copy()
+    B = A @ Xs
+    return A, B, Xs
+
+
 def hard_system(n: int, f: float, seed: int, nrhs: int = 1):
     """The paper-shaped generator (Section 4 draws entries uniformly from [0, 1]) made convergent: a
     positive diagonal ``f`` times the row sum.  ``rho(T) = ||T||_inf = 1/f``.  Returns ``(A, B, Xstar)``."""

@@ -51,3 +51,12 @@ def test_batch_shapes_ranges():
     assert f.min() >= 1.05 and f.max() <= 2.0
     # log-uniform: the median is near the geometric mean sqrt(64 * 1025) ~ 256
     assert 220 < np.median(n) < 300
+
+
+def test_symmetric_generator_structure():
+    A, B, Xs = synth.symmetric_system(40, 1.2, seed=9, nrhs=2)
+    np.testing.assert_array_equal(A, A.T)
+    d = np.abs(np.diag(A))
+    off = np.abs(A).sum(axis=1) - d
+    np.testing.assert_allclose(off / d, 1 / 1.2, rtol=1e-15)
+    np.testing.assert_allclose(B, A @ Xs, rtol=0, atol=0)
