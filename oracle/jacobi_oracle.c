@@ -499,9 +499,11 @@ int oracle_split(int64_t n, int64_t nrhs, const double* A, const double* B, doub
  * even, the C cast), then
  *   FP32:     kept as is;
  *   BF16:     rounded to nearest even into BF16 (sign, 8 exponent bits, 7 fraction bits);
- *   FP8 E4M3: per-row scale s_i = (max_{j != i} |a32_ij|) / 448 in FP32 (448 is the largest finite
- *             E4M3 value), s_i = 1 when that is 0; code q_ij = E4M3 value nearest to a32_ij / s_i (FP32
- *             division), ties to the code with an even last mantissa bit, saturating to +-448.
+ *   FP8 E4M3: per-row scale s_i = the smallest power of two 2^k (-126 <= k <= 127) with
+ *             max_{j != i} |a32_ij| <= 448 s_i (448 is the largest finite E4M3 value), s_i = 1 when the
+ *             maximum is 0; code q_ij = E4M3 value nearest to a32_ij / s_i (FP32 division, exact for a
+ *             power of two), ties to the code with an even last mantissa bit, saturating to +-448.  A
+ *             power-of-two scale leaves every entry's relative rounding error what it would be unscaled.
  * Both encoders below work from the formats' definitions (value tables), not from bit tricks. */
 
 static float or_bf16_value(uint16_t h) {
@@ -580,6 +582,17 @@ void oracle_offdiag_bf16(int64_t n, const double* A, uint16_t* out) {
       out[i * n + j] = (j == i) ? (uint16_t)0 : oracle_bf16_from_f32((float)A[i * n + j]);
 }
 
+/* The E4M3 row scale: smallest power of two 2^k, -126 <= k <= 127, with m <= 448 * 2^k (1 for m = 0). */
+static float or_e4m3_row_scale(float m) {
+  if (m == 0.0f) return 1.0f;
+  int k = -126;
+  if (!isfinite(m))
+    k = 127;
+  else
+    while (k < 127 && (double)m > 448.0 * ldexp(1.0, k)) ++k;
+  return ldexpf(1.0f, k);
+}
+
 /* Off-diagonal part of A as per-row scaled E4M3 codes (through FP32), zero code on the diagonal. */
 void oracle_offdiag_e4m3(int64_t n, const double* A, uint8_t* q, float* scale) {
   for (int64_t i = 0; i < n; ++i) {
@@ -589,8 +602,7 @@ void oracle_offdiag_e4m3(int64_t n, const double* A, uint8_t* q, float* scale) {
       float a = fabsf((float)A[i * n + j]);
       if (a > m) m = a;
     }
-    float s = m / 448.0f;
-    if (s == 0.0f) s = 1.0f;
+    float s = or_e4m3_row_scale(m);
     scale[i] = s;
     for (int64_t j = 0; j < n; ++j)
       q[i * n + j] = (j == i) ? (uint8_t)0 : oracle_e4m3_from_f32((float)A[i * n + j] / s);

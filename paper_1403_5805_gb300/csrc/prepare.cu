@@ -10,8 +10,9 @@
 //     hand sides, and a copy read out before any solve.  The BF16 / FP32 copies of the other handles are
 //     written by the first inner sweep of their first solve (solve.cu), with the same rounding.
 // Rounding of the narrow copies: a_ij -> FP32 (round to nearest even), then BF16 round to nearest even;
-// for E4M3 the row scale s_i = max_{j != i} |a32_ij| / 448 (FP32 division, s_i = 1 if that is 0) and
-// the code is the saturating round-to-nearest-even E4M3 of a32_ij / s_i (FP32 division).
+// for E4M3 the row scale s_i is the smallest power of two with max_{j != i} |a32_ij| <= 448 s_i (s_i = 1 if
+// the maximum is 0) and the code is the saturating round-to-nearest-even E4M3 of a32_ij / s_i (exact:
+// the product with 1 / s_i).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -119,13 +120,25 @@ __device__ __forceinline__ void encode_quad<__nv_bfloat16>(const float (&f)[4], 
   *reinterpret_cast<uint2*>(dst) = w;
 }
 template <>
-__device__ __forceinline__ void encode_quad<__nv_fp8_e4m3>(const float (&f)[4], float s, __nv_fp8_e4m3* dst) {
-  // saturating round-to-nearest-even E4M3 of fl32(a_ij) / s_i (FP32 division)
-  const __nv_fp8x2_storage_t lo =
-      __nv_cvt_float2_to_fp8x2(make_float2(__fdiv_rn(f[0], s), __fdiv_rn(f[1], s)), __NV_SATFINITE, __NV_E4M3);
-  const __nv_fp8x2_storage_t hi =
-      __nv_cvt_float2_to_fp8x2(make_float2(__fdiv_rn(f[2], s), __fdiv_rn(f[3], s)), __NV_SATFINITE, __NV_E4M3);
+__device__ __forceinline__ void encode_quad<__nv_fp8_e4m3>(const float (&f)[4], float inv_s, __nv_fp8_e4m3* dst) {
+  // saturating round-to-nearest-even E4M3 of fl32(a_ij) / s_i; s_i is a power of two, so the quotient is
+  // the product with the exact 1 / s_i (the same correctly rounded value as the division)
+  const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(__fmul_rn(f[0], inv_s), __fmul_rn(f[1], inv_s)),
+                                                           __NV_SATFINITE, __NV_E4M3);
+  const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(__fmul_rn(f[2], inv_s), __fmul_rn(f[3], inv_s)),
+                                                           __NV_SATFINITE, __NV_E4M3);
   *reinterpret_cast<uint32_t*>(dst) = static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
+// E4M3 row scale from the bits of m = max_{j != i} |fl32(a_ij)|: the smallest power of two 2^k with
+// m <= 448 * 2^k (448 = 1.75 * 2^8: k = e - 8 while m's significand is at most 1.75, else e - 7), k clamped
+// to [-126, 127]; 1 for m = 0.  Returns k.
+__device__ __forceinline__ int e4m3_scale_exponent(unsigned int mbits) {
+  if (mbits >= 0x7F800000u) return 127;
+  const int e = static_cast<int>(mbits >> 23);
+  if (e == 0) return -126;  // m < 2^-126 <= 448 * 2^-126
+  const int k = e - 135 + ((mbits & 0x7FFFFFu) > 0x600000u ? 1 : 0);
+  return k < -126 ? -126 : (k > 127 ? 127 : k);
 }
 
 template <typename T>
@@ -156,7 +169,7 @@ __global__ void __launch_bounds__(kPrepThreads) narrow_kernel(const double* __re
   const int64_t step = 4 * int64_t(blockDim.x);
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const double* row = A + i * lda;
-    float s = 1.0f;
+    float s = 1.0f, inv = 1.0f;  // the row scale (a power of two) and its exact reciprocal
     if (kScaled) {
       unsigned int m = 0;  // max_{j != i} |fl32(a_ij)| as bits (non-negative floats order like integers)
       for (int64_t j = 4 * int64_t(threadIdx.x); j < n; j += step) {
@@ -171,8 +184,11 @@ __global__ void __launch_bounds__(kPrepThreads) narrow_kernel(const double* __re
         }
       }
       m = block_max(m, shs);
-      s = __fdiv_rn(__uint_as_float(m), 448.0f);
-      if (s == 0.0f) s = 1.0f;
+      if (m != 0) {
+        const int k = e4m3_scale_exponent(m);
+        s = __uint_as_float(static_cast<unsigned int>(k + 127) << 23);
+        inv = k == 127 ? 0x1p-127f : __uint_as_float(static_cast<unsigned int>(127 - k) << 23);
+      }
     }
     TL* out = Nl + i * ldn;
     uint32_t mb = 0;  // max_j of the high word of |a_ij| (all j)
@@ -188,7 +204,7 @@ __global__ void __launch_bounds__(kPrepThreads) narrow_kernel(const double* __re
         }
       }
       quad_f32(a, j, n, i, f);
-      encode_quad<TL>(f, s, out + j);
+      encode_quad<TL>(f, inv, out + j);
     }
     if constexpr (kRexp) {
       mb = block_max(mb, shs);

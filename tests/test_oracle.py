@@ -384,15 +384,30 @@ def test_offdiag_encodings():
     want = torch.from_numpy(off.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
     np.testing.assert_array_equal(bf, want.view(np.uint16))
     q, s = oracle.offdiag_e4m3(A)
-    m = np.abs(off.astype(np.float32)).max(axis=1)
-    np.testing.assert_array_equal(s, m / np.float32(448.0))
+    m = np.abs(off.astype(np.float32)).max(axis=1).astype(np.float64)
+    # the row scale is the smallest power of two s with m <= 448 s
+    mant, _ = np.frexp(s.astype(np.float64))
+    assert np.all(mant == 0.5)                                   # powers of two
+    assert np.all(m <= 448.0 * s) and np.all(m > 224.0 * s)      # and the smallest such
     assert np.all(np.diag(q) == 0)
     scaled = (off.astype(np.float32) / s[:, None]).astype(np.float32)
     want_q = torch.from_numpy(scaled).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
     np.testing.assert_array_equal(q, want_q)
-    # the row maximum is encoded as the largest finite code, 448 (m / (m / 448) is within an FP32 ulp
-    # of 448, far inside E4M3's rounding interval there)
-    assert np.all((q & 0x7F).max(axis=1) == 0x7E)
+    # the row maximum, in (224, 448] after scaling, is encoded as one of the codes 224 .. 448
+    assert np.all((q & 0x7F).max(axis=1) >= 0x76)
+
+
+def test_e4m3_row_scale_edges():
+    # a zero row keeps scale 1; a row maximum of exactly 448 * 2^k gives 2^k (not 2^(k+1)); one ulp above
+    # gives 2^(k+1); the exponent is clamped to [-126, 127]
+    cases = [(0.0, 1.0), (448.0, 1.0), (np.nextafter(np.float32(448.0), np.float32(1e9)), 2.0), (1.0, 2.0 ** -8),
+             (1.75, 2.0 ** -8), (np.nextafter(np.float32(1.75), np.float32(9)), 2.0 ** -7), (1e-44, 2.0 ** -126),
+             (3e38, 2.0 ** 120)]
+    for m, want in cases:
+        A = np.array([[1.0, float(np.float32(m))], [0.0, 1.0]])
+        _, s = oracle.offdiag_e4m3(A)
+        assert s[0] == np.float32(want), (m, s[0], want)
+        assert s[1] == 1.0
 
 
 def test_f32_narrowing_of_edge_values():
