@@ -446,11 +446,11 @@ JACOBI_API int jacobi_measure_fma_rates(int64_t iters, double* fp64_fma_per_s, d
  *   stats  host, filled if not NULL.  stream: cudaStream_t (NULL: legacy default stream).
  * Returns the solve's jacobi_status; JACOBI_ERR_INVALID_ARG for n > JACOBI_NOALLOC_MAX_N, a misaligned
  * or non-device A / B / X_out, max_iter < 1, or tol not positive and finite.  JACOBI_ERR_ZERO_DIAGONAL /
- * JACOBI_ERR_NONFINITE as jacobi_setup_ex (first failing row).  Blocks until the solve is done.
- * The first call on a device looks up the scratch array's device address (cudaGetSymbolAddress) and
- * keeps it for the life of the process; make that first call before any stream capture, and do not call
- * this entry point after cudaDeviceReset on that device (the reset unloads the array and the kept
- * address goes stale).  Every call shares the one array and it keeps the last call's contents (each call
+ * JACOBI_ERR_NONFINITE as jacobi_setup_ex (first failing row).  Blocks until the solve is done: every
+ * call synchronises the stream and reads the solve's status back to the host, so no call may be made
+ * on a stream under capture.  The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; do not call this entry point after
+ * cudaDeviceReset on that device (the reset unloads the array and the kept address goes stale).  Every call shares the one array and it keeps the last call's contents (each call
  * clears what must start at zero), so calls that overlap on the GPU - from two streams or two host
  * threads on one device - race: serialise them. */
 JACOBI_API int jacobi_solve_fp64_noalloc(const double* A, int64_t lda, const double* B, int64_t n,

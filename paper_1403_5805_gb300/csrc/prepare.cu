@@ -17,6 +17,7 @@
 #include <cuda_fp8.h>
 
 #include "device_util.cuh"
+#include "f64tof32.cuh"
 #include "solver.cuh"
 #include "splitfloat.cuh"
 
@@ -101,7 +102,7 @@ __device__ __forceinline__ void load_quad(const double* row, int64_t j, int64_t 
 // fl32(a_ij) of the quad, 0 on the diagonal and past n.
 __device__ __forceinline__ void quad_f32(const double (&a)[4], int64_t j, int64_t n, int64_t i, float (&f)[4]) {
 #pragma unroll
-  for (int e = 0; e < 4; ++e) f[e] = (j + e < n && j + e != i) ? __double2float_rn(a[e]) : 0.0f;
+  for (int e = 0; e < 4; ++e) f[e] = (j + e < n && j + e != i) ? f64_to_f32_rn(a[e]) : 0.0f;
 }
 
 template <typename TL>

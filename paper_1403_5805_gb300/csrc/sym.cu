@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "device_util.cuh"
+#include "f64tof32.cuh"
 #include "solver.cuh"
 #include "sym.cuh"
 
@@ -27,11 +28,11 @@ template <typename TL>
 __device__ __forceinline__ TL sym_encode(double a);
 template <>
 __device__ __forceinline__ float sym_encode<float>(double a) {
-  return __double2float_rn(a);
+  return f64_to_f32_rn(a);
 }
 template <>
 __device__ __forceinline__ __nv_bfloat16 sym_encode<__nv_bfloat16>(double a) {
-  return __float2bfloat16_rn(__double2float_rn(a));  // FP64 -> FP32 -> BF16, each to nearest even
+  return __float2bfloat16_rn(f64_to_f32_rn(a));  // FP64 -> FP32 -> BF16, each to nearest even
 }
 
 // Four consecutive narrow entries of a tile row as FP32.
