@@ -441,9 +441,11 @@ def run_batch(args, jac, torch, dev):
             worst = float(max(x.final_delta for x in st))
         else:
             outer = np.array([x.outer_steps for x in st], dtype=np.float64)
-            # setup pass (read A, write the narrow copy) + FP64 residual passes + narrow inner sweeps
+            # setup pass (read A, write the narrow copy, the first inner sweep on the rounded values as
+            # they are written) + FP64 residual passes + the other narrow inner sweeps
             es = 2.0 if prec == "bf16_ir" else 4.0
-            alg = float(np.sum((8.0 + es) * n2 + np.maximum(outer - 1, 0) * 8.0 * n2 + sweeps * es * n2))
+            alg = float(np.sum((8.0 + es) * n2 + np.maximum(outer - 1, 0) * 8.0 * n2
+                               + np.maximum(sweeps - 1, 0) * es * n2))
             worst = float(max(x.rel_residual for x in st))
         out[name] = {"solves_per_s": round(count / (ms * 1e-3), 1), "ms_per_batch": round(ms, 4),
                      "converged": ok, "mean_sweeps": round(float(sweeps.mean()), 3),

@@ -3,8 +3,10 @@
 //
 // Each system is small (n <= JACOBI_BATCH_MAX_N), so one CTA owns it for the whole solve: its iterates
 // live in shared memory, its 8 warps stream the rows (RPW rows per warp at a time, 128-bit loads of the
-// narrow copy, 64-bit loads of FP64 A) and every sweep ends with one CTA barrier instead of a grid
-// barrier.  CTAs are persistent and take systems from a global atomic work queue, largest first, so
+// narrow copy, 128-bit loads of FP64 A where rows are 16-byte aligned, else 64-bit) and every sweep ends
+// with one CTA barrier instead of a grid barrier.  The setup phase writes the narrow copy a row per warp
+// with several loads per lane in flight, and computes the first inner sweep from the rounded values as it
+// writes them, so that sweep does not read the copy back.  CTAs are persistent and take systems from a global atomic work queue, largest first, so
 // systems of different sizes and sweep counts balance over the SMs.  This is the row-wise
 // distribution of Section 3.1 applied at two levels: systems over SMs, rows over warps.
 //
@@ -13,7 +15,7 @@
 //             max_i |a_ii (x_i^(k) - x_i^(k-1))| / ||b||_inf, drops below tol (strict).
 //   FP32/BF16 mixed precision: FP64 residual r = b - A x, inner Jacobi sweeps on the narrow copy of
 //             the off-diagonal part of A written by the first phase, x += delta in FP64, until
-//             ||b - A x||_inf / ||b||_inf <= tol.
+//             ||b - A x||_inf / ||b||_inf <= tol.  For the zero start vector r = b: no matrix pass.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -31,6 +33,8 @@ namespace jac {
 namespace {
 
 constexpr int kBWarps = 8;
+constexpr int kCopyLoads = 8;  // setup pass: FP64 loads per lane in flight (8-byte loads)
+constexpr int kCopyPairs = 4;  // the same with 16-byte loads (rows 16-byte aligned)
 constexpr int kBThreads = kBWarps * 32;
 
 struct BatchSys {
@@ -296,6 +300,33 @@ __device__ __forceinline__ __nv_bfloat16 encode_narrow<__nv_bfloat16>(double a) 
   return __float2bfloat16_rn(__double2float_rn(a));
 }
 
+// Two adjacent narrow values at p (p 2-element aligned: j even and ldn a multiple of 16).
+__device__ __forceinline__ void store_pair(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void store_pair(__nv_bfloat16* p, __nv_bfloat16 a, __nv_bfloat16 b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __halves2bfloat162(a, b);
+}
+
+// Maxima of two values over the CTA in one exchange (the barrier also publishes the shared-memory
+// writes made before the call).
+__device__ __forceinline__ void block_max2(unsigned long long& a, unsigned long long& b,
+                                           unsigned long long (*sa)[kBWarps], unsigned long long (*sb)[kBWarps],
+                                           int parity) {
+  a = warp_max_u64(a);
+  b = warp_max_u64(b);
+  if ((threadIdx.x & 31) == 0) {
+    sa[parity][threadIdx.x >> 5] = a;
+    sb[parity][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  a = b = 0;
+#pragma unroll
+  for (int w = 0; w < kBWarps; ++w) {
+    a = sa[parity][w] > a ? sa[parity][w] : a;
+    b = sb[parity][w] > b ? sb[parity][w] : b;
+  }
+}
+
+// Maximum over the CTA (the barrier also publishes the shared-memory writes made before the call).
 __device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long (*sred)[kBWarps],
                                                         int parity) {
   v = warp_max_u64(v);
@@ -317,6 +348,7 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
   extern __shared__ __align__(16) unsigned char bsmem[];
   __shared__ unsigned long long sred[2][kBWarps];   // phase-parity double buffer
   __shared__ unsigned long long sred2[2][kBWarps];
+  __shared__ unsigned long long sph0[5][kBWarps];  // the setup phase's maxima
   __shared__ long long s_sys;
   double* xs0 = reinterpret_cast<double*>(bsmem);
   double* xs1 = xs0 + p.smem_ld;
@@ -357,33 +389,115 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
       ds1[i] = 0.0f;
     }
     unsigned long long cm = 0;  // max_i |b_i / a_ii|: the iterate's scale for the split residual
+    unsigned long long chg1 = 0, mag1 = 0;  // the first inner sweep's max |change| and max |delta|
     if (kMode != 0) {
+      __syncthreads();  // reciprocals and zeroed vectors
+      // the residual of the zero start vector (r = b) and c = r / a_ii, the inner iteration's start
+      for (int64_t i = threadIdx.x; i < n; i += kBThreads) {
+        const double r = S.B[i] - 0.0;
+        const float c = static_cast<float>(r * S.rinv[i]);
+        S.c1[i] = c;
+        ds0[i] = c;
+        if constexpr (kSplit) {
+          const unsigned long long cb = abs_bits(S.B[i] * S.rinv[i]);
+          cm = cb > cm ? cb : cm;
+        }
+      }
+      __syncthreads();
+      // the narrow copy, a row per warp, and with it the first inner sweep on the rounded values:
+      // delta^(1)_i = c_i - (1/a_ii) sum_j fl(a_ij) c_j (the candidate x + delta^(1) = delta^(1))
       TL* Nl = static_cast<TL*>(S.Nlow);
       for (int64_t i = warp; i < n; i += kBWarps) {
         uint32_t mb = 0;
-        for (int64_t j = lane; j < S.ldn; j += 32) {
-          const double a = j < n ? __ldg(S.A + i * n + j) : 0.0;
-          if constexpr (kSplit) mb = max(mb, abs_hi(a));
-          Nl[i * S.ldn + j] = (j < n && j != i) ? encode_narrow<TL>(a) : TL(0.0f);
+        float acc = 0.0f;
+        // several loads per lane in flight before their conversions and stores; rows 16-byte aligned:
+        // column pairs (16-byte loads, paired stores)
+        if (al16) {
+          for (int64_t j0 = 0; j0 < S.ldn; j0 += 64 * kCopyPairs) {
+            double2 a[kCopyPairs];
+#pragma unroll
+            for (int u = 0; u < kCopyPairs; ++u) {
+              const int64_t j = j0 + 2 * lane + 64 * u;
+              a[u] = j < n ? __ldg(reinterpret_cast<const double2*>(S.A + i * n + j)) : double2{0.0, 0.0};
+            }
+#pragma unroll
+            for (int u = 0; u < kCopyPairs; ++u) {
+              const int64_t j = j0 + 2 * lane + 64 * u;
+              if (j < S.ldn) {
+                if constexpr (kSplit) mb = max(mb, max(abs_hi(a[u].x), abs_hi(a[u].y)));
+                const TL e0 = (j < n && j != i) ? encode_narrow<TL>(a[u].x) : TL(0.0f);
+                const TL e1 = (j + 1 < n && j + 1 != i) ? encode_narrow<TL>(a[u].y) : TL(0.0f);
+                store_pair(Nl + i * S.ldn + j, e0, e1);
+                const float2 c = *reinterpret_cast<const float2*>(ds0 + j);
+                acc = fmaf(static_cast<float>(e0), c.x, acc);
+                acc = fmaf(static_cast<float>(e1), c.y, acc);
+              }
+            }
+          }
+        } else {
+          for (int64_t j0 = 0; j0 < S.ldn; j0 += 32 * kCopyLoads) {
+            double a[kCopyLoads];
+#pragma unroll
+            for (int u = 0; u < kCopyLoads; ++u) {
+              const int64_t j = j0 + lane + 32 * u;
+              a[u] = j < n ? __ldg(S.A + i * n + j) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kCopyLoads; ++u) {
+              const int64_t j = j0 + lane + 32 * u;
+              if (j < S.ldn) {
+                if constexpr (kSplit) mb = max(mb, abs_hi(a[u]));
+                const TL e = (j < n && j != i) ? encode_narrow<TL>(a[u]) : TL(0.0f);
+                Nl[i * S.ldn + j] = e;
+                acc = fmaf(static_cast<float>(e), ds0[j], acc);
+              }
+            }
+          }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if constexpr (kSplit) {
           mb = __reduce_max_sync(0xffffffffu, mb);
           if (lane == 0) S.rexp[i] = split_exponent_hi(mb);
         }
-      }
-      if constexpr (kSplit)
-        for (int64_t i = threadIdx.x; i < n; i += kBThreads) {
-          const unsigned long long cb = abs_bits(S.B[i] * S.rinv[i]);
-          cm = cb > cm ? cb : cm;
+        if (lane == 0) {
+          const float v = fmaf(-S.rowfac[i], acc, S.c1[i]);
+          ds1[i] = v;
+          xs1[i] = xs0[i] + static_cast<double>(v);
+          const unsigned long long a1 = abs_bits(v - ds0[i]), a2 = abs_bits(v);
+          chg1 = a1 > chg1 ? a1 : chg1;
+          mag1 = a2 > mag1 ? a2 : mag1;
         }
+      }
     }
-    // first failing row decides (smallest index); stats are combined in the reduction slots
+    // the setup's maxima in one exchange; the first failing row decides (smallest index)
     if (bad) bad = ~bad;  // so that the max picks the smallest key
-    const unsigned long long badmax = block_max(bad, sred, 0);
-    const unsigned long long bmax_bits = block_max(bm, sred2, 0);
+    {
+      unsigned long long v[5] = {bad, bm, cm, chg1, mag1};
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] = warp_max_u64(v[k]);
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sph0[k][warp] = v[k];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        v[k] = 0;
+#pragma unroll
+        for (int w = 0; w < kBWarps; ++w) v[k] = sph0[k][w] > v[k] ? sph0[k][w] : v[k];
+      }
+      bad = v[0];
+      bm = v[1];
+      cm = v[2];
+      chg1 = v[3];
+      mag1 = v[4];
+    }
+    const unsigned long long badmax = bad;
+    const unsigned long long bmax_bits = bm;
     const double bnorm = __longlong_as_double(static_cast<long long>(bmax_bits));
     int xg = 0;
-    if constexpr (kSplit) xg = split_exponent(block_max(cm, sred, 1));
+    if constexpr (kSplit) xg = split_exponent(cm);
     jacobi_stats st{};
     st.rel_residual = __longlong_as_double(0x7FF8000000000000ll);
     int status = kStatusNotConverged;
@@ -411,7 +525,6 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
             mx = v > mx ? v : mx;
           }
         }
-        __syncthreads();
         const double delta = __longlong_as_double(static_cast<long long>(block_max(mx, sred, parity))) / bnorm;
         st.final_delta = delta;
         st.sweeps = k;
@@ -432,37 +545,39 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
       int64_t outer = 0, inner_total = 0;
       bool first = true;
       for (;;) {
-        // residual of the current iterate (no matrix pass while the iterate is the zero start vector)
+        // residual of the current iterate; for the zero start vector r = b (c and the first inner sweep
+        // were computed by the setup phase) and max |r_i| = ||b||
         const double* xc = cur ? xs1 : xs0;
-        if (kSplit && !first) {
-          for (int64_t i = threadIdx.x; i < p.smem_ld; i += kBThreads) xss[i] = i < n ? split_x(xc[i], xg) : float2{};
-          __syncthreads();
-        }
-        unsigned long long mr = 0, mc = 0;
-        for (int64_t i0 = static_cast<int64_t>(warp) * RPW; i0 < n; i0 += static_cast<int64_t>(kBWarps) * RPW) {
-          double dot = 0.0;
-          if (!first) {
+        unsigned long long mr = bmax_bits;
+        if (!first) {
+          if constexpr (kSplit) {
+            for (int64_t i = threadIdx.x; i < p.smem_ld; i += kBThreads) xss[i] = i < n ? split_x(xc[i], xg) : float2{};
+            __syncthreads();
+          }
+          mr = 0;
+          for (int64_t i0 = static_cast<int64_t>(warp) * RPW; i0 < n; i0 += static_cast<int64_t>(kBWarps) * RPW) {
+            double dot;
             if constexpr (kSplit)
               dot = rows_split<RPW>(S.A, n, n, i0, xss, S.rexp, lane) * pow2(xg);
             else
               dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane, al16);
+            const int64_t i = i0 + tr_row<RPW>(lane);
+            if (tr_owner<RPW>(lane) && i < n) {
+              const double r = S.B[i] - dot;
+              const float c = static_cast<float>(r * S.rinv[i]);
+              S.c1[i] = c;
+              ds0[i] = c;
+              const unsigned long long vr = abs_bits(r);
+              mr = vr > mr ? vr : mr;
+            }
           }
-          const int64_t i = i0 + tr_row<RPW>(lane);
-          if (tr_owner<RPW>(lane) && i < n) {
-            const double r = S.B[i] - dot;
-            const float c = static_cast<float>(r * S.rinv[i]);
-            S.c1[i] = c;
-            ds0[i] = c;
-            const unsigned long long vr = abs_bits(r), vc = abs_bits(c);
-            mr = vr > mr ? vr : mr;
-            mc = vc > mc ? vc : mc;
-          }
+          mr = block_max(mr, sred, parity);
+          parity ^= 1;
         }
-        __syncthreads();
+        const bool pre = first;  // the first inner sweep of this outer step is done (setup phase)
         first = false;
         ++outer;
-        const double rho = __longlong_as_double(static_cast<long long>(block_max(mr, sred, parity))) / bnorm;
-        parity ^= 1;
+        const double rho = __longlong_as_double(static_cast<long long>(mr)) / bnorm;
         st.rel_residual = rho;
         if (!isfinite(rho)) {
           status = kStatusNonfinite;
@@ -477,7 +592,23 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
         int dcur = 0;
         const double* xcc = cur ? xs1 : xs0;
         double* xalt = cur ? xs0 : xs1;
-        for (int64_t m = 1;; ++m) {
+        int64_t m0 = 1;
+        bool more = true;
+        if (pre) {
+          // delta^(1) is in ds1 and x + delta^(1) in xs1 (cur is 0 here)
+          const double chg = __longlong_as_double(static_cast<long long>(chg1));
+          const double mag = __longlong_as_double(static_cast<long long>(mag1));
+          ++inner_total;
+          st.final_delta = chg;
+          dcur = 1;
+          if (!isfinite(chg) || !isfinite(mag)) {
+            status = kStatusNonfinite;
+            break;
+          }
+          more = !(chg <= static_cast<double>(p.inner_rtol) * mag || 1 >= p.max_inner || inner_total >= p.max_iter);
+          m0 = 2;
+        }
+        for (int64_t m = m0; more; ++m) {
           const float* dc = dcur ? ds1 : ds0;
           float* dn = dcur ? ds0 : ds1;
           unsigned long long mchg = 0, mmag = 0;
@@ -494,9 +625,9 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
               mmag = a2 > mmag ? a2 : mmag;
             }
           }
-          __syncthreads();
-          const double chg = __longlong_as_double(static_cast<long long>(block_max(mchg, sred, parity)));
-          const double mag = __longlong_as_double(static_cast<long long>(block_max(mmag, sred2, parity)));
+          block_max2(mchg, mmag, sred, sred2, parity);
+          const double chg = __longlong_as_double(static_cast<long long>(mchg));
+          const double mag = __longlong_as_double(static_cast<long long>(mmag));
           parity ^= 1;
           ++inner_total;
           st.final_delta = chg;
