@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
       }
       __syncthreads();
       // the narrow copy, a row per warp, and with it the first inner sweep on the rounded values:
-      // delta^(1)_i = c_i - (1/a_ii) sum_j fl(a_ij) c_j (the candidate x + delta^(1) = delta^(1))
+      // delta^(1)_i = c_i - (1/a_ii) sum_j fl(a_ij) c_j
       TL* Nl = static_cast<TL*>(S.Nlow);
       for (int64_t i = warp; i < n; i += kBWarps) {
         uint32_t mb = 0;
@@ -463,7 +463,6 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
         if (lane == 0) {
           const float v = fmaf(-S.rowfac[i], acc, S.c1[i]);
           ds1[i] = v;
-          xs1[i] = xs0[i] + static_cast<double>(v);
           const unsigned long long a1 = abs_bits(v - ds0[i]), a2 = abs_bits(v);
           chg1 = a1 > chg1 ? a1 : chg1;
           mag1 = a2 > mag1 ? a2 : mag1;
@@ -595,7 +594,7 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
         int64_t m0 = 1;
         bool more = true;
         if (pre) {
-          // delta^(1) is in ds1 and x + delta^(1) in xs1 (cur is 0 here)
+          // delta^(1) is in ds1 (cur is 0 here)
           const double chg = __longlong_as_double(static_cast<long long>(chg1));
           const double mag = __longlong_as_double(static_cast<long long>(mag1));
           ++inner_total;
@@ -611,7 +610,9 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
         for (int64_t m = m0; more; ++m) {
           const float* dc = dcur ? ds1 : ds0;
           float* dn = dcur ? ds0 : ds1;
-          unsigned long long mchg = 0, mmag = 0;
+          // maxima as FP32 bits (non-negative floats order like their bits; NaN above infinity), widened
+          // once for the exchange
+          unsigned int fchg = 0, fmag = 0;
           for (int64_t i0 = static_cast<int64_t>(warp) * RPW; i0 < n; i0 += static_cast<int64_t>(kBWarps) * RPW) {
             const float dot = rows_narrow<TL, RPW>(Nl, S.ldn, n, i0, dc, lane);
             const int64_t i = i0 + tr_row<RPW>(lane);
@@ -619,12 +620,12 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
               const float v = fmaf(-S.rowfac[i], dot, S.c1[i]);
               const float old = dc[i];
               dn[i] = v;
-              xalt[i] = xcc[i] + static_cast<double>(v);
-              const unsigned long long a1 = abs_bits(v - old), a2 = abs_bits(v);
-              mchg = a1 > mchg ? a1 : mchg;
-              mmag = a2 > mmag ? a2 : mmag;
+              const unsigned int a1 = __float_as_uint(fabsf(v - old)), a2 = __float_as_uint(fabsf(v));
+              fchg = a1 > fchg ? a1 : fchg;
+              fmag = a2 > fmag ? a2 : fmag;
             }
           }
+          unsigned long long mchg = abs_bits(__uint_as_float(fchg)), mmag = abs_bits(__uint_as_float(fmag));
           block_max2(mchg, mmag, sred, sred2, parity);
           const double chg = __longlong_as_double(static_cast<long long>(mchg));
           const double mag = __longlong_as_double(static_cast<long long>(mmag));
@@ -640,7 +641,13 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
             break;
         }
         if (status == kStatusNonfinite) break;
-        cur ^= 1;  // x + delta becomes the current iterate
+        // x + delta becomes the current iterate (delta: the last sweep's, in ds[dcur])
+        {
+          const float* df = dcur ? ds1 : ds0;
+          for (int64_t i = threadIdx.x; i < n; i += kBThreads) xalt[i] = xcc[i] + static_cast<double>(df[i]);
+          __syncthreads();
+        }
+        cur ^= 1;
       }
       st.sweeps = inner_total;
       st.outer_steps = outer;
