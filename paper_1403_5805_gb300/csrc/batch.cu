@@ -36,6 +36,9 @@ constexpr int kBWarps = 8;
 constexpr int kCopyLoads = 8;  // setup pass: FP64 loads per lane in flight (8-byte loads)
 constexpr int kCopyPairs = 4;  // the same with 16-byte loads (rows 16-byte aligned)
 constexpr int kBThreads = kBWarps * 32;
+constexpr int kFL = 4;               // FP64 passes: lanes per row
+constexpr int kFR = 32 / kFL;        // FP64 passes: rows per warp
+constexpr int kFU = 4;               // FP64 passes: load steps per lane in flight
 
 struct BatchSys {
   const double* A;  // row-major n x n, row stride n (read in place)
@@ -105,81 +108,63 @@ __device__ __forceinline__ bool tr_owner(int lane) {
   return (lane & (low - 1)) == 0;
 }
 
-// Dot products of FP64 rows [i0, i0 + RPW) of A (row stride lda) with the shared-memory FP64 vector x.
-// al16 (rows 16-byte aligned: A aligned and lda even): lane l takes column pairs 2 l + 64 t, two 16-byte
-// loads per row and step; otherwise 8-byte loads of columns l + 32 t (any row alignment).  Either way each
-// lane has 4 columns of every row in flight.  Returns the lane's transposed total.
-template <int RPW>
-__device__ __forceinline__ double rows_fp64(const double* __restrict__ A, int64_t lda, int64_t n, int64_t i0,
-                                            const double* xs, int lane, bool al16) {
-  double acc[RPW];
+// Dot products of FP64 rows with the shared-memory FP64 vector x, L lanes per row: the warp takes rows
+// [i0, i0 + 32 / L) and lane l works on row i0 + l / L.  The L lanes of a row split its columns (lane s
+// takes the column pairs 2 s + 2 L t when rows are 16-byte aligned, else the columns s + L t), keep U
+// steps of loads in flight and one FP64 accumulator each, and a log2(L)-level exchange sums them: fewer
+// FP64 additions per row than the transposed reduction over 32 lanes below, which matters because the
+// FP64 pipe is the residual's bound.  Every lane of the row returns the row's total.
+template <int L, int U>
+__device__ __forceinline__ double rows_fp64_lanes(const double* __restrict__ A, int64_t lda, int64_t n, int64_t i0,
+                                                  const double* xs, int lane, bool al16) {
+  const int s = lane & (L - 1);
+  const int64_t i = i0 + lane / L;
+  double acc = 0.0;
+  if (i < n) {
+    const double* a = A + i * lda;
+    if (al16) {
+      int64_t j = 2 * s;
+      for (; j + 2 * L * (U - 1) + 1 < n; j += 2 * L * U) {
+        double2 v[U];
 #pragma unroll
-  for (int r = 0; r < RPW; ++r) acc[r] = 0.0;
-  const int rows = static_cast<int>(i64min(RPW, n - i0));
-  if (al16) {
-    int64_t j = 2 * lane;
-    for (; j + 65 < n; j += 128) {
-      const double2 x0 = *reinterpret_cast<const double2*>(xs + j);
-      const double2 x1 = *reinterpret_cast<const double2*>(xs + j + 64);
-      double2 a0[RPW], a1[RPW];
+        for (int u = 0; u < U; ++u) v[u] = __ldg(reinterpret_cast<const double2*>(a + j + 2 * L * u));
 #pragma unroll
-      for (int r = 0; r < RPW; ++r)
-        if (r < rows) {
-          const double* a = A + (i0 + r) * lda + j;
-          a0[r] = __ldg(reinterpret_cast<const double2*>(a));
-          a1[r] = __ldg(reinterpret_cast<const double2*>(a + 64));
+        for (int u = 0; u < U; ++u) {
+          const double2 x = *reinterpret_cast<const double2*>(xs + j + 2 * L * u);
+          acc = fma(v[u].x, x.x, acc);
+          acc = fma(v[u].y, x.y, acc);
         }
-#pragma unroll
-      for (int r = 0; r < RPW; ++r)
-        if (r < rows) {
-          acc[r] = fma(a0[r].x, x0.x, acc[r]);
-          acc[r] = fma(a0[r].y, x0.y, acc[r]);
-          acc[r] = fma(a1[r].x, x1.x, acc[r]);
-          acc[r] = fma(a1[r].y, x1.y, acc[r]);
-        }
-    }
-    for (; j < n; j += 64) {
-#pragma unroll
-      for (int r = 0; r < RPW; ++r)
-        if (r < rows) {
-          const double* a = A + (i0 + r) * lda + j;
-          if (j + 1 < n) {
-            const double2 v = __ldg(reinterpret_cast<const double2*>(a));
-            acc[r] = fma(v.x, xs[j], acc[r]);
-            acc[r] = fma(v.y, xs[j + 1], acc[r]);
-          } else {
-            acc[r] = fma(__ldg(a), xs[j], acc[r]);
-          }
-        }
-    }
-    return TR<RPW, 16, double>::run(acc, lane);
-  }
-  int64_t j = lane;
-  for (; j + 96 < n; j += 128) {
-    const double x0 = xs[j], x1 = xs[j + 32], x2 = xs[j + 64], x3 = xs[j + 96];
-#pragma unroll
-    for (int r = 0; r < RPW; ++r)
-      if (r < rows) {
-        const double* a = A + (i0 + r) * lda + j;
-        const double a0 = __ldg(a), a1 = __ldg(a + 32), a2 = __ldg(a + 64), a3 = __ldg(a + 96);
-        acc[r] = fma(a0, x0, acc[r]);
-        acc[r] = fma(a1, x1, acc[r]);
-        acc[r] = fma(a2, x2, acc[r]);
-        acc[r] = fma(a3, x3, acc[r]);
       }
-  }
-  for (; j < n; j += 32) {
-    const double x0 = xs[j];
+      for (; j < n; j += 2 * L) {
+        if (j + 1 < n) {
+          const double2 v = __ldg(reinterpret_cast<const double2*>(a + j));
+          acc = fma(v.x, xs[j], acc);
+          acc = fma(v.y, xs[j + 1], acc);
+        } else {
+          acc = fma(__ldg(a + j), xs[j], acc);
+        }
+      }
+    } else {
+      int64_t j = s;
+      for (; j + L * (2 * U - 1) < n; j += 2 * L * U) {
+        double v[2 * U];
 #pragma unroll
-    for (int r = 0; r < RPW; ++r)
-      if (r < rows) acc[r] = fma(__ldg(A + (i0 + r) * lda + j), x0, acc[r]);
+        for (int u = 0; u < 2 * U; ++u) v[u] = __ldg(a + j + L * u);
+#pragma unroll
+        for (int u = 0; u < 2 * U; ++u) acc = fma(v[u], xs[j + L * u], acc);
+      }
+      for (; j < n; j += L) acc = fma(__ldg(a + j), xs[j], acc);
+    }
   }
-  return TR<RPW, 16, double>::run(acc, lane);
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
 }
 
-// The same dot products with the split-float arithmetic of splitfloat.cuh: each a_ij split (row scale
-// 2^-e_i) as it is read, x as its two FP32 words in shared memory, float-float lane sums scaled back by
-// 2^e_i before the FP64 transposed reduction (the caller applies x's scale 2^g).
+// Dot products of FP64 rows [i0, i0 + RPW) (row stride lda) with x in the split-float arithmetic of
+// splitfloat.cuh: lane l takes columns l + 32 t, each a_ij split (row scale 2^-e_i) as it is read, x as
+// its two FP32 words in shared memory, float-float lane sums scaled back by 2^e_i before the FP64
+// transposed reduction (the caller applies x's scale 2^g).
 template <int RPW>
 __device__ __forceinline__ double rows_split(const double* __restrict__ A, int64_t lda, int64_t n, int64_t i0,
                                              const float2* xs, const int* __restrict__ rexp, int lane) {
@@ -512,10 +497,10 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
         const double* xc = cur ? xs1 : xs0;
         double* xn = cur ? xs0 : xs1;
         unsigned long long mx = 0;
-        for (int64_t i0 = static_cast<int64_t>(warp) * RPW; i0 < n; i0 += static_cast<int64_t>(kBWarps) * RPW) {
-          const double dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane, al16);
-          const int64_t i = i0 + tr_row<RPW>(lane);
-          if (tr_owner<RPW>(lane) && i < n) {
+        for (int64_t i0 = static_cast<int64_t>(warp) * kFR; i0 < n; i0 += static_cast<int64_t>(kBWarps) * kFR) {
+          const double dot = rows_fp64_lanes<kFL, kFU>(S.A, n, n, i0, xc, lane, al16);
+          const int64_t i = i0 + lane / kFL;
+          if ((lane & (kFL - 1)) == 0 && i < n) {
             const double xo = xc[i];
             const double sdot = fma(-S.d[i], xo, dot);
             const double xi = (S.B[i] - sdot) * S.rinv[i];
@@ -554,14 +539,22 @@ __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(BatchParams p) {
             __syncthreads();
           }
           mr = 0;
-          for (int64_t i0 = static_cast<int64_t>(warp) * RPW; i0 < n; i0 += static_cast<int64_t>(kBWarps) * RPW) {
+          // rows of the residual: RPW rows per warp (split-float), or kFR (FP64 FMAs, kFL lanes per row)
+          constexpr int64_t kRows = kSplit ? RPW : kFR;
+          for (int64_t i0 = static_cast<int64_t>(warp) * kRows; i0 < n; i0 += static_cast<int64_t>(kBWarps) * kRows) {
             double dot;
-            if constexpr (kSplit)
+            int64_t i;
+            bool owner;
+            if constexpr (kSplit) {
               dot = rows_split<RPW>(S.A, n, n, i0, xss, S.rexp, lane) * pow2(xg);
-            else
-              dot = rows_fp64<RPW>(S.A, n, n, i0, xc, lane, al16);
-            const int64_t i = i0 + tr_row<RPW>(lane);
-            if (tr_owner<RPW>(lane) && i < n) {
+              i = i0 + tr_row<RPW>(lane);
+              owner = tr_owner<RPW>(lane);
+            } else {
+              dot = rows_fp64_lanes<kFL, kFU>(S.A, n, n, i0, xc, lane, al16);
+              i = i0 + lane / kFL;
+              owner = (lane & (kFL - 1)) == 0;
+            }
+            if (owner && i < n) {
               const double r = S.B[i] - dot;
               const float c = static_cast<float>(r * S.rinv[i]);
               S.c1[i] = c;
