@@ -305,7 +305,8 @@ def fma_peaks(jac, torch, dev):
             "fp64_tflops": round(2 * f64 / 1e12, 3), "fp64_fma_per_clk_per_sm_at_max_clock":
             round(f64 / (sms * measured_peaks()[0].get("sm_max_mhz", 2070.0) * 1e6), 3),
             "fp64_derived_gfma_s": round(derived / 1e9, 1),
-            "how": "8 independent FMA chains per thread, 8 blocks of 256 threads per SM, CUDA events, best of 2"}
+            "how": "4 or 16 independent FMA chains per thread (recurrence or dot-product form), 4 or 8 blocks "
+                   "of 256 threads per SM, CUDA events, best of all shapes over 2 calls"}
 
 
 def composite_roofline(r, n, prec, peaks, dev, torch, fma=None):

@@ -420,8 +420,9 @@ JACOBI_API int jacobi_generate_request(int64_t n, int64_t r, double f, uint64_t 
  * ------------------------------------------------------------------------------------------------ */
 
 /* Time independent FMA chains on every SM of the current device (16 chains x `iters` iterations per
- * thread, or 4 chains x 4 iters, at 4 and 8 blocks of 256 threads per SM), in FP64 and then in FP32 (64
- * times as many iterations), each launch after an untimed one, with CUDA events on `stream` (a
+ * thread, or 4 chains x 4 iters, at 4 and 8 blocks of 256 threads per SM; each chain either the
+ * recurrence x = x m + c or the dot-product form acc = a b + acc), in FP64 and then in FP32 (64 times as
+ * many iterations), each launch after an untimed one, with CUDA events on `stream` (a
  * cudaStream_t; NULL: legacy default stream).  Writes the best FMAs per second of each (host doubles).
  * Blocks until done.  JACOBI_ERR_INVALID_ARG for iters < 1 or a NULL output. */
 JACOBI_API int jacobi_measure_fma_rates(int64_t iters, double* fp64_fma_per_s, double* fp32_fma_per_s, void* stream);

@@ -1,10 +1,13 @@
 // Measured arithmetic rates of this GPU's CUDA cores, the denominators of the FP64-FMA and FP32 bounds
 // that the FP64 sweeps, the FP64 residual passes and the split-float residual are held to.
 //
-// Each thread runs CH independent FMA chains (x <- x * m + c with |m| < 1, so values stay finite), so that
-// the issue of the FMA pipe, not its latency, limits the rate; the grid holds every SM with BPS blocks of
-// kPeakThreads threads.  Several (CH, BPS) shapes are timed, each launch after an untimed one on the same
-// stream (CUDA events), and the best rate is reported.
+// Each thread runs CH independent FMA chains, so that the issue of the FMA pipe, not its latency, limits
+// the rate; the grid holds every SM with BPS blocks of kPeakThreads threads.  Two operand forms are timed:
+// the recurrence x <- x * m + c (|m| < 1, values stay finite) and the dot-product form acc <- a * b + acc
+// with per-chain a and b, the form of the solver's row dot products.  On GB300 the FP64 pipe reaches its
+// 2 FMAs per clock per SM only in the second form with 4 chains (the recurrence stops near 0.84 of it).
+// Several (form, CH, BPS) shapes are timed, each launch after an untimed one on the same stream (CUDA
+// events), and the best rate is reported.
 #include <cuda_runtime.h>
 
 #include "solver.cuh"
@@ -30,6 +33,25 @@ __global__ void __launch_bounds__(kPeakThreads) fma_rate_kernel(int64_t iters, T
 }
 
 template <typename T, int CH>
+__global__ void __launch_bounds__(kPeakThreads) fma_dot_kernel(int64_t iters, T m, T c, T* sink) {
+  T acc[CH], a[CH], b[CH];
+#pragma unroll
+  for (int u = 0; u < CH; ++u) {
+    acc[u] = static_cast<T>(0);
+    a[u] = static_cast<T>(threadIdx.x + u) * c;
+    b[u] = m + static_cast<T>(u) * static_cast<T>(1e-3);
+  }
+  for (int64_t k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int u = 0; u < CH; ++u) acc[u] = fma(a[u], b[u], acc[u]);
+  }
+  T s = 0;
+#pragma unroll
+  for (int u = 0; u < CH; ++u) s += acc[u];
+  if (s == static_cast<T>(-1.5)) sink[0] = s;  // never true (every term is non-negative); keeps the chains live
+}
+
+template <typename T, int CH, bool kDot>
 cudaError_t time_rate_shape(int64_t iters, int bps, cudaStream_t s, double* per_s) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -43,9 +65,10 @@ cudaError_t time_rate_shape(int64_t iters, int bps, cudaStream_t s, double* per_
     return e;
   }
   const T m = static_cast<T>(0.999999), c = static_cast<T>(1e-7);
-  fma_rate_kernel<T, CH><<<grid, kPeakThreads, 0, s>>>(iters / 4 + 1, m, c, nullptr);
+  auto kern = kDot ? fma_dot_kernel<T, CH> : fma_rate_kernel<T, CH>;
+  kern<<<grid, kPeakThreads, 0, s>>>(iters / 4 + 1, m, c, nullptr);
   cudaEventRecord(a, s);
-  fma_rate_kernel<T, CH><<<grid, kPeakThreads, 0, s>>>(iters, m, c, nullptr);
+  kern<<<grid, kPeakThreads, 0, s>>>(iters, m, c, nullptr);
   cudaEventRecord(b, s);
   e = cudaEventSynchronize(b);
   float ms = 0.0f;
@@ -59,15 +82,22 @@ cudaError_t time_rate_shape(int64_t iters, int bps, cudaStream_t s, double* per_
   return cudaSuccess;
 }
 
-// Best over 4 or 16 chains per thread and 4 or 8 blocks per SM (the same FMA count per thread each time).
+// Best over both forms, 4 or 16 chains per thread and 4 or 8 blocks per SM (the same FMA count per
+// thread each time).
 template <typename T>
 cudaError_t time_rate(int64_t iters, cudaStream_t s, double* per_s) {
   double best = 0.0, r = 0.0;
   for (int bps : {4, 8}) {
-    cudaError_t e = time_rate_shape<T, 4>(iters * 4, bps, s, &r);
+    cudaError_t e = time_rate_shape<T, 4, false>(iters * 4, bps, s, &r);
     if (e != cudaSuccess) return e;
     best = r > best ? r : best;
-    e = time_rate_shape<T, 16>(iters, bps, s, &r);
+    e = time_rate_shape<T, 16, false>(iters, bps, s, &r);
+    if (e != cudaSuccess) return e;
+    best = r > best ? r : best;
+    e = time_rate_shape<T, 4, true>(iters * 4, bps, s, &r);
+    if (e != cudaSuccess) return e;
+    best = r > best ? r : best;
+    e = time_rate_shape<T, 16, true>(iters, bps, s, &r);
     if (e != cudaSuccess) return e;
     best = r > best ? r : best;
   }

@@ -3,8 +3,8 @@
 // One cooperative launch runs a whole solve.  Each CTA owns a contiguous block of rows (the paper's
 // row-wise distribution of Section 3.1, here over the SMs of one GPU).  Per sweep it streams its rows
 // of the matrix from HBM exactly once through a shared-memory ring: one producer warp issues 1-D TMA
-// bulk copies (one row segment of a column chunk each, 16 rows per ring item, 4 items of 48 KB) that
-// complete on mbarriers; twelve consumer warps (6 column slices x 2 groups of 8 rows) read them with
+// bulk copies (one row segment of a column chunk each, 16 rows per ring item, 3 items of 56 KB) that
+// complete on mbarriers; fourteen consumer warps (7 column slices x 2 groups of 8 rows) read them with
 // 128-bit shared-memory loads and accumulate row dot products against the current iterate (read from
 // L2), reduce them with warp shuffles and a fixed-order cross-warp sum, and apply the component update
 // of Section 2 in the epilogue.  When a CTA's rows fit in the ring (small systems), later sweeps reuse

@@ -14,10 +14,13 @@ namespace jac {
 // JAC_COL_WARPS warps split the columns of a ring item, JAC_ROW_GROUPS groups of 8 rows split its rows,
 // plus one producer warp.
 #ifndef JAC_COL_WARPS
-#define JAC_COL_WARPS 6
+#define JAC_COL_WARPS 7
 #endif
 #ifndef JAC_ROW_GROUPS
 #define JAC_ROW_GROUPS 2
+#endif
+#ifndef JAC_RING_KB
+#define JAC_RING_KB 192
 #endif
 constexpr int kColWarps = JAC_COL_WARPS;                 // warps across the columns of a ring item
 constexpr int kRowsPerWarp = 8;                          // rows each consumer warp accumulates
@@ -33,7 +36,7 @@ constexpr int kMaxRegs = kMaxRegsRaw > 255 ? 255 : kMaxRegsRaw;
 constexpr int kRows = kRowsPerWarp * kRowHalves;         // rows of a row group (one ring item)
 constexpr int kRowBytes = kColWarps * 32 * 16;           // bytes of one row per ring item
 constexpr int kStageBytes = kRows * kRowBytes;           // bytes per ring stage
-constexpr int kStages = (192 * 1024) / kStageBytes;      // ring depth within 192 KB
+constexpr int kStages = (JAC_RING_KB * 1024) / kStageBytes;  // ring depth within JAC_RING_KB KB
 constexpr int kDynSmem = kStages * kStageBytes + 128;    // + alignment slack
 static_assert(kRows <= 32, "one epilogue lane per row of a group");
 static_assert(kStages >= 2, "ring needs two stages");
