@@ -188,8 +188,11 @@ typedef enum { JACOBI_METHOD_JACOBI = 0, JACOBI_METHOD_SOR = 1 } jacobi_method;
  * digits stored as BF16 matrices (14 bytes per entry of A in the workspace), and each residual splits X
  * (each column scaled by its largest entry) the same way; the products of digit pairs whose levels add up
  * to at most 8 are summed by tcgen05.mma in FP32, exactly (1024-column chunks of integer products of at
- * most 2^14), the chunk sums in float-float, the diagonal term in FP64.  The representation and dropped-
- * pair errors are below 2^-50 of sum_j |a_ij| max |x_jc| per entry.  Not with JACOBI_FLAG_SPLIT_RESIDUAL;
+ * most 2^14), the chunk sums in float-float, the diagonal term in FP64.  When the 128-row tiles alone would
+ * leave part of the last wave of CTAs idle, each tile's K range is split into up to 8 parts whose float-
+ * float sums a second launch adds in part order (the workspace holds 8 x 8 bytes per entry of X for them).
+ * The representation and dropped-pair errors are below 2^-50 of sum_j |a_ij| max |x_jc| per entry.  Not
+ * with JACOBI_FLAG_SPLIT_RESIDUAL;
  * JACOBI_ERR_UNSUPPORTED for other precisions or one right-hand side.  Also a server flag
  * (jacobi_server_desc.flags), for requests of any size and right-hand-side count. */
 #define JACOBI_FLAG_TC_RESIDUAL 128

@@ -160,11 +160,12 @@ int validate_desc(const jacobi_desc* d) {
 // Extra device buffers of a many-right-hand-side handle (vectors v[c*ld + i]).
 struct MrhsLayout {
   size_t b, xa, xb, c1, da, db, dah, dbh, colmax, colsq, bcol, stats, status, xs, xexp, cols, adig, aexp, xdig,
-      total;
+      opart, total;
 };
 
-// tc: the tensor-core residual's digit matrices of A (kOzDigits x nr x ld BF16), row exponents and the
-// digits of X (kOzDigits x r x ld BF16).
+// tc: the tensor-core residual's digit matrices of A (kOzDigits x nr x ld BF16), row exponents, the
+// digits of X (kOzDigits x r x ld BF16) and the partial sums of its K-split tiles (kOzMaxParts x r x ld
+// float-float).
 MrhsLayout mrhs_layout(size_t base, int64_t n, int64_t ld, int64_t r, bool tc) {
   MrhsLayout M{};
   size_t o = base;
@@ -197,6 +198,7 @@ MrhsLayout mrhs_layout(size_t base, int64_t n, int64_t ld, int64_t r, bool tc) {
     M.adig = take(static_cast<size_t>(kOzDigits) * nr * ld * 2);
     M.aexp = take(static_cast<size_t>(nr) * 4);
     M.xdig = take(static_cast<size_t>(kOzDigits) * r * ld * 2);
+    M.opart = take(static_cast<size_t>(kOzMaxParts) * r * ld * 8);
   }
   M.total = o;
   return M;
@@ -594,6 +596,7 @@ int mrhs_solve(jacobi_handle* h, const double* X0, int64_t max_iter, double tol,
           q.nact = static_cast<int64_t>(act.size());
           q.status = status;
           q.wait_ns = h->wait_ns;
+          q.part = h->at<float2>(h->M.opart);
           CK(launch_oz_split_x(n, r, ld, xc, h->at<__nv_bfloat16>(h->M.xdig), h->at<int>(h->M.xexp), s));
           CK(launch_oz_resid(h->at<__nv_bfloat16>(h->M.adig), h->at<__nv_bfloat16>(h->M.xdig), q, s));
         } else {

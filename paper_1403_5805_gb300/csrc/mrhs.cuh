@@ -83,7 +83,13 @@ struct OzResidParams {
   // grouped launches only (launch_oz_grouped): where the X split writes X's digits and column exponents
   __nv_bfloat16* xd;
   int* xexp_w;
+  // launch_oz_resid only: scratch for the K-split (kOzMaxParts x r x ld float-float partial sums); NULL
+  // keeps every tile whole
+  float2* part;
 };
+// Most parts the K range of a residual tile is split into (launch_oz_resid splits it when the row tiles
+// alone would leave part of the last wave of CTAs empty).
+constexpr int kOzMaxParts = 8;
 // dig[(p*nr + i)*ld + j]: digit p of a_ij (j != i), zero elsewhere; aexp[i] as above.  A row-major with
 // 16-byte aligned rows (lda even).
 cudaError_t launch_oz_split_a(const double* A, int64_t lda, int64_t n, int64_t ld, __nv_bfloat16* dig, int* aexp,

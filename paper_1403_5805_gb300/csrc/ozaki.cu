@@ -214,9 +214,12 @@ struct OzSmem {
 
 // The residual of one tile: rows [m0, m0 + 128) and columns [c0, c0 + RC) of X, A's digits through the
 // tensor map *tmA, X's digits through *tmX (kernel parameters or maps in global memory).
+// Only the chunks [ch0, ch1) of K (1024 columns each) are summed; with nparts > 1 the tile's float-float sums
+// go to the part scratch (part index part) for oz_finish_kernel, else the tile applies the epilogue itself.
 template <int RC>
 __device__ __forceinline__ void oz_resid_tile(const CUtensorMap* tmA_, const CUtensorMap* tmX_,
-                                              const OzResidParams& p, int64_t m0, int c0) {
+                                              const OzResidParams& p, int64_t m0, int c0, int ch0, int ch1,
+                                              int nparts, int part) {
   using C = OzCfg<RC>;
   constexpr int S_ = C::kStages;
   constexpr int NB = C::kBufs;
@@ -227,7 +230,7 @@ __device__ __forceinline__ void oz_resid_tile(const CUtensorMap* tmA_, const CUt
   const CUtensorMap& tmA = *tmA_;
   const CUtensorMap& tmX = *tmX_;
   const int kb_count = static_cast<int>((p.n + kKBlock - 1) / kKBlock);
-  const int nchunk = (kb_count + kOzChunkKB - 1) / kOzChunkKB;
+  const int kb_lo = ch0 * kOzChunkKB, kb_hi = min(kb_count, ch1 * kOzChunkKB);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S_; ++s) {
@@ -261,7 +264,7 @@ __device__ __forceinline__ void oz_resid_tile(const CUtensorMap* tmA_, const CUt
       for (int gi = 0; gi < kOzDigits && !S.abort; ++gi) {
         const int pd = kOzDigits - 1 - gi;  // A digit (0-based); X digits 0 .. gi
         const int nq = gi + 1;
-        for (int kb = 0; kb < kb_count; ++kb, ++it) {
+        for (int kb = kb_lo; kb < kb_hi; ++kb, ++it) {
           const int s = it % S_;
           if (S.abort || !mbar_wait(&S.empty[s], ((it / S_) & 1) ^ 1, p.wait_ns) || S.abort) {
             S.abort = 1;
@@ -284,7 +287,7 @@ __device__ __forceinline__ void oz_resid_tile(const CUtensorMap* tmA_, const CUt
       int it = 0, t = 0;
       for (int gi = 0; gi < kOzDigits && !S.abort; ++gi) {
         const int nq = gi + 1;
-        for (int ch = 0; ch < nchunk && !S.abort; ++ch, ++t) {
+        for (int ch = ch0; ch < ch1 && !S.abort; ++ch, ++t) {
           const int b = t % NB, u = t / NB;
           if (!mbar_wait(&S.tempty[b], (u & 1) ^ 1, p.wait_ns) || S.abort) {
             S.abort = 1;
@@ -338,7 +341,7 @@ __device__ __forceinline__ void oz_resid_tile(const CUtensorMap* tmA_, const CUt
     int t = 0;
     for (int gi = 0; gi < kOzDigits && ok; ++gi) {
       const int nq = gi + 1;
-      for (int ch = 0; ch < nchunk && ok; ++ch, ++t) {
+      for (int ch = ch0; ch < ch1 && ok; ++ch, ++t) {
         const int b = t % NB, u = t / NB;
         bool got = lane == 0 ? (mbar_wait(&S.tfull[b], u & 1, p.wait_ns) && !S.abort) : false;
         got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;  // tcgen05.ld is warp-collective
@@ -377,6 +380,13 @@ __device__ __forceinline__ void oz_resid_tile(const CUtensorMap* tmA_, const CUt
       if (lane == 0) {
         S.abort = 1;
         atomicCAS(p.status, 0, kStatusTimeout);
+      }
+    } else if (nparts > 1) {
+      // this part's sums of rows [m0, m0 + 128) and the warp's columns, for oz_finish_kernel
+      if (i < p.n) {
+#pragma unroll
+        for (int c = 0; c < CW; ++c)
+          p.part[(static_cast<int64_t>(part) * p.r + c0 + cw + c) * p.ld + i] = make_float2(hi[c], lo[c]);
       }
     } else {
       const bool row_ok = i < p.n;
@@ -420,7 +430,46 @@ template <int RC>
 __global__ void __launch_bounds__(OzCfg<RC>::kThreads, 1)
     oz_resid_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                     OzResidParams p) {
-  oz_resid_tile<RC>(&tmA, &tmX, p, static_cast<int64_t>(blockIdx.x) * kOzTile, static_cast<int>(blockIdx.y) * RC);
+  // part blockIdx.z of gridDim.z takes chunks [z nchunk / P, (z + 1) nchunk / P) (P <= nchunk: none empty)
+  const int nchunk = static_cast<int>((p.n + kKBlock * kOzChunkKB - 1) / (kKBlock * kOzChunkKB));
+  const int P = static_cast<int>(gridDim.z), z = static_cast<int>(blockIdx.z);
+  oz_resid_tile<RC>(&tmA, &tmX, p, static_cast<int64_t>(blockIdx.x) * kOzTile, static_cast<int>(blockIdx.y) * RC,
+                    z * nchunk / P, (z + 1) * nchunk / P, P, z);
+}
+
+// The epilogue of a K-split residual: entry (i, c) adds its parts' float-float sums in part order, then
+// applies the tile epilogue (R = B - a_ii x - A_offdiag x, c1 = d1 = R / a_ii, the column maximum of |R|).
+// Block (x, k): rows 256 x .. + 255 of the k-th active column.
+__global__ void __launch_bounds__(256) oz_finish_kernel(OzResidParams p, int nparts) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x;
+  const int col = p.cols ? p.cols[blockIdx.y] : static_cast<int>(blockIdx.y);
+  unsigned long long bits = 0;
+  if (i < p.n) {
+    float hi = 0.0f, lo = 0.0f;
+    for (int z = 0; z < nparts; ++z) {
+      const float2 v = p.part[(static_cast<int64_t>(z) * p.r + col) * p.ld + i];
+      ff_add(hi, lo, v.x);
+      ff_add(hi, lo, v.y);
+    }
+    const float s = __fadd_rn(hi, lo);  // renormalise: |lo| <= ulp(hi) / 2
+    lo = __fsub_rn(lo, __fsub_rn(s, hi));
+    hi = s;
+    const int e = p.aexp[i], g = p.xexp[col];
+    double dot;
+    if (e == kExpNonfinite || g == kExpNonfinite)
+      dot = __longlong_as_double(0x7FF8000000000000ll);
+    else
+      dot = scale2(static_cast<double>(hi) + static_cast<double>(lo), e + g + 2 - 16);
+    const int64_t o = static_cast<int64_t>(col) * p.ld + i;
+    const double r = fma(-p.d[i], p.x[o], p.b[o]) - dot;
+    const float cc = static_cast<float>(r * p.rinv[i]);
+    p.c1[o] = cc;
+    p.d1[o] = cc;
+    if (p.d1h) p.d1h[o] = __float2bfloat16_rn(cc);
+    bits = abs_bits(r);
+  }
+  bits = warp_max_u64(bits);
+  if ((threadIdx.x & 31) == 0 && bits) atomicMax(p.colmax + col, bits);
 }
 
 // Many independent residuals in one launch (the serving rounds): CTA b takes row tile b - first[k] of
@@ -444,7 +493,8 @@ __global__ void __launch_bounds__(OzCfg<16>::kThreads, 1)
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + 2 * lo) : "memory");
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + 2 * lo + 1) : "memory");
   }
-  oz_resid_tile<16>(maps + 2 * lo, maps + 2 * lo + 1, p, (b - first[lo]) * kOzTile, 0);
+  const int nchunk = static_cast<int>((p.n + kKBlock * kOzChunkKB - 1) / (kKBlock * kOzChunkKB));
+  oz_resid_tile<16>(maps + 2 * lo, maps + 2 * lo + 1, p, (b - first[lo]) * kOzTile, 0, 0, nchunk, 1, 0);
 }
 
 // The X digits of many residuals: block (c, k) splits column c of request k, whose X has p.nact columns
@@ -472,13 +522,45 @@ __global__ void oz_split_x_grouped_kernel(const OzResidParams* __restrict__ ps) 
   }
 }
 
+// Parts of the K range per tile: one CTA per SM is resident (the ring takes the shared memory), so
+// `tiles` CTAs fill tiles / (sms ceil(tiles / sms)) of the waves they take; splitting K into P parts makes
+// tiles P CTAs of 1 / P the work.  The fewest parts whose waves are at least 2 % fuller than with fewer
+// parts, at most kOzMaxParts and at most one part per chunk of K.
+int oz_parts(int64_t tiles, int64_t nchunk, int sms) {
+  auto fill = [&](int P) {
+    const int64_t ctas = tiles * P;
+    const int64_t waves = (ctas + sms - 1) / sms;
+    return static_cast<double>(ctas) / static_cast<double>(waves * sms);
+  };
+  int best = 1;
+  double bf = fill(1);
+  for (int P = 2; P <= kOzMaxParts && P <= nchunk; ++P) {
+    const double f = fill(P);
+    if (f > bf + 0.02) {
+      best = P;
+      bf = f;
+    }
+  }
+  return best;
+}
+
 template <int RC>
 cudaError_t launch_resid_rc(const CUtensorMap& ta, const CUtensorMap& tx, const OzResidParams& p, cudaStream_t s) {
   constexpr int smem = OzCfg<RC>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(oz_resid_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid(static_cast<unsigned>(p.nr / kOzTile), static_cast<unsigned>(p.r / RC));
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int64_t tiles = (p.nr / kOzTile) * (p.r / RC);
+  const int64_t nchunk = (p.n + kKBlock * kOzChunkKB - 1) / (kKBlock * kOzChunkKB);
+  const int P = p.part ? oz_parts(tiles, nchunk, sms) : 1;
+  const dim3 grid(static_cast<unsigned>(p.nr / kOzTile), static_cast<unsigned>(p.r / RC), static_cast<unsigned>(P));
   oz_resid_kernel<RC><<<grid, OzCfg<RC>::kThreads, smem, s>>>(ta, tx, p);
+  if ((e = cudaGetLastError()) != cudaSuccess || P == 1) return e;
+  const int64_t ncols = p.cols ? p.nact : p.r;
+  if (ncols < 1) return cudaSuccess;
+  oz_finish_kernel<<<dim3(static_cast<unsigned>((p.n + 255) / 256), static_cast<unsigned>(ncols)), 256, 0, s>>>(p, P);
   return cudaGetLastError();
 }
 

@@ -151,12 +151,13 @@ def _one_residual(jac, A, B, X0, tc):
     return np.asarray(vals)
 
 
-@pytest.mark.parametrize("n,r", [(600, 16), (1000, 32), (517, 64), (300, 128)])
+@pytest.mark.parametrize("n,r", [(600, 16), (1000, 32), (517, 64), (300, 128), (2100, 16), (2500, 64)])
 def test_tc_residual_wild_scales(jac, n, r):
     """The tensor-core residual (digit split of A and X) of a given X0, rows of A scaled by 2^-300 .. 2^300
     and columns of B (so of X) by 2^-200 .. 2^200, against the oracle's FP64 residual per column, within
     2^-44 of max_i sum_j |a_ij x_jc| / ||b_c|| (the split's bound is about 2^-50 of it; the rest is the
-    oracle's own FP64 rounding)."""
+    oracle's own FP64 rounding).  n > 2048: three 1024-column chunks of K on a few row tiles, so each tile's
+    K range is split over several CTAs and a second launch adds the parts."""
     A, B, Xs = synth.dominant_system(n, 1.3, seed=97 + n, nrhs=r)
     rng = np.random.default_rng(n)
     rows = 2.0 ** rng.integers(-300, 300, n)
@@ -171,15 +172,15 @@ def test_tc_residual_wild_scales(jac, n, r):
         assert rel > 1e-9 and abs(got[c] - rel) <= 2.0 ** -44 * S, (c, got[c], rel, S)
 
 
-def test_tc_residual_against_a_near_exact_residual(jac):
+@pytest.mark.parametrize("n,r", [(512, 32), (2100, 16)])
+def test_tc_residual_against_a_near_exact_residual(jac, n, r):
     """Where long double is IEEE quad precision (113-bit significand, as on Arm Linux), the residual of a
     hard-generator system (all entries of A positive: no cancellation in A x) is formed with exact products
     and 113-bit sums; the tensor-core residual must be within 2^-50 of max_i sum_j |a_ij x_jc| of it per
     column.  The BF16 digits are balanced, so a dropped digit or a wrong digit weight shows up far above
-    that bound."""
+    that bound.  n = 2100: the K-split tiles (three chunks, partial sums added by a second launch)."""
     if np.finfo(np.longdouble).nmant < 105:
         pytest.skip("long double is not quad precision on this host")
-    n, r = 512, 32
     A, B, Xs = synth.hard_system(n, 1.2, seed=55, nrhs=r)
     X0 = Xs * (1 + 1e-7 * np.random.default_rng(3).standard_normal((n, r)))
     got = _one_residual(jac, A, B, X0, tc=True)
@@ -260,12 +261,13 @@ def test_fp64_column_retirement_matches_single_column_solves(jac):
     assert iters[1] == 1 and iters[2] < iters[0] < iters[4]
 
 
-@pytest.mark.parametrize("tc", [False, True], ids=["fp64_resid", "tc_resid"])
-def test_bf16_column_retirement(jac, tc):
+@pytest.mark.parametrize("tc,n", [(False, 777), (True, 777), (True, 2100)], ids=["fp64_resid", "tc_resid", "tc_resid_ksplit"])
+def test_bf16_column_retirement(jac, tc, n):
     """Columns whose start vector already meets the target retire at the first residual evaluation and
-    keep X0 bit for bit; the others refine on; every column ends at or below the 1e-10 target."""
+    keep X0 bit for bit; the others refine on; every column ends at or below the 1e-10 target.  n = 2100
+    with the tensor-core residual: its K-split tiles, whose second launch takes only the active columns."""
     import torch
-    n, r = 777, 16
+    r = 16
     A, B, Xs = synth.dominant_system(n, 1.1, seed=621, nrhs=r)
     X0 = np.zeros((n, r))
     X0[:, ::2] = Xs[:, ::2]
