@@ -66,6 +66,36 @@ def test_fp64_batch_matches_oracle(jac, rpw):
         assert np.max(np.abs(x - ref.X[:, 0])) <= 1e-12 * np.max(np.abs(ref.X)), k
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir", "bf16_ir"])
+def test_batch_rows_not_16_byte_aligned(jac, prec):
+    """A given 8 bytes past a 16-byte boundary (a view one element into a larger buffer), with even and odd
+    n: the kernel's 8-byte load paths.  FP64 against the oracle (sweep count, X within 1e-12); the mixed
+    modes reach the target, rechecked by the oracle."""
+    import torch
+    systems = make_batch(12, 2, 400, 1.05, 2.0, seed=707)
+    systems += [synth.dominant_system(n, 1.1, seed=708 + n) for n in (64, 256, 1000)]
+    As, Bs = [], []
+    for A, B, _ in systems:
+        n = A.shape[0]
+        buf = torch.zeros(n * n + 1, dtype=torch.float64, device="cuda")
+        buf[1:] = torch.from_numpy(A.ravel()).cuda()
+        As.append(buf[1:].view(n, n))
+        Bs.append(torch.from_numpy(B[:, 0].copy()).cuda())
+    assert all(a.data_ptr() % 16 == 8 for a in As)
+    bs = jac.BatchSolver(As, Bs, precision=prec)
+    X = bs.solve_async(max_iter=5000, tol=1e-10)
+    stats = bs.stats()
+    for k, (A, B, _) in enumerate(systems):
+        x = X[k].cpu().numpy()
+        if prec == "fp64":
+            ref = oracle.jacobi(A, B, max_iter=5000, tol=1e-10, norm=oracle.NORM_RESID)
+            assert (stats[k].status, stats[k].sweeps) == (ref.status, ref.iters), (k, A.shape[0])
+            assert np.max(np.abs(x - ref.X[:, 0])) <= 1e-12 * np.max(np.abs(ref.X)), k
+        else:
+            _, rel = oracle.residual(A, B, x)
+            assert stats[k].status == 0 and rel <= 1e-10, (k, A.shape[0], rel)
+
+
 @pytest.mark.parametrize("prec,split", [("fp32_ir", False), ("bf16_ir", False), ("fp32_ir", True), ("bf16_ir", True)])
 def test_mixed_batch_reaches_target(jac, prec, split):
     """split: residuals with the split-float arithmetic (FP32 units) instead of FP64 FMAs."""
