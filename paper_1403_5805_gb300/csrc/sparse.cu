@@ -480,7 +480,9 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrI
     float* dnew = q.da;
     bool timed_out = false;
     for (int l = 1;; ++l) {
-      unsigned long long mc = 0, mg = 0;
+      // maxima on FP32 bits (non-negative floats order like their bits, NaN above infinity), widened once
+      // per thread: a widening per row would put two conversions per row on the FP64 pipe
+      unsigned int fc = 0, fg = 0;
       for (int64_t s = gw; s < p.nslices; s += nw) {
         int64_t o0;
         const int w = F::width(p, s, o0);
@@ -494,11 +496,12 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrI
         if (live) {
           const float old = __ldcg(dold + i);
           dnew[i] = acc;
-          const unsigned long long b1 = abs_bits(acc - old), b2 = abs_bits(acc);
-          mc = b1 > mc ? b1 : mc;
-          mg = b2 > mg ? b2 : mg;
+          const unsigned int b1 = __float_as_uint(fabsf(acc - old)), b2 = __float_as_uint(fabsf(acc));
+          fc = b1 > fc ? b1 : fc;
+          fg = b2 > fg ? b2 : fg;
         }
       }
+      unsigned long long mc = abs_bits(__uint_as_float(fc)), mg = abs_bits(__uint_as_float(fg));
       const bool iok = grid_max2(p, phase++, JACOBI_PHASE_INNER, mc, mg, s0, s1, &s_ok);
       ++inner_total;
       if (!iok) {
