@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <initializer_list>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "sparse.cuh"
@@ -483,7 +484,41 @@ __global__ void __launch_bounds__(kCsrThreads, kCsrMinBlocks) csr_ir_kernel(CsrI
       // maxima on FP32 bits (non-negative floats order like their bits, NaN above infinity), widened once
       // per thread: a widening per row would put two conversions per row on the FP64 pipe
       unsigned int fc = 0, fg = 0;
-      for (int64_t s = gw; s < p.nslices; s += nw) {
+      int64_t s_first = gw;
+      if constexpr (std::is_same<F, DiaFmt>::value) {
+        // DIA: two slices per step (every slice has the same diagonals), their loads in flight together
+        const int w = p.ndiag;
+        for (; s_first + nw < p.nslices; s_first += 2 * nw) {
+          const int64_t sa = s_first, sb = s_first + nw;
+          const int64_t ia = sa * kSliceRows + lane, ib = sb * kSliceRows + lane;
+          const bool la = ia < p.n, lb = ib < p.n;
+          float acca = la ? __ldcg(q.rf + ia) : 0.0f, accb = lb ? __ldcg(q.rf + ib) : 0.0f;
+          const TV* ta = tlo + sa * w * kSliceRows + lane;
+          const TV* tb = tlo + sb * w * kSliceRows + lane;
+#pragma unroll 4
+          for (int t = 0; t < w; ++t) {
+            const float va = to_f32<TV>(__ldcs(ta + kSliceRows * t)), vb = to_f32<TV>(__ldcs(tb + kSliceRows * t));
+            const float ga = __ldcg(dold + ia + sdoff[t]), gb = __ldcg(dold + ib + sdoff[t]);
+            acca = fmaf(va, ga, acca);
+            accb = fmaf(vb, gb, accb);
+          }
+          if (la) {
+            const float old = __ldcg(dold + ia);
+            dnew[ia] = acca;
+            const unsigned int b1 = __float_as_uint(fabsf(acca - old)), b2 = __float_as_uint(fabsf(acca));
+            fc = b1 > fc ? b1 : fc;
+            fg = b2 > fg ? b2 : fg;
+          }
+          if (lb) {
+            const float old = __ldcg(dold + ib);
+            dnew[ib] = accb;
+            const unsigned int b1 = __float_as_uint(fabsf(accb - old)), b2 = __float_as_uint(fabsf(accb));
+            fc = b1 > fc ? b1 : fc;
+            fg = b2 > fg ? b2 : fg;
+          }
+        }
+      }
+      for (int64_t s = s_first; s < p.nslices; s += nw) {
         int64_t o0;
         const int w = F::width(p, s, o0);
         const int64_t i = s * kSliceRows + lane;
