@@ -332,8 +332,10 @@ JACOBI_API int jacobi_batch_grid(jacobi_batch* b);
 /* Release the batch (waits for its stream; NULL is a no-op). */
 JACOBI_API void jacobi_batch_destroy(jacobi_batch* b);
 
-/* One call for a whole batch, the batched form of jacobi_solve: create with default tuning on the legacy
- * default stream, solve every system from X = 0, copy the per-system records into stats (host array
+/* One call for a whole batch, the batched form of jacobi_solve: create on the legacy default stream with the
+ * launch shape the autotuner picks for thousands of systems of a few hundred unknowns (4 rows per warp, the
+ * 64-register build at 4 CTAs per SM, inner tolerance 2^-10 for the IR precisions), solve every system from
+ * X = 0, copy the per-system records into stats (host array
  * [count], may be NULL) and release.  A, B, X_out: host arrays [count] of device pointers as in
  * jacobi_batch_desc; precision JACOBI_FP64, JACOBI_FP32_IR or JACOBI_BF16_IR.  Returns the worst outcome
  * over the systems (an error status, else JACOBI_NOT_CONVERGED if any system hit its cap, else JACOBI_OK),

@@ -921,6 +921,10 @@ int jacobi_batch_solve(int64_t count, const int64_t* n, const double* const* A, 
   d.B = B;
   d.X = X_out;
   d.precision = precision;
+  // the autotuner's shape for thousands of systems of a few hundred unknowns
+  d.rows_per_warp = 4;
+  d.ctas_per_sm = 4;
+  d.inner_rtol = 1.0 / 1024;
   jacobi_batch* b = nullptr;
   int st = jacobi_batch_create(&d, &b);
   if (st != JACOBI_OK) return st;

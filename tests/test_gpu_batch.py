@@ -174,12 +174,13 @@ def test_full_size_batch_sampled(jac):
 
 
 def test_one_call_batch_solve_equals_the_handle_path(jac):
-    """jacobi_batch_solve (create, solve, records, release in one call) gives the handle path's results
-    bit for bit, and its return value is the worst per-system outcome."""
+    """jacobi_batch_solve (create, solve, records, release in one call, with the autotuner's launch shape
+    for large batches: 4 rows per warp, 4 CTAs per SM, inner tolerance 2^-10) gives the handle path's
+    results with that shape bit for bit, and its return value is the worst per-system outcome."""
     import torch
     systems = make_batch(23, 1, 400, 1.05, 2.0, seed=131)
     As, Bs = to_dev(systems)
-    bs = jac.BatchSolver(As, Bs, precision="fp32_ir")
+    bs = jac.BatchSolver(As, Bs, precision="fp32_ir", rows_per_warp=4, ctas_per_sm=4, inner_rtol=2.0 ** -10)
     Xh = bs.solve_async(max_iter=5000, tol=1e-10)
     sh = bs.stats()
     Xs = [torch.empty(A.shape[0], dtype=torch.float64, device="cuda") for A in As]
