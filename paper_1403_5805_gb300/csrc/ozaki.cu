@@ -21,13 +21,16 @@
 // and its exact chunk sums are added into a float-float (two FP32 words) accumulator per output entry
 // with Knuth's two-sum, lowest digit levels first.  The diagonal term a_ii x_ic is applied in FP64.
 //
-// Kernel.  One CTA per 128 rows and RC columns of X, 6 warps: warp 0 issues the TMA loads (the A digit
-// tile, 128 x 64 BF16, and one X digit block of RC x 64 per digit) into a 4-stage 128-byte-swizzled
-// ring; one thread of warp 1 issues tcgen05.mma.kind::f16 (M = 128, N = digits x RC, K = 16) into one of
-// two 256-column tensor-memory buffers, alternating per chunk; warps 2..5 read a finished buffer with
-// tcgen05.ld, add it into their registers (one output row per thread, RC columns) and hand the buffer
-// back, so the readout of one chunk overlaps the products of the next.  The groups run from A digit 7
-// (one X digit, the lowest level) to A digit 1 (seven X digits).
+// Kernel.  One CTA per 128 rows and RC columns of X (and, when the row tiles alone would leave part of
+// the last wave of CTAs idle, per part of the K range: the parts' float-float sums go to scratch and a
+// second launch adds them in part order): warp 0 issues the TMA loads (the A digit tile, 128 x 64 BF16,
+// and one X digit block of RC x 64 per digit) into a 128-byte-swizzled ring of up to 4 stages; one
+// thread of warp 1 issues tcgen05.mma.kind::f16 (M = 128, N = digits x RC, at most 256 per instruction,
+// K = 16) into tensor memory; the readout warps read a finished chunk with tcgen05.ld, add it into their
+// registers (one output row per thread) and hand the columns back.  For RC <= 32 a group's accumulator
+// fits in 256 columns and two such buffers alternate per chunk, so the readout of one chunk overlaps
+// the products of the next; for RC = 64 (up to 448 columns) one buffer serves.  The groups run from A
+// digit 7 (one X digit, the lowest level) to A digit 1 (seven X digits).
 #include <cuda_bf16.h>
 
 #include <algorithm>
