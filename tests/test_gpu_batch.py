@@ -151,6 +151,29 @@ def test_bad_system_does_not_disturb_the_others(jac):
         assert stats[k].status == 0 and rel <= 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp32_ir", "fp64"])
+def test_zero_right_hand_side_in_the_mix(jac, prec):
+    """One system with B = 0 (solution X = 0) among ordinary ones.  Both batch modes stop on the relative
+    residual ||B - A X|| / ||B||, which is 0 / 0 there: that system reports JACOBI_ERR_NONFINITE with X = 0,
+    as the oracle's residual-norm stop does, and the others are not disturbed."""
+    import torch
+    systems = make_batch(6, 10, 80, 1.2, 1.5, seed=405)
+    A0, _, _ = synth.dominant_system(50, 1.3, seed=406)
+    systems.insert(2, (A0, np.zeros((50, 1)), None))
+    As, Bs = to_dev(systems)
+    bs = jac.BatchSolver(As, Bs, precision=prec)
+    X = bs.solve_async(max_iter=1000, tol=1e-10)
+    stats = bs.stats()
+    ref = oracle.jacobi(A0, np.zeros(50), max_iter=1000, tol=1e-10, norm=oracle.NORM_RESID)
+    assert stats[2].status == ref.status == jac.ERR_NONFINITE
+    assert int(torch.count_nonzero(X[2])) == 0
+    for k, (A, B, _) in enumerate(systems):
+        if k == 2:
+            continue
+        _, rel = oracle.residual(A, B, X[k].cpu().numpy())
+        assert stats[k].status == 0 and rel <= 1e-10
+
+
 @pytest.mark.parametrize("prec,shape", [("fp32_ir", {}), ("fp32_ir", {"rows_per_warp": 4, "ctas_per_sm": 4,
                                                                     "inner_rtol": 2.0 ** -10}),
                                         ("fp64", {"rows_per_warp": 8, "ctas_per_sm": 4})],

@@ -178,6 +178,29 @@ def test_nonzero_start_vector(jac):
     assert torch.equal(X2, X)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir", "bf16_ir", "fp8_ir"])
+def test_zero_right_hand_side(jac, prec):
+    """B = 0, the degenerate case (the solution is X = 0).  The max-norm stop (FP64) sees no change in the
+    first sweep and stops there, as the oracle does.  The relative-residual stop of the refinement is
+    ||B - A X|| / ||B|| = 0 / 0: reported as JACOBI_ERR_NONFINITE at the first residual with X left at the
+    zero start vector, as the oracle's residual-norm stop reports it."""
+    import torch
+    n = 300
+    A, _, _ = synth.dominant_system(n, 1.2, seed=71)
+    B = np.zeros((n, 1))
+    s = dev_solver(jac, A, B, precision=prec)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    out = s.solve_async(None, 100, tol)
+    st = s.last_stats()
+    ref = oracle.jacobi(A, B, max_iter=100, tol=tol, norm=oracle.NORM_INF if prec == "fp64" else oracle.NORM_RESID)
+    assert st.status == ref.status, (st.status, ref.status)
+    assert int(torch.count_nonzero(out)) == 0
+    if prec == "fp64":
+        assert st.status == 0 and st.sweeps == ref.iters == 1
+    else:
+        assert st.status == jac.ERR_NONFINITE
+
+
 def test_outer_cap_reports_not_converged(jac):
     A, B, _ = synth.hard_system(500, 1.1, seed=62)
     s = dev_solver(jac, A, B, precision="bf16_ir", max_outer=2)
