@@ -160,6 +160,29 @@ def test_wait_for_one_request(jac):
         srv.wait(12345)
 
 
+@pytest.mark.parametrize("residual", RESIDUALS)
+def test_zero_right_hand_side_columns(jac, residual):
+    """The server's reading of a zero right-hand side: a zero column of B is solved exactly by its zero
+    start and counts as met.  A request with B = 0 finishes OK with X = 0; in a request whose second column
+    is zero that column stays 0 and the others meet 1e-10 by the oracle."""
+    import torch
+    srv = make_server(jac, 1 << 30, residual)
+    A0, _, _ = synth.dominant_system(200, 1.3, seed=81, nrhs=2)
+    A1, B1, _ = synth.dominant_system(300, 1.3, seed=82, nrhs=3)
+    B1[:, 1] = 0.0
+    x0 = torch.ones(2, 200, dtype=torch.float64, device="cuda")
+    x1 = torch.ones(3, 300, dtype=torch.float64, device="cuda")
+    r0 = srv.submit(torch.from_numpy(A0).cuda(), torch.zeros(2, 200, dtype=torch.float64, device="cuda"), x0)
+    r1 = srv.submit(torch.from_numpy(A1).cuda(), torch.from_numpy(np.ascontiguousarray(B1.T)).cuda(), x1)
+    done = drain(srv)
+    assert done[r0].status == 0 and int(torch.count_nonzero(x0)) == 0
+    X1 = x1.cpu().numpy().T
+    assert done[r1].status == 0 and not X1[:, 1].any()
+    for c in (0, 2):
+        _, rel = oracle.residual(A1, B1[:, c:c + 1], X1[:, c:c + 1])
+        assert rel <= 1e-10, (c, rel)
+
+
 def test_tc_residual_rounds_wild_scales(jac):
     """Requests whose A rows and B columns span 2^-60 .. 2^60 (inside the range of the FP32 copy the inner
     sweeps read): the tensor-core residual rounds scale each row and column by its own power of two, so every
