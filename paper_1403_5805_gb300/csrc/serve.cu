@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "f64tof32.cuh"
 #include "mrhs.cuh"
 #include "solver.cuh"
 #include "splitfloat.cuh"
@@ -35,6 +36,7 @@ constexpr int kSRows = 16;        // rows per work item
 constexpr int kSRhs = 16;         // right-hand sides per request (JACOBI_SERVE_MAX_RHS)
 constexpr int kKC = 256;          // columns of the iterate staged in shared memory per step
 constexpr int kSThreads = 256;    // 8 warps x 2 rows
+constexpr int kPrepSteps = 4;     // setup: 128-column steps of a row whose loads are in flight together
 constexpr int kStatSlots = 64;    // per request per round: [0,16) |R| or change per column, [16,32) |B|,
                                   // 32 inner change, 33 inner magnitude, 34 bad-diagonal key (~key),
                                   // [40,56) max |b / a_ii| per column (setup round)
@@ -97,14 +99,25 @@ __device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint32_t stream, 
   }
 }
 
-__device__ __forceinline__ double signed_unit(uint32_t w) { return static_cast<double>(static_cast<int32_t>(w)) * 0x1p-31; }
+// int32(word) * 2^-31 (exact), assembled from the bits on the integer units: on GB300 an int -> double
+// conversion and a double multiply each take the FP64 pipe, which the residual rounds need.
+__device__ __forceinline__ double signed_unit(uint32_t word) {
+  const int32_t w = static_cast<int32_t>(word);
+  if (w == 0) return 0.0;
+  const uint32_t u = w < 0 ? 0u - word : word;  // |w|, 1 .. 2^31
+  const int lz = __clz(u);                      // |w| in [2^(31 - lz), 2^(32 - lz))
+  const uint64_t frac = (static_cast<uint64_t>(u) << (21 + lz)) & 0xFFFFFFFFFFFFFull;
+  const uint64_t bits = (static_cast<uint64_t>(w < 0) << 63) | (static_cast<uint64_t>(1023 - lz) << 52) | frac;
+  return __longlong_as_double(static_cast<long long>(bits));
+}
 
 // One CTA per row (grid-stride): A row i (row stride lda), its diagonal, and B (column stride ld).
 __global__ void serve_generate_kernel(int64_t n, int64_t r, int64_t lda, int64_t ld, double f, uint64_t seed,
                                       double* A, double* B) {
-  __shared__ double part[kSThreads / 32];
+  __shared__ unsigned long long part[kSThreads / 32];
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-    double s = 0.0;
+    // sum_{j != i} |a_ij| 2^31 as an integer (below 2^44): exactly the FP64 sum of the |a_ij|, in any order
+    unsigned long long s = 0;
     // words i n .. i n + n - 1 of stream 0, one Philox block (4 words) per thread and step
     const uint64_t w0 = static_cast<uint64_t>(i * n), w1 = w0 + static_cast<uint64_t>(n);
     for (uint64_t q = (w0 >> 2) + threadIdx.x; 4 * q < w1; q += blockDim.x) {
@@ -116,17 +129,19 @@ __global__ void serve_generate_kernel(int64_t n, int64_t r, int64_t lda, int64_t
         if (w < w0 || w >= w1) continue;
         const int64_t j = static_cast<int64_t>(w - w0);
         if (j == i) continue;
-        const double a = signed_unit(words[e]);
-        A[i * lda + j] = a;
-        s += fabs(a);  // integers times 2^-31 below 2^13: exact in any order
+        A[i * lda + j] = signed_unit(words[e]);
+        const int32_t v = static_cast<int32_t>(words[e]);
+        s += v < 0 ? 0u - words[e] : words[e];
       }
     }
-    s = warp_sum(s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
+      unsigned long long tot = 0;
+      for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) tot += part[w];
+      const double t = static_cast<double>(tot) * 0x1p-31;
       const double sign = (philox_word(seed, 1u, static_cast<uint64_t>(i)) & 1u) ? -1.0 : 1.0;
       A[i * lda + i] = n > 1 ? f * t * sign : f * sign;
     }
@@ -187,26 +202,38 @@ __device__ void prep_rows(const SrvReq& q, int64_t i0, int lane) {
     const double* Ai = q.A + i * ld;
     float* Ni = q.Nl + i * ld;
     uint32_t mb = 0;  // max_j of the high word of |a_ij|
-    for (int64_t j = 4 * lane; j < ld; j += 128) {
-      double a[4];
-      if (j + 4 <= n) {
-        const double2 v0 = __ldcs(reinterpret_cast<const double2*>(Ai + j));
-        const double2 v1 = __ldcs(reinterpret_cast<const double2*>(Ai + j + 2));
-        a[0] = v0.x;
-        a[1] = v0.y;
-        a[2] = v1.x;
-        a[3] = v1.y;
-      } else {
+    // kPrepSteps steps of 128 columns per pass: all of their loads are issued before the conversions, so
+    // a warp keeps that many 32-byte loads per lane in flight
+    for (int64_t jb = 4 * lane; jb < ld; jb += 128 * kPrepSteps) {
+      double a[kPrepSteps][4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) a[e] = j + e < n ? Ai[j + e] : 0.0;
-      }
-      float f[4];
+      for (int u = 0; u < kPrepSteps; ++u) {
+        const int64_t j = jb + 128 * u;
+        if (j + 4 <= n) {
+          const double2 v0 = __ldcs(reinterpret_cast<const double2*>(Ai + j));
+          const double2 v1 = __ldcs(reinterpret_cast<const double2*>(Ai + j + 2));
+          a[u][0] = v0.x;
+          a[u][1] = v0.y;
+          a[u][2] = v1.x;
+          a[u][3] = v1.y;
+        } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        mb = max(mb, abs_hi(a[e]));
-        f[e] = (j + e < n && j + e != i) ? __double2float_rn(a[e]) : 0.0f;
+          for (int e = 0; e < 4; ++e) a[u][e] = j + e < n ? Ai[j + e] : 0.0;
+        }
       }
-      *reinterpret_cast<float4*>(Ni + j) = make_float4(f[0], f[1], f[2], f[3]);
+#pragma unroll
+      for (int u = 0; u < kPrepSteps; ++u) {
+        const int64_t j = jb + 128 * u;
+        if (j < ld) {
+          float f[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            mb = max(mb, abs_hi(a[u][e]));
+            f[e] = (j + e < n && j + e != i) ? f64_to_f32_rn(a[u][e]) : 0.0f;  // off the FP64 pipe
+          }
+          *reinterpret_cast<float4*>(Ni + j) = make_float4(f[0], f[1], f[2], f[3]);
+        }
+      }
     }
     if (q.split) {
       mb = __reduce_max_sync(0xffffffffu, mb);
@@ -241,14 +268,33 @@ __device__ __forceinline__ double2 load_pair(const double* row, int64_t j, int64
 
 // Shared memory of one round CTA: the staged chunk of the iterate (FP64 X, its split words, or the
 // FP32 inner iterate D; kSRhs columns x kKC entries) and the cross-warp partial sums of the inner sweep.
+constexpr int kIStages = 3;  // chunks of the inner sweep in flight (asynchronous copies)
 struct SrvSmem {
   union {
     double x[kSRhs][kKC];
     float2 xs[kSRhs][kKC];
-    float4 d[kSRhs][kKC / 4];
+    struct {
+      // the item's rows of the narrow matrix, one chunk per stage; one quad of padding per row puts the
+      // 16 rows of a quad column on different banks
+      float4 a[kIStages][kSRows][kKC / 4 + 1];
+      float4 d[kIStages][kSRhs][kKC / 4];  // D_cur, one chunk per stage
+    } in;
+    float part[kSThreads / 32][kSRows][kSRhs];  // inner sweep: each warp's row sums, after the chunks
   };
-  float part[kSRows / 4][4][kSRhs];
 };
+
+// 16-byte asynchronous copy global -> shared (cp.async, the L2-only form); with valid == false nothing is
+// read and the 16 bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most N of this thread's most recent copy groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Stage entries [j0, j0 + kKC) of r columns of a [r][ld] vector block (zero past ld) into shared memory.
 template <typename T>
@@ -356,96 +402,110 @@ __device__ void resid_item(const SrvReq& q, int64_t r0, int warp, int lane, SrvS
   }
 }
 
-// FP32 inner sweep of the work item's 16 rows: D_new = C1 - (1/a_ii) N D_cur, X_alt = X_cur + D_new.
-// D_cur is staged per CTA in chunks of kKC columns.  Warps form 16 / RW row groups of RW rows; with RW = 4
-// the two warps of a group take one half of each chunk each and meet in shared memory, so every staged
-// value feeds RW rows (RW = 2 for 16 right-hand sides keeps the accumulators in registers).
-template <int RB, int RW>
-__device__ void inner_item(const SrvReq& q, int64_t r0, int warp, int lane, SrvSmem& sm) {
-  constexpr int KS = RW / 2;               // warps sharing a row group, each on 1 / KS of a chunk
-  constexpr int NG = kSRows / RW;          // row groups
-  constexpr int QPL = kKC / KS / 128;      // float4 quads per lane per chunk
-  static_assert(NG * KS == kSThreads / 32, "one warp per (row group, chunk part)");
-  const int grp = warp % NG, ks = warp / NG;
-  const int64_t n = q.n, ld = q.ld, ib = r0 + RW * grp;
-  float acc[RW][RB];
+// Issues the asynchronous copies of chunk j0 of the inner sweep into stage st: the item's 16 rows of the
+// narrow matrix (rows past n zero-filled; the narrow rows are zero-padded up to ld, so whole quads below ld
+// are read) and the r staged columns of D_cur; then closes the copy group.  Each thread copies 4 quads of
+// the rows and up to 4 of D.
+__device__ __forceinline__ void inner_issue(const SrvReq& q, const float* Dc, int64_t r0, int64_t j0, int st,
+                                            SrvSmem& sm) {
+  const int64_t n = q.n, ld = q.ld;
+  const int nq = static_cast<int>(q.r) * (kKC / 4);
 #pragma unroll
-  for (int rr = 0; rr < RW; ++rr)
+  for (int k = 0; k < kSRows * (kKC / 4) / kSThreads; ++k) {
+    const int e = threadIdx.x + k * kSThreads;
+    const int row = e / (kKC / 4), q4 = e % (kKC / 4);
+    const int64_t i = r0 + row, j = j0 + 4 * q4;
+    const bool ok = i < n && j < ld;
+    cp_async16(&sm.in.a[st][row][q4], ok ? q.Nl + i * ld + j : q.Nl, ok);
+  }
 #pragma unroll
-    for (int c = 0; c < RB; ++c) acc[rr][c] = 0.0f;
-  const float* Dc = q.dsel ? q.D[1] : q.D[0];
-  for (int64_t j0 = 0; j0 < n; j0 += kKC) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < static_cast<int>(q.r) * (kKC / 4); e += kSThreads) {
+  for (int k = 0; k < kSRhs * (kKC / 4) / kSThreads; ++k) {
+    const int e = threadIdx.x + k * kSThreads;
+    if (e < nq) {
       const int c = e / (kKC / 4), q4 = e % (kKC / 4);
-      const int64_t j = j0 + 4 * q4;  // ld is a multiple of 16: a quad never straddles it
-      sm.d[c][q4] = j < ld ? __ldcg(reinterpret_cast<const float4*>(Dc + c * ld + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int qq = 0; qq < QPL; ++qq) {
-      const int q4 = (kKC / KS) * ks / 4 + 32 * qq + lane;
       const int64_t j = j0 + 4 * q4;
-      if (j < n) {  // the narrow rows are zero-padded up to ld, so the quad at j < ld is safe to read
-        float4 m[RW];
+      cp_async16(&sm.in.d[st][c][q4], j < ld ? Dc + c * ld + j : Dc, j < ld);
+    }
+  }
+  cp_async_commit();
+}
+
+// FP32 inner sweep of the work item's 16 rows: D_new = C1 - (1/a_ii) N D_cur, X_alt = X_cur + D_new.
+// The item's rows of N and the iterate D_cur stream through shared memory in chunks of kKC columns by
+// asynchronous copies, kIStages chunks in flight, so the loads of the next chunks overlap the arithmetic
+// of this one (one barrier per chunk).  Lane 16 h + t of warp w takes row t of the item and, in step s of
+// a chunk, quad 16 s + 2 w + h: the 16 lanes of a half-warp read the same D_cur quads (a broadcast), so
+// each quad of D read from shared memory feeds 16 rows.  Each lane accumulates its row for every
+// right-hand side; the two halves and then the 8 warps are added in a fixed order.
+template <int RB>
+__device__ void inner_item(const SrvReq& q, int64_t r0, int warp, int lane, SrvSmem& sm) {
+  constexpr int kWarps = kSThreads / 32;
+  constexpr int kSteps = (kKC / 4) / (2 * kWarps);  // quads of a chunk per lane
+  static_assert(kSteps * 2 * kWarps == kKC / 4, "the warps' quads tile a chunk");
+  static_assert(kIStages == 3, "the copy-group accounting below keeps two chunks ahead");
+  static_assert(RB * kSRows <= kSThreads, "one thread per (row, right-hand side) in the epilogue");
+  const int t = lane & 15, h = lane >> 4;
+  const int64_t n = q.n, ld = q.ld;
+  float acc[RB];
 #pragma unroll
-        for (int rr = 0; rr < RW; ++rr)
-          m[rr] = ib + rr < n ? __ldcs(reinterpret_cast<const float4*>(q.Nl + (ib + rr) * ld + j))
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = 0; c < RB; ++c) acc[c] = 0.0f;
+  const float* Dc = q.dsel ? q.D[1] : q.D[0];
+  const int64_t nch = (n + kKC - 1) / kKC;
+  // the previous item's readers of shared memory passed the barrier that ends it
+  inner_issue(q, Dc, r0, 0, 0, sm);
+  if (nch > 1)
+    inner_issue(q, Dc, r0, kKC, 1, sm);
+  else
+    cp_async_commit();  // an empty group keeps the count of groups in flight the same
+#pragma unroll 1
+  for (int64_t ch = 0; ch < nch; ++ch) {
+    const int st = static_cast<int>(ch % kIStages);
+    cp_async_wait<1>();  // this thread's copies of chunk ch have landed
+    __syncthreads();     // everyone's have; every reader of the stage chunk ch + 2 reuses is done
+    if (ch + 2 < nch)
+      inner_issue(q, Dc, r0, (ch + 2) * kKC, static_cast<int>((ch + 2) % kIStages), sm);
+    else
+      cp_async_commit();
+    const int64_t j0 = ch * kKC;
+#pragma unroll
+    for (int s = 0; s < kSteps; ++s) {
+      const int q4 = 2 * kWarps * s + 2 * warp + h;
+      if (j0 + 4 * q4 < n) {
+        const float4 m = sm.in.a[st][t][q4];
 #pragma unroll
         for (int c = 0; c < RB; ++c)
           if (c < q.r) {
-            const float4 x = sm.d[c][q4];
-#pragma unroll
-            for (int rr = 0; rr < RW; ++rr)
-              acc[rr][c] =
-                  fmaf(m[rr].x, x.x, fmaf(m[rr].y, x.y, fmaf(m[rr].z, x.z, fmaf(m[rr].w, x.w, acc[rr][c]))));
+            const float4 x = sm.in.d[st][c][q4];
+            acc[c] = fmaf(m.x, x.x, fmaf(m.y, x.y, fmaf(m.z, x.z, fmaf(m.w, x.w, acc[c]))));
           }
       }
     }
   }
-  // lane sums: RW / 2 transposed reductions of 2 RB values (rows {0, 1}, {2, 3})
-  float tot[RW / 2];
-  int vidx = 0;
+  cp_async_wait<0>();  // only empty groups remain; nothing is left in flight
 #pragma unroll
-  for (int p = 0; p < RW / 2; ++p) {
-    float w[2 * RB];
+  for (int c = 0; c < RB; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 16);
+  __syncthreads();  // the stages are read; part aliases them
+  if (h == 0) {
 #pragma unroll
-    for (int c = 0; c < RB; ++c) {
-      w[c] = acc[2 * p][c];
-      w[RB + c] = acc[2 * p + 1][c];
-    }
-    tot[p] = tr_finish<2 * RB>(TRs<2 * RB, 16, float>::run(w, lane));
-    vidx = tr_index<2 * RB>(lane);
+    for (int c = 0; c < RB; ++c) sm.part[warp][t][c] = acc[c];
   }
-  const bool owner = (lane & (32 / (2 * RB) - 1)) == 0;
-  const int c = vidx % RB, rsub = vidx / RB;
-  if (KS == 2) {
-    if (ks == 1 && owner) {
-#pragma unroll
-      for (int p = 0; p < RW / 2; ++p) sm.part[grp][2 * p + rsub][c] = tot[p];
-    }
-    __syncthreads();
-  }
+  __syncthreads();
   unsigned long long chg = 0, mag = 0;
-  if (ks == 0 && owner && c < q.r) {
+  const int row = threadIdx.x / RB, c = threadIdx.x % RB;
+  const int64_t i = r0 + row;
+  if (row < kSRows && i < n && c < q.r) {
+    float sum = sm.part[0][row][c];
 #pragma unroll
-    for (int p = 0; p < RW / 2; ++p) {
-      const int64_t i = ib + 2 * p + rsub;
-      if (i < n) {
-        const float sum = KS == 2 ? tot[p] + sm.part[grp][2 * p + rsub][c] : tot[p];
-        const int64_t o = c * ld + i;
-        const float val = fmaf(-q.rowfac[i], sum, q.C1[o]);
-        const float old = Dc[o];
-        (q.dsel ? q.D[0] : q.D[1])[o] = val;
-        const double xn = (q.xsel ? q.X[1] : q.X[0])[o] + static_cast<double>(val);
-        (q.xsel ? q.X[0] : q.X[1])[o] = xn;
-        if (q.split) (q.xsel ? q.xs[0] : q.xs[1])[o] = split_x(xn, q.xg[c]);
-        const unsigned long long cb = abs_bits(val - old), mb = abs_bits(val);
-        chg = cb > chg ? cb : chg;
-        mag = mb > mag ? mb : mag;
-      }
-    }
+    for (int w = 1; w < kWarps; ++w) sum += sm.part[w][row][c];  // fixed order
+    const int64_t o = c * ld + i;
+    const float val = fmaf(-q.rowfac[i], sum, q.C1[o]);
+    const float old = Dc[o];
+    (q.dsel ? q.D[0] : q.D[1])[o] = val;
+    const double xn = (q.xsel ? q.X[1] : q.X[0])[o] + static_cast<double>(val);
+    (q.xsel ? q.X[0] : q.X[1])[o] = xn;
+    if (q.split) (q.xsel ? q.xs[0] : q.xs[1])[o] = split_x(xn, q.xg[c]);
+    chg = abs_bits(val - old);
+    mag = abs_bits(val);
   }
   chg = warp_max_u64(chg);
   mag = warp_max_u64(mag);
@@ -463,7 +523,7 @@ __device__ __forceinline__ void run_item(const SrvReq& q, int64_t r0, int warp, 
     else
       resid_item<RB, false>(q, r0, warp, lane, sm);
   } else {
-    inner_item<RB, RB == 16 ? 2 : 4>(q, r0, warp, lane, sm);
+    inner_item<RB>(q, r0, warp, lane, sm);
   }
 }
 
@@ -473,7 +533,8 @@ __device__ __forceinline__ void run_item(const SrvReq& q, int64_t r0, int warp, 
 __global__ void __launch_bounds__(kSThreads, 2) serve_round_kernel(const SrvReq* __restrict__ reqs, int nreq,
                                                                    const int64_t* __restrict__ first, int64_t items,
                                                                    unsigned long long* queue) {
-  __shared__ SrvSmem sm;
+  extern __shared__ __align__(16) unsigned char srv_dyn_smem[];
+  SrvSmem& sm = *reinterpret_cast<SrvSmem*>(srv_dyn_smem);
   __shared__ long long s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (;;) {
@@ -797,7 +858,9 @@ int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads, 0);
+  cudaFuncSetAttribute(serve_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(sizeof(SrvSmem)));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads, sizeof(SrvSmem));
   s->grid = std::max(1, per_sm) * sms;
   if (grow(s, 64) != JACOBI_OK || cudaMalloc(&s->d_queue, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&s->d_cols, kOzServeCols * sizeof(int)) != cudaSuccess ||
@@ -939,7 +1002,8 @@ int jacobi_server_step(jacobi_server* s, int32_t* active_out, int32_t* pending_o
     }
     if (items > 0) {
       const int grid = static_cast<int>(std::min<int64_t>(items, s->grid));
-      serve_round_kernel<<<grid, kSThreads, 0, s->stream>>>(s->d_reqs, na, s->d_first, items, s->d_queue);
+      serve_round_kernel<<<grid, kSThreads, sizeof(SrvSmem), s->stream>>>(s->d_reqs, na, s->d_first, items,
+                                                                          s->d_queue);
       if (cudaGetLastError() != cudaSuccess) return JACOBI_ERR_CUDA;
     }
     *s->h_tcstat = 0;
