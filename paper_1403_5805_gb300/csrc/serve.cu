@@ -858,10 +858,16 @@ int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(serve_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(sizeof(SrvSmem)));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads, sizeof(SrvSmem));
+  // the round kernel's shared memory (the inner sweep's copy stages) is above the 48 KB default
+  const bool smem_ok = cudaFuncSetAttribute(serve_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(sizeof(SrvSmem))) == cudaSuccess &&
+                       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads,
+                                                                     sizeof(SrvSmem)) == cudaSuccess;
   s->grid = std::max(1, per_sm) * sms;
+  if (!smem_ok) {
+    jacobi_server_destroy(s);
+    return JACOBI_ERR_CUDA;
+  }
   if (grow(s, 64) != JACOBI_OK || cudaMalloc(&s->d_queue, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&s->d_cols, kOzServeCols * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&s->d_tcstat, sizeof(int)) != cudaSuccess || cudaMallocHost(&s->h_tcstat, sizeof(int)) != cudaSuccess) {
