@@ -860,9 +860,10 @@ int jacobi_server_create(const jacobi_server_desc* d, jacobi_server** out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // the round kernel's shared memory (the inner sweep's copy stages) is above the 48 KB default
   const bool smem_ok = cudaFuncSetAttribute(serve_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(sizeof(SrvSmem))) == cudaSuccess &&
-                       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads,
-                                                                     sizeof(SrvSmem)) == cudaSuccess;
+                                            static_cast<int>(sizeof(SrvSmem))) == cudaSuccess;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_round_kernel, kSThreads, sizeof(SrvSmem)) !=
+      cudaSuccess)
+    per_sm = 1;  // one resident CTA per SM is always possible
   s->grid = std::max(1, per_sm) * sms;
   if (!smem_ok) {
     jacobi_server_destroy(s);
