@@ -47,3 +47,12 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(jac.JacobiDesc) == 120
     # jacobi_csr_desc: 2 x int64, 4 pointers, 2 x int32, 1 pointer, 4 x int32, 1 double
     assert ctypes.sizeof(jac.JacobiCsrDesc) == 88
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """With the library absent the binding raises instead of falling back to anything else."""
+    from paper_1403_5805_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libjacobi.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.load()
